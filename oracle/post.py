@@ -1,0 +1,113 @@
+"""Post-processing: SWR to r, fields off the surface, axis fit, far field.
+
+* Standing-wave ratio to reflection (Sec. I, Table 1): r = (SWR-1)/(SWR+1),
+  with SWR = max|E| / min|E| along the guide axis in the standing-wave region.
+* Field at off-surface points from the interior currents (Sec. II, Eq. 8):
+  inside the guide the total field is E_inc + E_i(J_i, M_i), evaluated by the
+  triangle quadrature rule with the point-source Green's function.
+* Axis fit (reading of the paper's SWR measure): least squares for
+  E(x_k) = a exp(-j beta x_k) + c exp(+j beta x_k); r = c/a, with beta fixed
+  or scanned to minimise the residual.
+* Far field of the exterior currents, exp(+jwt):
+  E ~ F exp(-jkr)/r,  F = -jk/(4 pi) [z (J^ - r (r.J^)) - r x M^],
+  J^ = int J exp(jk r.r') dS'.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from .mesh import Geometry
+from .operator import current_sets
+
+
+def swr_to_r(swr):
+    swr = np.asarray(swr, dtype=np.float64)
+    return (swr - 1.0) / (swr + 1.0)
+
+
+def _point_currents(g: Geometry, summ):
+    a, beta = summ
+    rel = g.qpts - g.centroid[:, None, :]
+    J = rel[..., None] * a[:, None, None, :] - beta[:, None, :, :]  # (nt, q, 3, B)
+    rho = 2.0 * np.broadcast_to(a[:, None, :], (g.nt, g.q, a.shape[-1]))
+    return J, rho
+
+
+def radiated(g: Geometry, x, pts, k, z, side: str):
+    """E of the ``side`` ('i' or 'e') current set radiating in (k, z) at pts (P,3)."""
+    x = np.asarray(x, dtype=np.complex128)
+    X2 = x[:, None] if x.ndim == 1 else x
+    Jes, Jis, Ms = current_sets(g, X2)
+    if side == "i":
+        Js, Mss = Jis, (-Ms[0], -Ms[1])
+    else:
+        Js, Mss = Jes, Ms
+    J, rhoJ = _point_currents(g, Js)
+    M, _ = _point_currents(g, Mss)
+    src = g.qpts.reshape(-1, 3)
+    w = g.qw.reshape(-1)
+    J = J.reshape(-1, 3, J.shape[-1]) * w[:, None, None]
+    M = M.reshape(-1, 3, M.shape[-1]) * w[:, None, None]
+    rhoJ = rhoJ.reshape(-1, rhoJ.shape[-1]) * w[:, None]
+    out = []
+    for p in pts:
+        D = p - src
+        R = np.linalg.norm(D, axis=1)
+        G = np.exp(-1j * k * R) / (4 * np.pi * R)
+        gG = (-(1j * k + 1.0 / R) * G / R)[:, None] * D  # grad_r G
+        A = np.einsum("s,sib->ib", G, J)
+        gphi = np.einsum("si,sb->ib", gG, rhoJ)
+        curlF = np.einsum("ijk,sj,skb->ib", _EPS, gG, M)
+        out.append(-z * (1j * k * A + (1j / k) * gphi) - curlF)
+    E = np.array(out)
+    return E[..., 0] if x.ndim == 1 else E
+
+
+_EPS = np.zeros((3, 3, 3))
+_EPS[0, 1, 2] = _EPS[1, 2, 0] = _EPS[2, 0, 1] = 1.0
+_EPS[0, 2, 1] = _EPS[2, 1, 0] = _EPS[1, 0, 2] = -1.0
+
+
+def fit_reflection(xs, E, beta=None, betas=None):
+    """Least-squares split of samples E(x) into forward and backward waves.
+
+    Returns (r = c/a, beta, residual).  If ``beta`` is None, it is scanned
+    over ``betas`` (1-D array) for the smallest residual.
+    """
+    xs = np.asarray(xs, dtype=np.float64)
+    E = np.asarray(E, dtype=np.complex128)
+
+    def solve(bt):
+        Mx = np.stack([np.exp(-1j * bt * xs), np.exp(1j * bt * xs)], axis=1)
+        coef, *_ = np.linalg.lstsq(Mx, E, rcond=None)
+        res = np.linalg.norm(Mx @ coef - E) / np.linalg.norm(E)
+        return coef, res
+
+    if beta is None:
+        best = None
+        for bt in betas:
+            coef, res = solve(bt)
+            if best is None or res < best[2]:
+                best = (coef, bt, res)
+        coef, beta, res = best
+    else:
+        coef, res = solve(beta)
+    return coef[1] / coef[0], beta, res
+
+
+def far_field(g: Geometry, x, k, z, rhat):
+    """Far-field pattern F(rhat) of the exterior current set (rhat: (P,3))."""
+    x = np.asarray(x, dtype=np.complex128)
+    Jes, _, Ms = current_sets(g, x[:, None])
+    J, _ = _point_currents(g, Jes)
+    M, _ = _point_currents(g, Ms)
+    src = g.qpts.reshape(-1, 3)
+    w = g.qw.reshape(-1)
+    J = J[..., 0].reshape(-1, 3) * w[:, None]
+    M = M[..., 0].reshape(-1, 3) * w[:, None]
+    ph = np.exp(1j * k * (rhat @ src.T))  # (P, S)
+    Jh = ph @ J
+    Mh = ph @ M
+    rJ = np.sum(rhat * Jh, axis=1)
+    return (-1j * k / (4 * np.pi)) * (z * (Jh - rhat * rJ[:, None]) - np.cross(rhat, Mh))

@@ -1,0 +1,363 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names the fact it checks: values printed in the paper, closed
+forms, brute-force integration, textbook series (Mie), identities the
+formulation implies, and planted mistakes that those pins must catch.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ETA0, excitation, integrals, mesh, mie, operator, pfft, post
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ Table 1
+def test_swr_to_r_matches_table1():
+    """Table 1 (Sec. I): r = (SWR-1)/(SWR+1) for the four printed pairs."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1_swr.txt")) if l.strip() and not l.startswith("#")]
+    swr = np.array([float(r[1]) for r in rows])
+    r = np.array([float(r[2]) for r in rows])
+    got = post.swr_to_r(swr)
+    # the paper prints 4-5 significant digits
+    assert np.allclose(got, r, rtol=2e-3, atol=2e-5)
+
+
+# ------------------------------------------------------------------ quadrature
+@pytest.mark.parametrize("q,deg", [(1, 1), (3, 2), (6, 4), (7, 5)])
+def test_quadrature_rules_exact_on_monomials(q, deg):
+    """Each rule integrates x^a y^b exactly on the unit triangle up to its degree.
+
+    Closed form: int_T x^a y^b = a! b! / (a+b+2)!.
+    """
+    bary, w = mesh.RULES[q]
+    x, y = bary[:, 1], bary[:, 2]
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs(0.5 * np.sum(w * x**a * y**b) - exact) < 1e-13
+
+
+# ------------------------------------------------------------------ panel integrals
+def _subdivided(v, level):
+    tris = [tuple(v)]
+    for _ in range(level):
+        nt = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            nt += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        tris = nt
+    tr = np.array(tris)
+    bary, w = mesh.RULES[7]
+    P = np.einsum("qi,tij->tqj", bary, tr).reshape(-1, 3)
+    A = 0.5 * np.linalg.norm(np.cross(tr[:, 1] - tr[:, 0], tr[:, 2] - tr[:, 0]), axis=1)
+    W = (w[None, :] * A[:, None]).reshape(-1)
+    return P, W
+
+
+def test_static_triangle_integrals_against_brute_force():
+    """Closed-form int 1/R, int (rho'-rho)/R, int grad(1/R) vs fine quadrature."""
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        v = rng.standard_normal((3, 3))
+        P, W = _subdivided(v, 6)
+        n = np.cross(v[1] - v[0], v[2] - v[0])
+        n /= np.linalg.norm(n)
+        c = v.mean(0)
+        for r in (c + 0.8 * n, c - 0.25 * n + 0.3 * (v[1] - v[0]), v[0] + 1.7 * (v[1] - v[0]), v[2] + 0.9 * (v[2] - c)):
+            I, Ir, gI, rho = integrals.static_triangle(r, v[0], v[1], v[2], False)
+            d = r - P
+            R = np.linalg.norm(d, axis=1)
+            assert abs(I - np.sum(W / R)) < 1e-9 * abs(I)
+            assert np.linalg.norm(Ir - ((W / R)[:, None] * (P - rho)).sum(0)) < 1e-9 * np.linalg.norm(Ir)
+            assert np.linalg.norm(gI + ((W / R**3)[:, None] * d).sum(0)) < 1e-9 * np.linalg.norm(gI)
+
+
+def test_static_normal_gradient_is_solid_angle_jump():
+    """Approaching the triangle from +n the normal gradient tends to -2 pi, on it the PV is 0."""
+    v = np.array([[0, 0, 0], [1.0, 0, 0], [0, 1.0, 0]])
+    r = np.array([0.2, 0.3, 1e-9])
+    _, _, g_plus, _ = integrals.static_triangle(r, v[0], v[1], v[2], False)
+    _, _, g_pv, _ = integrals.static_triangle(r, v[0], v[1], v[2], True)
+    assert abs(g_plus[2] + 2 * np.pi) < 1e-6
+    assert abs(g_pv[2]) < 1e-15
+
+
+def test_point_triangle_moments_against_brute_force():
+    """P0, P1, Q of the full Helmholtz kernel at an off-panel point vs fine quadrature."""
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal((3, 3)) * 0.06  # panel about lambda/10 across at k = 5
+    P, W = _subdivided(v, 6)
+    k = 5.0
+    c = v.mean(0)
+    bary, w = mesh.RULES[6]
+    A = 0.5 * np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0]))
+    sp_, sw = bary @ v, w * A
+    r = c + np.array([0.01, -0.02, 0.06])
+    D = r - P
+    R = np.linalg.norm(D, axis=1)
+    G = np.exp(-1j * k * R) / (4 * np.pi * R)
+    dG = (-(1j * k + 1 / R) * G / R)[:, None] * D
+    ref = (np.sum(W * G), ((W * G)[:, None] * (P - c)).sum(0), (W[:, None] * dG).sum(0))
+    # with the fine points as the source rule, extraction + closed form is exact
+    fine = integrals.point_triangle(r, v, c, P, W, k, False, -1)
+    for got, want in zip(fine, ref):
+        assert np.linalg.norm(got - want) < 1e-9 * np.linalg.norm(want)
+    # with the 6-point rule the remainder carries that rule's error only
+    six = integrals.point_triangle(r, v, c, sp_, sw, k, False, -1)
+    for got, want in zip(six, ref):
+        assert np.linalg.norm(got - want) < 5e-3 * np.linalg.norm(want)
+
+
+def test_smooth_kernel_stable_forms():
+    """(e^{-jkR}-1)/R and its derivative against their Taylor series at small kR."""
+    k, R = 3.0, 1e-5
+    kr = k * R
+    assert abs(integrals.gs_value(R, k) - (-1j * k - k * kr / 2 + 1j * k * kr**2 / 6)) < 1e-12
+    assert abs(integrals.gs_deriv(R, k) - (-k * k / 2 + 1j * k**3 * R / 3)) < 1e-6
+
+
+# ------------------------------------------------------------------ Mie (whole-operator physics)
+def _sphere_far_error(level, region_R, sigma_S, planted=None, monkeypatch=None):
+    m = synth.icosphere(level, 1.0)
+    reg = np.ones(m.nt, int) if region_R else m.region
+    g = mesh.build(m.V, m.T, reg, q=6)
+    med = operator.Media(2.25, 1.0, 1.0, 1.0, 1.55)
+    sig = np.full((g.nt, g.q), sigma_S)
+    if planted is not None:
+        monkeypatch.setattr(operator, "test_rows", planted)
+    A = operator.assemble(g, med, sig)
+    b = excitation.rhs(g, med, sig, "e", "planewave", d=[0, 0, 1], e=[1, 0, 0])
+    x = np.linalg.solve(A, b)
+    ke, ze = med.k[0], med.z[0]
+    th = np.linspace(0.01, np.pi - 0.01, 25)
+    r0 = np.stack([np.sin(th), 0 * th, np.cos(th)], 1)
+    r90 = np.stack([0 * th, np.sin(th), np.cos(th)], 1)
+    thh = np.stack([np.cos(th), 0 * th, -np.sin(th)], 1)
+    Fth = np.abs(np.sum(post.far_field(g, x, ke, ze, r0) * thh, 1))
+    Fph = np.abs(post.far_field(g, x, ke, ze, r90)[:, 0])
+    S1, S2 = mie.amplitudes(1.5, ke * 1.0, th, s=sigma_S * ETA0 * ze)
+    e2 = np.linalg.norm(Fth - np.abs(S2) / ke) / np.linalg.norm(np.abs(S2) / ke)
+    e1 = np.linalg.norm(Fph - np.abs(S1) / ke) / np.linalg.norm(np.abs(S1) / ke)
+    return max(e1, e2), g, A, x
+
+
+def test_mie_sphere_plain_pmchw():
+    """Dielectric sphere (r=1 um, eps=2.25, 1.55 um, 320 triangles) vs the Mie series."""
+    err, *_ = _sphere_far_error(2, False, 0.0)
+    assert err < 0.05
+
+
+def test_mie_sphere_absorber_rows_with_sheet():
+    """All-absorber sphere with sigma = 1/eta0 S vs Mie with a conducting sheet (Eq. 4 jump)."""
+    err, *_ = _sphere_far_error(2, True, 1.0 / ETA0)
+    assert err < 0.06
+
+
+def test_mie_catches_planted_sign_of_sigma(monkeypatch):
+    """Planted mistake: conductivity entering with the wrong sign (gain) must fail the pin."""
+    orig = operator.test_rows
+
+    def wrong(g, tris, fe, fi, Js, Ml, sig):
+        return orig(g, tris, fe, fi, Js, Ml, -sig)
+
+    err, *_ = _sphere_far_error(2, True, 1.0 / ETA0, wrong, monkeypatch)
+    assert err > 0.15
+
+
+def test_mie_catches_planted_jump_sign(monkeypatch):
+    """Planted mistake: the n x M / 2 side-limit term with the wrong sign must fail the pin."""
+    orig = operator.test_rows
+
+    def wrong(g, tris, fe, fi, Js, Ml, sig):
+        val = orig(g, tris, fe, fi, Js, Ml, sig)
+        # add twice the (-1/2 <sigma X, n x M>) term back, i.e. flip its sign
+        fz = {k: np.zeros_like(v) for k, v in fe.items()}
+        only = orig(g, tris, fz, fz, np.zeros_like(Js), Ml, sig)
+        return val - 2.0 * only
+
+    err, *_ = _sphere_far_error(2, True, 1.0 / ETA0, wrong, monkeypatch)
+    assert err > 0.10
+
+
+def test_sigma_zero_absorber_rows_give_opposite_currents():
+    """With sigma = 0, Eq. 14 reduces to <X, J_e + J_i> = 0, so J_e^R = -J_i^R exactly."""
+    m = synth.icosphere(1, 1.0)
+    g = mesh.build(m.V, m.T, np.ones(m.nt, int), q=6)
+    med = operator.Media(2.25, 1.0, 1.0, 1.0, 1.55)
+    sig = np.zeros((g.nt, g.q))
+    A = operator.assemble(g, med, sig)
+    b = excitation.rhs(g, med, sig, "e", "planewave", d=[0, 0, 1], e=[1, 0, 0])
+    x = np.linalg.solve(A, b)
+    nR = g.nR
+    assert np.linalg.norm(x[:nR] + x[nR : 2 * nR]) < 1e-10 * np.linalg.norm(x[:nR])
+
+
+def test_mie_series_limits():
+    """Mie with a sheet: lossless equality, loss > 0, Rayleigh limit, PEC limit."""
+    m, x = 1.5, 4.05
+    qs, qe = mie.efficiencies(m, x, 0.0)
+    assert abs(qs - qe) < 1e-10 * qe  # lossless: extinction = scattering
+    qs, qe = mie.efficiencies(m, x, 1.0)
+    assert qe - qs > 1e-3  # a resistive sheet absorbs
+    xs = 0.01
+    qs, _ = mie.efficiencies(m, xs, 0.0)
+    ray = 8.0 / 3.0 * xs**4 * abs((m * m - 1) / (m * m + 2)) ** 2
+    assert abs(qs - ray) < 1e-3 * ray
+    n, a, b = mie.coefficients(m, x, 1e9)
+    from scipy.special import spherical_jn, spherical_yn
+
+    psi = x * spherical_jn(n, x)
+    dpsi = spherical_jn(n, x) + x * spherical_jn(n, x, True)
+    h = spherical_jn(n, x) + 1j * spherical_yn(n, x)
+    dh = spherical_jn(n, x, True) + 1j * spherical_yn(n, x, True)
+    assert np.allclose(a, dpsi / (h + x * dh), atol=1e-6)
+    assert np.allclose(b, psi / (x * h), atol=1e-6)
+
+
+def test_galerkin_l_blocks_reciprocal_and_k_asymmetry_shrinks():
+    """L-blocks are complex symmetric (reciprocity) up to outer-quadrature error,
+    which falls with the rule; the K-block's near-singular outer error falls too."""
+    m = synth.icosphere(1, 1.0)
+    med = operator.Media(2.25, 1.0, 1.0, 1.0, 1.55)
+    asym = []
+    for q in (3, 6, 7):
+        g = mesh.build(m.V, m.T, m.region, q=q)
+        A = operator.assemble(g, med, np.zeros((g.nt, g.q)))
+        n = g.nL
+        f = lambda M: np.linalg.norm(M - M.T) / np.linalg.norm(M)
+        asym.append((f(A[:n, :n]), f(A[n:, n:]), f(A[:n, n:])))
+        assert np.linalg.norm(A[:n, n:] + A[n:, :n]) < 1e-12 * np.linalg.norm(A[:n, n:])
+    assert asym[1][0] < 2e-3 and asym[1][1] < 2e-3
+    assert asym[0][2] > asym[1][2] > asym[2][2]
+
+
+def test_dense_assembly_equals_direct_matvec():
+    m = synth.icosphere(1, 1.0)
+    reg = (m.V[m.T].mean(1)[:, 0] > 0.1).astype(int)
+    g = mesh.build(m.V, m.T, reg, q=6)
+    med = operator.Media(12.1, 1.0, 2.1, 1.0, 1.55)
+    sig = synth.random_sigma_qpoints(g.nt, g.q, reg, 0.01, seed=2)
+    x = synth.complex_normal(g.N, seed=5)
+    A = operator.assemble(g, med, sig)
+    assert np.linalg.norm(A @ x - operator.matvec(g, med, x, sig)) < 1e-12 * np.linalg.norm(A @ x)
+
+
+# ------------------------------------------------------------------ grid operator (O2)
+def _small_case(level=1, pgrid=(32, 32, 32), p=3):
+    m = synth.icosphere(level, 1.0)
+    reg = (m.V[m.T].mean(1)[:, 0] > 0.2).astype(int)
+    g = mesh.build(m.V, m.T, reg, q=6)
+    med = operator.Media(2.25, 1.0, 1.0, 1.0, 1.55)
+    sig = synth.random_sigma_qpoints(g.nt, g.q, reg, 0.003, seed=0)
+    grid = synth.grid_for_mesh(m.V, pgrid, p=p)
+    return g, med, sig, grid
+
+
+def test_grid_operator_equals_dense_when_all_pairs_near():
+    """Precorrection with an infinite near radius cancels the grid exactly: O2 == O1."""
+    g, med, sig, grid = _small_case(level=0, pgrid=(16, 16, 16))
+    x = synth.complex_normal(g.N, seed=1)
+    y1 = operator.matvec(g, med, x, sig)
+    y2 = pfft.PFFT(g, med, grid, 1e3).apply(x, sig)
+    assert np.linalg.norm(y1 - y2) < 1e-12 * np.linalg.norm(y1)
+
+
+def test_grid_operator_error_falls_with_radius_and_order():
+    g, med, sig, grid = _small_case(level=1)
+    x = synth.complex_normal(g.N, seed=1)
+    y1 = operator.matvec(g, med, x, sig)
+    errs = []
+    for r in (0.3, 0.6, 0.9):
+        y2 = pfft.PFFT(g, med, grid, r).apply(x, sig)
+        errs.append(np.linalg.norm(y1 - y2) / np.linalg.norm(y1))
+    # on this deliberately coarse grid (k_i h ~ 1.06) the error is a few percent
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 0.03
+    g4, med, sig, grid4 = _small_case(level=1, p=4)
+    y4 = pfft.PFFT(g4, med, grid4, 0.6).apply(x, sig)
+    assert np.linalg.norm(y1 - y4) / np.linalg.norm(y1) < 0.7 * errs[1]
+
+
+def test_fft_convolution_equals_direct_sum():
+    grid = synth.GridSpec(n=(4, 3, 5), h=0.3, origin=(0, 0, 0), p=3)
+    rng = np.random.default_rng(0)
+    src = rng.standard_normal((4, 3, 5, 2)) + 1j * rng.standard_normal((4, 3, 5, 2))
+    a = pfft.convolve(grid, pfft.padded_green(grid, 2.0), src)
+    b = pfft.direct_convolve(grid, 2.0, src)
+    assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_lagrange_stencils_reproduce_polynomials(p):
+    """Interpolation is exact for polynomials of degree < p (values and gradients)."""
+    grid = synth.GridSpec(n=(12, 12, 12), h=0.25, origin=(-1.0, -1.1, -0.9), p=p)
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(-0.4, 0.4, (20, 3))
+    gidx, W, gW, _ = pfft.stencil_weights(grid, pts)
+    idx = np.stack(np.unravel_index(np.arange(np.prod(grid.n)), grid.n), -1)
+    X = np.asarray(grid.origin) + grid.h * idx
+    coef = rng.standard_normal(3)
+    deg = p - 1
+    f = lambda Y: 0.7 + (Y @ coef) ** deg
+    df = lambda Y: (deg * (Y @ coef) ** (deg - 1))[:, None] * coef if deg > 0 else 0 * Y
+    F = f(X)
+    assert np.allclose(np.sum(W * F[gidx], 1), f(pts), atol=1e-11)
+    assert np.allclose(np.einsum("pxs,ps->px", gW, F[gidx]), df(pts), atol=1e-9)
+
+
+def test_projection_is_transpose_of_interpolation():
+    g, med, sig, grid = _small_case(level=1)
+    O = pfft.PFFT(g, med, grid, 0.3)
+    assert abs(O.P - O.I.T).sum() == 0
+
+
+# ------------------------------------------------------------------ excitation
+def _curl(fun, r, h=1e-4):
+    J = np.zeros((3, 3), dtype=complex)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        J[:, a] = (fun(r + e) - fun(r - e)) / (2 * h)
+    return np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+
+
+@pytest.mark.parametrize(
+    "kind,kw",
+    [
+        ("planewave", dict(d=[0.6, 0.0, 0.8], e=[0.8, 0.0, -0.6])),
+        ("dipole", dict(rs=[0.1, -0.2, 0.05], p=[0.3, 1.0, 0.2])),
+        ("beam", dict(r0=[0.0, 0.0, 0.0], d=[1.0, 0, 0], b=0.07, p=[0.0, 1.0, 0.0])),
+    ],
+)
+def test_incident_fields_satisfy_maxwell(kind, kw):
+    """curl E = -jkz H and curl H = (jk/z) E (exp(+jwt), eta0 = 1 units)."""
+    k, z = 14.1, 0.29
+    r = np.array([0.7, 0.3, -0.4])
+    E = lambda p: excitation.incident(kind, p[None], k, z, **kw)[0][0]
+    H = lambda p: excitation.incident(kind, p[None], k, z, **kw)[1][0]
+    cE, cH = _curl(E, r), _curl(H, r)
+    assert np.linalg.norm(cE + 1j * k * z * H(r)) < 1e-5 * np.linalg.norm(cE)
+    assert np.linalg.norm(cH - 1j * k / z * E(r)) < 1e-5 * np.linalg.norm(cH)
+
+
+def test_complex_source_beam_is_directional():
+    """On the beam axis |E| ahead / behind tends to exp(2kb) (complex source at r0 - jb d)."""
+    k, z, b = 14.1, 0.29, 0.07
+    s = 3.0
+    pts = np.array([[s, 0, 0], [-s, 0, 0]])
+    E, _ = excitation.beam(pts, k, z, [0, 0, 0], [1, 0, 0], b, [0, 1, 0])
+    ratio = np.linalg.norm(E[0]) / np.linalg.norm(E[1])
+    assert abs(ratio / math.exp(2 * k * b) - 1) < 1e-2
+
+
+def test_reflection_fit_recovers_two_waves():
+    xs = np.linspace(1.0, 3.0, 40)
+    beta, r = 11.3, 0.0123 * np.exp(0.4j)
+    E = np.exp(-1j * beta * xs) + r * np.exp(1j * beta * xs)
+    got, bt, res = post.fit_reflection(xs, E, betas=np.linspace(10, 12.5, 2501))
+    assert abs(bt - beta) < 1e-3 and abs(got - r) < 1e-4 and res < 1e-3
