@@ -1,0 +1,322 @@
+"""Benchmark: operator matvecs per second of the grid-accelerated PMCHW operator
+with surface-conductive absorbers, on the 12 um guide (19,420 triangles,
+FFT grid 512 x 64 x 64, complex64), one GB300 per process.
+
+A step is one full matvec y = A x (projection, FFT convolution with both
+Green's functions, interpolation, near-field precorrection, testing of all
+rows including the sigma-weighted absorber rows) on device-resident x.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+N > 1 runs as N independent replicas (one per GPU, launched by
+torch.distributed.run); the only collective is the max-over-ranks of the
+timed region.  Prints one JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+# the oracle baseline runs single-threaded; pin numpy's BLAS pools before import
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+METRIC = "operator matvecs/sec and GMRES solve time at N unknowns (%HBM roofline); FP32-batched vs FP64"
+UNIT = "matvec/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_rate(case, seconds: float, max_tris: int | None = None):
+    """Time the oracle's direct matvec (O1) on a bounded sample of target
+    triangles and extrapolate to a full matvec.  Returns (matvec/s, sample text, threads)."""
+    from oracle import mesh, operator
+
+    g = mesh.build(case.mesh.V, case.mesh.T, case.mesh.region, q=case.q)
+    import cases
+
+    sig = cases.sigma_points(case, g.qpts)
+    med = operator.Media(*case.media)
+    x = cases.synth.complex_normal(g.N, seed=1)
+    rng = np.random.default_rng(0)
+    order = rng.permutation(g.nt)
+    done, t0 = 0, time.perf_counter()
+    chunk = 2
+    threads = 1  # BLAS pools are pinned to one thread at start-up (see top of file)
+    while True:
+        tris = order[done : done + chunk]
+        operator.matvec(g, med, x, sig, chunk=chunk, tris=tris)
+        done += len(tris)
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= g.nt or (max_tris and done >= max_tris):
+            break
+    per_tri = el / done
+    rate = 1.0 / (per_tri * g.nt)
+    sample = f"O1 direct matvec rows of {done} random target triangles of {g.nt} ({el:.1f} s), extrapolated"
+    return rate, sample, threads, el
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ byte models
+def stage_bytes(info, case, b):
+    """Algorithmic HBM bytes per apply of each stage (one complex word = b bytes)."""
+    n0, n1, n2 = case.grid.n
+    P0 = 2 * n0
+    C = n1 * n2
+    ng = n0 * C
+    oct_ = (P0 // 2 + 1) * (n1 + 1) * (n2 + 1)
+    Q = info["qpoints"]
+    nt = Q // case.q
+    npairs = info["near_pairs"]
+    return {
+        "fft_axis0_fwd": b * 12 * (ng + P0 * C),
+        "fft_planes_green": b * (12 * P0 * C + 16 * P0 * C + 2 * oct_),
+        "fft_axis0_inv": b * 16 * (P0 * C + ng),
+        "near_field": b * (npairs * case.q * 2 * 10 + 2 * Q * 2 * 20 + nt * 12) + 4 * (nt + 1 + npairs),
+        "interpolation": b * (16 * ng + Q * 2 * 20),
+    }
+
+
+def run_gpu(args):
+    ws, rank, local = dist_env()
+    import cases
+
+    case = cases.guide_full()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, sample, threads, el = oracle_rate(case, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+    import torch
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import paper_1004_5076_gb300 as sc
+    from paper_1004_5076_gb300 import build
+
+    build.build()
+    m = case.mesh
+    stream = torch.cuda.current_stream()
+    t_setup = time.perf_counter()
+    mh = sc.scabem_mesh_create(m.V, m.T, m.region)
+    op = sc.scabem_op_create(mh, case.media, case.grid.n, case.grid.h, case.grid.origin, case.grid.p, case.q,
+                             case.r_near, 1, stream=stream)
+    sc.scabem_set_sigma(op, segments=case.sigma_segments)
+    t_setup = time.perf_counter() - t_setup
+    info = sc.scabem_op_info(op)
+    N = sc.scabem_mesh_info(mh)[2]
+    gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    x = torch.complex(torch.randn(N, device="cuda", generator=gen), torch.randn(N, device="cuda", generator=gen))
+    x = (x / math.sqrt(2)).to(torch.complex64).contiguous()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        sc.scabem_apply(op, x, y, prec=sc.SCABEM_C64, stream=stream)
+    torch.cuda.synchronize()
+    sc.scabem_profile(op, True, max(args.steps, 1))
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            sc.scabem_apply(op, x, y, prec=sc.SCABEM_C64, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    stages, napp = sc.scabem_profile_read(op)
+    sc.scabem_profile(op, False)
+    ms_max = max_over_ranks(ms, ws, device=torch.device("cuda", local))
+    value = ws * args.steps / (ms_max / 1e3)
+
+    # end to end through the C-ABI with pinned host buffers
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    sc.scabem_apply(op, xh, yh, prec=sc.SCABEM_C64, stream=stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sc.scabem_apply(op, xh, yh, prec=sc.SCABEM_C64, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, device=torch.device("cuda", local))
+    barrier(ws)
+
+    # roofline of the dominant kernel
+    hbm, src = peaks()
+    per = {k: v / max(napp, 1) for k, v in stages.items()}
+    bmodel = stage_bytes(info, case, 8)
+    dom = max(per, key=per.get)
+    roof = None
+    if dom in bmodel:
+        ach = bmodel[dom] / (per[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": src, "algorithmic_bytes": bmodel[dom]}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "guide_12um: 0.5x0.22 um eps 12.1 core in eps 2.1, 12 um, 4 um sigma0 (x/L)^3 "
+                                   "absorbers at both ends, lambda 1.55 um",
+                       "triangles": int(m.nt), "unknowns": int(N), "fft_grid": "512x64x64", "stencil_p": case.grid.p,
+                       "q": case.q, "r_near_um": case.r_near, "near_pairs": info["near_pairs"],
+                       "l2": "working set per step > L2 (near data %.0f MB)" % (info["near_bytes_c64"] / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": t_setup},
+            "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
+                    "d2h_bytes_per_step": int(N * 8)},
+            "gpu_launches": 9 * args.steps,
+            "stages_ms_per_step": per,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    sc.scabem_op_destroy(op)
+    sc.scabem_mesh_destroy(mh)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import cases
+
+    case = cases.guide_full()
+    per_step = []
+    sample = None
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        rate, sample, threads, el = oracle_rate(case, args.ref_seconds)
+        if i >= args.warmup:
+            per_step.append(rate)
+    value = float(np.mean(per_step))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "guide_12um (same as the GPU arm)", "triangles": int(case.mesh.nt)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

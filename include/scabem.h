@@ -1,0 +1,235 @@
+/*
+ * scabem: grid-accelerated PMCHW operator with a surface-conductive absorber,
+ * for one NVIDIA GB300 (sm_103a).
+ *
+ * The operator is the boundary-element system of Zhang et al., "A Novel
+ * Boundary Element Method Using Surface Conductive Absorbers for Full-Wave
+ * Analysis of 3-D Nanophotonics": Galerkin-tested RWG currents on a closed
+ * triangle mesh, PMCHW rows on plain surfaces (Eqs. 1-2), the modified rows
+ * on the absorber surface (Eqs. 3, 13, 14) with the MPIE operators of
+ * Eqs. 15-16.  Its matrix-vector product is evaluated by projecting the
+ * currents onto a uniform grid, convolving with the interior and exterior
+ * Helmholtz Green's functions by 3-D FFT, interpolating back, and adding a
+ * near-field precorrection (the FFT acceleration of Appendix B, in the
+ * precorrected-FFT form of the paper's reference Phillips97a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Time dependence exp(+j w t) (Sec. II); outward normals.
+ * - Lengths in micrometres.  Fields and currents are normalised so that the
+ *   free-space impedance is 1: electric currents are eta0*J (V/m), magnetic
+ *   currents M (V/m), tested H rows carry eta0*H.  Conductivities are passed
+ *   in siemens and multiplied by eta0 = 376.730313668 ohm internally.
+ * - Complex vectors are interleaved (re, im): complex64 (two floats) or
+ *   complex128 (two doubles), column-major with leading dimension ld >= N.
+ * - Unknown order (Appendix A): x = [J^L, M^L, J_e^R, J_i^R, M^R]; rows of
+ *   A x = b: [Eq.1 (L edges), Eq.2 (L), Eq.3 (R), Eq.13 (R), Eq.14 (R)].
+ *   Within a block, edges follow the canonical edge order: undirected edges
+ *   sorted by (min vertex, max vertex); T+ of an edge is the triangle that
+ *   traverses it from its smaller to its larger vertex.  An edge is an
+ *   absorber ("R") edge iff both of its triangles carry region flag 1.
+ * - Ownership: the caller owns every data buffer; the library owns handles
+ *   and their device workspaces.  Handles are not thread-safe; work is
+ *   ordered on the CUDA stream passed in (NULL = legacy default stream).
+ * - Errors: every call returns a scabem_status; nothing aborts or throws
+ *   across this interface.  scabem_last_error() describes the last failure
+ *   of the calling thread.  There is no CPU fallback: without an sm_103
+ *   device the calls return SCABEM_E_DEVICE.
+ */
+#ifndef SCABEM_H
+#define SCABEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scabem_mesh* scabem_mesh_t;
+typedef struct scabem_op* scabem_op_t;
+
+typedef enum {
+  SCABEM_OK = 0,
+  SCABEM_E_ARG = -1,       /* invalid argument or size */
+  SCABEM_E_MESH = -2,      /* open, non-manifold or degenerate mesh */
+  SCABEM_E_DEVICE = -3,    /* no usable sm_103 device, or a CUDA error */
+  SCABEM_E_NOMEM = -4,     /* device allocation failed */
+  SCABEM_E_NOCONV = -5,    /* solver did not reach the tolerance */
+  SCABEM_E_BREAKDOWN = -6, /* Krylov breakdown */
+  SCABEM_E_NONFINITE = -7, /* NaN or Inf in an input or a residual */
+  SCABEM_E_TIMEOUT = -8    /* a bounded device wait expired */
+} scabem_status;
+
+typedef enum { SCABEM_C64 = 0, SCABEM_C128 = 1 } scabem_prec;
+
+/* Relative permittivity / permeability (real, positive) of the interior and
+ * exterior media, and the free-space wavelength in um.  k_l = 2 pi
+ * sqrt(eps_l mu_l)/lambda0, relative impedance z_l = sqrt(mu_l/eps_l). */
+typedef struct {
+  double eps_i, mu_i, eps_e, mu_e, lambda0;
+} scabem_media;
+
+/* Grid and discretisation options.
+ *   n[3]      physical grid points per axis (x, y, z); the FFT size is 2n.
+ *             Each 2n must be a power of two in [8, 1024], and
+ *             (2 n_y) * (2 n_z) <= 4096.
+ *   h         grid spacing [um]; origin[3] coordinates of grid point 0.
+ *   p         stencil points per axis (2, 3 or 4), Lagrange interpolation;
+ *             every stencil must fall inside the physical grid.
+ *   q         quadrature points per triangle (1, 3, 6 or 7; Dunavant rules).
+ *   r_near    near-field radius [um]: triangle pairs with centroid distance
+ *             below it get the exact panel interaction (precorrection).
+ *   prec_mask bit 0: build complex64 operator data, bit 1: complex128. */
+typedef struct {
+  int32_t n[3];
+  double h;
+  double origin[3];
+  int32_t p;
+  int32_t q;
+  double r_near;
+  int32_t prec_mask;
+} scabem_grid_opts;
+
+/* Create a mesh from host arrays: xyz (nv x 3, um), tri (nt x 3, vertex
+ * indices, counter-clockwise seen from outside), region (nt; 0 = plain
+ * surface with sigma = 0 (Sec. II "L"), 1 = absorber surface ("R")).
+ * The mesh must be closed and consistently oriented (SCABEM_E_MESH).
+ * Host-side topology only; no device memory is touched. */
+int scabem_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                       const int32_t* region, scabem_mesh_t* out);
+
+/* Edge counts and the number of unknowns N = 2 n_L + 3 n_R. */
+int scabem_mesh_info(scabem_mesh_t mesh, int64_t* n_edges_L, int64_t* n_edges_R, int64_t* n_unknowns);
+
+/* Canonical edge table (host arrays of n_edges = n_L + n_R rows):
+ * edge_v (ne x 2, min/max vertex), edge_t (ne x 2, T+ / T-), edge_class
+ * (0 = L, 1 = R).  Any pointer may be NULL. */
+int scabem_mesh_edges(scabem_mesh_t mesh, int64_t* edge_v, int64_t* edge_t, int32_t* edge_class);
+
+void scabem_mesh_destroy(scabem_mesh_t mesh);
+
+/* Build the operator on the current device: triangle geometry, quadrature,
+ * stencils, the two Green's spectra (one 3-D FFT each) and the near-field
+ * precorrection (closed-form panel integrals with singularity extraction,
+ * minus the grid's own near interaction).  Conductivity starts at zero.
+ * `stream` orders the set-up work; the call returns when it is complete. */
+int scabem_op_create(scabem_mesh_t mesh, const scabem_media* media, const scabem_grid_opts* opts,
+                     void* stream, scabem_op_t* out);
+
+/* Sizes of the built operator: near pairs, bytes of near data per matvec in
+ * the given precision, quadrature points. */
+int scabem_op_info(scabem_op_t op, int64_t* n_near_pairs, int64_t* near_bytes_c64,
+                   int64_t* near_bytes_c128, int64_t* n_qpoints);
+
+void scabem_op_destroy(scabem_op_t op);
+
+/* Conductivity profile (Sec. IV, Eq. 23).
+ *   SCABEM_SIGMA_MONOMIAL: sum over nseg segments of
+ *       sigma0 * u(s)^d,  s = dir * (x_axis - x0) / L,  u = 0 for s < 0,
+ *       u = s for 0 <= s <= 1, u = 1 for s > 1,
+ *     seg[6*i .. 6*i+5] = {x0 [um], L [um], sigma0 [S], d, axis (0..2), dir (+1/-1)};
+ *     d = 0 gives a step of height sigma0 at x0.
+ *   SCABEM_SIGMA_PER_QPOINT: per_qpoint[t*q + a] [S], host array.
+ * Conductivity enters only the Eq. 13 / Eq. 14 rows of absorber edges. */
+typedef enum { SCABEM_SIGMA_MONOMIAL = 0, SCABEM_SIGMA_PER_QPOINT = 1 } scabem_sigma_kind;
+typedef struct {
+  int32_t kind;
+  int32_t nseg;
+  const double* seg;
+  const double* per_qpoint;
+} scabem_sigma;
+int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sigma);
+
+/* y = A x for nrhs right-hand sides.  x and y may be device or host memory
+ * (host buffers are staged through device copies on `stream`).  prec selects
+ * complex64 or complex128 arithmetic; the operator must have been built with
+ * that precision.  Stream-ordered: returns after enqueueing (device buffers)
+ * or after completion (host buffers). */
+int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream);
+
+/* Excitation (Sec. II): kind 0 = plane wave (dir, pol), 1 = electric dipole
+ * (pos, pol), 2 = complex-source-point beam at pos - j*b*dir radiating along
+ * dir (pos, dir, b, pol).  side 0 = source in the interior medium (the
+ * paper's case, Eqs. 8-9), 1 = exterior medium. */
+typedef struct {
+  int32_t kind;
+  int32_t side;
+  double pos[3];
+  double dir[3];
+  double pol[3];
+  double b;
+} scabem_source;
+
+/* Tested right-hand side b (Appendix A) for nsrc sources into columns of b
+ * (device or host, precision prec).  Uses the current conductivity. */
+int scabem_rhs(scabem_op_t op, const scabem_source* src, int32_t nsrc, void* b, int64_t ld, int32_t prec,
+               void* stream);
+
+/* GMRES solve of A x = b (complex128 b and x, device or host).  prec = inner
+ * precision: SCABEM_C128 runs restarted GMRES on the FP64 operator; SCABEM_C64
+ * runs the inner GMRES on the complex64 operator with FP64 Arnoldi and an
+ * outer FP64 iterative refinement r = b - A x (needs both precisions built).
+ * No preconditioner.  x holds the initial guess on entry; on return the
+ * achieved relative residual |b - A x| / |b| (FP64 operator) is in info. */
+typedef struct {
+  double tol;        /* inner relative residual */
+  int32_t restart;   /* Krylov dimension, <= 200 */
+  int32_t maxit;     /* total inner iterations */
+  double refine_tol; /* outer relative residual (C64 mode) */
+  int32_t max_refine;
+  int32_t prec;
+} scabem_solve_opts;
+typedef struct {
+  int32_t iters;
+  int32_t refinements;
+  double relres;
+  int32_t status;
+} scabem_solve_info;
+int scabem_solve(scabem_op_t op, const void* b, void* x, int32_t nrhs, int64_t ld, const scabem_solve_opts* opts,
+                 void* stream, scabem_solve_info* info);
+
+/* Interior electric field at npts host points (pts: npts x 3) from the
+ * interior current set of x (complex128), plus the incident field of `inc`
+ * if it is not NULL (Eq. 8: total interior field = E_inc + E_i(J_i, M_i)).
+ * E_out: host, npts x 3 complex128 per right-hand side. */
+int scabem_fields(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const double* pts, int32_t npts,
+                  const scabem_source* inc, double* E_out, void* stream);
+
+/* Reflection on a line of probe points inside the guide (Sec. I, Table 1):
+ * samples the component `comp` of the total interior field at npts points
+ * p0 + t * e_axis, t in [t0, t1]; fits E = a exp(-j beta t) + c exp(j beta t)
+ * by least squares (beta scanned over nbeta values in [beta_lo, beta_hi], or
+ * fixed when nbeta == 1) and reports r = c/a.  Also returns the standing-wave
+ * ratio max|E|/min|E| and (SWR-1)/(SWR+1).
+ * out (host, per rhs): {Re r, Im r, beta, residual, SWR, r_swr}. */
+typedef struct {
+  int32_t axis;
+  int32_t comp;
+  double p0[3];
+  double t0, t1;
+  int32_t npts;
+  double beta_lo, beta_hi;
+  int32_t nbeta;
+} scabem_probe;
+int scabem_reflection(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_probe* probe,
+                      const scabem_source* inc, double* out, void* stream);
+
+/* Stage timing of scabem_apply (instrumentation, not part of the paper's
+ * method).  While enabled, every apply records CUDA events at its 8 stage
+ * boundaries on its own stream, for at most max_applies applies (events are
+ * created here, so enable before any stream capture).  scabem_profile_read
+ * waits for the recorded events, returns per-stage summed milliseconds in
+ * stage_ms[8] = {summaries, projection, FFT axis-0 forward, FFT planes with
+ * the Green multiply, FFT axis-0 inverse, interpolation, near field,
+ * testing + rows} and the number of applies, and starts a new record.
+ * enable = 0 releases the events. */
+int scabem_profile(scabem_op_t op, int32_t enable, int32_t max_applies);
+int scabem_profile_read(scabem_op_t op, double* stage_ms, int64_t* n_applies);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* scabem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCABEM_H */

@@ -1,0 +1,276 @@
+"""Python binding of the scabem C-ABI (include/scabem.h).
+
+Argument marshalling only: every computation runs in the CUDA library
+``libscabem.so`` built in this directory (``build.py``).  Importing this
+package does not load the library; the first call does, and raises if it is
+missing.  There is no CPU fallback.
+
+Data buffers may be torch tensors (device or host) or numpy arrays (host);
+complex64 / complex128 arrays are passed as interleaved (re, im) pointers.
+Streams: pass ``stream=`` an integer handle or a ``torch.cuda.Stream``;
+the default is torch's current stream when torch has CUDA, else 0.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libscabem.so")
+_lib = None
+
+SCABEM_C64, SCABEM_C128 = 0, 1
+SIGMA_MONOMIAL, SIGMA_PER_QPOINT = 0, 1
+STATUS = {
+    0: "SCABEM_OK", -1: "SCABEM_E_ARG", -2: "SCABEM_E_MESH", -3: "SCABEM_E_DEVICE", -4: "SCABEM_E_NOMEM",
+    -5: "SCABEM_E_NOCONV", -6: "SCABEM_E_BREAKDOWN", -7: "SCABEM_E_NONFINITE", -8: "SCABEM_E_TIMEOUT",
+}
+
+
+class ScabemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Media(C.Structure):
+    _fields_ = [("eps_i", C.c_double), ("mu_i", C.c_double), ("eps_e", C.c_double), ("mu_e", C.c_double),
+                ("lambda0", C.c_double)]
+
+
+class GridOpts(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("h", C.c_double), ("origin", C.c_double * 3), ("p", C.c_int32),
+                ("q", C.c_int32), ("r_near", C.c_double), ("prec_mask", C.c_int32)]
+
+
+class Sigma(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nseg", C.c_int32), ("seg", C.POINTER(C.c_double)),
+                ("per_qpoint", C.POINTER(C.c_double))]
+
+
+class Source(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("side", C.c_int32), ("pos", C.c_double * 3), ("dir", C.c_double * 3),
+                ("pol", C.c_double * 3), ("b", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32), ("refine_tol", C.c_double),
+                ("max_refine", C.c_int32), ("prec", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("relres", C.c_double), ("status", C.c_int32)]
+
+
+class Probe(C.Structure):
+    _fields_ = [("axis", C.c_int32), ("comp", C.c_int32), ("p0", C.c_double * 3), ("t0", C.c_double),
+                ("t1", C.c_double), ("npts", C.c_int32), ("beta_lo", C.c_double), ("beta_hi", C.c_double),
+                ("nbeta", C.c_int32)]
+
+
+EXPORTS = [
+    "scabem_mesh_create", "scabem_mesh_info", "scabem_mesh_edges", "scabem_mesh_destroy", "scabem_op_create",
+    "scabem_op_info", "scabem_op_destroy", "scabem_set_sigma", "scabem_apply", "scabem_rhs", "scabem_solve",
+    "scabem_fields", "scabem_reflection", "scabem_last_error",
+]
+
+
+def lib():
+    """Load libscabem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise RuntimeError(f"CUDA library not built: {LIBPATH} missing (run paper_1004_5076_gb300/build.py)")
+    L = C.CDLL(LIBPATH)
+    vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
+    L.scabem_mesh_create.argtypes = [vp, i64, vp, i64, vp, C.POINTER(vp)]
+    L.scabem_mesh_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.scabem_mesh_edges.argtypes = [vp, vp, vp, vp]
+    L.scabem_mesh_destroy.argtypes = [vp]
+    L.scabem_mesh_destroy.restype = None
+    L.scabem_op_create.argtypes = [vp, C.POINTER(Media), C.POINTER(GridOpts), vp, C.POINTER(vp)]
+    L.scabem_op_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.scabem_op_destroy.argtypes = [vp]
+    L.scabem_op_destroy.restype = None
+    L.scabem_set_sigma.argtypes = [vp, C.POINTER(Sigma)]
+    L.scabem_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
+    L.scabem_rhs.argtypes = [vp, C.POINTER(Source), i32, vp, i64, i32, vp]
+    L.scabem_solve.argtypes = [vp, vp, vp, i32, i64, C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo)]
+    L.scabem_fields.argtypes = [vp, vp, i32, i64, vp, i32, C.POINTER(Source), vp, vp]
+    L.scabem_reflection.argtypes = [vp, vp, i32, i64, C.POINTER(Probe), C.POINTER(Source), vp, vp]
+    L.scabem_profile.argtypes = [vp, i32, i32]
+    L.scabem_profile_read.argtypes = [vp, vp, C.POINTER(i64)]
+    L.scabem_last_error.argtypes = []
+    L.scabem_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise ScabemError(rc, lib().scabem_last_error().decode())
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    a = np.asarray(a)
+    if not a.flags["C_CONTIGUOUS"] and not a.flags["F_CONTIGUOUS"]:
+        raise ValueError("buffer must be contiguous")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# ------------------------------------------------------------------ C-ABI, same names
+def scabem_mesh_create(V, T, region):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    region = np.ascontiguousarray(region, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().scabem_mesh_create(_ptr(V), len(V), _ptr(T), len(T), _ptr(region), C.byref(h)))
+    return h
+
+
+def scabem_mesh_info(mesh):
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().scabem_mesh_info(mesh, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def scabem_mesh_edges(mesh):
+    nL, nR, _ = scabem_mesh_info(mesh)
+    ne = nL + nR
+    ev = np.zeros((ne, 2), np.int64)
+    et = np.zeros((ne, 2), np.int64)
+    ec = np.zeros(ne, np.int32)
+    _check(lib().scabem_mesh_edges(mesh, _ptr(ev), _ptr(et), _ptr(ec)))
+    return ev, et, ec
+
+
+def scabem_mesh_destroy(mesh):
+    lib().scabem_mesh_destroy(mesh)
+
+
+def scabem_op_create(mesh, media, n, h, origin, p=3, q=6, r_near=0.0, prec_mask=3, stream=None):
+    md = Media(*media)
+    go = GridOpts((C.c_int32 * 3)(*n), h, (C.c_double * 3)(*origin), p, q, r_near, prec_mask)
+    op = C.c_void_p()
+    _check(lib().scabem_op_create(mesh, C.byref(md), C.byref(go), _stream(stream), C.byref(op)))
+    return op
+
+
+def scabem_op_info(op):
+    a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().scabem_op_info(op, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return {"near_pairs": a.value, "near_bytes_c64": b.value, "near_bytes_c128": c.value, "qpoints": d.value}
+
+
+def scabem_op_destroy(op):
+    lib().scabem_op_destroy(op)
+
+
+def scabem_set_sigma(op, segments=None, per_qpoint=None):
+    """segments: list of (x0, L, sigma0 [S], d, axis, dir); or per_qpoint (nt*q) [S]."""
+    if per_qpoint is not None:
+        arr = np.ascontiguousarray(per_qpoint, dtype=np.float64).reshape(-1)
+        sg = Sigma(SIGMA_PER_QPOINT, 0, None, arr.ctypes.data_as(C.POINTER(C.c_double)))
+        _check(lib().scabem_set_sigma(op, C.byref(sg)))
+        return
+    seg = np.ascontiguousarray(np.asarray(segments if segments else [], dtype=np.float64).reshape(-1))
+    sg = Sigma(SIGMA_MONOMIAL, len(seg) // 6, seg.ctypes.data_as(C.POINTER(C.c_double)) if len(seg) else None,
+               None)
+    _check(lib().scabem_set_sigma(op, C.byref(sg)))
+
+
+def scabem_apply(op, x, y, nrhs=1, ld=None, prec=SCABEM_C128, stream=None):
+    if ld is None:
+        ld = x.shape[0]
+    _check(lib().scabem_apply(op, _ptr(x), _ptr(y), nrhs, ld, prec, _stream(stream)))
+
+
+def make_source(kind, side=0, pos=(0, 0, 0), dir=(1, 0, 0), pol=(0, 1, 0), b=0.0):
+    kinds = {"planewave": 0, "dipole": 1, "beam": 2}
+    k = kinds[kind] if isinstance(kind, str) else int(kind)
+    s = {"i": 0, "e": 1}.get(side, side)
+    return Source(k, int(s), (C.c_double * 3)(*pos), (C.c_double * 3)(*dir), (C.c_double * 3)(*pol), b)
+
+
+def scabem_rhs(op, sources, b, ld=None, prec=SCABEM_C128, stream=None):
+    arr = (Source * len(sources))(*sources)
+    if ld is None:
+        ld = b.shape[0]
+    _check(lib().scabem_rhs(op, arr, len(sources), _ptr(b), ld, prec, _stream(stream)))
+
+
+def scabem_solve(op, b, x, nrhs=1, ld=None, tol=1e-6, restart=60, maxit=2000, refine_tol=1e-8, max_refine=10,
+                 prec=SCABEM_C128, stream=None):
+    if ld is None:
+        ld = b.shape[0]
+    o = SolveOpts(tol, restart, maxit, refine_tol, max_refine, prec)
+    info = (SolveInfo * max(nrhs, 1))()
+    rc = lib().scabem_solve(op, _ptr(b), _ptr(x), nrhs, ld, C.byref(o), _stream(stream), info)
+    out = [{"iters": i.iters, "refinements": i.refinements, "relres": i.relres, "status": i.status}
+           for i in info[:nrhs]]
+    _check(rc)
+    return out
+
+
+def scabem_fields(op, x, pts, inc=None, nrhs=1, ld=None, stream=None):
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    if ld is None:
+        ld = x.shape[0]
+    E = np.zeros((nrhs, len(pts), 3), np.complex128)
+    _check(lib().scabem_fields(op, _ptr(x), nrhs, ld, _ptr(pts), len(pts), C.byref(inc) if inc else None, _ptr(E),
+                               _stream(stream)))
+    return E
+
+
+def scabem_reflection(op, x, axis, comp, p0, t0, t1, npts, beta_lo, beta_hi, nbeta, inc=None, nrhs=1, ld=None,
+                      stream=None):
+    if ld is None:
+        ld = x.shape[0]
+    pr = Probe(axis, comp, (C.c_double * 3)(*p0), t0, t1, npts, beta_lo, beta_hi, nbeta)
+    out = np.zeros((nrhs, 6), np.float64)
+    _check(lib().scabem_reflection(op, _ptr(x), nrhs, ld, C.byref(pr), C.byref(inc) if inc else None, _ptr(out),
+                                   _stream(stream)))
+    return out
+
+
+STAGES = ["summaries", "projection", "fft_axis0_fwd", "fft_planes_green", "fft_axis0_inv", "interpolation",
+          "near_field", "testing_rows"]
+
+
+def scabem_profile(op, enable=True, max_applies=1024):
+    _check(lib().scabem_profile(op, int(bool(enable)), max_applies))
+
+
+def scabem_profile_read(op):
+    ms = np.zeros(len(STAGES), np.float64)
+    n = C.c_int64()
+    _check(lib().scabem_profile_read(op, _ptr(ms), C.byref(n)))
+    return dict(zip(STAGES, ms.tolist())), n.value
+
+
+def scabem_last_error():
+    return lib().scabem_last_error().decode()

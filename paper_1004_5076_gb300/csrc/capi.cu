@@ -1,0 +1,683 @@
+// C-ABI of the scabem library: handle management, argument validation, the
+// RWG edge table (host topology), and dispatch to the device kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return SCABEM_E_NOMEM;
+  return SCABEM_E_DEVICE;
+}
+
+template <typename R>
+int compute_summ(scabem_op* op, const cx<R>* x, cx<R>* summ, cudaStream_t s);
+
+namespace {
+
+int check_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3) {
+    set_error("this library is built for sm_103a (GB300) only; found compute capability " +
+              std::to_string(prop.major) + "." + std::to_string(prop.minor));
+    return SCABEM_E_DEVICE;
+  }
+  return SCABEM_OK;
+}
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+template <typename T>
+int dalloc(T** p, int64_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+  if (e != cudaSuccess) {
+    set_error(std::string("device allocation of ") + std::to_string(sizeof(T) * count) + " bytes failed");
+    return SCABEM_E_NOMEM;
+  }
+  return SCABEM_OK;
+}
+
+#define TRY(x)                  \
+  do {                          \
+    int rc_ = (x);              \
+    if (rc_ != SCABEM_OK) {     \
+      scabem_op_destroy(op);    \
+      return rc_;               \
+    }                           \
+  } while (0)
+
+template <typename R>
+void free_prec(PrecData<R>& pd) {
+  cudaFree(pd.ghat[0]);
+  cudaFree(pd.ghat[1]);
+  cudaFree(pd.near);
+  for (int a = 0; a < 3; ++a) cudaFree(pd.tw[a]);
+  cudaFree(pd.L);
+  cudaFree(pd.dL);
+  cudaFree(pd.sig);
+  cudaFree(pd.summ);
+  cudaFree(pd.src);
+  cudaFree(pd.stA);
+  cudaFree(pd.stB);
+  cudaFree(pd.grid);
+  cudaFree(pd.fpt);
+  cudaFree(pd.val);
+  cudaFree(pd.xs);
+  cudaFree(pd.ys);
+  pd = PrecData<R>();
+}
+
+template <typename R>
+int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) {
+  int rc;
+  if ((rc = dalloc(&pd.L, op->Q * 3 * op->p))) return rc;
+  if ((rc = dalloc(&pd.dL, op->Q * 3 * op->p))) return rc;
+  if ((rc = dalloc(&pd.sig, op->Q))) return rc;
+  if (!workspaces) return SCABEM_OK;
+  const int64_t ng = (int64_t)op->n[0] * op->n[1] * op->n[2];
+  const int64_t C = (int64_t)op->n[1] * op->n[2];
+  for (int a = 0; a < 3; ++a) {
+    if ((rc = dalloc(&pd.tw[a], op->P[a]))) return rc;
+    if ((rc = make_twiddles<R>(pd.tw[a], op->P[a], s))) return rc;
+  }
+  if ((rc = dalloc(&pd.summ, op->nt * 12))) return rc;
+  if ((rc = dalloc(&pd.src, NFIELD_IN * ng))) return rc;
+  if ((rc = dalloc(&pd.stA, (int64_t)NFIELD_IN * op->P[0] * C))) return rc;
+  if ((rc = dalloc(&pd.stB, (int64_t)NFIELD_OUT * op->P[0] * C))) return rc;
+  if ((rc = dalloc(&pd.grid, NFIELD_OUT * ng))) return rc;
+  if ((rc = dalloc(&pd.fpt, op->Q * 2 * NREC))) return rc;
+  if ((rc = dalloc(&pd.val, op->nt * 12))) return rc;
+  pd.built = true;
+  return SCABEM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename R>
+int apply_prec(scabem_op* op, const void* xv, void* yv, int nrhs, int64_t ld, cudaStream_t s) {
+  PrecData<R>& pd = *reinterpret_cast<PrecData<R>*>(sizeof(R) == 4 ? (void*)&op->f : (void*)&op->d);
+  if (!pd.built) {
+    set_error("operator was not built for this precision (prec_mask)");
+    return SCABEM_E_ARG;
+  }
+  const bool xd = is_device_ptr(xv), yd = is_device_ptr(yv);
+  const int64_t N = op->N;
+  if (xd && yd) {
+    for (int c = 0; c < nrhs; ++c) {
+      int rc = apply_one<R>(op, (const cx<R>*)xv + c * ld, (cx<R>*)yv + c * ld, s);
+      if (rc) return rc;
+    }
+    return SCABEM_OK;
+  }
+  if (pd.stage_cap < N) {
+    cudaFree(pd.xs);
+    cudaFree(pd.ys);
+    pd.xs = pd.ys = nullptr;
+    int rc;
+    if ((rc = dalloc(&pd.xs, N)) || (rc = dalloc(&pd.ys, N))) return rc;
+    pd.stage_cap = N;
+  }
+  for (int c = 0; c < nrhs; ++c) {
+    const cx<R>* xc = (const cx<R>*)xv + c * ld;
+    cx<R>* yc = (cx<R>*)yv + c * ld;
+    const cx<R>* xin = xc;
+    if (!xd) {
+      CK(cudaMemcpyAsync(pd.xs, xc, sizeof(cx<R>) * N, cudaMemcpyHostToDevice, s));
+      xin = pd.xs;
+    }
+    cx<R>* yout = yd ? yc : pd.ys;
+    int rc = apply_one<R>(op, xin, yout, s);
+    if (rc) return rc;
+    if (!yd) CK(cudaMemcpyAsync(yc, pd.ys, sizeof(cx<R>) * N, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return SCABEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* scabem_last_error(void) { return g_last_error.c_str(); }
+
+int scabem_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, const int32_t* region,
+                       scabem_mesh_t* out) {
+  if (!out || !xyz || !tri || !region || nv < 3 || nt < 2) {
+    set_error("scabem_mesh_create: null pointer or too few vertices/triangles");
+    return SCABEM_E_ARG;
+  }
+  if (nt > INT32_MAX / 8 || nv > INT32_MAX / 2) {
+    set_error("scabem_mesh_create: mesh too large");
+    return SCABEM_E_ARG;
+  }
+  *out = nullptr;
+  scabem_mesh* m = new (std::nothrow) scabem_mesh();
+  if (!m) {
+    set_error("host allocation failed");
+    return SCABEM_E_NOMEM;
+  }
+  m->nv = nv;
+  m->nt = nt;
+  m->V.assign(xyz, xyz + 3 * nv);
+  m->T.assign(tri, tri + 3 * nt);
+  m->region.assign(region, region + nt);
+  for (int64_t i = 0; i < 3 * nv; ++i)
+    if (!std::isfinite(m->V[i])) {
+      set_error("non-finite vertex coordinate");
+      delete m;
+      return SCABEM_E_NONFINITE;
+    }
+  for (int64_t t = 0; t < nt; ++t) {
+    if (m->region[t] != 0 && m->region[t] != 1) {
+      set_error("region flags must be 0 or 1");
+      delete m;
+      return SCABEM_E_ARG;
+    }
+    int32_t a = m->T[3 * t], b = m->T[3 * t + 1], c = m->T[3 * t + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv || a == b || b == c || a == c) {
+      set_error("triangle " + std::to_string(t) + " has invalid vertex indices");
+      delete m;
+      return SCABEM_E_MESH;
+    }
+    const double* p0 = &m->V[3 * a];
+    const double* p1 = &m->V[3 * b];
+    const double* p2 = &m->V[3 * c];
+    double u[3], v[3];
+    for (int k = 0; k < 3; ++k) {
+      u[k] = p1[k] - p0[k];
+      v[k] = p2[k] - p0[k];
+    }
+    const double cx_ = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+    if (!(cx_ * cx_ + cy * cy + cz * cz > 0)) {
+      set_error("triangle " + std::to_string(t) + " is degenerate (zero area)");
+      delete m;
+      return SCABEM_E_MESH;
+    }
+  }
+  // directed edges: local edge k runs from vertex k+1 to vertex k+2
+  std::unordered_map<uint64_t, int64_t> dir;
+  dir.reserve((size_t)(3 * nt * 2));
+  const uint64_t NV = (uint64_t)nv;
+  for (int64_t t = 0; t < nt; ++t)
+    for (int k = 0; k < 3; ++k) {
+      const uint64_t u = (uint64_t)m->T[3 * t + (k + 1) % 3], w = (uint64_t)m->T[3 * t + (k + 2) % 3];
+      if (!dir.emplace(u * NV + w, 3 * t + k).second) {
+        set_error("non-manifold or inconsistently oriented mesh (directed edge used twice)");
+        delete m;
+        return SCABEM_E_MESH;
+      }
+    }
+  std::vector<uint64_t> keys;
+  keys.reserve(dir.size() / 2 + 1);
+  for (auto& kv : dir) {
+    const uint64_t u = kv.first / NV, w = kv.first % NV;
+    if (u < w) keys.push_back(kv.first);
+  }
+  std::sort(keys.begin(), keys.end());
+  const int64_t ne = (int64_t)keys.size();
+  if (2 * ne != 3 * nt) {
+    set_error("open mesh: every edge must be shared by exactly two triangles");
+    delete m;
+    return SCABEM_E_MESH;
+  }
+  m->ne = ne;
+  m->ev.resize(2 * ne);
+  m->et.resize(2 * ne);
+  m->eclass.resize(ne);
+  m->ecidx.resize(ne);
+  m->elen.resize(ne);
+  m->tri_edge.assign(3 * nt, -1);
+  m->tri_sign.assign(3 * nt, 0);
+  for (int64_t e = 0; e < ne; ++e) {
+    const uint64_t u = keys[e] / NV, w = keys[e] % NV;
+    auto fp = dir.find(u * NV + w);
+    auto fm = dir.find(w * NV + u);
+    if (fm == dir.end()) {
+      set_error("open mesh: every edge must be shared by exactly two triangles");
+      delete m;
+      return SCABEM_E_MESH;
+    }
+    const int64_t tp = fp->second / 3, kp = fp->second % 3, tm = fm->second / 3, km = fm->second % 3;
+    m->ev[2 * e] = (int64_t)u;
+    m->ev[2 * e + 1] = (int64_t)w;
+    m->et[2 * e] = tp;
+    m->et[2 * e + 1] = tm;
+    m->tri_edge[3 * tp + kp] = (int32_t)e;
+    m->tri_sign[3 * tp + kp] = 1;
+    m->tri_edge[3 * tm + km] = (int32_t)e;
+    m->tri_sign[3 * tm + km] = -1;
+    m->eclass[e] = (m->region[tp] == 1 && m->region[tm] == 1) ? 1 : 0;
+    double d2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double dd = m->V[3 * w + k] - m->V[3 * u + k];
+      d2 += dd * dd;
+    }
+    m->elen[e] = std::sqrt(d2);
+  }
+  int64_t cnt[2] = {0, 0};
+  for (int64_t e = 0; e < ne; ++e) m->ecidx[e] = (int32_t)cnt[m->eclass[e]]++;
+  m->nL = cnt[0];
+  m->nR = cnt[1];
+  m->N = 2 * m->nL + 3 * m->nR;
+  if (m->N > INT32_MAX / 2) {
+    set_error("too many unknowns");
+    delete m;
+    return SCABEM_E_ARG;
+  }
+  *out = m;
+  return SCABEM_OK;
+}
+
+int scabem_mesh_info(scabem_mesh_t m, int64_t* nL, int64_t* nR, int64_t* N) {
+  if (!m) {
+    set_error("null mesh");
+    return SCABEM_E_ARG;
+  }
+  if (nL) *nL = m->nL;
+  if (nR) *nR = m->nR;
+  if (N) *N = m->N;
+  return SCABEM_OK;
+}
+
+int scabem_mesh_edges(scabem_mesh_t m, int64_t* edge_v, int64_t* edge_t, int32_t* edge_class) {
+  if (!m) {
+    set_error("null mesh");
+    return SCABEM_E_ARG;
+  }
+  if (edge_v) std::memcpy(edge_v, m->ev.data(), sizeof(int64_t) * 2 * m->ne);
+  if (edge_t) std::memcpy(edge_t, m->et.data(), sizeof(int64_t) * 2 * m->ne);
+  if (edge_class) std::memcpy(edge_class, m->eclass.data(), sizeof(int32_t) * m->ne);
+  return SCABEM_OK;
+}
+
+void scabem_mesh_destroy(scabem_mesh_t m) { delete m; }
+
+int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_opts* o, void* stream,
+                     scabem_op_t* out) {
+  if (!m || !md || !o || !out) {
+    set_error("scabem_op_create: null argument");
+    return SCABEM_E_ARG;
+  }
+  *out = nullptr;
+  int rc = check_device();
+  if (rc) return rc;
+  const double vals[5] = {md->eps_i, md->mu_i, md->eps_e, md->mu_e, md->lambda0};
+  for (double v : vals)
+    if (!(v > 0) || !std::isfinite(v)) {
+      set_error("media parameters and wavelength must be finite and positive");
+      return SCABEM_E_ARG;
+    }
+  for (int a = 0; a < 3; ++a)
+    if (!pow2_in(2 * o->n[a], 8, 1024)) {
+      set_error("grid: 2*n[axis] must be a power of two in [8, 1024]");
+      return SCABEM_E_ARG;
+    }
+  if (4 * o->n[1] * o->n[2] > 4096) {
+    set_error("grid: (2 n_y)(2 n_z) must not exceed 4096");
+    return SCABEM_E_ARG;
+  }
+  if (o->p < 2 || o->p > MAXP || !(o->q == 1 || o->q == 3 || o->q == 6 || o->q == 7) || !(o->h > 0) ||
+      !(o->r_near >= 0) || o->prec_mask < 1 || o->prec_mask > 3) {
+    set_error("grid options: need p in 2..4, q in {1,3,6,7}, h > 0, r_near >= 0, prec_mask in 1..3");
+    return SCABEM_E_ARG;
+  }
+  scabem_op* op = new (std::nothrow) scabem_op();
+  if (!op) {
+    set_error("host allocation failed");
+    return SCABEM_E_NOMEM;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetDevice(&op->device);
+  op->nt = m->nt;
+  op->ne = m->ne;
+  op->N = m->N;
+  op->nL = m->nL;
+  op->nR = m->nR;
+  op->q = o->q;
+  op->p = o->p;
+  op->Q = m->nt * o->q;
+  op->h = o->h;
+  op->r_near = o->r_near;
+  op->prec_mask = o->prec_mask;
+  for (int a = 0; a < 3; ++a) {
+    op->n[a] = o->n[a];
+    op->P[a] = 2 * o->n[a];
+    op->origin[a] = o->origin[a];
+  }
+  const double w = 2.0 * M_PI / md->lambda0;
+  op->ke = w * std::sqrt(md->eps_e * md->mu_e);
+  op->ki = w * std::sqrt(md->eps_i * md->mu_i);
+  op->ze = std::sqrt(md->mu_e / md->eps_e);
+  op->zi = std::sqrt(md->mu_i / md->eps_i);
+
+  // host tables: unknown codes per (triangle, local edge, set) and row sources
+  std::vector<int32_t> unk(9 * m->nt, 0), rowsrc(2 * m->N, 0);
+  const int64_t nL = m->nL, nR = m->nR;
+  for (int64_t t = 0; t < m->nt; ++t)
+    for (int k = 0; k < 3; ++k) {
+      const int32_t e = m->tri_edge[3 * t + k];
+      const int64_t ci = m->ecidx[e];
+      int32_t* u = &unk[(3 * t + k) * 3];
+      if (m->eclass[e] == 0) {
+        u[0] = (int32_t)(ci + 1);
+        u[1] = -(int32_t)(ci + 1);
+        u[2] = (int32_t)(nL + ci + 1);
+      } else {
+        u[0] = (int32_t)(2 * nL + ci + 1);
+        u[1] = (int32_t)(2 * nL + nR + ci + 1);
+        u[2] = (int32_t)(2 * nL + 2 * nR + ci + 1);
+      }
+    }
+  for (int64_t e = 0; e < m->ne; ++e) {
+    int64_t src[2];
+    for (int side = 0; side < 2; ++side) {
+      const int64_t t = m->et[2 * e + side];
+      int kk = 0;
+      while (m->tri_edge[3 * t + kk] != e) ++kk;
+      src[side] = (t * 3 + kk) * 4;
+    }
+    const int64_t ci = m->ecidx[e];
+    if (m->eclass[e] == 0) {
+      const int64_t r0 = ci, r1 = nL + ci;
+      rowsrc[2 * r0] = (int32_t)(src[0] + 0);
+      rowsrc[2 * r0 + 1] = (int32_t)(src[1] + 0);
+      rowsrc[2 * r1] = (int32_t)(src[0] + 1);
+      rowsrc[2 * r1 + 1] = (int32_t)(src[1] + 1);
+    } else {
+      const int64_t r0 = 2 * nL + ci, r2 = 2 * nL + nR + ci, r3 = 2 * nL + 2 * nR + ci;
+      rowsrc[2 * r0] = (int32_t)(src[0] + 0);
+      rowsrc[2 * r0 + 1] = (int32_t)(src[1] + 0);
+      rowsrc[2 * r2] = (int32_t)(src[0] + 2);
+      rowsrc[2 * r2 + 1] = (int32_t)(src[1] + 2);
+      rowsrc[2 * r3] = (int32_t)(src[0] + 3);
+      rowsrc[2 * r3 + 1] = (int32_t)(src[1] + 3);
+    }
+  }
+  TRY(dalloc(&op->tri, 16 * op->nt));
+  TRY(dalloc(&op->cX, 3 * op->nt));
+  TRY(dalloc(&op->unk, 9 * op->nt));
+  TRY(dalloc(&op->region, op->nt));
+  TRY(dalloc(&op->rowsrc, 2 * op->N));
+  TRY(dalloc(&op->qp, 3 * op->Q));
+  TRY(dalloc(&op->qw, op->Q));
+  TRY(dalloc(&op->base, 3 * op->Q));
+  TRY(dalloc(&op->sig64, op->Q));
+  TRY(dalloc(&op->err, 1));
+  TRY(alloc_prec(op, op->d, (op->prec_mask & 2) != 0, s));
+  TRY(alloc_prec(op, op->f, (op->prec_mask & 1) != 0, s));
+  auto upload = [&](void* dst, const void* src, size_t bytes) -> int {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? SCABEM_OK : cuda_fail(e, "cudaMemcpyAsync (host tables)");
+  };
+  TRY(upload(op->unk, unk.data(), sizeof(int32_t) * unk.size()));
+  TRY(upload(op->rowsrc, rowsrc.data(), sizeof(int32_t) * rowsrc.size()));
+  TRY(upload(op->region, m->region.data(), sizeof(int32_t) * m->nt));
+  TRY(setup_geometry(op, m, s));
+  TRY(setup_green(op, s));
+  TRY(setup_near(op, s));
+  TRY(setup_sigma_monomial(op, 0, nullptr, s));
+  *out = op;
+  return SCABEM_OK;
+}
+
+int scabem_op_info(scabem_op_t op, int64_t* npairs, int64_t* b64, int64_t* b128, int64_t* nq) {
+  if (!op) {
+    set_error("null operator");
+    return SCABEM_E_ARG;
+  }
+  const int64_t rec = op->npairs * op->q * 2 * NCORR;
+  if (npairs) *npairs = op->npairs;
+  if (b64) *b64 = rec * (int64_t)sizeof(cx<float>);
+  if (b128) *b128 = rec * (int64_t)sizeof(cx<double>);
+  if (nq) *nq = op->Q;
+  return SCABEM_OK;
+}
+
+int scabem_profile(scabem_op_t op, int32_t enable, int32_t max_applies) {
+  if (!op || (enable && max_applies < 1)) {
+    set_error("scabem_profile: null operator or max_applies < 1");
+    return SCABEM_E_ARG;
+  }
+  Profiler& p = op->prof;
+  for (auto e : p.ev) cudaEventDestroy(e);
+  p.ev.clear();
+  p.used = 0;
+  p.on = false;
+  if (!enable) return SCABEM_OK;
+  p.ev.resize((size_t)(NSTAGE + 1) * max_applies);
+  for (auto& e : p.ev) CK(cudaEventCreate(&e));
+  p.on = true;
+  return SCABEM_OK;
+}
+
+int scabem_profile_read(scabem_op_t op, double* stage_ms, int64_t* n_applies) {
+  if (!op || !stage_ms) {
+    set_error("scabem_profile_read: null argument");
+    return SCABEM_E_ARG;
+  }
+  Profiler& p = op->prof;
+  const int64_t n = p.used / (NSTAGE + 1);
+  for (int k = 0; k < NSTAGE; ++k) stage_ms[k] = 0.0;
+  for (int64_t a = 0; a < n; ++a) {
+    for (int k = 0; k < NSTAGE; ++k) {
+      float ms = 0.f;
+      cudaEvent_t e0 = p.ev[a * (NSTAGE + 1) + k], e1 = p.ev[a * (NSTAGE + 1) + k + 1];
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      stage_ms[k] += ms;
+    }
+  }
+  if (n_applies) *n_applies = n;
+  p.used = 0;
+  return SCABEM_OK;
+}
+
+void scabem_op_destroy(scabem_op_t op) {
+  if (!op) return;
+  for (auto e : op->prof.ev) cudaEventDestroy(e);
+  cudaFree(op->tri);
+  cudaFree(op->cX);
+  cudaFree(op->unk);
+  cudaFree(op->region);
+  cudaFree(op->trirow);
+  cudaFree(op->rowsrc);
+  cudaFree(op->qp);
+  cudaFree(op->qw);
+  cudaFree(op->base);
+  cudaFree(op->sig64);
+  cudaFree(op->noff);
+  cudaFree(op->nsrc);
+  cudaFree(op->gspatial[0]);
+  cudaFree(op->gspatial[1]);
+  cudaFree(op->err);
+  free_prec(op->f);
+  free_prec(op->d);
+  delete op;
+}
+
+int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sg) {
+  if (!op || !sg) {
+    set_error("scabem_set_sigma: null argument");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = nullptr;
+  if (sg->kind == SCABEM_SIGMA_MONOMIAL) {
+    if (sg->nseg < 0 || (sg->nseg > 0 && !sg->seg)) {
+      set_error("monomial profile: bad segment list");
+      return SCABEM_E_ARG;
+    }
+    for (int i = 0; i < sg->nseg; ++i) {
+      const double* g = sg->seg + 6 * i;
+      for (int c = 0; c < 6; ++c)
+        if (!std::isfinite(g[c])) {
+          set_error("monomial profile: non-finite parameter");
+          return SCABEM_E_NONFINITE;
+        }
+      if (!(g[1] > 0) || g[2] < 0 || g[3] < 0 || (g[4] != 0 && g[4] != 1 && g[4] != 2) ||
+          (g[5] != 1 && g[5] != -1)) {
+        set_error("monomial profile: need L > 0, sigma0 >= 0, d >= 0, axis in {0,1,2}, dir = +-1");
+        return SCABEM_E_ARG;
+      }
+    }
+    return setup_sigma_monomial(op, sg->nseg, sg->seg, s);
+  }
+  if (sg->kind == SCABEM_SIGMA_PER_QPOINT) {
+    if (!sg->per_qpoint) {
+      set_error("per-point profile: null array");
+      return SCABEM_E_ARG;
+    }
+    for (int64_t i = 0; i < op->Q; ++i) {
+      if (!std::isfinite(sg->per_qpoint[i])) {
+        set_error("per-point profile: non-finite conductivity");
+        return SCABEM_E_NONFINITE;
+      }
+      if (sg->per_qpoint[i] < 0) {
+        set_error("per-point profile: negative conductivity");
+        return SCABEM_E_ARG;
+      }
+    }
+    return setup_sigma_values(op, sg->per_qpoint, s);
+  }
+  set_error("unknown conductivity kind");
+  return SCABEM_E_ARG;
+}
+
+int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream) {
+  if (!op || !x || !y || nrhs < 0 || ld < op->N) {
+    set_error("scabem_apply: null argument, nrhs < 0 or ld < N");
+    return SCABEM_E_ARG;
+  }
+  if (nrhs == 0) return SCABEM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == SCABEM_C64) return apply_prec<float>(op, x, y, nrhs, ld, s);
+  if (prec == SCABEM_C128) return apply_prec<double>(op, x, y, nrhs, ld, s);
+  set_error("scabem_apply: prec must be SCABEM_C64 or SCABEM_C128");
+  return SCABEM_E_ARG;
+}
+
+int scabem_rhs(scabem_op_t op, const scabem_source* src, int32_t nsrc, void* b, int64_t ld, int32_t prec,
+               void* stream) {
+  if (!op || !src || !b || nsrc < 0 || ld < op->N || (prec != SCABEM_C64 && prec != SCABEM_C128)) {
+    set_error("scabem_rhs: bad argument");
+    return SCABEM_E_ARG;
+  }
+  for (int i = 0; i < nsrc; ++i)
+    if (src[i].kind < 0 || src[i].kind > 2 || src[i].side < 0 || src[i].side > 1) {
+      set_error("scabem_rhs: source kind must be 0..2 and side 0..1");
+      return SCABEM_E_ARG;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t es = prec == SCABEM_C64 ? sizeof(cx<float>) : sizeof(cx<double>);
+  if (is_device_ptr(b)) return rhs_impl(op, src, nsrc, b, ld, prec, s);
+  void* db = nullptr;
+  CK(cudaMalloc(&db, es * ld * std::max(nsrc, 1)));
+  int rc = rhs_impl(op, src, nsrc, db, ld, prec, s);
+  if (rc == SCABEM_OK) {
+    CK(cudaMemcpyAsync(b, db, es * ld * nsrc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  cudaFree(db);
+  return rc;
+}
+
+int scabem_solve(scabem_op_t op, const void* b, void* x, int32_t nrhs, int64_t ld, const scabem_solve_opts* o,
+                 void* stream, scabem_solve_info* info) {
+  if (!op || !b || !x || !o || nrhs < 0 || ld < op->N || o->restart < 1 || o->restart > 200 || o->maxit < 1 ||
+      !(o->tol > 0) || (o->prec != SCABEM_C64 && o->prec != SCABEM_C128)) {
+    set_error("scabem_solve: bad argument");
+    return SCABEM_E_ARG;
+  }
+  if (!op->d.built) {
+    set_error("scabem_solve needs the complex128 operator (prec_mask bit 1) for the FP64 residual");
+    return SCABEM_E_ARG;
+  }
+  if (o->prec == SCABEM_C64 && !op->f.built) {
+    set_error("scabem_solve in complex64 mode needs the complex64 operator (prec_mask bit 0)");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
+  if (bd && xd) return solve_impl(op, b, x, nrhs, ld, o, s, info);
+  const size_t bytes = sizeof(cx<double>) * ld * nrhs;
+  void *db = nullptr, *dx = nullptr;
+  CK(cudaMalloc(&db, bytes));
+  CK(cudaMalloc(&dx, bytes));
+  CK(cudaMemcpyAsync(db, b, bytes, bd ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dx, x, bytes, xd ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  int rc = solve_impl(op, db, dx, nrhs, ld, o, s, info);
+  CK(cudaMemcpyAsync(x, dx, bytes, xd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(db);
+  cudaFree(dx);
+  return rc;
+}
+
+int scabem_fields(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const double* pts, int32_t npts,
+                  const scabem_source* inc, double* E, void* stream) {
+  if (!op || !x || !pts || !E || npts <= 0 || nrhs < 0 || ld < op->N) {
+    set_error("scabem_fields: bad argument");
+    return SCABEM_E_ARG;
+  }
+  if (!op->d.built) {
+    set_error("scabem_fields needs the complex128 operator");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (is_device_ptr(x)) return fields_impl(op, x, nrhs, ld, pts, npts, inc, E, s);
+  void* dx = nullptr;
+  const size_t bytes = sizeof(cx<double>) * ld * nrhs;
+  CK(cudaMalloc(&dx, bytes));
+  CK(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, s));
+  int rc = fields_impl(op, dx, nrhs, ld, pts, npts, inc, E, s);
+  cudaFree(dx);
+  return rc;
+}
+
+int scabem_reflection(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_probe* pr,
+                      const scabem_source* inc, double* out, void* stream) {
+  if (!op || !x || !pr || !out || pr->npts < 4 || pr->nbeta < 1 || pr->axis < 0 || pr->axis > 2 || pr->comp < 0 ||
+      pr->comp > 2 || nrhs < 0 || ld < op->N) {
+    set_error("scabem_reflection: bad argument (npts >= 4, nbeta >= 1, axis/comp in 0..2)");
+    return SCABEM_E_ARG;
+  }
+  if (!op->d.built) {
+    set_error("scabem_reflection needs the complex128 operator");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (is_device_ptr(x)) return reflection_impl(op, x, nrhs, ld, pr, inc, out, s);
+  void* dx = nullptr;
+  const size_t bytes = sizeof(cx<double>) * ld * nrhs;
+  CK(cudaMalloc(&dx, bytes));
+  CK(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, s));
+  int rc = reflection_impl(op, dx, nrhs, ld, pr, inc, out, s);
+  cudaFree(dx);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+// Internal declarations shared by the scabem translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/scabem.h"
+
+// ------------------------------------------------------------------ complex
+template <typename R>
+struct __align__(2 * sizeof(R)) cx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
+  cx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a) { return mk(-a.re, -a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mk(s * a.re, s * a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, R s) { return mk(s * a.re, s * a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R>& operator+=(cx<R>& a, cx<R> b) {
+  a.re += b.re;
+  a.im += b.im;
+  return a;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R>& operator-=(cx<R>& a, cx<R> b) {
+  a.re -= b.re;
+  a.im -= b.im;
+  return a;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> conj(cx<R> a) { return mk(a.re, -a.im); }
+// multiply by j
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mulj(cx<R> a) { return mk(-a.im, a.re); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> czero() { return mk(R(0), R(0)); }
+// a += s * b (s real)
+template <typename R>
+__host__ __device__ __forceinline__ void axpy(cx<R>& a, R s, cx<R> b) {
+  a.re = fma(s, b.re, a.re);
+  a.im = fma(s, b.im, a.im);
+}
+// a += b * c (complex)
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cx<R>& a, cx<R> b, cx<R> c) {
+  a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
+  a.im = fma(b.re, c.im, fma(b.im, c.re, a.im));
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cvt(cx<double> a) { return mk(R(a.re), R(a.im)); }
+
+// small 3-vectors of complex
+template <typename R>
+struct cv3 {
+  cx<R> x, y, z;
+};
+
+// ------------------------------------------------------------------ limits
+constexpr int MAXQ = 7;    // quadrature points per triangle
+constexpr int MAXP = 4;    // stencil points per axis
+constexpr int NFIELD_IN = 12;
+constexpr int NFIELD_OUT = 16;
+constexpr int NREC = 20;   // per point and medium: A(3) phi gphi(3) curlA(3) F(3) psi gpsi(3) curlF(3)
+constexpr int NCORR = 10;  // per point and medium: dP0, dP1(3), dQ(3), dC(3)
+constexpr double ETA0 = 376.730313668;
+
+// ------------------------------------------------------------------ profiling
+// Stage boundaries of one apply: start, summaries, projection, FFT axis 0
+// forward, FFT planes with the Green multiply, FFT axis 0 inverse,
+// interpolation, near field, testing and rows.
+constexpr int NSTAGE = 8;
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // (NSTAGE + 1) per recorded apply
+  int64_t used = 0;             // events recorded so far
+};
+
+// ------------------------------------------------------------------ handles
+struct scabem_mesh {
+  int64_t nv = 0, nt = 0, ne = 0, nL = 0, nR = 0, N = 0;
+  std::vector<double> V;        // nv*3
+  std::vector<int32_t> T;       // nt*3
+  std::vector<int32_t> region;  // nt
+  std::vector<int64_t> ev, et;  // ne*2
+  std::vector<int32_t> eclass, ecidx;
+  std::vector<int32_t> tri_edge, tri_sign;  // nt*3
+  std::vector<double> elen;                 // ne
+};
+
+template <typename R>
+struct PrecData {
+  bool built = false;
+  cx<R>* ghat[2] = {nullptr, nullptr};  // octant spectra, scaled by 1/(P0 P1 P2)
+  cx<R>* near = nullptr;                // npairs * q * 2 * NCORR
+  cx<R>* tw[3] = {nullptr, nullptr, nullptr};  // forward twiddles per axis length
+  R* L = nullptr;                       // Q * 3 * p stencil weights
+  R* dL = nullptr;                      // Q * 3 * p derivative weights [1/um]
+  R* sig = nullptr;                     // Q normalised conductivity
+  // workspaces
+  cx<R>* summ = nullptr;  // nt * 3 sets * 4
+  cx<R>* src = nullptr;   // 12 * n0 n1 n2
+  cx<R>* stA = nullptr;   // 12 * P0 * n1 n2
+  cx<R>* stB = nullptr;   // 16 * P0 * n1 n2
+  cx<R>* grid = nullptr;  // 16 * n0 n1 n2
+  cx<R>* fpt = nullptr;   // Q * 2 * NREC
+  cx<R>* val = nullptr;   // nt * 3 * 4
+  cx<R>* xs = nullptr;    // staging for host x/y: N * nrhs_cap
+  cx<R>* ys = nullptr;
+  int64_t stage_cap = 0;
+};
+
+struct scabem_op {
+  int device = 0;
+  int64_t nt = 0, ne = 0, N = 0, Q = 0, nL = 0, nR = 0;
+  double ke = 0, ki = 0, ze = 1, zi = 1;
+  int n[3] = {0, 0, 0}, P[3] = {0, 0, 0};
+  double h = 0, origin[3] = {0, 0, 0};
+  int p = 3, q = 6;
+  double r_near = 0;
+  int prec_mask = 0;
+  // geometry (double)
+  double* tri = nullptr;    // nt * 16: v0 v1 v2 c n area
+  double* cX = nullptr;     // nt * 3: s_k l_k / (2 A)
+  int32_t* unk = nullptr;   // nt * 3 (local k) * 3 (set): (index+1)*sign, 0 = none
+  int32_t* region = nullptr;
+  int32_t* trirow = nullptr;  // nt * 3 * 4: 1 if that (t,k,type) row exists
+  int32_t* rowsrc = nullptr;  // N * 2 : ((t*3+k)*4+type) of T+ and T-
+  double* qp = nullptr;       // Q * 3
+  double* qw = nullptr;       // Q
+  int32_t* base = nullptr;    // Q * 3
+  double* sig64 = nullptr;    // Q normalised (master copy)
+  // near list
+  int64_t npairs = 0;
+  int32_t* noff = nullptr;  // nt + 1
+  int32_t* nsrc = nullptr;  // npairs
+  cx<double>* gspatial[2] = {nullptr, nullptr};  // padded G tables, set-up only
+  PrecData<float> f;
+  PrecData<double> d;
+  int* err = nullptr;  // device error flag
+  Profiler prof;
+};
+
+// Record the next stage-boundary event when profiling is on.
+inline void prof_mark(scabem_op* op, cudaStream_t s) {
+  Profiler& p = op->prof;
+  if (p.on && p.used < (int64_t)p.ev.size()) cudaEventRecord(p.ev[p.used++], s);
+}
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------------ launchers
+// setup.cu
+int setup_geometry(scabem_op* op, const scabem_mesh* m, cudaStream_t s);
+int setup_green(scabem_op* op, cudaStream_t s);
+int setup_near(scabem_op* op, cudaStream_t s);
+int setup_sigma_monomial(scabem_op* op, int nseg, const double* seg, cudaStream_t s);
+int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s);
+// apply.cu
+template <typename R>
+int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s);
+// fft.cu
+template <typename R>
+int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s);
+template <typename R>
+int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cudaStream_t s);
+template <typename R>
+int make_twiddles(cx<R>* tw, int len, cudaStream_t s);
+// solve.cu
+int rhs_impl(scabem_op* op, const scabem_source* src, int nsrc, void* b, int64_t ld, int prec, cudaStream_t s);
+int solve_impl(scabem_op* op, const void* b, void* x, int nrhs, int64_t ld, const scabem_solve_opts* o,
+               cudaStream_t s, scabem_solve_info* info);
+int fields_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double* pts, int npts,
+                const scabem_source* inc, double* E, cudaStream_t s);
+int reflection_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_probe* pr,
+                    const scabem_source* inc, double* out, cudaStream_t s);

@@ -1,0 +1,585 @@
+// Operator set-up on the device: triangle geometry and quadrature, grid
+// stencils, the two Green's spectra, the near-pair list and the near-field
+// precorrection, and the conductivity at the quadrature points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+// Symmetric triangle rules (Dunavant 1985): barycentric coordinates and
+// weights summing to one; the point order is part of the interface.
+__constant__ double c_bary[MAXQ][3];
+__constant__ double c_w[MAXQ];
+
+int load_rule(int q) {
+  const double a6 = 0.445948490915965, b6 = 0.091576213509771;
+  const double wa6 = 0.223381589678011, wb6 = 0.109951743655322;
+  const double a7 = 0.059715871789770, b7 = 0.470142064105115;
+  const double c7 = 0.797426985353087, d7 = 0.101286507323456;
+  double B[MAXQ][3] = {};
+  double W[MAXQ] = {};
+  if (q == 1) {
+    B[0][0] = B[0][1] = B[0][2] = 1.0 / 3.0;
+    W[0] = 1.0;
+  } else if (q == 3) {
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) B[i][j] = (i == j) ? 2.0 / 3.0 : 1.0 / 6.0;
+      W[i] = 1.0 / 3.0;
+    }
+  } else if (q == 6) {
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) {
+        B[i][j] = (i == j) ? 1.0 - 2.0 * a6 : a6;
+        B[3 + i][j] = (i == j) ? 1.0 - 2.0 * b6 : b6;
+      }
+      W[i] = wa6;
+      W[3 + i] = wb6;
+    }
+  } else if (q == 7) {
+    B[0][0] = B[0][1] = B[0][2] = 1.0 / 3.0;
+    W[0] = 0.225;
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) {
+        B[1 + i][j] = (i == j) ? a7 : b7;
+        B[4 + i][j] = (i == j) ? c7 : d7;
+      }
+      W[1 + i] = 0.132394152788506;
+      W[4 + i] = 0.125939180544827;
+    }
+  } else {
+    set_error("q must be 1, 3, 6 or 7");
+    return SCABEM_E_ARG;
+  }
+  CK(cudaMemcpyToSymbol(c_bary, B, sizeof(B)));
+  CK(cudaMemcpyToSymbol(c_w, W, sizeof(W)));
+  return SCABEM_OK;
+}
+
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Lagrange basis on nodes 0..p-1 at t, and its derivative.
+__device__ void lagrange(double t, int p, double* L, double* dL) {
+  for (int i = 0; i < p; ++i) {
+    double v = 1.0;
+    for (int m = 0; m < p; ++m)
+      if (m != i) v *= (t - m) / (double)(i - m);
+    L[i] = v;
+    double d = 0.0;
+    for (int j = 0; j < p; ++j) {
+      if (j == i) continue;
+      double term = 1.0 / (double)(i - j);
+      for (int m = 0; m < p; ++m)
+        if (m != i && m != j) term *= (t - m) / (double)(i - m);
+      d += term;
+    }
+    dL[i] = d;
+  }
+}
+
+// Per triangle: vertices, centroid, unit normal, area, s_k l_k/(2A), and the
+// quadrature points with their stencils.
+__global__ void k_geometry(const double* __restrict__ V, const int32_t* __restrict__ T,
+                           const int32_t* __restrict__ tsign, int64_t nt, int q, int p, double h, double ox,
+                           double oy, double oz, int n0, int n1, int n2, double* __restrict__ tri,
+                           double* __restrict__ cX, double* __restrict__ qp, double* __restrict__ qw,
+                           int32_t* __restrict__ base, double* __restrict__ Ld, double* __restrict__ dLd,
+                           float* __restrict__ Lf, float* __restrict__ dLf, int* err) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double v[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 3; ++c) v[i][c] = V[3 * (int64_t)T[3 * t + i] + c];
+  double e1[3], e2[3], nr[3];
+  for (int c = 0; c < 3; ++c) {
+    e1[c] = v[1][c] - v[0][c];
+    e2[c] = v[2][c] - v[0][c];
+  }
+  cross3(e1, e2, nr);
+  const double nn = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+  const double area = 0.5 * nn;
+  double* o = tri + 16 * t;
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 3; ++c) o[3 * i + c] = v[i][c];
+  for (int c = 0; c < 3; ++c) {
+    o[9 + c] = (v[0][c] + v[1][c] + v[2][c]) / 3.0;
+    o[12 + c] = nr[c] / nn;
+  }
+  o[15] = area;
+  for (int k = 0; k < 3; ++k) {
+    const double* a = v[(k + 1) % 3];
+    const double* b = v[(k + 2) % 3];
+    const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    const double len = sqrt(dx * dx + dy * dy + dz * dz);
+    cX[3 * t + k] = tsign[3 * t + k] * len / (2.0 * area);
+  }
+  const double org[3] = {ox, oy, oz};
+  const int nn3[3] = {n0, n1, n2};
+  for (int a = 0; a < q; ++a) {
+    const int64_t Qi = t * q + a;
+    double r[3];
+    for (int c = 0; c < 3; ++c) r[c] = c_bary[a][0] * v[0][c] + c_bary[a][1] * v[1][c] + c_bary[a][2] * v[2][c];
+    for (int c = 0; c < 3; ++c) qp[3 * Qi + c] = r[c];
+    qw[Qi] = c_w[a] * area;
+    for (int ax = 0; ax < 3; ++ax) {
+      const double u = (r[ax] - org[ax]) / h;
+      const int b = (int)floor(u - 0.5 * (p - 2));
+      base[3 * Qi + ax] = b;
+      if (b < 0 || b + p - 1 >= nn3[ax]) atomicOr(err, 1);
+      double L[MAXP], dL[MAXP];
+      lagrange(u - b, p, L, dL);
+      for (int i = 0; i < p; ++i) {
+        Ld[(3 * Qi + ax) * p + i] = L[i];
+        dLd[(3 * Qi + ax) * p + i] = dL[i] / h;
+        Lf[(3 * Qi + ax) * p + i] = (float)L[i];
+        dLf[(3 * Qi + ax) * p + i] = (float)(dL[i] / h);
+      }
+    }
+  }
+}
+
+// G(d) = exp(-jk|d|h)/(4 pi |d| h) on the padded grid with circular offsets;
+// zero at d = 0 and on the unused offset n of each axis.
+__global__ void k_green_fill(cx<double>* G, int P0, int P1, int P2, int n0, int n1, int n2, double h, double k) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t tot = (int64_t)P0 * P1 * P2;
+  if (idx >= tot) return;
+  int i2 = (int)(idx % P2);
+  int i1 = (int)((idx / P2) % P1);
+  int i0 = (int)(idx / ((int64_t)P1 * P2));
+  cx<double> g = mk(0.0, 0.0);
+  if (i0 != n0 && i1 != n1 && i2 != n2) {
+    double d0 = i0 < n0 ? i0 : i0 - P0;
+    double d1 = i1 < n1 ? i1 : i1 - P1;
+    double d2 = i2 < n2 ? i2 : i2 - P2;
+    double dist = h * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    if (dist > 0) {
+      double s, c;
+      sincos(k * dist, &s, &c);
+      double inv = 1.0 / (4.0 * M_PI * dist);
+      g = mk(c * inv, -s * inv);
+    }
+  }
+  G[idx] = g;
+}
+
+// Octant of the (even) spectrum, scaled by 1/(P0 P1 P2).
+__global__ void k_octant(const cx<double>* __restrict__ F, cx<double>* __restrict__ od, cx<float>* __restrict__ of,
+                         int P0, int P1, int P2) {
+  const int h0 = P0 / 2 + 1, h1 = P1 / 2 + 1, h2 = P2 / 2 + 1;
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t tot = (int64_t)h0 * h1 * h2;
+  if (idx >= tot) return;
+  int q2 = (int)(idx % h2);
+  int q1 = (int)((idx / h2) % h1);
+  int q0 = (int)(idx / ((int64_t)h1 * h2));
+  const double sc = 1.0 / ((double)P0 * P1 * P2);
+  cx<double> v = F[((int64_t)q0 * P1 + q1) * P2 + q2];
+  v = sc * v;
+  if (od) od[idx] = v;
+  if (of) of[idx] = mk((float)v.re, (float)v.im);
+}
+
+// ---------------------------------------------------------------- near list
+__global__ void k_near_count(const double* __restrict__ tri, int64_t nt, double r2, int32_t* __restrict__ cnt) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double cx0 = tri[16 * t + 9], cy0 = tri[16 * t + 10], cz0 = tri[16 * t + 11];
+  int c = 0;
+  for (int64_t s = 0; s < nt; ++s) {
+    const double dx = cx0 - tri[16 * s + 9], dy = cy0 - tri[16 * s + 10], dz = cz0 - tri[16 * s + 11];
+    if (dx * dx + dy * dy + dz * dz < r2) ++c;
+  }
+  cnt[t] = c;
+}
+
+__global__ void k_near_fill(const double* __restrict__ tri, int64_t nt, double r2, const int32_t* __restrict__ off,
+                            int32_t* __restrict__ src) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double cx0 = tri[16 * t + 9], cy0 = tri[16 * t + 10], cz0 = tri[16 * t + 11];
+  int64_t o = off[t];
+  for (int64_t s = 0; s < nt; ++s) {
+    const double dx = cx0 - tri[16 * s + 9], dy = cy0 - tri[16 * s + 10], dz = cz0 - tri[16 * s + 11];
+    if (dx * dx + dy * dy + dz * dz < r2) src[o++] = (int32_t)s;
+  }
+}
+
+// ---------------------------------------------------------------- panel integrals
+// Closed-form int 1/R, int (rho'-rho)/R and int grad_r(1/R) over the flat
+// triangle (singularity extraction of Eqs. 15-16; line-integral formulas of
+// Wilton et al. / Graglia restated from the divergence theorem).
+__device__ void static_tri(const double* r, const double* v, const double* nrm, bool self, double& I,
+                           double* Irho, double* gI, double* rho) {
+  const double d0 = (r[0] - v[0]) * nrm[0] + (r[1] - v[1]) * nrm[1] + (r[2] - v[2]) * nrm[2];
+  const double d = self ? 0.0 : d0;
+  const double ad = fabs(d);
+  for (int c = 0; c < 3; ++c) rho[c] = r[c] - d * nrm[c];
+  I = 0.0;
+  double om = 0.0;
+  for (int c = 0; c < 3; ++c) Irho[c] = gI[c] = 0.0;
+  for (int e = 0; e < 3; ++e) {
+    const double* a = v + 3 * e;
+    const double* b = v + 3 * ((e + 1) % 3);
+    double lv[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double ll = sqrt(lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2]);
+    for (int c = 0; c < 3; ++c) lv[c] /= ll;
+    double uh[3];
+    cross3(lv, nrm, uh);
+    double am[3] = {a[0] - rho[0], a[1] - rho[1], a[2] - rho[2]};
+    double bm[3] = {b[0] - rho[0], b[1] - rho[1], b[2] - rho[2]};
+    const double sm = am[0] * lv[0] + am[1] * lv[1] + am[2] * lv[2];
+    const double sp = bm[0] * lv[0] + bm[1] * lv[1] + bm[2] * lv[2];
+    const double t = am[0] * uh[0] + am[1] * uh[1] + am[2] * uh[2];
+    const double r0 = t * t + d * d;
+    const double Rm = sqrt(r0 + sm * sm), Rp = sqrt(r0 + sp * sp);
+    const double f = (sp + sm > 0) ? log((Rp + sp) / (Rm + sm)) : log((Rm - sm) / (Rp - sp));
+    const double be = atan2(t * sp, r0 + ad * Rp) - atan2(t * sm, r0 + ad * Rm);
+    I += t * f - ad * be;
+    const double g = 0.5 * (r0 * f + sp * Rp - sm * Rm);
+    for (int c = 0; c < 3; ++c) {
+      Irho[c] += g * uh[c];
+      gI[c] -= f * uh[c];
+    }
+    om += be;
+  }
+  const double sg = (d > 0) ? 1.0 : ((d < 0) ? -1.0 : 0.0);
+  for (int c = 0; c < 3; ++c) gI[c] -= sg * om * nrm[c];
+}
+
+// Near-field precorrection: one thread per (near pair, target point).  For
+// both media, exact potential moments (P0, P1, Q, C) of the source panel at
+// the target point minus the grid's version of the same interaction.
+// corr layout: [pair][a][medium][NCORR].
+template <typename RG>
+__global__ void k_near_corr(const double* __restrict__ tri, const double* __restrict__ qp, const double* __restrict__ qw,
+                            const int32_t* __restrict__ base, const double* __restrict__ Ld,
+                            const double* __restrict__ dLd, const int32_t* __restrict__ noff,
+                            const int32_t* __restrict__ nsrc, int64_t nt, int64_t npairs, int q, int p, double ke,
+                            double ki, const cx<RG>* __restrict__ Ge, const cx<RG>* __restrict__ Gi, int P0, int P1,
+                            int P2, cx<double>* __restrict__ outd, cx<float>* __restrict__ outf) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= npairs * q) return;
+  const int64_t j = gid / q;
+  const int a = (int)(gid - j * q);
+  // target triangle: binary search in noff
+  int64_t lo = 0, hi = nt;
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) / 2;
+    if (noff[mid] <= j) lo = mid;
+    else hi = mid;
+  }
+  const int64_t t = lo;
+  const int64_t s = nsrc[j];
+  const int64_t Qa = t * q + a;
+  const double r[3] = {qp[3 * Qa], qp[3 * Qa + 1], qp[3 * Qa + 2]};
+  const double* ts = tri + 16 * s;
+  const double cs[3] = {ts[9], ts[10], ts[11]};
+  const bool self = (s == t);
+  double I, Irho[3], gI[3], rho[3];
+  static_tri(r, ts, ts + 12, self, I, Irho, gI, rho);
+  const double inv4pi = 1.0 / (4.0 * M_PI);
+  // target stencil weights
+  const int ba[3] = {base[3 * Qa], base[3 * Qa + 1], base[3 * Qa + 2]};
+  double La[3][MAXP], dLa[3][MAXP];
+  for (int ax = 0; ax < 3; ++ax)
+    for (int i = 0; i < p; ++i) {
+      La[ax][i] = Ld[(3 * Qa + ax) * p + i];
+      dLa[ax][i] = dLd[(3 * Qa + ax) * p + i];
+    }
+  const int nd = 2 * p - 1;
+  for (int med = 0; med < 2; ++med) {
+    const double k = med == 0 ? ke : ki;
+    const cx<RG>* G = med == 0 ? Ge : Gi;
+    cx<double> P0s = mk(0.0, 0.0), P1s[3], Qs[3];
+    cx<double> P0g = mk(0.0, 0.0), P1g[3], Qg[3], Cg[3];
+    for (int c = 0; c < 3; ++c) P1s[c] = Qs[c] = P1g[c] = Qg[c] = Cg[c] = mk(0.0, 0.0);
+    for (int b = 0; b < q; ++b) {
+      const int64_t Qb = s * q + b;
+      const double rb[3] = {qp[3 * Qb], qp[3 * Qb + 1], qp[3 * Qb + 2]};
+      const double wb = qw[Qb];
+      const double rel[3] = {rb[0] - cs[0], rb[1] - cs[1], rb[2] - cs[2]};
+      const double D[3] = {r[0] - rb[0], r[1] - rb[1], r[2] - rb[2]};
+      // smooth remainder (exp(-jkR) - 1)/R and its radial derivative
+      cx<double> gv, gd;
+      if (self && b == a) {
+        gv = mk(0.0, -k);
+        gd = mk(0.0, 0.0);
+      } else {
+        const double R = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+        const double kr = k * R;
+        double sn, cn, sh, ch;
+        sincos(kr, &sn, &cn);
+        sincos(0.5 * kr, &sh, &ch);
+        gv = mk(-2.0 * sh * sh / R, -sn / R);
+        gd = mk((2.0 * sh * sh - kr * sn) / (R * R * R), (sn - kr * cn) / (R * R * R));
+      }
+      P0s += wb * gv;
+      for (int c = 0; c < 3; ++c) {
+        P1s[c] += (wb * rel[c]) * gv;
+        Qs[c] += (wb * D[c]) * gd;
+      }
+      // grid interaction Gh(a,b) and grad_a Gh(a,b), separable over axes
+      const int bb[3] = {base[3 * Qb], base[3 * Qb + 1], base[3 * Qb + 2]};
+      double K[3][2 * MAXP - 1], dK[3][2 * MAXP - 1];
+      for (int ax = 0; ax < 3; ++ax) {
+        double Lb[MAXP];
+        for (int i = 0; i < p; ++i) Lb[i] = Ld[(3 * Qb + ax) * p + i];
+        for (int dd = 0; dd < nd; ++dd) {
+          const int delta = dd - (p - 1);
+          double sv = 0.0, sd = 0.0;
+          for (int i = 0; i < p; ++i) {
+            const int ip = i - delta;
+            if (ip < 0 || ip >= p) continue;
+            sv += La[ax][i] * Lb[ip];
+            sd += dLa[ax][i] * Lb[ip];
+          }
+          K[ax][dd] = sv;
+          dK[ax][dd] = sd;
+        }
+      }
+      const int Dg[3] = {ba[0] - bb[0], ba[1] - bb[1], ba[2] - bb[2]};
+      cx<double> gh = mk(0.0, 0.0), gx = gh, gy = gh, gz = gh;
+      for (int dx = 0; dx < nd; ++dx) {
+        int o0 = Dg[0] + dx - (p - 1);
+        o0 = o0 < 0 ? o0 + P0 : o0;
+        for (int dy = 0; dy < nd; ++dy) {
+          int o1 = Dg[1] + dy - (p - 1);
+          o1 = o1 < 0 ? o1 + P1 : o1;
+          const double kxy = K[0][dx] * K[1][dy];
+          const double dxy = dK[0][dx] * K[1][dy];
+          const double xdy = K[0][dx] * dK[1][dy];
+          const cx<RG>* row = G + ((int64_t)o0 * P1 + o1) * P2;
+          for (int dz = 0; dz < nd; ++dz) {
+            int o2 = Dg[2] + dz - (p - 1);
+            o2 = o2 < 0 ? o2 + P2 : o2;
+            const cx<RG> gg = row[o2];
+            const cx<double> g = mk((double)gg.re, (double)gg.im);
+            axpy(gh, kxy * K[2][dz], g);
+            axpy(gx, dxy * K[2][dz], g);
+            axpy(gy, xdy * K[2][dz], g);
+            axpy(gz, kxy * dK[2][dz], g);
+          }
+        }
+      }
+      P0g += wb * gh;
+      const cx<double> gg3[3] = {gx, gy, gz};
+      for (int c = 0; c < 3; ++c) {
+        P1g[c] += (wb * rel[c]) * gh;
+        Qg[c] += wb * gg3[c];
+      }
+      // Cg += wb * grad Gh x rel
+      Cg[0] += wb * (rel[2] * gg3[1] - rel[1] * gg3[2]);
+      Cg[1] += wb * (rel[0] * gg3[2] - rel[2] * gg3[0]);
+      Cg[2] += wb * (rel[1] * gg3[0] - rel[0] * gg3[1]);
+    }
+    // exact moments
+    cx<double> P0e = inv4pi * (mk(I, 0.0) + P0s);
+    cx<double> P1e[3], Qe[3], Ce[3];
+    for (int c = 0; c < 3; ++c) {
+      P1e[c] = inv4pi * (mk(Irho[c] + (rho[c] - cs[c]) * I, 0.0) + P1s[c]);
+      Qe[c] = inv4pi * (mk(gI[c], 0.0) + Qs[c]);
+    }
+    const double rc[3] = {r[0] - cs[0], r[1] - cs[1], r[2] - cs[2]};
+    Ce[0] = rc[2] * Qe[1] - rc[1] * Qe[2];
+    Ce[1] = rc[0] * Qe[2] - rc[2] * Qe[0];
+    Ce[2] = rc[1] * Qe[0] - rc[0] * Qe[1];
+    cx<double> o[NCORR];
+    o[0] = P0e - P0g;
+    for (int c = 0; c < 3; ++c) {
+      o[1 + c] = P1e[c] - P1g[c];
+      o[4 + c] = Qe[c] - Qg[c];
+      o[7 + c] = Ce[c] - Cg[c];
+    }
+    const int64_t dst = ((j * q + a) * 2 + med) * NCORR;
+    for (int c = 0; c < NCORR; ++c) {
+      if (outd) outd[dst + c] = o[c];
+      if (outf) outf[dst + c] = mk((float)o[c].re, (float)o[c].im);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- conductivity
+__global__ void k_sigma_monomial(const double* __restrict__ qp, int64_t Q, int nseg, const double* __restrict__ seg,
+                                 double* __restrict__ sd, float* __restrict__ sf, double* __restrict__ s64) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  double sig = 0.0;
+  for (int g = 0; g < nseg; ++g) {
+    const double* sgp = seg + 6 * g;
+    const int ax = (int)sgp[4];
+    const double s = sgp[5] * (qp[3 * i + ax] - sgp[0]) / sgp[1];
+    if (s < 0.0) continue;
+    const double u = s > 1.0 ? 1.0 : s;
+    sig += sgp[2] * pow(u, sgp[3]);
+  }
+  sig *= ETA0;
+  s64[i] = sig;
+  if (sd) sd[i] = sig;
+  if (sf) sf[i] = (float)sig;
+}
+
+__global__ void k_sigma_copy(const double* __restrict__ in, int64_t Q, double* __restrict__ sd, float* __restrict__ sf,
+                             double* __restrict__ s64) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  const double sig = in[i] * ETA0;
+  s64[i] = sig;
+  if (sd) sd[i] = sig;
+  if (sf) sf[i] = (float)sig;
+}
+
+}  // namespace
+
+int setup_geometry(scabem_op* op, const scabem_mesh* m, cudaStream_t s) {
+  int rc = load_rule(op->q);
+  if (rc) return rc;
+  double* dV = nullptr;
+  int32_t* dT = nullptr;
+  int32_t* dS = nullptr;
+  CK(cudaMalloc(&dV, sizeof(double) * 3 * m->nv));
+  CK(cudaMalloc(&dT, sizeof(int32_t) * 3 * m->nt));
+  CK(cudaMalloc(&dS, sizeof(int32_t) * 3 * m->nt));
+  CK(cudaMemcpyAsync(dV, m->V.data(), sizeof(double) * 3 * m->nv, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dT, m->T.data(), sizeof(int32_t) * 3 * m->nt, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dS, m->tri_sign.data(), sizeof(int32_t) * 3 * m->nt, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(op->err, 0, sizeof(int), s));
+  k_geometry<<<(int)cdiv(op->nt, 128), 128, 0, s>>>(dV, dT, dS, op->nt, op->q, op->p, op->h, op->origin[0],
+                                                     op->origin[1], op->origin[2], op->n[0], op->n[1], op->n[2],
+                                                     op->tri, op->cX, op->qp, op->qw, op->base, op->d.L, op->d.dL,
+                                                     op->f.L, op->f.dL, op->err);
+  CK(cudaGetLastError());
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, op->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dV);
+  cudaFree(dT);
+  cudaFree(dS);
+  if (herr) {
+    set_error("a quadrature point's stencil falls outside the physical grid (enlarge n or h, or move origin)");
+    return SCABEM_E_ARG;
+  }
+  return SCABEM_OK;
+}
+
+int setup_green(scabem_op* op, cudaStream_t s) {
+  const int64_t tot = (int64_t)op->P[0] * op->P[1] * op->P[2];
+  const int64_t oct = (int64_t)(op->P[0] / 2 + 1) * (op->P[1] / 2 + 1) * (op->P[2] / 2 + 1);
+  cx<double>* twd[3] = {nullptr, nullptr, nullptr};
+  for (int a = 0; a < 3; ++a) {
+    CK(cudaMalloc(&twd[a], sizeof(cx<double>) * op->P[a]));
+    int rc = make_twiddles<double>(twd[a], op->P[a], s);
+    if (rc) return rc;
+  }
+  cx<double>* F = nullptr;
+  CK(cudaMalloc(&F, sizeof(cx<double>) * tot));
+  for (int med = 0; med < 2; ++med) {
+    const double k = med == 0 ? op->ke : op->ki;
+    // spatial table kept for the near-field set-up
+    CK(cudaMalloc(&op->gspatial[med], sizeof(cx<double>) * tot));
+    k_green_fill<<<(int)cdiv(tot, 256), 256, 0, s>>>(op->gspatial[med], op->P[0], op->P[1], op->P[2], op->n[0],
+                                                     op->n[1], op->n[2], op->h, k);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(F, op->gspatial[med], sizeof(cx<double>) * tot, cudaMemcpyDeviceToDevice, s));
+    const cx<double>* const tws[3] = {twd[0], twd[1], twd[2]};
+    int rc = fft3d_full<double>(op, F, tws, -1, s);
+    if (rc) return rc;
+    if (op->prec_mask & 2) CK(cudaMalloc(&op->d.ghat[med], sizeof(cx<double>) * oct));
+    if (op->prec_mask & 1) CK(cudaMalloc(&op->f.ghat[med], sizeof(cx<float>) * oct));
+    k_octant<<<(int)cdiv(oct, 256), 256, 0, s>>>(F, op->d.ghat[med], op->f.ghat[med], op->P[0], op->P[1], op->P[2]);
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(F);
+  for (int a = 0; a < 3; ++a) cudaFree(twd[a]);
+  return SCABEM_OK;
+}
+
+int setup_near(scabem_op* op, cudaStream_t s) {
+  const int64_t nt = op->nt;
+  int32_t* cnt = nullptr;
+  CK(cudaMalloc(&cnt, sizeof(int32_t) * nt));
+  const double r2 = op->r_near * op->r_near;
+  k_near_count<<<(int)cdiv(nt, 128), 128, 0, s>>>(op->tri, nt, r2, cnt);
+  CK(cudaGetLastError());
+  std::vector<int32_t> hc(nt), ho(nt + 1);
+  CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int64_t acc = 0;
+  for (int64_t t = 0; t < nt; ++t) {
+    ho[t] = (int32_t)acc;
+    acc += hc[t];
+  }
+  ho[nt] = (int32_t)acc;
+  if (acc > INT32_MAX / 16) {
+    set_error("near list too long: reduce r_near");
+    cudaFree(cnt);
+    return SCABEM_E_ARG;
+  }
+  op->npairs = acc;
+  CK(cudaMalloc(&op->noff, sizeof(int32_t) * (nt + 1)));
+  CK(cudaMalloc(&op->nsrc, sizeof(int32_t) * (acc > 0 ? acc : 1)));
+  CK(cudaMemcpyAsync(op->noff, ho.data(), sizeof(int32_t) * (nt + 1), cudaMemcpyHostToDevice, s));
+  k_near_fill<<<(int)cdiv(nt, 128), 128, 0, s>>>(op->tri, nt, r2, op->noff, op->nsrc);
+  CK(cudaGetLastError());
+  const int64_t nrec = acc * op->q * 2 * NCORR;
+  if (op->prec_mask & 2) {
+    cudaError_t e = cudaMalloc(&op->d.near, sizeof(cx<double>) * (nrec > 0 ? nrec : 1));
+    if (e != cudaSuccess) {
+      set_error("out of device memory for the near-field data");
+      return SCABEM_E_NOMEM;
+    }
+  }
+  if (op->prec_mask & 1) {
+    cudaError_t e = cudaMalloc(&op->f.near, sizeof(cx<float>) * (nrec > 0 ? nrec : 1));
+    if (e != cudaSuccess) {
+      set_error("out of device memory for the near-field data");
+      return SCABEM_E_NOMEM;
+    }
+  }
+  const int64_t work = acc * op->q;
+  if (work > 0) {
+    k_near_corr<double><<<(int)cdiv(work, 128), 128, 0, s>>>(
+        op->tri, op->qp, op->qw, op->base, op->d.L, op->d.dL, op->noff, op->nsrc, nt, acc, op->q, op->p, op->ke,
+        op->ki, op->gspatial[0], op->gspatial[1], op->P[0], op->P[1], op->P[2], op->d.near, op->f.near);
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(cnt);
+  for (int med = 0; med < 2; ++med) {
+    cudaFree(op->gspatial[med]);
+    op->gspatial[med] = nullptr;
+  }
+  return SCABEM_OK;
+}
+
+int setup_sigma_monomial(scabem_op* op, int nseg, const double* seg, cudaStream_t s) {
+  double* dseg = nullptr;
+  if (nseg > 0) {
+    CK(cudaMalloc(&dseg, sizeof(double) * 6 * nseg));
+    CK(cudaMemcpyAsync(dseg, seg, sizeof(double) * 6 * nseg, cudaMemcpyHostToDevice, s));
+  }
+  k_sigma_monomial<<<(int)cdiv(op->Q, 256), 256, 0, s>>>(op->qp, op->Q, nseg, dseg, op->d.sig, op->f.sig, op->sig64);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  if (dseg) cudaFree(dseg);
+  return SCABEM_OK;
+}
+
+int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s) {
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * op->Q));
+  CK(cudaMemcpyAsync(tmp, per_q_host, sizeof(double) * op->Q, cudaMemcpyHostToDevice, s));
+  k_sigma_copy<<<(int)cdiv(op->Q, 256), 256, 0, s>>>(tmp, op->Q, op->d.sig, op->f.sig, op->sig64);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  cudaFree(tmp);
+  return SCABEM_OK;
+}

@@ -1,0 +1,681 @@
+// Right-hand side, GMRES with FP64 Arnoldi and iterative refinement, fields
+// at interior points and the reflection fit.
+//
+// * rhs: tested incident field b (Appendix A): per absorber/plain row type,
+//   <X, E_inc>, <X, H_inc>, <X, n x H_inc>, <sigma X, E_inc> for an interior
+//   source (Eqs. 8-9), and the mirrored combination for an exterior source.
+// * solve: restarted GMRES (the paper's iterative solver, Appendix B) with
+//   classical Gram-Schmidt applied twice in FP64 on the device; Hessenberg
+//   least squares by Givens rotations.  In complex64 mode the Krylov vectors
+//   stay FP64 and only the operator runs in complex64; an outer FP64 residual
+//   r = b - A x drives iterative refinement.
+// * fields / reflection: total interior field E_inc + E_i(J_i, M_i) (Eq. 8) at
+//   probe points by the triangle quadrature, and a least-squares split of the
+//   on-axis field into forward and backward waves (Table 1's reflection).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+template <typename R>
+int compute_summ(scabem_op* op, const cx<R>* x, cx<R>* summ, cudaStream_t s);
+
+namespace {
+
+using cd = cx<double>;
+
+__device__ __forceinline__ cd cexpd(cd z) {
+  double s, c;
+  sincos(z.im, &s, &c);
+  const double e = exp(z.re);
+  return mk(e * c, e * s);
+}
+__device__ __forceinline__ cd cdivd(cd a, cd b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return mk((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+__device__ __forceinline__ cd csqrtd(cd z) {
+  const double r = hypot(z.re, z.im);
+  if (r == 0.0) return mk(0.0, 0.0);
+  const double s = sqrt(0.5 * (r + fabs(z.re)));
+  if (z.re >= 0.0) return mk(s, z.im / (2.0 * s));
+  return mk(fabs(z.im) / (2.0 * s), copysign(s, z.im));
+}
+
+// Incident E and H (eta0 = 1 units) of source S in a medium (k, z).
+__device__ void incident(const scabem_source& S, double k, double z, const double* r, cd* E, cd* H) {
+  if (S.kind == 0) {
+    const double ph = k * (S.dir[0] * r[0] + S.dir[1] * r[1] + S.dir[2] * r[2]);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const cd e = mk(cs, -sn);
+    const double dxp[3] = {S.dir[1] * S.pol[2] - S.dir[2] * S.pol[1], S.dir[2] * S.pol[0] - S.dir[0] * S.pol[2],
+                           S.dir[0] * S.pol[1] - S.dir[1] * S.pol[0]};
+    for (int c = 0; c < 3; ++c) {
+      E[c] = S.pol[c] * e;
+      H[c] = (dxp[c] / z) * e;
+    }
+    return;
+  }
+  const double b = S.kind == 2 ? S.b : 0.0;
+  cd D[3];
+  for (int c = 0; c < 3; ++c) D[c] = mk(r[c] - S.pos[c], b * S.dir[c]);  // r - (pos - j b dir)
+  const cd R2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+  const cd R = csqrtd(R2);
+  const cd iR = cdivd(mk(1.0, 0.0), R);
+  cd Rh[3];
+  for (int c = 0; c < 3; ++c) Rh[c] = D[c] * iR;
+  const cd G = (1.0 / (4.0 * M_PI)) * (cexpd(mk(0.0, -k) * R) * iR);
+  const cd u = mk(0.0, k) + iR;
+  const cd G1 = -(u * G);
+  const cd G2 = (u * u + iR * iR) * G;
+  const cd rp = S.pol[0] * Rh[0] + S.pol[1] * Rh[1] + S.pol[2] * Rh[2];
+  const cd G1R = G1 * iR;
+  for (int c = 0; c < 3; ++c) {
+    const cd hess = (G2 * rp) * Rh[c] + G1R * (mk(S.pol[c], 0.0) - rp * Rh[c]);
+    const cd L = mk(0.0, k) * (S.pol[c] * G + (1.0 / (k * k)) * hess);
+    E[c] = -z * L;
+  }
+  H[0] = G1 * (Rh[1] * S.pol[2] - Rh[2] * S.pol[1]);
+  H[1] = G1 * (Rh[2] * S.pol[0] - Rh[0] * S.pol[2]);
+  H[2] = G1 * (Rh[0] * S.pol[1] - Rh[1] * S.pol[0]);
+}
+
+__global__ void k_rhs(scabem_source S, const double* __restrict__ tri, const double* __restrict__ cX,
+                      const double* __restrict__ qp, const double* __restrict__ qw, const double* __restrict__ sig,
+                      int64_t nt, int q, double k, double z, cd* __restrict__ val) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= nt * 3) return;
+  const int64_t t = gid / 3;
+  const int kk = (int)(gid - t * 3);
+  const double* g = tri + 16 * t;
+  const double cxk = cX[gid];
+  cd tE = mk(0.0, 0.0), tH = tE, tnH = tE, tsE = tE;
+  for (int a = 0; a < q; ++a) {
+    const int64_t Qa = t * q + a;
+    const double r[3] = {qp[3 * Qa], qp[3 * Qa + 1], qp[3 * Qa + 2]};
+    cd E[3], H[3];
+    incident(S, k, z, r, E, H);
+    double X[3];
+    for (int c = 0; c < 3; ++c) X[c] = cxk * (r[c] - g[3 * kk + c]);
+    const double* n = g + 12;
+    const cd nH[3] = {n[1] * H[2] - n[2] * H[1], n[2] * H[0] - n[0] * H[2], n[0] * H[1] - n[1] * H[0]};
+    const double w = qw[Qa];
+    const cd xe = X[0] * E[0] + X[1] * E[1] + X[2] * E[2];
+    tE += w * xe;
+    tH += w * (X[0] * H[0] + X[1] * H[1] + X[2] * H[2]);
+    tnH += w * (X[0] * nH[0] + X[1] * nH[1] + X[2] * nH[2]);
+    tsE += (w * sig[Qa]) * xe;
+  }
+  cd* o = val + gid * 4;
+  if (S.side == 0) {
+    o[0] = tE;
+    o[1] = tH;
+    o[2] = tnH;
+    o[3] = tsE;
+  } else {
+    o[0] = -tE;
+    o[1] = -tH;
+    o[2] = tsE - tnH;
+    o[3] = mk(0.0, 0.0);
+  }
+}
+
+template <typename R>
+__global__ void k_rows_out(const cd* __restrict__ val, const int32_t* __restrict__ rowsrc, int64_t N,
+                           cx<R>* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const cd v = val[rowsrc[2 * i]] + val[rowsrc[2 * i + 1]];
+  y[i] = mk((R)v.re, (R)v.im);
+}
+
+// ---------------------------------------------------------------- BLAS-1 style kernels (FP64)
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_BLOCKS = 304;  // 2 x 152 SMs
+
+// part[b*nv + c] = sum over block b's rows of conj(V[:,c]) . w
+__global__ void k_dots(const cd* __restrict__ V, int64_t ldv, int nv, const cd* __restrict__ w, int64_t N,
+                       cd* __restrict__ part) {
+  __shared__ double sre[DOT_THREADS], sim[DOT_THREADS];
+  for (int c = 0; c < nv; ++c) {
+    const cd* v = V + (int64_t)c * ldv;
+    double ar = 0.0, ai = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+      const cd a = v[i], b = w[i];
+      ar += a.re * b.re + a.im * b.im;
+      ai += a.re * b.im - a.im * b.re;
+    }
+    sre[threadIdx.x] = ar;
+    sim[threadIdx.x] = ai;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        sre[threadIdx.x] += sre[threadIdx.x + st];
+        sim[threadIdx.x] += sim[threadIdx.x + st];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * nv + c] = mk(sre[0], sim[0]);
+    __syncthreads();
+  }
+}
+
+__global__ void k_reduce_parts(const cd* __restrict__ part, int nb, int nv, cd* __restrict__ out) {
+  __shared__ double sre[DOT_THREADS], sim[DOT_THREADS];
+  const int c = blockIdx.x;
+  double ar = 0.0, ai = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    ar += part[(int64_t)b * nv + c].re;
+    ai += part[(int64_t)b * nv + c].im;
+  }
+  sre[threadIdx.x] = ar;
+  sim[threadIdx.x] = ai;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sre[threadIdx.x] += sre[threadIdx.x + st];
+      sim[threadIdx.x] += sim[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = mk(sre[0], sim[0]);
+}
+
+// w -= V h   (h on the device, nv entries)
+__global__ void k_vsub(const cd* __restrict__ V, int64_t ldv, int nv, const cd* __restrict__ h, cd* __restrict__ w,
+                       int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    cd acc = w[i];
+    for (int c = 0; c < nv; ++c) {
+      const cd a = V[(int64_t)c * ldv + i], b = h[c];
+      acc.re -= a.re * b.re - a.im * b.im;
+      acc.im -= a.re * b.im + a.im * b.re;
+    }
+    w[i] = acc;
+  }
+}
+
+__global__ void k_scale_to(const cd* __restrict__ w, double s, cd* __restrict__ v, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = s * w[i];
+}
+__global__ void k_sub(const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ o, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = a[i] - b[i];
+}
+__global__ void k_add(cd* __restrict__ x, const cd* __restrict__ d, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+__global__ void k_to_f(const cd* __restrict__ a, cx<float>* __restrict__ o, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = mk((float)a[i].re, (float)a[i].im);
+}
+__global__ void k_from_f(const cx<float>* __restrict__ a, cd* __restrict__ o, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = mk((double)a[i].re, (double)a[i].im);
+}
+
+struct Work {
+  cd* V = nullptr;     // N x (m+1)
+  cd* w = nullptr;     // N
+  cd* t = nullptr;     // N
+  cd* part = nullptr;  // DOT_BLOCKS x (m+1)
+  cd* h = nullptr;     // m+1
+  cx<float>* xf = nullptr;
+  cx<float>* yf = nullptr;
+  ~Work() {
+    cudaFree(V);
+    cudaFree(w);
+    cudaFree(t);
+    cudaFree(part);
+    cudaFree(h);
+    cudaFree(xf);
+    cudaFree(yf);
+  }
+};
+
+int dots(const cd* V, int64_t ldv, int nv, const cd* w, int64_t N, Work& W, cudaStream_t s, std::vector<cd>& out) {
+  k_dots<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(V, ldv, nv, w, N, W.part);
+  CK(cudaGetLastError());
+  k_reduce_parts<<<nv, DOT_THREADS, 0, s>>>(W.part, DOT_BLOCKS, nv, W.h);
+  CK(cudaGetLastError());
+  out.resize(nv);
+  CK(cudaMemcpyAsync(out.data(), W.h, sizeof(cd) * nv, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SCABEM_OK;
+}
+
+int norm2(const cd* w, int64_t N, Work& W, cudaStream_t s, double& nrm) {
+  std::vector<cd> d;
+  int rc = dots(w, N, 1, w, N, W, s, d);
+  if (rc) return rc;
+  nrm = std::sqrt(std::max(d[0].re, 0.0));
+  return SCABEM_OK;
+}
+
+// y = A v in FP64 storage, arithmetic in `prec`.
+int op_apply64(scabem_op* op, const cd* v, cd* y, int prec, Work& W, cudaStream_t s) {
+  const int64_t N = op->N;
+  if (prec == SCABEM_C128) return apply_one<double>(op, v, y, s);
+  k_to_f<<<DOT_BLOCKS, 256, 0, s>>>(v, W.xf, N);
+  CK(cudaGetLastError());
+  int rc = apply_one<float>(op, W.xf, W.yf, s);
+  if (rc) return rc;
+  k_from_f<<<DOT_BLOCKS, 256, 0, s>>>(W.yf, y, N);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
+// Restarted GMRES for A d = r from d = 0 (d, r on the device).  Returns the
+// status and accumulates iterations.
+int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int maxit, Work& W, cudaStream_t s,
+          int& iters, double& relres_est) {
+  const int64_t N = op->N;
+  CK(cudaMemsetAsync(d, 0, sizeof(cd) * N, s));
+  double rn0;
+  int rc = norm2(r, N, W, s, rn0);
+  if (rc) return rc;
+  if (!std::isfinite(rn0)) {
+    set_error("non-finite right-hand side");
+    return SCABEM_E_NONFINITE;
+  }
+  relres_est = 0.0;
+  if (rn0 == 0.0) return SCABEM_OK;
+  // working residual: t = r - A d (d accumulates over restarts)
+  CK(cudaMemcpyAsync(W.t, r, sizeof(cd) * N, cudaMemcpyDeviceToDevice, s));
+  std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hv, hv2;
+  double beta = rn0;
+  while (true) {
+    k_scale_to<<<DOT_BLOCKS, 256, 0, s>>>(W.t, 1.0 / beta, W.V, N);
+    CK(cudaGetLastError());
+    for (auto& z : g) z = mk(0.0, 0.0);
+    g[0] = mk(beta, 0.0);
+    int j = 0;
+    bool done = false;
+    for (; j < m && iters < maxit; ++j) {
+      ++iters;
+      rc = op_apply64(op, W.V + (int64_t)j * N, W.w, prec, W, s);
+      if (rc) return rc;
+      rc = dots(W.V, N, j + 1, W.w, N, W, s, hv);
+      if (rc) return rc;
+      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j + 1, W.h, W.w, N);
+      CK(cudaGetLastError());
+      rc = dots(W.V, N, j + 1, W.w, N, W, s, hv2);
+      if (rc) return rc;
+      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j + 1, W.h, W.w, N);
+      CK(cudaGetLastError());
+      double hn;
+      rc = norm2(W.w, N, W, s, hn);
+      if (rc) return rc;
+      if (!std::isfinite(hn)) {
+        set_error("non-finite Krylov vector");
+        return SCABEM_E_NONFINITE;
+      }
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i] + hv2[i];
+      H[(size_t)(j + 1) * m + j] = mk(hn, 0.0);
+      // apply previous rotations
+      for (int i = 0; i < j; ++i) {
+        const cd a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = conj(cs[i]) * a + conj(sn[i]) * b;
+        H[(size_t)(i + 1) * m + j] = -(sn[i] * a) + cs[i] * b;
+      }
+      const cd a = H[(size_t)j * m + j];
+      const double bre = hn;
+      const double den = std::sqrt(a.re * a.re + a.im * a.im + bre * bre);
+      if (den == 0.0) {
+        set_error("GMRES breakdown");
+        return SCABEM_E_BREAKDOWN;
+      }
+      cs[j] = mk(a.re / den, a.im / den);
+      sn[j] = mk(bre / den, 0.0);
+      H[(size_t)j * m + j] = mk(den, 0.0);
+      H[(size_t)(j + 1) * m + j] = mk(0.0, 0.0);
+      const cd gj = g[j];
+      g[j] = conj(cs[j]) * gj;
+      g[j + 1] = -(sn[j] * gj);
+      relres_est = std::sqrt(g[j + 1].re * g[j + 1].re + g[j + 1].im * g[j + 1].im) / rn0;
+      if (hn <= 1e-300 || relres_est <= tol) {
+        ++j;
+        done = true;
+        break;
+      }
+      k_scale_to<<<DOT_BLOCKS, 256, 0, s>>>(W.w, 1.0 / hn, W.V + (int64_t)(j + 1) * N, N);
+      CK(cudaGetLastError());
+    }
+    // back substitution, d += V y
+    std::vector<cd> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      cd acc = g[i];
+      for (int l = i + 1; l < j; ++l) acc -= H[(size_t)i * m + l] * y[l];
+      const cd hd = H[(size_t)i * m + i];
+      const double dd = hd.re * hd.re + hd.im * hd.im;
+      y[i] = mk((acc.re * hd.re + acc.im * hd.im) / dd, (acc.im * hd.re - acc.re * hd.im) / dd);
+    }
+    for (auto& z : y) z = -z;
+    if (j > 0) {
+      CK(cudaMemcpyAsync(W.h, y.data(), sizeof(cd) * j, cudaMemcpyHostToDevice, s));
+      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j, W.h, d, N);
+      CK(cudaGetLastError());
+    }
+    if (done || iters >= maxit) break;
+    // true residual for the restart
+    rc = op_apply64(op, d, W.w, prec, W, s);
+    if (rc) return rc;
+    k_sub<<<DOT_BLOCKS, 256, 0, s>>>(r, W.w, W.t, N);
+    CK(cudaGetLastError());
+    rc = norm2(W.t, N, W, s, beta);
+    if (rc) return rc;
+    relres_est = beta / rn0;
+    if (relres_est <= tol) break;
+  }
+  return SCABEM_OK;
+}
+
+// ---------------------------------------------------------------- fields at points
+// One block per (point, rhs): sum over all source quadrature points of the
+// interior set: E = -z_i (jk A + (j/k) grad phi) - curl F_i, M_i = -M.
+__global__ void k_fields(const cd* __restrict__ summ, const double* __restrict__ tri, const double* __restrict__ qp,
+                         const double* __restrict__ qw, int64_t Q, int q, const double* __restrict__ pts, double k,
+                         double z, scabem_source inc, int has_inc, cd* __restrict__ E) {
+  const int pi = blockIdx.x;
+  const double r[3] = {pts[3 * pi], pts[3 * pi + 1], pts[3 * pi + 2]};
+  cd A[3], gp[3], cF[3];
+  for (int c = 0; c < 3; ++c) A[c] = gp[c] = cF[c] = mk(0.0, 0.0);
+  for (int64_t b = threadIdx.x; b < Q; b += blockDim.x) {
+    const int64_t t = b / q;
+    const double* g = tri + 16 * t;
+    const double rel[3] = {qp[3 * b] - g[9], qp[3 * b + 1] - g[10], qp[3 * b + 2] - g[11]};
+    const cd* si = summ + (3 * t + 1) * 4;
+    const cd* sm = summ + (3 * t + 2) * 4;
+    const double D[3] = {r[0] - qp[3 * b], r[1] - qp[3 * b + 1], r[2] - qp[3 * b + 2]};
+    const double R = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    const double w = qw[b] / (4.0 * M_PI * R);
+    const cd G = mk(w * cs, -w * sn);
+    const cd dG = -(mk(1.0 / R, k) * G) * (1.0 / R);  // times D gives grad G
+    const cd rho = 2.0 * si[0];
+    cd J[3], M[3];
+    for (int c = 0; c < 3; ++c) {
+      J[c] = rel[c] * si[0] - si[1 + c];
+      M[c] = -(rel[c] * sm[0] - sm[1 + c]);
+    }
+    for (int c = 0; c < 3; ++c) {
+      A[c] += G * J[c];
+      gp[c] += (D[c] * dG) * rho;
+    }
+    const cd gx = D[0] * dG, gy = D[1] * dG, gz = D[2] * dG;
+    cF[0] += gy * M[2] - gz * M[1];
+    cF[1] += gz * M[0] - gx * M[2];
+    cF[2] += gx * M[1] - gy * M[0];
+  }
+  __shared__ double red[256][2];
+  cd* accs[9] = {&A[0], &A[1], &A[2], &gp[0], &gp[1], &gp[2], &cF[0], &cF[1], &cF[2]};
+  cd tot[9];
+  for (int v = 0; v < 9; ++v) {
+    red[threadIdx.x][0] = accs[v]->re;
+    red[threadIdx.x][1] = accs[v]->im;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        red[threadIdx.x][0] += red[threadIdx.x + st][0];
+        red[threadIdx.x][1] += red[threadIdx.x + st][1];
+      }
+      __syncthreads();
+    }
+    tot[v] = mk(red[0][0], red[0][1]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    cd Ei[3], Hi[3];
+    for (int c = 0; c < 3; ++c) Ei[c] = mk(0.0, 0.0);
+    if (has_inc) incident(inc, k, z, r, Ei, Hi);
+    for (int c = 0; c < 3; ++c) {
+      const cd jA = mk(-tot[c].im, tot[c].re), jg = mk(-tot[3 + c].im, tot[3 + c].re);
+      E[3 * pi + c] = Ei[c] - z * (k * jA + (1.0 / k) * jg) - tot[6 + c];
+    }
+  }
+}
+
+// Least-squares split E(t) = a exp(-j beta t) + c exp(j beta t); one block,
+// threads over beta candidates.  out: {Re r, Im r, beta, residual, SWR, r_swr}.
+__global__ void k_fit(const cd* __restrict__ E, const double* __restrict__ tt, int npts, double blo, double bhi,
+                      int nbeta, double* __restrict__ out) {
+  __shared__ double best_res[256];
+  __shared__ int best_i[256];
+  double enorm = 0.0;
+  for (int i = 0; i < npts; ++i) enorm += E[i].re * E[i].re + E[i].im * E[i].im;
+  double bres = 1e300;
+  int bi = -1;
+  for (int ib = threadIdx.x; ib < nbeta; ib += blockDim.x) {
+    const double beta = nbeta > 1 ? blo + (bhi - blo) * ib / (nbeta - 1) : blo;
+    cd a12 = mk(0.0, 0.0), r1 = a12, r2 = a12;
+    for (int i = 0; i < npts; ++i) {
+      double sn, cs;
+      sincos(beta * tt[i], &sn, &cs);
+      const cd ep = mk(cs, sn);    // exp(+j beta t)
+      const cd em = mk(cs, -sn);   // exp(-j beta t)
+      a12 += ep * ep;              // conj(em) * ep
+      r1 += ep * E[i];             // conj(em) * E
+      r2 += em * E[i];             // conj(ep) * E
+    }
+    const double n = npts;
+    const double det = n * n - (a12.re * a12.re + a12.im * a12.im);
+    const cd a = (1.0 / det) * (n * r1 - a12 * r2);
+    const cd c = (1.0 / det) * (n * r2 - conj(a12) * r1);
+    double res = 0.0;
+    for (int i = 0; i < npts; ++i) {
+      double sn, cs;
+      sincos(beta * tt[i], &sn, &cs);
+      const cd f = a * mk(cs, -sn) + c * mk(cs, sn) - E[i];
+      res += f.re * f.re + f.im * f.im;
+    }
+    if (res < bres) {
+      bres = res;
+      bi = ib;
+    }
+  }
+  best_res[threadIdx.x] = bres;
+  best_i[threadIdx.x] = bi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = -1;
+    double r = 1e300;
+    for (int i = 0; i < blockDim.x; ++i)
+      if (best_i[i] >= 0 && (best_res[i] < r || (best_res[i] == r && best_i[i] < b))) {
+        r = best_res[i];
+        b = best_i[i];
+      }
+    const double beta = nbeta > 1 ? blo + (bhi - blo) * b / (nbeta - 1) : blo;
+    cd a12 = mk(0.0, 0.0), r1 = a12, r2 = a12;
+    double emax = 0.0, emin = 1e300;
+    for (int i = 0; i < npts; ++i) {
+      double sn, cs;
+      sincos(beta * tt[i], &sn, &cs);
+      const cd ep = mk(cs, sn), em = mk(cs, -sn);
+      a12 += ep * ep;
+      r1 += ep * E[i];
+      r2 += em * E[i];
+      const double m = sqrt(E[i].re * E[i].re + E[i].im * E[i].im);
+      emax = fmax(emax, m);
+      emin = fmin(emin, m);
+    }
+    const double n = npts;
+    const double det = n * n - (a12.re * a12.re + a12.im * a12.im);
+    const cd a = (1.0 / det) * (n * r1 - a12 * r2);
+    const cd c = (1.0 / det) * (n * r2 - conj(a12) * r1);
+    const cd rr = cdivd(c, a);
+    const double swr = emax / emin;
+    out[0] = rr.re;
+    out[1] = rr.im;
+    out[2] = beta;
+    out[3] = sqrt(r / enorm);
+    out[4] = swr;
+    out[5] = (swr - 1.0) / (swr + 1.0);
+  }
+}
+
+}  // namespace
+
+int rhs_impl(scabem_op* op, const scabem_source* src, int nsrc, void* b, int64_t ld, int prec, cudaStream_t s) {
+  cd* val = nullptr;
+  CK(cudaMalloc(&val, sizeof(cd) * op->nt * 12));
+  for (int i = 0; i < nsrc; ++i) {
+    const scabem_source S = src[i];
+    const double k = S.side == 0 ? op->ki : op->ke;
+    const double z = S.side == 0 ? op->zi : op->ze;
+    k_rhs<<<(int)cdiv(op->nt * 3, 128), 128, 0, s>>>(S, op->tri, op->cX, op->qp, op->qw, op->sig64, op->nt, op->q, k,
+                                                     z, val);
+    CK(cudaGetLastError());
+    if (prec == SCABEM_C128)
+      k_rows_out<double><<<(int)cdiv(op->N, 256), 256, 0, s>>>(val, op->rowsrc, op->N, (cd*)b + (int64_t)i * ld);
+    else
+      k_rows_out<float><<<(int)cdiv(op->N, 256), 256, 0, s>>>(val, op->rowsrc, op->N,
+                                                              (cx<float>*)b + (int64_t)i * ld);
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(val);
+  return SCABEM_OK;
+}
+
+int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, const scabem_solve_opts* o,
+               cudaStream_t s, scabem_solve_info* info) {
+  const int64_t N = op->N;
+  const int m = o->restart;
+  const int prec = o->prec;
+  Work W;
+  CK(cudaMalloc(&W.V, sizeof(cd) * N * (m + 1)));
+  CK(cudaMalloc(&W.w, sizeof(cd) * N));
+  CK(cudaMalloc(&W.t, sizeof(cd) * N));
+  CK(cudaMalloc(&W.part, sizeof(cd) * DOT_BLOCKS * (m + 1)));
+  CK(cudaMalloc(&W.h, sizeof(cd) * (m + 1)));
+  if (prec == SCABEM_C64) {
+    CK(cudaMalloc(&W.xf, sizeof(cx<float>) * N));
+    CK(cudaMalloc(&W.yf, sizeof(cx<float>) * N));
+  }
+  cd* r = nullptr;
+  cd* d = nullptr;
+  CK(cudaMalloc(&r, sizeof(cd) * N));
+  CK(cudaMalloc(&d, sizeof(cd) * N));
+  int status = SCABEM_OK;
+  for (int col = 0; col < nrhs; ++col) {
+    const cd* b = (const cd*)bv + (int64_t)col * ld;
+    cd* x = (cd*)xv + (int64_t)col * ld;
+    double bn;
+    int rc = norm2(b, N, W, s, bn);
+    if (rc) return rc;
+    int iters = 0, refs = 0;
+    double relres = 0.0;
+    const int outer = prec == SCABEM_C64 ? o->max_refine : 1;
+    const double tol_out = prec == SCABEM_C64 ? o->refine_tol : o->tol;
+    int st = SCABEM_E_NOCONV;
+    for (int it = 0; it <= outer; ++it) {
+      rc = apply_one<double>(op, x, W.w, s);
+      if (rc) return rc;
+      k_sub<<<DOT_BLOCKS, 256, 0, s>>>(b, W.w, r, N);
+      CK(cudaGetLastError());
+      double rn;
+      rc = norm2(r, N, W, s, rn);
+      if (rc) return rc;
+      relres = bn > 0 ? rn / bn : 0.0;
+      if (!std::isfinite(relres)) {
+        st = SCABEM_E_NONFINITE;
+        break;
+      }
+      if (relres <= tol_out) {
+        st = SCABEM_OK;
+        break;
+      }
+      if (it == outer || iters >= o->maxit) break;
+      double est;
+      rc = gmres(op, r, d, prec, o->tol, m, o->maxit, W, s, iters, est);
+      if (rc) return rc;
+      k_add<<<DOT_BLOCKS, 256, 0, s>>>(x, d, N);
+      CK(cudaGetLastError());
+      if (prec == SCABEM_C64) ++refs;
+    }
+    if (info) {
+      info[col].iters = iters;
+      info[col].refinements = refs;
+      info[col].relres = relres;
+      info[col].status = st;
+    }
+    if (st != SCABEM_OK && status == SCABEM_OK) status = st;
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(r);
+  cudaFree(d);
+  if (status != SCABEM_OK) set_error("solver did not reach the requested residual");
+  return status;
+}
+
+static int fields_dev(scabem_op* op, const cd* x, const double* dpts, int npts, const scabem_source* inc, cd* dE,
+                      cudaStream_t s) {
+  int rc = compute_summ<double>(op, x, op->d.summ, s);
+  if (rc) return rc;
+  scabem_source S{};
+  if (inc) S = *inc;
+  k_fields<<<npts, 256, 0, s>>>(op->d.summ, op->tri, op->qp, op->qw, op->Q, op->q, dpts, op->ki, op->zi, S,
+                                inc ? 1 : 0, dE);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
+int fields_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double* pts, int npts,
+                const scabem_source* inc, double* E, cudaStream_t s) {
+  double* dpts = nullptr;
+  cd* dE = nullptr;
+  CK(cudaMalloc(&dpts, sizeof(double) * 3 * npts));
+  CK(cudaMalloc(&dE, sizeof(cd) * 3 * npts));
+  CK(cudaMemcpyAsync(dpts, pts, sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, s));
+  for (int col = 0; col < nrhs; ++col) {
+    int rc = fields_dev(op, (const cd*)x + (int64_t)col * ld, dpts, npts, inc, dE, s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(E + (int64_t)col * 6 * npts, dE, sizeof(cd) * 3 * npts, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dpts);
+  cudaFree(dE);
+  return SCABEM_OK;
+}
+
+int reflection_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_probe* pr,
+                    const scabem_source* inc, double* out, cudaStream_t s) {
+  const int npts = pr->npts;
+  std::vector<double> pts(3 * npts), tt(npts);
+  for (int i = 0; i < npts; ++i) {
+    const double t = npts > 1 ? pr->t0 + (pr->t1 - pr->t0) * i / (npts - 1) : pr->t0;
+    tt[i] = t;
+    for (int c = 0; c < 3; ++c) pts[3 * i + c] = pr->p0[c] + (c == pr->axis ? t : 0.0);
+  }
+  double *dpts = nullptr, *dtt = nullptr, *dout = nullptr;
+  cd *dE = nullptr, *dc = nullptr;
+  CK(cudaMalloc(&dpts, sizeof(double) * 3 * npts));
+  CK(cudaMalloc(&dtt, sizeof(double) * npts));
+  CK(cudaMalloc(&dE, sizeof(cd) * 3 * npts));
+  CK(cudaMalloc(&dc, sizeof(cd) * npts));
+  CK(cudaMalloc(&dout, sizeof(double) * 6));
+  CK(cudaMemcpyAsync(dpts, pts.data(), sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dtt, tt.data(), sizeof(double) * npts, cudaMemcpyHostToDevice, s));
+  for (int col = 0; col < nrhs; ++col) {
+    int rc = fields_dev(op, (const cd*)x + (int64_t)col * ld, dpts, npts, inc, dE, s);
+    if (rc) return rc;
+    CK(cudaMemcpy2DAsync(dc, sizeof(cd), (const char*)dE + sizeof(cd) * pr->comp, 3 * sizeof(cd), sizeof(cd), npts,
+                         cudaMemcpyDeviceToDevice, s));
+    k_fit<<<1, 256, 0, s>>>(dc, dtt, npts, pr->beta_lo, pr->beta_hi, pr->nbeta, dout);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out + 6 * col, dout, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dpts);
+  cudaFree(dtt);
+  cudaFree(dE);
+  cudaFree(dc);
+  cudaFree(dout);
+  return SCABEM_OK;
+}

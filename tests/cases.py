@@ -1,0 +1,78 @@
+"""Seeded test workloads shared by the parity tests, smoke() and bench.py.
+
+Each case fixes a mesh (synth), media, grid, conductivity and excitation.  The
+CUDA operator and the oracle are both built from exactly these inputs.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+import synth
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    mesh: synth.Mesh
+    media: tuple  # eps_i, mu_i, eps_e, mu_e, lambda0
+    grid: synth.GridSpec
+    q: int
+    r_near: float
+    sigma_segments: list | None = None
+    sigma_scale: float = 0.0  # random per-point conductivity [S] when > 0
+    seed: int = 0
+
+
+def sphere_mixed(level=2, padded=(32, 32, 32), p=3, q=6, r_near=0.5):
+    """Dielectric sphere (r = 1 um, eps 2.25 in vacuum, 1.55 um) with an absorber cap x > 0.2."""
+    m = synth.icosphere(level, 1.0)
+    reg = (m.V[m.T].mean(1)[:, 0] > 0.2).astype(np.int32)
+    m = synth.Mesh(m.V, m.T, reg)
+    grid = synth.grid_for_mesh(m.V, padded, p=p)
+    return Case("sphere_mixed", m, (2.25, 1.0, 1.0, 1.0, 1.55), grid, q, r_near, sigma_scale=0.003, seed=11)
+
+
+def guide_small(nx=40, ny=6, nz=3, length=2.0, absorber=0.6, padded=(64, 32, 16), p=3, q=6, r_near=0.16, d=2):
+    """Short silicon-like guide (eps 12.1 in 2.1) with monomial absorbers at both ends."""
+    m = synth.waveguide(length, 0.5, 0.22, nx, ny, nz, absorber, absorber)
+    grid = synth.grid_for_mesh(m.V, padded, p=p)
+    s0 = 0.004
+    segs = [
+        (length - absorber, absorber, s0, d, 0, 1.0),
+        (absorber, absorber, s0, d, 0, -1.0),
+    ]
+    return Case("guide_small", m, (12.1, 1.0, 2.1, 1.0, 1.55), grid, q, r_near, sigma_segments=segs, seed=12)
+
+
+def plate_thin(padded=(32, 16, 8), p=2, q=3, r_near=0.3):
+    """Flat thin box with a one-sided absorber: exercises p = 2 stencils and the 3-point rule."""
+    m = synth.waveguide(1.5, 0.3, 0.1, 10, 3, 1, 0.4, 0.0)
+    grid = synth.grid_for_mesh(m.V, padded, p=p)
+    return Case("plate_thin", m, (4.0, 1.0, 1.5, 1.0, 1.3), grid, q, r_near, sigma_scale=0.002, seed=13)
+
+
+def guide_full(p=3, q=6, r_near=None):
+    """The 12 um guide: 0.5 x 0.22 um core (eps 12.1) in eps 2.1, 4 um absorbers
+    sigma0 (x/L)^3 at both ends, 19,420 triangles, FFT grid 512 x 64 x 64."""
+    m = synth.waveguide()
+    grid = synth.grid_for_mesh(m.V, (512, 64, 64), p=p)
+    if r_near is None:
+        r_near = 2.05 * grid.h
+    L = 4.0
+    s0 = 0.002 * (4.0 / L) * 4  # (p+1) with p = d+1 = 3
+    segs = [(12.0 - L, L, s0, 3, 0, 1.0), (L, L, s0, 3, 0, -1.0)]
+    return Case("guide_12um", m, (12.1, 1.0, 2.1, 1.0, 1.55), grid, q, r_near, sigma_segments=segs, seed=0)
+
+
+def sigma_points(case: Case, qpts):
+    """Conductivity [S] at the quadrature points (nt, q) for a case."""
+    from oracle import sigma as osig  # the oracle evaluates the profile on its side
+
+    if case.sigma_segments:
+        return osig.monomial(qpts, case.sigma_segments)
+    if case.sigma_scale > 0:
+        return synth.random_sigma_qpoints(case.mesh.nt, case.q, case.mesh.region, case.sigma_scale, case.seed)
+    return np.zeros(qpts.shape[:2])

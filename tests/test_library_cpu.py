@@ -1,0 +1,100 @@
+"""Host-side checks of the CUDA library that need no GPU: it builds, loads,
+exports every symbol the header declares, and its host topology (RWG edge
+table, unknown layout, mesh validation) agrees with the oracle's."""
+
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1004_5076_gb300 as sc
+from oracle import mesh as omesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "scabem.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1004_5076_gb300 import build
+
+    build.build()
+    return sc.lib()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(scabem_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "scabem_apply" in names and "scabem_solve" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", sc.LIBPATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (scabem_[a-z_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_binding_wraps_every_declared_symbol():
+    for n in _declared():
+        assert callable(getattr(sc, n)), n
+
+
+@pytest.mark.parametrize("make", [lambda: synth.icosphere(2), lambda: synth.waveguide(2.0, 0.5, 0.22, 20, 4, 2, 0.5, 0.5)])
+def test_edge_table_and_layout_match_oracle(lib, make):
+    m = make()
+    if m.region.sum() == 0:
+        m.region[m.V[m.T].mean(1)[:, 0] > 0.1] = 1
+    h = sc.scabem_mesh_create(m.V, m.T, m.region)
+    nL, nR, N = sc.scabem_mesh_info(h)
+    ev, et, ec = sc.scabem_mesh_edges(h)
+    g = omesh.build(m.V, m.T, m.region, q=1)
+    assert (nL, nR, N) == (g.nL, g.nR, g.N)
+    assert np.array_equal(ev, g.edge_v) and np.array_equal(et, g.edge_t) and np.array_equal(ec, g.edge_class)
+    sc.scabem_mesh_destroy(h)
+
+
+def test_mesh_validation_errors(lib):
+    m = synth.icosphere(1)
+    # open mesh: drop a triangle
+    with pytest.raises(sc.ScabemError) as e:
+        sc.scabem_mesh_create(m.V, m.T[1:], m.region[1:])
+    assert e.value.code == -2
+    # inconsistent orientation: flip one triangle
+    T = m.T.copy()
+    T[0, 1], T[0, 2] = T[0, 2], T[0, 1]
+    with pytest.raises(sc.ScabemError) as e:
+        sc.scabem_mesh_create(m.V, T, m.region)
+    assert e.value.code == -2
+    # bad region flag
+    r = m.region.copy()
+    r[0] = 2
+    with pytest.raises(sc.ScabemError) as e:
+        sc.scabem_mesh_create(m.V, m.T, r)
+    assert e.value.code == -1
+    # non-finite vertex
+    V = m.V.copy()
+    V[0, 0] = np.nan
+    with pytest.raises(sc.ScabemError) as e:
+        sc.scabem_mesh_create(V, m.T, m.region)
+    assert e.value.code == -7
+
+
+def test_operator_needs_a_gb300(lib):
+    """Without an sm_103 device op creation fails loudly; there is no CPU fallback."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = synth.icosphere(1)
+    h = sc.scabem_mesh_create(m.V, m.T, m.region)
+    with pytest.raises(sc.ScabemError) as e:
+        sc.scabem_op_create(h, (2.25, 1, 1, 1, 1.55), (16, 16, 16), 0.2, (-1.5, -1.5, -1.5), 3, 6, 0.3, 3)
+    assert e.value.code == -3
+    sc.scabem_mesh_destroy(h)
