@@ -14,10 +14,11 @@ Time convention exp(+jwt) (Sec. II).  Units: eta0 = 1, so H here is eta0*H.
   branch Re R >= 0; it radiates a Gaussian beam along +d with waist
   sqrt(2b/k) at r0.
 
-Right-hand side rows (row types as in ``mesh.row_index``).  Interior
-incidence (the paper's case, Eqs. 8-9): [<X,E_inc>, <X,H_inc>,
-<X, n x H_inc>, <sigma X, E_inc>].  Exterior incidence (mirror of Eqs. 6-7,
-used for the sphere): [-<X,E_inc>, -<X,H_inc>, -<X, n x H_inc> + <sigma X, E_inc>, 0].
+Right-hand side rows (row types as in ``mesh.row_index``; Eq. 13 tested as
+in ``operator``).  Interior incidence (the paper's case, Eqs. 8-9):
+[<X,E_inc>, <X,H_inc>, <X,H_inc>, <sigma X, E_inc>].  Exterior incidence
+(mirror of Eqs. 6-7, used for the sphere):
+[-<X,E_inc>, -<X,H_inc>, -<X,H_inc> + <sigma (n x X), E_inc>, 0].
 """
 
 from __future__ import annotations
@@ -86,12 +87,13 @@ def rhs(g: Geometry, media, sigma_pts_S, side: str, kind: str, **kw):
     w = g.qw
     tE = np.einsum("tkqx,tq,tqx->tk", X, w, E)
     tH = np.einsum("tkqx,tq,tqx->tk", X, w, H)
-    tnH = np.einsum("tkqx,tq,tqx->tk", X, w, np.cross(n[:, None, :], H))
+    nX = np.cross(n[:, None, None, :], X)
+    tnsE = np.einsum("tkqx,tq,tqx->tk", nX, w * sig, E)
     tsE = np.einsum("tkqx,tq,tqx->tk", X, w * sig, E)
     if side == "i":
-        val = np.stack([tE, tH, tnH, tsE], axis=-1)
+        val = np.stack([tE, tH, tH, tsE], axis=-1)
     else:
-        val = np.stack([-tE, -tH, -tnH + tsE, np.zeros_like(tE)], axis=-1)
+        val = np.stack([-tE, -tH, -tH + tnsE, np.zeros_like(tE)], axis=-1)
     b = np.zeros(g.N, dtype=np.complex128)
     rows = row_index(g)[g.tri_edge]  # (nt, 3, 4)
     m = rows >= 0

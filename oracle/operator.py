@@ -15,18 +15,22 @@ Definitions followed (paper Sec. II and Appendix A):
 * Rows, tested with the RWG X_n (Eqs. testedLOp/testedKOp, testedSig*):
       Eq. 1 / Eq. 3:  <X_n, E_e - E_i>                      (weak form)
       Eq. 2:          <X_n, H_e - H_i>                      (weak form)
-      Eq. 13:         <X_n, n x (H_e^+ - H_i^-)> - <sigma X_n, E_e^+>
+      Eq. 13:         <X_n, H_e^+ - H_i^-> - <sigma (n x X_n), E_e^+>
       Eq. 14:         <X_n, J_e + J_i> - <sigma X_n, E_i^->
   Readings of the paper (it is silent on these; see the design notes):
-  the operators of Eqs. 15-16 are principal values, and the side limits add
-  n x H^+- = n x H_pv +- J/2 and E_tan^+- = E_tan,pv +- (n x M)/2 (for the
-  exterior set on the + side, the interior set on the - side).  Hence
-  Eq. 13 gains +<X_n, J_e + J_i>/2 and both sigma terms gain
-  -<sigma X_n, n x M>/2 (M = exterior magnetic current).  Eq. 13 is tested
-  with X_n on the rotated quantity n x dH, so the H and E fields there are
-  evaluated in strong form (gradients of the scalar potentials at the points).
-  The weak forms use <X_n, grad phi> = -<div X_n, phi> (RWG is
-  div-conforming, no boundary terms).
+  - The operators of Eqs. 15-16 are principal values; the side limits add
+    H_tan^+- = H_tan,pv +- (J x n)/2 and E_tan^+- = E_tan,pv +- (n x M)/2
+    (exterior set on the + side, interior set on the - side).
+  - Eq. 13 (n x dH = sigma E_tan) is tested the way the paper tests Eq. 2,
+    whose n x H continuity becomes <X_n, H> with the Galerkin operators:
+    rotating both sides gives dH_tan = -sigma n x E, so
+    <X_n, dH> = <sigma (n x X_n), E>.  The H part is then exactly the
+    Eq. 2 row (Appendix A's tested operators); with sigma = 0 the absorber
+    rows reduce exactly to PMCHW.  Side-limit terms: +<X_n, (J_e+J_i) x n>/2
+    and -<sigma X_n, M>/2 in Eq. 13, -<sigma X_n, n x M>/2 in Eq. 14.
+  - The sigma-weighted E is evaluated in strong form (gradient of the scalar
+    potential at the points).  The weak forms use
+    <X_n, grad phi> = -<div X_n, phi> (RWG is div-conforming).
 
 Everything is evaluated at the triangle quadrature points: per target point
 the potentials of every source triangle S follow from three moments
@@ -165,6 +169,10 @@ def test_rows(g: Geometry, tris, fe, fi, Jsum_loc, Mloc, sig):
     def tX_sig(V):
         return np.einsum("tkqx,tq,tqxb->tkb", X, w * sig, V)
 
+    def tnX_sig(V):  # <sigma n x X_k, V>
+        nX = np.cross(n[:, None, None, :], X)
+        return np.einsum("tkqx,tq,tqxb->tkb", nX, w * sig, V)
+
     def tdiv(s):
         return np.einsum("tk,tq,tqb->tkb", divX, w, s)
 
@@ -177,7 +185,7 @@ def test_rows(g: Geometry, tris, fe, fi, Jsum_loc, Mloc, sig):
     val[:, :, 1] = tX(fe["WH"] - fi["WH"]) + tdiv(fe["wH"] - fi["wH"])
     nM = ncross(Mloc)
     val[:, :, 2] = (
-        tX(ncross(fe["H"] - fi["H"])) + 0.5 * tX(Jsum_loc) - tX_sig(fe["E"]) - 0.5 * tX_sig(nM)
+        val[:, :, 1] - 0.5 * tX(ncross(Jsum_loc)) - tnX_sig(fe["E"]) - 0.5 * tX_sig(Mloc)
     )
     val[:, :, 3] = tX(Jsum_loc) - tX_sig(fi["E"]) - 0.5 * tX_sig(nM)
     return val

@@ -100,7 +100,10 @@ def test_apply_complex64_matches_oracle(mk):
 
 
 def test_apply_batched_columns_and_host_buffers():
-    """nrhs > 1 with ld > N, from host (pinned-less numpy) buffers: same as column by column."""
+    """nrhs > 1 with ld > N, from host (pinned-less numpy) buffers: same as column by column.
+
+    The projection accumulates with atomics, so two calls agree to rounding
+    (summation order), not bit for bit."""
     case = cases.sphere_mixed()
     mh, op, g, med, sig = build(case)
     N = g.N
@@ -112,7 +115,8 @@ def test_apply_batched_columns_and_host_buffers():
     sc.scabem_apply(op, X, Y, nrhs=3, ld=ld, prec=sc.SCABEM_C128)
     for c in range(3):
         yc = gpu_apply(op, X[c, :N], sc.SCABEM_C128)
-        assert np.array_equal(Y[c, :N], yc)
+        assert np.linalg.norm(Y[c, :N] - yc) <= 1e-13 * np.linalg.norm(yc)
+        assert np.all(Y[c, N:] == 0)
 
 
 @pytest.mark.parametrize(

@@ -150,13 +150,13 @@ def _sphere_far_error(level, region_R, sigma_S, planted=None, monkeypatch=None):
 def test_mie_sphere_plain_pmchw():
     """Dielectric sphere (r=1 um, eps=2.25, 1.55 um, 320 triangles) vs the Mie series."""
     err, *_ = _sphere_far_error(2, False, 0.0)
-    assert err < 0.05
+    assert err < 0.035
 
 
 def test_mie_sphere_absorber_rows_with_sheet():
     """All-absorber sphere with sigma = 1/eta0 S vs Mie with a conducting sheet (Eq. 4 jump)."""
     err, *_ = _sphere_far_error(2, True, 1.0 / ETA0)
-    assert err < 0.06
+    assert err < 0.04
 
 
 def test_mie_catches_planted_sign_of_sigma(monkeypatch):
@@ -196,6 +196,28 @@ def test_sigma_zero_absorber_rows_give_opposite_currents():
     x = np.linalg.solve(A, b)
     nR = g.nR
     assert np.linalg.norm(x[:nR] + x[nR : 2 * nR]) < 1e-10 * np.linalg.norm(x[:nR])
+
+
+def test_sigma_zero_absorber_rows_equal_plain_pmchw():
+    """With sigma = 0 the absorber formulation (Eqs. 3, 13, 14) is algebraically the
+    plain PMCHW system (Eqs. 1-2): J_e^R = J^L, J_i^R = -J^L, M^R = M^L."""
+    m = synth.icosphere(1, 1.0)
+    med = operator.Media(2.25, 1.0, 1.0, 1.0, 1.55)
+    out = []
+    for reg in (np.zeros(m.nt, int), np.ones(m.nt, int)):
+        g = mesh.build(m.V, m.T, reg, q=6)
+        sig = np.zeros((g.nt, g.q))
+        A = operator.assemble(g, med, sig)
+        b = excitation.rhs(g, med, sig, "e", "planewave", d=[0, 0, 1], e=[1, 0, 0])
+        out.append((g, np.linalg.solve(A, b)))
+    (gL, xL), (gR, xR) = out
+    ne = gL.ne
+    JL, ML = xL[:ne], xL[ne:]
+    JeR, JiR, MR = xR[:ne], xR[ne : 2 * ne], xR[2 * ne :]
+    s = np.linalg.norm(JL)
+    assert np.linalg.norm(JeR - JL) < 1e-10 * s
+    assert np.linalg.norm(JiR + JL) < 1e-10 * s
+    assert np.linalg.norm(MR - ML) < 1e-10 * np.linalg.norm(ML)
 
 
 def test_mie_series_limits():
