@@ -165,17 +165,22 @@ typedef struct {
 int scabem_rhs(scabem_op_t op, const scabem_source* src, int32_t nsrc, void* b, int64_t ld, int32_t prec,
                void* stream);
 
-/* GMRES solve of A x = b (complex128 b and x, device or host).  prec = inner
- * precision: SCABEM_C128 runs restarted GMRES on the FP64 operator; SCABEM_C64
- * runs the inner GMRES on the complex64 operator with FP64 Arnoldi and an
- * outer FP64 iterative refinement r = b - A x (needs both precisions built).
- * No preconditioner.  x holds the initial guess on entry; on return the
- * achieved relative residual |b - A x| / |b| (FP64 operator) is in info. */
+/* GMRES solve of A x = b (complex128 b and x, device or host; Appendix B's
+ * iterative solver).  An outer loop forms the FP64 residual r = b - A x with
+ * the complex128 operator and solves A d = r by restarted GMRES, x += d,
+ * until |r|/|b| <= refine_tol or max_refine rounds.  prec = precision of the
+ * operator inside GMRES: SCABEM_C128, or SCABEM_C64 (complex64 operator with
+ * FP64 Krylov vectors, Arnoldi and least squares; needs both precisions
+ * built).  GMRES is right-preconditioned by the inverse per-edge diagonal
+ * blocks of A (the block-diagonal preconditioner of Appendix B), rebuilt on
+ * every scabem_set_sigma.  x holds the initial guess on entry; info reports
+ * iterations, refinement rounds and the final FP64 relative residual.
+ * Returns SCABEM_E_NOCONV if refine_tol was not reached. */
 typedef struct {
-  double tol;        /* inner relative residual */
+  double tol;        /* relative residual of each inner GMRES solve */
   int32_t restart;   /* Krylov dimension, <= 200 */
   int32_t maxit;     /* total inner iterations */
-  double refine_tol; /* outer relative residual (C64 mode) */
+  double refine_tol; /* outer FP64 relative residual */
   int32_t max_refine;
   int32_t prec;
 } scabem_solve_opts;

@@ -228,9 +228,9 @@ __global__ void k_test(const cx<R>* __restrict__ fpt, const cx<R>* __restrict__ 
       X[c] = cxk * (R)(qp[3 * Qa + c] - g[3 * kk + c]);
       rel[c] = (R)(qp[3 * Qa + c] - g[9 + c]);
     }
-    cx<R> WE[3], WH[3], E[2][3], Hd[3];
+    cx<R> WE[3], WH[3], E[2][3];
     cx<R> wE = czero<R>(), wH = czero<R>();
-    for (int c = 0; c < 3; ++c) WE[c] = WH[c] = Hd[c] = czero<R>();
+    for (int c = 0; c < 3; ++c) WE[c] = WH[c] = czero<R>();
     for (int m = 0; m < 2; ++m) {
       const cx<R>* r = fpt + (Qa * 2 + m) * NREC;
       const R k = kl[m], z = zl[m];
@@ -239,12 +239,11 @@ __global__ void k_test(const cx<R>* __restrict__ fpt, const cx<R>* __restrict__ 
       wE += (sgm * z / k) * mulj(phi);
       wH += (sgm / (k * z)) * mulj(psi);
       for (int c = 0; c < 3; ++c) {
-        const cx<R> A = r[c], gphi = r[4 + c], cA = r[7 + c], F = r[10 + c], gpsi = r[14 + c], cF = r[17 + c];
+        const cx<R> A = r[c], gphi = r[4 + c], cA = r[7 + c], F = r[10 + c], cF = r[17 + c];
         const cx<R> jA = mulj(A), jF = mulj(F);
         WE[c] += sgm * ((-z * k) * jA - cF);
         WH[c] += sgm * (cA - (k / z) * jF);
         E[m][c] = -z * (k * jA + (R(1) / k) * mulj(gphi)) - cF;
-        Hd[c] += sgm * (cA - (R(1) / z) * (k * jF + (R(1) / k) * mulj(gpsi)));
       }
     }
     cx<R> Js[3], M[3];  // J_e + J_i and M of this triangle at the point
@@ -252,18 +251,22 @@ __global__ void k_test(const cx<R>* __restrict__ fpt, const cx<R>* __restrict__ 
       Js[c] = rel[c] * se[0] - se[1 + c] + rel[c] * si[0] - si[1 + c];
       M[c] = rel[c] * sM[0] - sM[1 + c];
     }
-    // n x (H_e - H_i) and n x M
-    cx<R> nH[3], nM[3];
-    nH[0] = nrm[1] * Hd[2] - nrm[2] * Hd[1];
-    nH[1] = nrm[2] * Hd[0] - nrm[0] * Hd[2];
-    nH[2] = nrm[0] * Hd[1] - nrm[1] * Hd[0];
+    // n x (J_e + J_i), n x M and n x X
+    cx<R> nJ[3], nM[3];
+    nJ[0] = nrm[1] * Js[2] - nrm[2] * Js[1];
+    nJ[1] = nrm[2] * Js[0] - nrm[0] * Js[2];
+    nJ[2] = nrm[0] * Js[1] - nrm[1] * Js[0];
     nM[0] = nrm[1] * M[2] - nrm[2] * M[1];
     nM[1] = nrm[2] * M[0] - nrm[0] * M[2];
     nM[2] = nrm[0] * M[1] - nrm[1] * M[0];
+    const R nX[3] = {nrm[1] * X[2] - nrm[2] * X[1], nrm[2] * X[0] - nrm[0] * X[2], nrm[0] * X[1] - nrm[1] * X[0]};
     const cx<R> XJ = dot3(X, Js), XnM = dot3(X, nM);
+    const cx<R> hterm = dot3(X, WH) + divX * wH;
     v0 += w * (dot3(X, WE) + divX * wE);
-    v1 += w * (dot3(X, WH) + divX * wH);
-    v2 += w * (dot3(X, nH) + R(0.5) * XJ - sg * dot3(X, E[0]) - (R(0.5) * sg) * XnM);
+    v1 += w * hterm;
+    // Eq. 13: <X, dH> - <sigma n x X, E_e^+>, side limits (J_e+J_i) x n / 2 and sigma M / 2
+    v2 += w * (hterm - R(0.5) * dot3(X, nJ) - sg * dot3(nX, E[0]) - (R(0.5) * sg) * dot3(X, M));
+    // Eq. 14: <X, J_e + J_i> - <sigma X, E_i^->, side limit n x M / 2
     v3 += w * (XJ - sg * dot3(X, E[1]) - (R(0.5) * sg) * XnM);
   }
   cx<R>* o = val + gid * 4;

@@ -417,6 +417,30 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
       rowsrc[2 * r3 + 1] = (int32_t)(src[1] + 3);
     }
   }
+  std::vector<int32_t> etk(4 * m->ne), ecls(m->ne), eunk(3 * m->ne, -1);
+  for (int64_t e = 0; e < m->ne; ++e) {
+    for (int side = 0; side < 2; ++side) {
+      const int64_t t = m->et[2 * e + side];
+      int kk = 0;
+      while (m->tri_edge[3 * t + kk] != e) ++kk;
+      etk[4 * e + 2 * side] = (int32_t)t;
+      etk[4 * e + 2 * side + 1] = kk;
+    }
+    ecls[e] = m->eclass[e];
+    const int64_t ci = m->ecidx[e];
+    if (m->eclass[e] == 0) {
+      eunk[3 * e] = (int32_t)ci;
+      eunk[3 * e + 1] = (int32_t)(nL + ci);
+    } else {
+      eunk[3 * e] = (int32_t)(2 * nL + ci);
+      eunk[3 * e + 1] = (int32_t)(2 * nL + nR + ci);
+      eunk[3 * e + 2] = (int32_t)(2 * nL + 2 * nR + ci);
+    }
+  }
+  TRY(dalloc(&op->etk, 4 * op->ne));
+  TRY(dalloc(&op->ecls, op->ne));
+  TRY(dalloc(&op->eunk, 3 * op->ne));
+  TRY(dalloc(&op->pinv, 9 * op->ne));
   TRY(dalloc(&op->tri, 16 * op->nt));
   TRY(dalloc(&op->cX, 3 * op->nt));
   TRY(dalloc(&op->unk, 9 * op->nt));
@@ -437,6 +461,9 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   TRY(upload(op->unk, unk.data(), sizeof(int32_t) * unk.size()));
   TRY(upload(op->rowsrc, rowsrc.data(), sizeof(int32_t) * rowsrc.size()));
   TRY(upload(op->region, m->region.data(), sizeof(int32_t) * m->nt));
+  TRY(upload(op->etk, etk.data(), sizeof(int32_t) * etk.size()));
+  TRY(upload(op->ecls, ecls.data(), sizeof(int32_t) * ecls.size()));
+  TRY(upload(op->eunk, eunk.data(), sizeof(int32_t) * eunk.size()));
   TRY(setup_geometry(op, m, s));
   TRY(setup_green(op, s));
   TRY(setup_near(op, s));
@@ -514,6 +541,10 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->nsrc);
   cudaFree(op->gspatial[0]);
   cudaFree(op->gspatial[1]);
+  cudaFree(op->etk);
+  cudaFree(op->ecls);
+  cudaFree(op->eunk);
+  cudaFree(op->pinv);
   cudaFree(op->err);
   free_prec(op->f);
   free_prec(op->d);

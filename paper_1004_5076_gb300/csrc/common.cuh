@@ -155,6 +155,12 @@ struct scabem_op {
   int32_t* noff = nullptr;  // nt + 1
   int32_t* nsrc = nullptr;  // npairs
   cx<double>* gspatial[2] = {nullptr, nullptr};  // padded G tables, set-up only
+  // per-edge block-diagonal preconditioner (exact self blocks, inverted)
+  int32_t* etk = nullptr;   // ne * 4: T+, k+, T-, k-
+  int32_t* ecls = nullptr;  // ne: 0 = plain, 1 = absorber
+  int32_t* eunk = nullptr;  // ne * 3: unknown (= row) indices of the edge, -1 unused
+  cx<double>* pinv = nullptr;  // ne * 9
+  int precond_singular = 0;
   PrecData<float> f;
   PrecData<double> d;
   int* err = nullptr;  // device error flag
@@ -185,6 +191,8 @@ int setup_green(scabem_op* op, cudaStream_t s);
 int setup_near(scabem_op* op, cudaStream_t s);
 int setup_sigma_monomial(scabem_op* op, int nseg, const double* seg, cudaStream_t s);
 int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s);
+int setup_precond(scabem_op* op, cudaStream_t s);
+int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s);
 // apply.cu
 template <typename R>
 int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s);

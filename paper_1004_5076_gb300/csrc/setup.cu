@@ -436,7 +436,264 @@ __global__ void k_sigma_copy(const double* __restrict__ in, int64_t Q, double* _
   if (sf) sf[i] = (float)sig;
 }
 
+// ---------------------------------------------------------------- block-diagonal preconditioner
+using cd = cx<double>;
+
+// Exact moments P0, P1 (about the source centroid), Q, C = Q x (r - c) of
+// source triangle s at point r for wavenumber k, given the static integrals.
+__device__ void exact_moments(const double* r, const double* ts, const double* __restrict__ qp,
+                              const double* __restrict__ qw, int64_t s, int q, bool self, int aself, double k,
+                              double I, const double* Irho, const double* gI, const double* rho, cd* o) {
+  const double cs[3] = {ts[9], ts[10], ts[11]};
+  cd P0s = mk(0.0, 0.0), P1s[3], Qs[3];
+  for (int c = 0; c < 3; ++c) P1s[c] = Qs[c] = mk(0.0, 0.0);
+  for (int b = 0; b < q; ++b) {
+    const int64_t Qb = s * q + b;
+    const double D[3] = {r[0] - qp[3 * Qb], r[1] - qp[3 * Qb + 1], r[2] - qp[3 * Qb + 2]};
+    const double wb = qw[Qb];
+    cd gv, gd;
+    if (self && b == aself) {
+      gv = mk(0.0, -k);
+      gd = mk(0.0, 0.0);
+    } else {
+      const double R = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      const double kr = k * R;
+      double sn, cn, sh, ch;
+      sincos(kr, &sn, &cn);
+      sincos(0.5 * kr, &sh, &ch);
+      gv = mk(-2.0 * sh * sh / R, -sn / R);
+      gd = mk((2.0 * sh * sh - kr * sn) / (R * R * R), (sn - kr * cn) / (R * R * R));
+    }
+    P0s += wb * gv;
+    for (int c = 0; c < 3; ++c) {
+      P1s[c] += (wb * (qp[3 * Qb + c] - cs[c])) * gv;
+      Qs[c] += (wb * D[c]) * gd;
+    }
+  }
+  const double f = 1.0 / (4.0 * M_PI);
+  o[0] = f * (mk(I, 0.0) + P0s);
+  for (int c = 0; c < 3; ++c) {
+    o[1 + c] = f * (mk(Irho[c] + (rho[c] - cs[c]) * I, 0.0) + P1s[c]);
+    o[4 + c] = f * (mk(gI[c], 0.0) + Qs[c]);
+  }
+  const double rc[3] = {r[0] - cs[0], r[1] - cs[1], r[2] - cs[2]};
+  o[7] = rc[2] * o[5] - rc[1] * o[6];
+  o[8] = rc[0] * o[6] - rc[2] * o[4];
+  o[9] = rc[1] * o[4] - rc[0] * o[5];
+}
+
+// Potentials A, phi, grad phi, curl A of the summary (alpha, beta) from moments.
+__device__ void unit_pot(const cd* m, double al, const double* be, cd* U) {
+  for (int c = 0; c < 3; ++c) {
+    U[c] = al * m[1 + c] - be[c] * m[0];
+    U[4 + c] = (2.0 * al) * m[4 + c];
+  }
+  U[3] = (2.0 * al) * m[0];
+  U[7] = al * m[7] - (be[2] * m[5] - be[1] * m[6]);
+  U[8] = al * m[8] - (be[0] * m[6] - be[2] * m[4]);
+  U[9] = al * m[9] - (be[1] * m[4] - be[0] * m[5]);
+}
+
+// Row values (types 0..3) at one point from J- and M-type potentials of both
+// media (same expressions as the operator's testing).
+__device__ void test_point(const cd* Je, const cd* Me, const cd* Ji, const cd* Mi, double ke, double ki, double ze,
+                           double zi, const double* X, const double* nX, double divX, const double* n, double sg,
+                           const double* Js, const double* M, cd* out) {
+  const cd* J[2] = {Je, Ji};
+  const cd* Mm[2] = {Me, Mi};
+  const double kl[2] = {ke, ki}, zl[2] = {ze, zi};
+  cd WE = mk(0.0, 0.0), WH = WE, wE = WE, wH = WE, XE[2] = {WE, WE}, nXE = WE;
+  for (int m = 0; m < 2; ++m) {
+    const double k = kl[m], z = zl[m], sgm = m == 0 ? 1.0 : -1.0;
+    const cd* a = J[m];
+    const cd* f = Mm[m];
+    wE += (sgm * z / k) * mulj(a[3]);
+    wH += (sgm / (k * z)) * mulj(f[3]);
+    for (int c = 0; c < 3; ++c) {
+      const cd we = (-z * k) * mulj(a[c]) - f[7 + c];
+      const cd wh = a[7 + c] - (k / z) * mulj(f[c]);
+      const cd E = -z * (k * mulj(a[c]) + (1.0 / k) * mulj(a[4 + c])) - f[7 + c];
+      WE += (sgm * X[c]) * we;
+      WH += (sgm * X[c]) * wh;
+      XE[m] += X[c] * E;
+      if (m == 0) nXE += nX[c] * E;
+    }
+  }
+  const double nJ[3] = {n[1] * Js[2] - n[2] * Js[1], n[2] * Js[0] - n[0] * Js[2], n[0] * Js[1] - n[1] * Js[0]};
+  const double nM[3] = {n[1] * M[2] - n[2] * M[1], n[2] * M[0] - n[0] * M[2], n[0] * M[1] - n[1] * M[0]};
+  const double XJ = X[0] * Js[0] + X[1] * Js[1] + X[2] * Js[2];
+  const double XnJ = X[0] * nJ[0] + X[1] * nJ[1] + X[2] * nJ[2];
+  const double XM = X[0] * M[0] + X[1] * M[1] + X[2] * M[2];
+  const double XnM = X[0] * nM[0] + X[1] * nM[1] + X[2] * nM[2];
+  const cd h = WH + divX * wH;
+  out[0] = WE + divX * wE;
+  out[1] = h;
+  out[2] = h - sg * nXE + mk(-0.5 * XnJ - 0.5 * sg * XM, 0.0);
+  out[3] = mk(XJ - 0.5 * sg * XnM, 0.0) - sg * XE[1];
+}
+
+// Invert a complex n x n matrix (n <= 3) in place by Gauss-Jordan with
+// partial pivoting; returns false if singular.
+__device__ bool cinv(cd* A, int n) {
+  cd B[9];
+  for (int i = 0; i < 9; ++i) B[i] = mk(0.0, 0.0);
+  for (int i = 0; i < n; ++i) B[i * 3 + i] = mk(1.0, 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    double best = 0.0;
+    for (int r = c; r < n; ++r) {
+      const double m = A[r * 3 + c].re * A[r * 3 + c].re + A[r * 3 + c].im * A[r * 3 + c].im;
+      if (m > best) {
+        best = m;
+        piv = r;
+      }
+    }
+    if (!(best > 0.0)) return false;
+    if (piv != c)
+      for (int j = 0; j < 3; ++j) {
+        cd t = A[c * 3 + j];
+        A[c * 3 + j] = A[piv * 3 + j];
+        A[piv * 3 + j] = t;
+        t = B[c * 3 + j];
+        B[c * 3 + j] = B[piv * 3 + j];
+        B[piv * 3 + j] = t;
+      }
+    const cd p = A[c * 3 + c];
+    const double pd = p.re * p.re + p.im * p.im;
+    const cd ip = mk(p.re / pd, -p.im / pd);
+    for (int j = 0; j < 3; ++j) {
+      A[c * 3 + j] = A[c * 3 + j] * ip;
+      B[c * 3 + j] = B[c * 3 + j] * ip;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const cd fct = A[r * 3 + c];
+      for (int j = 0; j < 3; ++j) {
+        A[r * 3 + j] -= fct * A[c * 3 + j];
+        B[r * 3 + j] -= fct * B[c * 3 + j];
+      }
+    }
+  }
+  for (int i = 0; i < 9; ++i) A[i] = B[i];
+  return true;
+}
+
+// One thread per edge: the edge's own block of the operator (its two
+// triangles as targets and sources, exact panel interactions), inverted.
+// Columns: plain edge (J^L, M^L), absorber edge (J_e^R, J_i^R, M^R); rows:
+// plain (Eq. 1, Eq. 2), absorber (Eq. 3, Eq. 13, Eq. 14).
+__global__ void k_precond(const double* __restrict__ tri, const double* __restrict__ cX, const double* __restrict__ qp,
+                          const double* __restrict__ qw, const double* __restrict__ sig,
+                          const int32_t* __restrict__ etk, const int32_t* __restrict__ ecls, int64_t ne, int q,
+                          double ke, double ki, double ze, double zi, cd* __restrict__ pinv, int* __restrict__ bad) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  // B[col type (Je, Ji, M)][row type 0..3]
+  cd B[3][4];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 4; ++j) B[i][j] = mk(0.0, 0.0);
+  const cd zero10[10] = {};
+  for (int it = 0; it < 2; ++it) {
+    const int64_t t = etk[4 * e + 2 * it];
+    const int kt = etk[4 * e + 2 * it + 1];
+    const double* gt = tri + 16 * t;
+    const double cxt = cX[3 * t + kt];
+    const double* n = gt + 12;
+    for (int is = 0; is < 2; ++is) {
+      const int64_t s = etk[4 * e + 2 * is];
+      const int ks = etk[4 * e + 2 * is + 1];
+      const double* gs = tri + 16 * s;
+      const double al = cX[3 * s + ks];
+      const double be[3] = {al * (gs[3 * ks] - gs[9]), al * (gs[3 * ks + 1] - gs[10]), al * (gs[3 * ks + 2] - gs[11])};
+      const bool self = (s == t);
+      for (int a = 0; a < q; ++a) {
+        const int64_t Qa = t * q + a;
+        const double r[3] = {qp[3 * Qa], qp[3 * Qa + 1], qp[3 * Qa + 2]};
+        double I, Irho[3], gI[3], rho[3];
+        static_tri(r, gs, gs + 12, self, I, Irho, gI, rho);
+        cd me[10], mi[10], Ue[10], Ui[10], nUi[10];
+        exact_moments(r, gs, qp, qw, s, q, self, a, ke, I, Irho, gI, rho, me);
+        exact_moments(r, gs, qp, qw, s, q, self, a, ki, I, Irho, gI, rho, mi);
+        unit_pot(me, al, be, Ue);
+        unit_pot(mi, al, be, Ui);
+        for (int c = 0; c < 10; ++c) nUi[c] = -Ui[c];
+        double X[3], nX[3], Xe[3] = {0, 0, 0};
+        for (int c = 0; c < 3; ++c) X[c] = cxt * (r[c] - gt[3 * kt + c]);
+        nX[0] = n[1] * X[2] - n[2] * X[1];
+        nX[1] = n[2] * X[0] - n[0] * X[2];
+        nX[2] = n[0] * X[1] - n[1] * X[0];
+        if (self)
+          for (int c = 0; c < 3; ++c) Xe[c] = al * (r[c] - gs[3 * ks + c]);  // the basis itself at the point
+        const double zero3[3] = {0, 0, 0};
+        const double w = qw[Qa], sg = sig[Qa];
+        cd o[4];
+        test_point(Ue, zero10, zero10, zero10, ke, ki, ze, zi, X, nX, 2.0 * cxt, n, sg, Xe, zero3, o);
+        for (int j = 0; j < 4; ++j) B[0][j] += w * o[j];
+        test_point(zero10, zero10, Ui, zero10, ke, ki, ze, zi, X, nX, 2.0 * cxt, n, sg, Xe, zero3, o);
+        for (int j = 0; j < 4; ++j) B[1][j] += w * o[j];
+        test_point(zero10, Ue, zero10, nUi, ke, ki, ze, zi, X, nX, 2.0 * cxt, n, sg, zero3, Xe, o);
+        for (int j = 0; j < 4; ++j) B[2][j] += w * o[j];
+      }
+    }
+  }
+  cd A[9];
+  for (int i = 0; i < 9; ++i) A[i] = mk(0.0, 0.0);
+  int nb;
+  if (ecls[e] == 0) {  // rows (0, 1), cols (J = Je - Ji, M)
+    nb = 2;
+    for (int r = 0; r < 2; ++r) {
+      A[r * 3 + 0] = B[0][r] - B[1][r];
+      A[r * 3 + 1] = B[2][r];
+    }
+  } else {  // rows (0, 2, 3), cols (Je, Ji, M)
+    nb = 3;
+    const int rt[3] = {0, 2, 3};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) A[r * 3 + c] = B[c][rt[r]];
+  }
+  if (!cinv(A, nb)) {
+    atomicAdd(bad, 1);
+    for (int i = 0; i < 9; ++i) A[i] = mk(0.0, 0.0);
+    for (int i = 0; i < nb; ++i) A[i * 3 + i] = mk(1.0, 0.0);
+  }
+  for (int i = 0; i < 9; ++i) pinv[9 * e + i] = A[i];
+}
+
+// out[unknowns of e] = Binv_e * in[rows of e] (rows and unknowns of an edge
+// share the same index set).
+__global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __restrict__ eunk, int64_t ne,
+                                const cd* __restrict__ in, cd* __restrict__ out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int nb = eunk[3 * e + 2] < 0 ? 2 : 3;
+  cd v[3];
+  for (int i = 0; i < nb; ++i) v[i] = in[eunk[3 * e + i]];
+  for (int i = 0; i < nb; ++i) {
+    cd acc = mk(0.0, 0.0);
+    for (int j = 0; j < nb; ++j) acc += pinv[9 * e + 3 * i + j] * v[j];
+    out[eunk[3 * e + i]] = acc;
+  }
+}
+
 }  // namespace
+
+int setup_precond(scabem_op* op, cudaStream_t s) {
+  CK(cudaMemsetAsync(op->err, 0, sizeof(int), s));
+  k_precond<<<(int)cdiv(op->ne, 64), 64, 0, s>>>(op->tri, op->cX, op->qp, op->qw, op->sig64, op->etk, op->ecls,
+                                                  op->ne, op->q, op->ke, op->ki, op->ze, op->zi, op->pinv, op->err);
+  CK(cudaGetLastError());
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, op->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  op->precond_singular = bad;
+  return SCABEM_OK;
+}
+
+int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s) {
+  k_precond_apply<<<(int)cdiv(op->ne, 256), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
 
 int setup_geometry(scabem_op* op, const scabem_mesh* m, cudaStream_t s) {
   int rc = load_rule(op->q);
@@ -570,7 +827,7 @@ int setup_sigma_monomial(scabem_op* op, int nseg, const double* seg, cudaStream_
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   if (dseg) cudaFree(dseg);
-  return SCABEM_OK;
+  return setup_precond(op, s);  // the absorber blocks depend on sigma
 }
 
 int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s) {
@@ -581,5 +838,5 @@ int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s) 
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   cudaFree(tmp);
-  return SCABEM_OK;
+  return setup_precond(op, s);
 }

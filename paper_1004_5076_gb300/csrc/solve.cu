@@ -1,14 +1,17 @@
 // Right-hand side, GMRES with FP64 Arnoldi and iterative refinement, fields
 // at interior points and the reflection fit.
 //
-// * rhs: tested incident field b (Appendix A): per absorber/plain row type,
-//   <X, E_inc>, <X, H_inc>, <X, n x H_inc>, <sigma X, E_inc> for an interior
-//   source (Eqs. 8-9), and the mirrored combination for an exterior source.
+// * rhs: tested incident field b (Appendix A): per row type <X, E_inc>,
+//   <X, H_inc>, <X, H_inc> (Eq. 13), <sigma X, E_inc> (Eq. 14) for an
+//   interior source (Eqs. 8-9); the mirrored combination, with
+//   <sigma n x X, E_inc> in Eq. 13, for an exterior source.
 // * solve: restarted GMRES (the paper's iterative solver, Appendix B) with
 //   classical Gram-Schmidt applied twice in FP64 on the device; Hessenberg
-//   least squares by Givens rotations.  In complex64 mode the Krylov vectors
-//   stay FP64 and only the operator runs in complex64; an outer FP64 residual
-//   r = b - A x drives iterative refinement.
+//   least squares by Givens rotations; right-preconditioned by the inverse
+//   per-edge diagonal blocks (the block-diagonal preconditioner of
+//   Appendix B).  In complex64 mode the Krylov vectors stay FP64 and only
+//   the operator runs in complex64.  An outer FP64 residual r = b - A x
+//   drives iterative refinement in both modes.
 // * fields / reflection: total interior field E_inc + E_i(J_i, M_i) (Eq. 8) at
 //   probe points by the triangle quadrature, and a least-squares split of the
 //   on-axis field into forward and backward waves (Table 1's reflection).
@@ -92,7 +95,7 @@ __global__ void k_rhs(scabem_source S, const double* __restrict__ tri, const dou
   const int kk = (int)(gid - t * 3);
   const double* g = tri + 16 * t;
   const double cxk = cX[gid];
-  cd tE = mk(0.0, 0.0), tH = tE, tnH = tE, tsE = tE;
+  cd tE = mk(0.0, 0.0), tH = tE, tnsE = tE, tsE = tE;
   for (int a = 0; a < q; ++a) {
     const int64_t Qa = t * q + a;
     const double r[3] = {qp[3 * Qa], qp[3 * Qa + 1], qp[3 * Qa + 2]};
@@ -101,24 +104,25 @@ __global__ void k_rhs(scabem_source S, const double* __restrict__ tri, const dou
     double X[3];
     for (int c = 0; c < 3; ++c) X[c] = cxk * (r[c] - g[3 * kk + c]);
     const double* n = g + 12;
-    const cd nH[3] = {n[1] * H[2] - n[2] * H[1], n[2] * H[0] - n[0] * H[2], n[0] * H[1] - n[1] * H[0]};
+    const double nX[3] = {n[1] * X[2] - n[2] * X[1], n[2] * X[0] - n[0] * X[2], n[0] * X[1] - n[1] * X[0]};
     const double w = qw[Qa];
     const cd xe = X[0] * E[0] + X[1] * E[1] + X[2] * E[2];
     tE += w * xe;
     tH += w * (X[0] * H[0] + X[1] * H[1] + X[2] * H[2]);
-    tnH += w * (X[0] * nH[0] + X[1] * nH[1] + X[2] * nH[2]);
+    tnsE += (w * sig[Qa]) * (nX[0] * E[0] + nX[1] * E[1] + nX[2] * E[2]);
     tsE += (w * sig[Qa]) * xe;
   }
+  // rows: <X,E>, <X,H>, Eq. 13 (<X,H> and <sigma n x X, E>), Eq. 14
   cd* o = val + gid * 4;
   if (S.side == 0) {
     o[0] = tE;
     o[1] = tH;
-    o[2] = tnH;
+    o[2] = tH;
     o[3] = tsE;
   } else {
     o[0] = -tE;
     o[1] = -tH;
-    o[2] = tsE - tnH;
+    o[2] = tnsE - tH;
     o[3] = mk(0.0, 0.0);
   }
 }
@@ -225,9 +229,13 @@ struct Work {
   cd* t = nullptr;     // N
   cd* part = nullptr;  // DOT_BLOCKS x (m+1)
   cd* h = nullptr;     // m+1
+  cd* z = nullptr;     // N, preconditioned Krylov vector
+  cd* u = nullptr;     // N, solution in the preconditioned variables
   cx<float>* xf = nullptr;
   cx<float>* yf = nullptr;
   ~Work() {
+    cudaFree(z);
+    cudaFree(u);
     cudaFree(V);
     cudaFree(w);
     cudaFree(t);
@@ -276,6 +284,7 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
           int& iters, double& relres_est) {
   const int64_t N = op->N;
   CK(cudaMemsetAsync(d, 0, sizeof(cd) * N, s));
+  CK(cudaMemsetAsync(W.u, 0, sizeof(cd) * N, s));
   double rn0;
   int rc = norm2(r, N, W, s, rn0);
   if (rc) return rc;
@@ -298,7 +307,10 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
     bool done = false;
     for (; j < m && iters < maxit; ++j) {
       ++iters;
-      rc = op_apply64(op, W.V + (int64_t)j * N, W.w, prec, W, s);
+      // right preconditioning: w = A P^-1 v_j
+      rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s);
+      if (rc) return rc;
+      rc = op_apply64(op, W.z, W.w, prec, W, s);
       if (rc) return rc;
       rc = dots(W.V, N, j + 1, W.w, N, W, s, hv);
       if (rc) return rc;
@@ -358,9 +370,11 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
     for (auto& z : y) z = -z;
     if (j > 0) {
       CK(cudaMemcpyAsync(W.h, y.data(), sizeof(cd) * j, cudaMemcpyHostToDevice, s));
-      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j, W.h, d, N);
+      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j, W.h, W.u, N);
       CK(cudaGetLastError());
     }
+    rc = precond_apply(op, W.u, d, s);  // d = P^-1 u
+    if (rc) return rc;
     if (done || iters >= maxit) break;
     // true residual for the restart
     rc = op_apply64(op, d, W.w, prec, W, s);
@@ -552,6 +566,8 @@ int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, co
   CK(cudaMalloc(&W.V, sizeof(cd) * N * (m + 1)));
   CK(cudaMalloc(&W.w, sizeof(cd) * N));
   CK(cudaMalloc(&W.t, sizeof(cd) * N));
+  CK(cudaMalloc(&W.z, sizeof(cd) * N));
+  CK(cudaMalloc(&W.u, sizeof(cd) * N));
   CK(cudaMalloc(&W.part, sizeof(cd) * DOT_BLOCKS * (m + 1)));
   CK(cudaMalloc(&W.h, sizeof(cd) * (m + 1)));
   if (prec == SCABEM_C64) {
@@ -571,8 +587,8 @@ int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, co
     if (rc) return rc;
     int iters = 0, refs = 0;
     double relres = 0.0;
-    const int outer = prec == SCABEM_C64 ? o->max_refine : 1;
-    const double tol_out = prec == SCABEM_C64 ? o->refine_tol : o->tol;
+    const int outer = o->max_refine > 0 ? o->max_refine : 1;
+    const double tol_out = o->refine_tol > 0 ? o->refine_tol : o->tol;
     int st = SCABEM_E_NOCONV;
     for (int it = 0; it <= outer; ++it) {
       rc = apply_one<double>(op, x, W.w, s);
@@ -597,7 +613,7 @@ int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, co
       if (rc) return rc;
       k_add<<<DOT_BLOCKS, 256, 0, s>>>(x, d, N);
       CK(cudaGetLastError());
-      if (prec == SCABEM_C64) ++refs;
+      ++refs;
     }
     if (info) {
       info[col].iters = iters;
