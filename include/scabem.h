@@ -165,6 +165,29 @@ typedef struct {
 int scabem_rhs(scabem_op_t op, const scabem_source* src, int32_t nsrc, void* b, int64_t ld, int32_t prec,
                void* stream);
 
+/* The same tested right-hand side as scabem_rhs, for callers that cannot
+ * allocate device memory while they run (code inside another framework's
+ * memory pool that has already reserved the device, real-time loops that
+ * cannot take the device-wide synchronisation of a cudaFree, services that
+ * must not hit out-of-memory mid-run).  The paper has no counterpart: this is
+ * an interface variant, not part of the method.
+ *   - b must be device memory (complex64 or complex128 per prec, ld >= N).
+ *   - The per-call scratch (12 complex128 values per triangle) lives in one
+ *     fixed device array of 32768 triangles (6 MiB), held by every GPU that
+ *     loads the library until the process exits; meshes with more triangles
+ *     are rejected with SCABEM_E_ARG.  No cudaMalloc, cudaFree or allocating
+ *     library routine is called.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) once, with that device current; make that first
+ *     call before any stream capture.
+ *   - Every call shares the array: two calls whose work overlaps on the GPU
+ *     (different streams, or different operators at once) race on it.  Each
+ *     call writes every scratch entry it later reads, so the previous call's
+ *     contents never leak into a result.
+ *   - Work is enqueued on `stream`; the call does not synchronise. */
+int scabem_rhs_noalloc(scabem_op_t op, const scabem_source* src, int32_t nsrc, void* b, int64_t ld, int32_t prec,
+                       void* stream);
+
 /* GMRES solve of A x = b (complex128 b and x, device or host; Appendix B's
  * iterative solver).  An outer loop forms the FP64 residual r = b - A x with
  * the complex128 operator and solves A d = r by restarted GMRES, x += d,

@@ -74,7 +74,8 @@ class Probe(C.Structure):
 EXPORTS = [
     "scabem_mesh_create", "scabem_mesh_info", "scabem_mesh_edges", "scabem_mesh_destroy", "scabem_op_create",
     "scabem_op_info", "scabem_op_destroy", "scabem_set_sigma", "scabem_apply", "scabem_rhs", "scabem_solve",
-    "scabem_fields", "scabem_reflection", "scabem_last_error",
+    "scabem_fields", "scabem_reflection", "scabem_last_error", "scabem_rhs_noalloc", "scabem_profile",
+    "scabem_profile_read",
 ]
 
 
@@ -102,6 +103,7 @@ def lib():
     L.scabem_solve.argtypes = [vp, vp, vp, i32, i64, C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo)]
     L.scabem_fields.argtypes = [vp, vp, i32, i64, vp, i32, C.POINTER(Source), vp, vp]
     L.scabem_reflection.argtypes = [vp, vp, i32, i64, C.POINTER(Probe), C.POINTER(Source), vp, vp]
+    L.scabem_rhs_noalloc.argtypes = [vp, C.POINTER(Source), i32, vp, i64, i32, vp]
     L.scabem_profile.argtypes = [vp, i32, i32]
     L.scabem_profile_read.argtypes = [vp, vp, C.POINTER(i64)]
     L.scabem_last_error.argtypes = []
@@ -221,6 +223,19 @@ def scabem_rhs(op, sources, b, ld=None, prec=SCABEM_C128, stream=None):
     if ld is None:
         ld = b.shape[0]
     _check(lib().scabem_rhs(op, arr, len(sources), _ptr(b), ld, prec, _stream(stream)))
+
+
+def scabem_rhs_noalloc(op, sources, b, ld=None, prec=SCABEM_C128, stream=None):
+    """scabem_rhs without any device allocation (b must be a device buffer).
+
+    For callers that cannot allocate device memory while they run; the
+    library keeps the scratch in one fixed device array (meshes of at most
+    32768 triangles), shared by all calls, so calls must not overlap on the GPU.
+    """
+    arr = (Source * len(sources))(*sources)
+    if ld is None:
+        ld = b.shape[0]
+    _check(lib().scabem_rhs_noalloc(op, arr, len(sources), _ptr(b), ld, prec, _stream(stream)))
 
 
 def scabem_solve(op, b, x, nrhs=1, ld=None, tol=1e-6, restart=60, maxit=2000, refine_tol=1e-8, max_refine=10,

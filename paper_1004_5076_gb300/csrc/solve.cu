@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -693,5 +695,94 @@ int reflection_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const sc
   cudaFree(dE);
   cudaFree(dc);
   cudaFree(dout);
+  return SCABEM_OK;
+}
+
+// ---------------------------------------------------------------- right-hand side without allocation
+// Some callers cannot allocate device memory while they run: code that lives
+// inside another framework's memory pool (which has already reserved the
+// device), real-time loops that cannot afford the device-wide
+// synchronisation a cudaFree implies, and services that must not meet an
+// out-of-memory error halfway through a run.  scabem_rhs allocates its
+// per-call row-value scratch; scabem_rhs_noalloc runs the same two kernels
+// with that scratch in the fixed device array below instead.
+constexpr int64_t NOALLOC_MAX_TRIANGLES = 32768;
+// nt * 3 local edges * 4 row types complex128 values: 6 MiB, held by every
+// GPU that loads this library until the process exits.
+static __device__ __align__(256) cd g_rhs_scratch[NOALLOC_MAX_TRIANGLES * 12];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 256;
+std::mutex g_noalloc_mu;
+cd* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the array's name is only a host-side stand-in in host code).
+int noalloc_scratch(int dev, cd** out) {
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    set_error("scabem_rhs_noalloc: device ordinal out of range");
+    return SCABEM_E_DEVICE;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_rhs_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_rhs_scratch)");
+    g_noalloc_ptr[dev] = static_cast<cd*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SCABEM_OK;
+}
+}  // namespace
+
+extern "C" int scabem_rhs_noalloc(scabem_op_t op, const scabem_source* src, int32_t nsrc, void* b, int64_t ld,
+                                  int32_t prec, void* stream) {
+  if (!op || !src || !b || nsrc < 0 || ld < op->N || (prec != SCABEM_C64 && prec != SCABEM_C128)) {
+    set_error("scabem_rhs_noalloc: bad argument");
+    return SCABEM_E_ARG;
+  }
+  if (op->nt > NOALLOC_MAX_TRIANGLES) {
+    set_error("scabem_rhs_noalloc: mesh has " + std::to_string(op->nt) + " triangles; the fixed scratch holds at most " +
+              std::to_string(NOALLOC_MAX_TRIANGLES) + " (use scabem_rhs)");
+    return SCABEM_E_ARG;
+  }
+  for (int i = 0; i < nsrc; ++i)
+    if (src[i].kind < 0 || src[i].kind > 2 || src[i].side < 0 || src[i].side > 1) {
+      set_error("scabem_rhs_noalloc: source kind must be 0..2 and side 0..1");
+      return SCABEM_E_ARG;
+    }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev != op->device) {
+    set_error("scabem_rhs_noalloc: the operator's device is not the current device");
+    return SCABEM_E_ARG;
+  }
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, b) != cudaSuccess ||
+      (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+    cudaGetLastError();
+    set_error("scabem_rhs_noalloc: b must be device memory (host buffers would need staging)");
+    return SCABEM_E_ARG;
+  }
+  cd* val = nullptr;
+  int rc = noalloc_scratch(dev, &val);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < nsrc; ++i) {
+    const scabem_source S = src[i];
+    const double k = S.side == 0 ? op->ki : op->ke;
+    const double z = S.side == 0 ? op->zi : op->ze;
+    // k_rhs writes all nt*12 entries that k_rows_out reads, so the previous
+    // call's contents never leak into this one.
+    k_rhs<<<(int)cdiv(op->nt * 3, 128), 128, 0, s>>>(S, op->tri, op->cX, op->qp, op->qw, op->sig64, op->nt, op->q, k,
+                                                     z, val);
+    CK(cudaGetLastError());
+    if (prec == SCABEM_C128)
+      k_rows_out<double><<<(int)cdiv(op->N, 256), 256, 0, s>>>(val, op->rowsrc, op->N, (cd*)b + (int64_t)i * ld);
+    else
+      k_rows_out<float><<<(int)cdiv(op->N, 256), 256, 0, s>>>(val, op->rowsrc, op->N,
+                                                              (cx<float>*)b + (int64_t)i * ld);
+    CK(cudaGetLastError());
+  }
   return SCABEM_OK;
 }
