@@ -71,8 +71,8 @@ typedef struct {
 
 /* Grid and discretisation options.
  *   n[3]      physical grid points per axis (x, y, z); the FFT size is 2n.
- *             Each 2n must be a power of two in [8, 1024], and
- *             (2 n_y) * (2 n_z) <= 4096.
+ *             Each 2n must be a power of two, in [8, 1024] along x and in
+ *             [8, 128] along y and z, with (2 n_y) * (2 n_z) <= 4096.
  *   h         grid spacing [um]; origin[3] coordinates of grid point 0.
  *   p         stencil points per axis (2, 3 or 4), Lagrange interpolation;
  *             every stencil must fall inside the physical grid.

@@ -151,47 +151,78 @@ __global__ void k_interp(const cx<R>* __restrict__ grids, const int32_t* __restr
   }
 }
 
-// K7: one thread per (target point, medium, source kind J/M).
+// K7: one thread per (target point, medium).  Each near record (10 complex:
+// dP0, dP1, dQ, dC) is loaded once and applied to the J and the M source of
+// the pair; two pairs are kept in flight.
 template <typename R>
-__global__ void k_near(const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
-                       const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, int64_t Q, int q,
-                       cx<R>* __restrict__ fpt) {
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= Q * 4) return;
-  const int64_t Qa = gid >> 2;
-  const int med = (int)((gid >> 1) & 1);
-  const int hk = (int)(gid & 1);
-  const int64_t t = Qa / q;
-  const int a = (int)(Qa - t * q);
-  const int set = hk == 0 ? med : 2;
-  const R sgn = (hk == 1 && med == 1) ? R(-1) : R(1);
-  cx<R> acc[NCORR];
-  for (int c = 0; c < NCORR; ++c) acc[c] = czero<R>();
-  const int j0 = noff[t], j1 = noff[t + 1];
-  for (int j = j0; j < j1; ++j) {
-    const int64_t s = nsrc[j];
-    const cx<R>* d = corr + (((int64_t)j * q + a) * 2 + med) * NCORR;
-    const cx<R>* sm = summ + (3 * s + set) * 4;
-    const cx<R> al = sgn * sm[0];
-    const cx<R> be[3] = {sgn * sm[1], sgn * sm[2], sgn * sm[3]};
-    const cx<R> d0 = d[0];
-    const cx<R> d1[3] = {d[1], d[2], d[3]};
-    const cx<R> dq[3] = {d[4], d[5], d[6]};
-    const cx<R> dc[3] = {d[7], d[8], d[9]};
+__device__ __forceinline__ void near_accumulate(const cx<R>* d, const cx<R>* sj, const cx<R>* sm, R sgnm,
+                                                cx<R>* accJ, cx<R>* accM) {
+  const cx<R> d0 = d[0];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const cx<R>* sv = h == 0 ? sj : sm;
+    const R sg = h == 0 ? R(1) : sgnm;
+    cx<R>* acc = h == 0 ? accJ : accM;
+    const cx<R> al = sg * sv[0];
+    const cx<R> be0 = sg * sv[1], be1 = sg * sv[2], be2 = sg * sv[3];
+    const cx<R> be[3] = {be0, be1, be2};
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
-      cfma(acc[c], al, d1[c]);
+      cfma(acc[c], al, d[1 + c]);
       acc[c] -= be[c] * d0;
-      cfma(acc[4 + c], R(2) * al, dq[c]);
-      cfma(acc[7 + c], al, dc[c]);
+      cfma(acc[4 + c], R(2) * al, d[4 + c]);
+      cfma(acc[7 + c], al, d[7 + c]);
     }
     cfma(acc[3], R(2) * al, d0);
-    // - dQ x beta
-    acc[7] -= dq[1] * be[2] - dq[2] * be[1];
-    acc[8] -= dq[2] * be[0] - dq[0] * be[2];
-    acc[9] -= dq[0] * be[1] - dq[1] * be[0];
+    acc[7] -= d[5] * be2 - d[6] * be1;  // - dQ x beta
+    acc[8] -= d[6] * be0 - d[4] * be2;
+    acc[9] -= d[4] * be1 - d[5] * be0;
   }
-  cx<R>* o = fpt + (Qa * 2 + med) * NREC + 10 * hk;
-  for (int c = 0; c < NCORR; ++c) o[c] += acc[c];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_near(const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
+                                              const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ,
+                                              int64_t Q, int q, cx<R>* __restrict__ fpt) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= Q * 2) return;
+  const int64_t Qa = gid >> 1;
+  const int med = (int)(gid & 1);
+  const int64_t t = Qa / q;
+  const int a = (int)(Qa - t * q);
+  const R sgnm = med == 1 ? R(-1) : R(1);  // interior M = -M
+  cx<R> accJ[NCORR], accM[NCORR];
+  for (int c = 0; c < NCORR; ++c) accJ[c] = accM[c] = czero<R>();
+  const int j0 = noff[t], j1 = noff[t + 1];
+  const int64_t rec = (int64_t)q * 2 * NCORR;  // complex per pair
+  const cx<R>* base = corr + ((int64_t)a * 2 + med) * NCORR;
+  int j = j0;
+  for (; j + 1 < j1; j += 2) {
+    cx<R> dA[NCORR], dB[NCORR];
+    const int64_t sA = nsrc[j], sB = nsrc[j + 1];
+    const cx<R>* pA = base + (int64_t)j * rec;
+    const cx<R>* pB = pA + rec;
+#pragma unroll
+    for (int c = 0; c < NCORR; ++c) {
+      dA[c] = pA[c];
+      dB[c] = pB[c];
+    }
+    near_accumulate(dA, summ + (3 * sA + med) * 4, summ + (3 * sA + 2) * 4, sgnm, accJ, accM);
+    near_accumulate(dB, summ + (3 * sB + med) * 4, summ + (3 * sB + 2) * 4, sgnm, accJ, accM);
+  }
+  if (j < j1) {
+    cx<R> dA[NCORR];
+    const int64_t sA = nsrc[j];
+    const cx<R>* pA = base + (int64_t)j * rec;
+#pragma unroll
+    for (int c = 0; c < NCORR; ++c) dA[c] = pA[c];
+    near_accumulate(dA, summ + (3 * sA + med) * 4, summ + (3 * sA + 2) * 4, sgnm, accJ, accM);
+  }
+  cx<R>* o = fpt + gid * NREC;
+  for (int c = 0; c < NCORR; ++c) {
+    o[c] += accJ[c];
+    o[10 + c] += accM[c];
+  }
 }
 
 template <typename R>
@@ -320,7 +351,7 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   CK(cudaGetLastError());
   prof_mark(op, s);
   if (op->npairs > 0) {
-    k_near<R><<<(int)cdiv(Q * 4, 128), 128, 0, s>>>(pd.near, op->noff, op->nsrc, pd.summ, Q, op->q, pd.fpt);
+    k_near<R><<<(int)cdiv(Q * 2, 128), 128, 0, s>>>(pd.near, op->noff, op->nsrc, pd.summ, Q, op->q, pd.fpt);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);

@@ -331,11 +331,10 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
       set_error("media parameters and wavelength must be finite and positive");
       return SCABEM_E_ARG;
     }
-  for (int a = 0; a < 3; ++a)
-    if (!pow2_in(2 * o->n[a], 8, 1024)) {
-      set_error("grid: 2*n[axis] must be a power of two in [8, 1024]");
-      return SCABEM_E_ARG;
-    }
+  if (!pow2_in(2 * o->n[0], 8, 1024) || !pow2_in(2 * o->n[1], 8, 128) || !pow2_in(2 * o->n[2], 8, 128)) {
+    set_error("grid: 2*n must be a power of two, in [8, 1024] along x and in [8, 128] along y and z");
+    return SCABEM_E_ARG;
+  }
   if (4 * o->n[1] * o->n[2] > 4096) {
     set_error("grid: (2 n_y)(2 n_z) must not exceed 4096");
     return SCABEM_E_ARG;

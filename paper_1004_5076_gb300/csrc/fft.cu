@@ -10,25 +10,23 @@
 //            physical n1 x n2 corner), multiply by the Green spectrum of the
 //            medium, inverse 2-D FFT, keep the physical corner: 12 -> 16 fields;
 //   stage C: inverse FFT along axis 0, keep i0 < n0.
-// Every FFT is a shared-memory Stockham transform (radix 8, then 4 or 2), one
-// CTA owning whole lines, so each field makes one HBM round trip per stage.
-// The 1/(P0 P1 P2) scale is folded into the stored spectra.
+// Every FFT is an in-place shared-memory Stockham transform (radix 8, then 4
+// or 2) with compile-time power-of-two lengths: each pass loads its
+// butterflies into registers, synchronises, and stores them at their sorted
+// positions.  One CTA owns whole lines, so each field makes one HBM round trip
+// per stage.  The 1/(P0 P1 P2) scale is folded into the stored spectra.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 
 namespace {
 
+constexpr int FFT_THREADS = 512;
+constexpr int FFT_LTHREADS = 9;
+
 template <typename R, int DIR>
 __device__ __forceinline__ cx<R> rot(cx<R> a) {  // multiply by DIR * j
   return DIR < 0 ? mk(a.im, -a.re) : mk(-a.im, a.re);
-}
-
-template <typename R, int DIR>
-__device__ __forceinline__ void dft2(cx<R>& a, cx<R>& b) {
-  cx<R> t = a;
-  a = t + b;
-  b = t - b;
 }
 
 template <typename R, int DIR>
@@ -43,7 +41,9 @@ __device__ __forceinline__ void dft4(cx<R>& a0, cx<R>& a1, cx<R>& a2, cx<R>& a3)
 template <typename R, int RAD, int DIR>
 __device__ __forceinline__ void dft(cx<R>* v) {
   if constexpr (RAD == 2) {
-    dft2<R, DIR>(v[0], v[1]);
+    const cx<R> t = v[0];
+    v[0] = t + v[1];
+    v[1] = t - v[1];
   } else if constexpr (RAD == 4) {
     dft4<R, DIR>(v[0], v[1], v[2], v[3]);
   } else {
@@ -54,9 +54,9 @@ __device__ __forceinline__ void dft(cx<R>* v) {
     dft4<R, DIR>(o0, o1, o2, o3);
     const R s = R(0.70710678118654752440);
     // w8^1 = (1 + DIR j)/sqrt2, w8^2 = DIR j, w8^3 = (-1 + DIR j)/sqrt2
-    cx<R> w1 = s * (o1 + rot<R, DIR>(o1));
-    cx<R> w2 = rot<R, DIR>(o2);
-    cx<R> w3 = s * (rot<R, DIR>(o3) - o3);
+    const cx<R> w1 = s * (o1 + rot<R, DIR>(o1));
+    const cx<R> w2 = rot<R, DIR>(o2);
+    const cx<R> w3 = s * (rot<R, DIR>(o3) - o3);
     v[0] = e0 + o0;
     v[4] = e0 - o0;
     v[1] = e1 + w1;
@@ -68,97 +68,198 @@ __device__ __forceinline__ void dft(cx<R>* v) {
   }
 }
 
-// One out-of-place Stockham pass over `nlines` lines of length `len`.
-// Element j of line l lives at buf[l*ls + j*es].  Ns = product of the radices
-// of the previous passes.  JFAST maps consecutive threads to consecutive j
-// (for contiguous lines); otherwise to consecutive lines.
-template <typename R, int RAD, int DIR, bool JFAST>
-__device__ __forceinline__ void pass(const cx<R>* __restrict__ src, cx<R>* __restrict__ dst, int len, int Ns,
-                                     int nlines, int ls, int es, const cx<R>* __restrict__ tw) {
-  const int per = len / RAD;
-  const int nb = nlines * per;
-  const int ts = len / (Ns * RAD);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    int line, j;
-    if (JFAST) {
-      j = b % per;
-      line = b / per;
-    } else {
-      line = b % nlines;
-      j = b / nlines;
-    }
-    const cx<R>* s = src + (int64_t)line * ls;
-    cx<R>* d = dst + (int64_t)line * ls;
-    const int k = j % Ns;
-    cx<R> v[RAD];
+// One in-place Stockham pass of radix 2^LR over the 2^lnl lines of length
+// N = 2^LN; element j of line l lives at buf[l*ls + j*es].  2^LNS is the
+// product of the radices of the previous passes.  Consecutive threads take
+// consecutive lines.  TOTL = log2 of the largest element count a caller
+// passes, which bounds the butterflies each thread holds.
+template <typename R, int LN, int LR, int LNS, int DIR, int TOTL>
+__device__ __forceinline__ void pass_ip(cx<R>* buf, int lnl, int ls, int es, const cx<R>* tw) {
+  constexpr int RAD = 1 << LR;
+  constexpr int LPER = LN - LR;
+  constexpr int NSM = (1 << LNS) - 1;
+  constexpr int LTS = LN - LNS - LR;
+  constexpr int MB0 = TOTL - LR - FFT_LTHREADS;
+  constexpr int MAXB = MB0 > 0 ? (1 << MB0) : 1;
+  const int nb = 1 << (lnl + LPER);
+  const int lmask = (1 << lnl) - 1;
+  cx<R> v[MAXB][RAD];
+  int dst[MAXB];
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[r] = s[(j + r * per) * es];
-    if (Ns > 1) {
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * FFT_THREADS;
+    if (b < nb) {
+      const int line = b & lmask;
+      const int j = b >> lnl;
+      const cx<R>* s = buf + line * ls;
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        cx<R> t = tw[r * k * ts];
-        if (DIR > 0) t = conj(t);
-        v[r] = v[r] * t;
+      for (int r = 0; r < RAD; ++r) v[i][r] = s[(j + (r << LPER)) * es];
+      if (LNS > 0) {
+        const int k = j & NSM;
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          cx<R> t = tw[(r * k) << LTS];
+          if (DIR > 0) t = conj(t);
+          v[i][r] = v[i][r] * t;
+        }
       }
+      dft<R, RAD, DIR>(v[i]);
+      dst[i] = line * ls + ((((j >> LNS) << (LNS + LR)) + (j & NSM)) * es);
     }
-    dft<R, RAD, DIR>(v);
-    const int o = (j / Ns) * Ns * RAD + k;
+  }
+  __syncthreads();
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) d[(o + r * Ns) * es] = v[r];
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * FFT_THREADS;
+    if (b < nb) {
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) buf[dst[i] + ((r << LNS) * es)] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R, int LN, int LNS, int DIR, int TOTL>
+__device__ __forceinline__ void fft_ip(cx<R>* buf, int lnl, int ls, int es, const cx<R>* tw) {
+  if constexpr (LNS < LN) {
+    constexpr int REM = LN - LNS;
+    constexpr int LR = REM >= 3 ? 3 : REM;
+    pass_ip<R, LN, LR, LNS, DIR, TOTL>(buf, lnl, ls, es, tw);
+    fft_ip<R, LN, LNS + LR, DIR, TOTL>(buf, lnl, ls, es, tw);
   }
 }
 
-// Full FFT of nlines lines, ping-ponging between b0 (input) and b1.  Returns
-// the buffer that holds the result.  All threads of the block must call it.
-template <typename R, int DIR, bool JFAST>
-__device__ cx<R>* fft_lines(cx<R>* b0, cx<R>* b1, int len, int nlines, int ls, int es, const cx<R>* tw) {
-  cx<R>* in = b0;
-  cx<R>* out = b1;
-  int Ns = 1;
-  while (Ns < len) {
-    const int rem = len / Ns;
-    if (rem >= 8) {
-      pass<R, 8, DIR, JFAST>(in, out, len, Ns, nlines, ls, es, tw);
-      Ns *= 8;
-    } else if (rem == 4) {
-      pass<R, 4, DIR, JFAST>(in, out, len, Ns, nlines, ls, es, tw);
-      Ns *= 4;
-    } else {
-      pass<R, 2, DIR, JFAST>(in, out, len, Ns, nlines, ls, es, tw);
-      Ns *= 2;
-    }
-    __syncthreads();
-    cx<R>* t = in;
-    in = out;
-    out = t;
+// FFT of 2^lnl lines of length 2^ln (3 <= ln <= 10), all threads of the CTA.
+template <typename R, int DIR, int TOTL>
+__device__ __forceinline__ void fft_lines(cx<R>* buf, int ln, int lnl, int ls, int es, const cx<R>* tw) {
+  switch (ln) {
+    case 3: fft_ip<R, 3, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
+    case 4: fft_ip<R, 4, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
+    case 5: fft_ip<R, 5, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
+    case 6: fft_ip<R, 6, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
+    case 7: fft_ip<R, 7, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
+    case 8: fft_ip<R, 8, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
+    case 9: fft_ip<R, 9, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
+    default: fft_ip<R, 10, 0, DIR, TOTL>(buf, lnl, ls, es, tw); break;
   }
-  return in;
 }
+
+__host__ __device__ inline int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// largest element count (log2) one CTA transforms: complex64 8192, complex128 4096
+template <typename R>
+struct Tot {
+  static constexpr int L = sizeof(R) == 4 ? 13 : 12;
+};
 
 // ---------------------------------------------------------------- stage A / C
 // Columns c in [0, C) of the [field][i0][c] layout; one CTA owns CB columns
-// of one field over the whole axis 0.
+// of one field over the whole axis 0 (smem: [P0][CB], lines = columns).
 template <typename R, int DIR>
-__global__ void k_axis0(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, int n_in, int n_out, int P0, int C,
-                        int CB, const cx<R>* __restrict__ tw) {
+__global__ void __launch_bounds__(FFT_THREADS) k_axis0(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
+                                                       int n_in, int n_out, int P0, int C, int CB,
+                                                       const cx<R>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* b0 = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* b1 = b0 + P0 * CB;
+  cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* b0 = tws + P0;
   const int f = blockIdx.y;
   const int c0 = blockIdx.x * CB;
+  const int lcb = ilog2(CB);
+  for (int i = threadIdx.x; i < P0; i += FFT_THREADS) tws[i] = tw[i];
   const int64_t fin = (int64_t)f * n_in * C;
-  for (int idx = threadIdx.x; idx < P0 * CB; idx += blockDim.x) {
-    const int i0 = idx / CB, l = idx - (idx / CB) * CB;
+  for (int idx = threadIdx.x; idx < P0 * CB; idx += FFT_THREADS) {
+    const int i0 = idx >> lcb, l = idx & (CB - 1);
     cx<R> v = czero<R>();
     if (i0 < n_in && c0 + l < C) v = in[fin + (int64_t)i0 * C + c0 + l];
     b0[idx] = v;
   }
   __syncthreads();
-  cx<R>* res = fft_lines<R, DIR, false>(b0, b1, P0, CB, 1, CB, tw);
+  fft_lines<R, DIR, Tot<R>::L>(b0, ilog2(P0), lcb, 1, CB, tws);
   const int64_t fout = (int64_t)f * n_out * C;
-  for (int idx = threadIdx.x; idx < n_out * CB; idx += blockDim.x) {
-    const int k0 = idx / CB, l = idx - (idx / CB) * CB;
-    if (c0 + l < C) out[fout + (int64_t)k0 * C + c0 + l] = res[idx];
+  for (int idx = threadIdx.x; idx < n_out * CB; idx += FFT_THREADS) {
+    const int k0 = idx >> lcb, l = idx & (CB - 1);
+    if (c0 + l < C) out[fout + (int64_t)k0 * C + c0 + l] = b0[idx];
+  }
+}
+
+// ---------------------------------------------------------------- warp-owned lines
+// FFT of one line of length 2^LN owned by T = 2^(LN-3) consecutive lanes of a
+// warp (lane tl of the group).  The first pass reads element j through
+// ld(j), the last pass writes element j through st(j, v); the passes in
+// between exchange through the line's shared-memory storage line[j*es]
+// with warp-level synchronisation only.
+template <typename R, int LN, int LNS, int DIR, class LD, class ST>
+__device__ __forceinline__ void wline_fft(cx<R>* line, int es, int tl, bool act, const cx<R>* tw, const LD& ld,
+                                          const ST& st) {
+  if constexpr (LNS < LN) {
+    constexpr int REM = LN - LNS;
+    constexpr int LR = REM >= 3 ? 3 : REM;
+    constexpr int RAD = 1 << LR;
+    constexpr int LT = LN - 3;
+    constexpr int LPER = LN - LR;
+    constexpr int NBT = 1 << (LPER - LT);  // butterflies per lane
+    constexpr int NSM = (1 << LNS) - 1;
+    constexpr int LTS = LN - LNS - LR;
+    constexpr bool FIRST = LNS == 0, LAST = LNS + LR == LN;
+    cx<R> v[NBT][RAD];
+    int dst[NBT];
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < NBT; ++i) {
+        const int j = tl + (i << LT);
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+          const int e = j + (r << LPER);
+          v[i][r] = FIRST ? ld(e) : line[e * es];
+        }
+        if (LNS > 0) {
+          const int k = j & NSM;
+#pragma unroll
+          for (int r = 1; r < RAD; ++r) {
+            cx<R> t = tw[(r * k) << LTS];
+            if (DIR > 0) t = conj(t);
+            v[i][r] = v[i][r] * t;
+          }
+        }
+        dft<R, RAD, DIR>(v[i]);
+        dst[i] = ((j >> LNS) << (LNS + LR)) + (j & NSM);
+      }
+    }
+    if (!LAST) __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < NBT; ++i)
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+          const int e = dst[i] + (r << LNS);
+          if (LAST)
+            st(e, v[i][r]);
+          else
+            line[e * es] = v[i][r];
+        }
+    }
+    if (!LAST) {
+      __syncwarp();
+      wline_fft<R, LN, LNS + LR, DIR>(line, es, tl, act, tw, ld, st);
+    }
+  }
+}
+
+// Runs f(l, line, tl, act) for lines l < nlines spread over the warps of the
+// CTA (2^(5-LT) lines per warp); trip counts are uniform within a warp.
+template <int LN, class F>
+__device__ __forceinline__ void for_warp_lines(int nlines, const F& f) {
+  constexpr int LT = LN - 3;
+  constexpr int LPW = 32 >> LT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int tl = lane & ((1 << LT) - 1), sub = lane >> LT;
+  for (int l0 = warp * LPW; l0 < nlines; l0 += nw * LPW) {
+    const int l = l0 + sub;
+    f(l < nlines ? l : 0, tl, l < nlines);
   }
 }
 
@@ -167,37 +268,55 @@ __global__ void k_axis0(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, i
 //   0..3  exterior J (x, y, z, div)  -> outputs 0..3 with G_e
 //   4..7  interior J                 -> outputs 8..11 with G_i
 //   8..11 exterior M                 -> outputs 4..7 with G_e and 12..15 with -G_i
-template <typename R>
-__global__ void k_planes(const cx<R>* __restrict__ A, cx<R>* __restrict__ B, const cx<R>* __restrict__ ghE,
-                         const cx<R>* __restrict__ ghI, int P0, int n1, int n2, int P1, int P2,
-                         const cx<R>* __restrict__ tw1, const cx<R>* __restrict__ tw2) {
+// The plane lives in shared memory with row stride P2 + 2; S holds the
+// forward spectrum, W the working plane of one output.  The forward row pass
+// reads the physical n1 x n2 corner straight from global memory, the forward
+// column pass skips the zero rows, the Green multiply is applied as the
+// inverse column pass loads S, only the n1 physical rows are kept, and the
+// inverse row pass writes the physical corner straight to global memory.
+constexpr int PLANE_THREADS = 256;
+
+template <typename R, int L1, int L2>
+__global__ void __launch_bounds__(PLANE_THREADS) k_planes(const cx<R>* __restrict__ A, cx<R>* __restrict__ B,
+                                                          const cx<R>* __restrict__ ghE,
+                                                          const cx<R>* __restrict__ ghI, int P0, int n1, int n2,
+                                                          const cx<R>* __restrict__ tw1,
+                                                          const cx<R>* __restrict__ tw2) {
   extern __shared__ unsigned char smem_raw[];
-  const int plane = P1 * P2;
-  cx<R>* X = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* Y = X + plane;
-  cx<R>* Z = Y + plane;
+  constexpr int P1 = 1 << L1, P2 = 1 << L2;
+  constexpr int LS = P2 + 2;
+  constexpr int plane = P1 * LS;
+  cx<R>* t1 = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* t2 = t1 + P1;
+  cx<R>* S = t2 + P2;
+  cx<R>* W = S + plane;
   const int k0 = blockIdx.x;
   const int f = blockIdx.y;
+  for (int i = threadIdx.x; i < P1; i += PLANE_THREADS) t1[i] = tw1[i];
+  for (int i = threadIdx.x; i < P2; i += PLANE_THREADS) t2[i] = tw2[i];
+  __syncthreads();
   const int64_t C = (int64_t)n1 * n2;
   const cx<R>* src = A + ((int64_t)f * P0 + k0) * C;
-  for (int idx = threadIdx.x; idx < plane; idx += blockDim.x) {
-    const int i1 = idx / P2, i2 = idx - (idx / P2) * P2;
-    cx<R> v = czero<R>();
-    if (i1 < n1 && i2 < n2) v = src[i1 * n2 + i2];
-    X[idx] = v;
-    Y[idx] = czero<R>();
-  }
+  // forward rows (axis 2): the n1 non-zero rows, read from global memory
+  for_warp_lines<L2>(n1, [&](int i1, int tl, bool act) {
+    cx<R>* row = S + i1 * LS;
+    wline_fft<R, L2, 0, -1>(
+        row, 1, tl, act, t2, [&](int e) { return e < n2 ? src[i1 * n2 + e] : czero<R>(); },
+        [&](int e, cx<R> v) { row[e] = v; });
+  });
   __syncthreads();
-  // rows (axis 2), only the n1 non-zero rows
-  cx<R>* r = fft_lines<R, -1, true>(X, Y, P2, n1, P2, 1, tw2);
-  cx<R>* o = (r == X) ? Y : X;
-  // columns (axis 1), all P2 of them
-  cx<R>* S = fft_lines<R, -1, false>(r, o, P1, P2, 1, P2, tw1);
-  cx<R>* T = (S == X) ? Y : X;  // free buffer besides Z
+  // forward columns (axis 1): rows >= n1 are zero and are not read
+  for_warp_lines<L1>(P2, [&](int k2, int tl, bool act) {
+    cx<R>* col = S + k2;
+    wline_fft<R, L1, 0, -1>(
+        col, LS, tl, act, t1, [&](int e) { return e < n1 ? col[e * LS] : czero<R>(); },
+        [&](int e, cx<R> v) { col[e * LS] = v; });
+  });
+  __syncthreads();
 
-  const int h0 = P0 / 2 + 1, h1 = P1 / 2 + 1, h2 = P2 / 2 + 1;
+  const int h1 = P1 / 2 + 1, h2 = P2 / 2 + 1;
   const int q0 = min(k0, P0 - k0);
-  int nout = (f >= 8) ? 2 : 1;
+  const int nout = (f >= 8) ? 2 : 1;
   for (int which = 0; which < nout; ++which) {
     int fo;
     const cx<R>* gh;
@@ -217,44 +336,91 @@ __global__ void k_planes(const cx<R>* __restrict__ A, cx<R>* __restrict__ B, con
       sgn = R(-1);
     }
     const cx<R>* g0 = gh + (int64_t)q0 * h1 * h2;
-    for (int idx = threadIdx.x; idx < plane; idx += blockDim.x) {
-      const int k1 = idx / P2, k2 = idx - (idx / P2) * P2;
-      const int q1 = min(k1, P1 - k1), q2 = min(k2, P2 - k2);
-      Z[idx] = sgn * (S[idx] * g0[q1 * h2 + q2]);
-    }
+    // inverse columns: load S times the Green spectrum, keep rows < n1 in W
+    for_warp_lines<L1>(P2, [&](int k2, int tl, bool act) {
+      const cx<R>* scol = S + k2;
+      cx<R>* wcol = W + k2;
+      const cx<R>* gcol = g0 + min(k2, P2 - k2);
+      wline_fft<R, L1, 0, 1>(
+          wcol, LS, tl, act, t1,
+          [&](int e) { return sgn * (scol[e * LS] * gcol[min(e, P1 - e) * h2]); },
+          [&](int e, cx<R> v) {
+            if (e < n1) wcol[e * LS] = v;
+          });
+    });
     __syncthreads();
-    cx<R>* u = fft_lines<R, 1, false>(Z, T, P1, P2, 1, P2, tw1);
-    cx<R>* w = (u == Z) ? T : Z;
-    cx<R>* v = fft_lines<R, 1, true>(u, w, P2, n1, P2, 1, tw2);
+    // inverse rows: the n1 physical rows, written straight to global memory
     cx<R>* dst = B + ((int64_t)fo * P0 + k0) * C;
-    for (int idx = threadIdx.x; idx < n1 * n2; idx += blockDim.x) {
-      const int i1 = idx / n2, i2 = idx - (idx / n2) * n2;
-      dst[idx] = v[i1 * P2 + i2];
-    }
+    for_warp_lines<L2>(n1, [&](int i1, int tl, bool act) {
+      cx<R>* row = W + i1 * LS;
+      wline_fft<R, L2, 0, 1>(
+          row, 1, tl, act, t2, [&](int e) { return row[e]; },
+          [&](int e, cx<R> v) {
+            if (e < n2) dst[i1 * n2 + e] = v;
+          });
+    });
     __syncthreads();
   }
 }
 
-// ---------------------------------------------------------------- generic 3-D FFT (set-up)
+template <typename R>
+using PlanesFn = void (*)(const cx<R>*, cx<R>*, const cx<R>*, const cx<R>*, int, int, int, const cx<R>*,
+                          const cx<R>*);
+
+template <typename R, int L1, int L2>
+PlanesFn<R> planes_fn() {
+  if constexpr (L1 + L2 <= 12) return k_planes<R, L1, L2>;
+  else return nullptr;
+}
+
+template <typename R, int L1>
+PlanesFn<R> planes_row(int l2) {
+  switch (l2) {
+    case 3: return planes_fn<R, L1, 3>();
+    case 4: return planes_fn<R, L1, 4>();
+    case 5: return planes_fn<R, L1, 5>();
+    case 6: return planes_fn<R, L1, 6>();
+    case 7: return planes_fn<R, L1, 7>();
+    default: return nullptr;
+  }
+}
+
+// Compiled plane sizes: (2^l1) x (2^l2) with 3 <= l1, l2 <= 7 and l1 + l2 <= 12.
+template <typename R>
+PlanesFn<R> planes_kernel(int l1, int l2) {
+  switch (l1) {
+    case 3: return planes_row<R, 3>(l2);
+    case 4: return planes_row<R, 4>(l2);
+    case 5: return planes_row<R, 5>(l2);
+    case 6: return planes_row<R, 6>(l2);
+    case 7: return planes_row<R, 7>(l2);
+    default: return nullptr;
+  }
+}
+
+// ---------------------------------------------------------------- generic 3-D FFT (set-up, complex128)
 template <typename R, int DIR>
-__global__ void k_fft_axis(cx<R>* data, int len, int inner, int64_t nlines, int CB, const cx<R>* __restrict__ tw) {
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(cx<R>* data, int len, int inner, int64_t nlines, int CB,
+                                                          const cx<R>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* b0 = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* b1 = b0 + len * CB;
+  cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* b0 = tws + len;
   const int64_t L0 = (int64_t)blockIdx.x * CB;
-  for (int idx = threadIdx.x; idx < len * CB; idx += blockDim.x) {
-    const int j = idx / CB, l = idx - (idx / CB) * CB;
+  const int lcb = ilog2(CB);
+  for (int i = threadIdx.x; i < len; i += FFT_THREADS) tws[i] = tw[i];
+  for (int idx = threadIdx.x; idx < len * CB; idx += FFT_THREADS) {
+    const int j = idx >> lcb, l = idx & (CB - 1);
     const int64_t L = L0 + l;
     cx<R> v = czero<R>();
     if (L < nlines) v = data[(L / inner) * ((int64_t)len * inner) + (L % inner) + (int64_t)j * inner];
     b0[idx] = v;
   }
   __syncthreads();
-  cx<R>* res = fft_lines<R, DIR, false>(b0, b1, len, CB, 1, CB, tw);
-  for (int idx = threadIdx.x; idx < len * CB; idx += blockDim.x) {
-    const int j = idx / CB, l = idx - (idx / CB) * CB;
+  fft_lines<R, DIR, Tot<R>::L>(b0, ilog2(len), lcb, 1, CB, tws);
+  for (int idx = threadIdx.x; idx < len * CB; idx += FFT_THREADS) {
+    const int j = idx >> lcb, l = idx & (CB - 1);
     const int64_t L = L0 + l;
-    if (L < nlines) data[(L / inner) * ((int64_t)len * inner) + (L % inner) + (int64_t)j * inner] = res[idx];
+    if (L < nlines) data[(L / inner) * ((int64_t)len * inner) + (L % inner) + (int64_t)j * inner] = b0[idx];
   }
 }
 
@@ -267,12 +433,12 @@ __global__ void k_twiddles(cx<R>* tw, int len) {
   tw[m] = mk(R(c), R(-s));
 }
 
+// Lines per CTA for a transform of length len: up to 2^Tot<R>::L elements,
+// at most 16 lines.
 template <typename R>
-int cb_for(int len) {
-  // lines per CTA so that two buffers stay within ~96 KB (c64) / 128 KB (c128)
-  int budget = (sizeof(R) == 4) ? 96 * 1024 : 128 * 1024;
-  int cb = budget / (2 * len * (int)sizeof(cx<R>));
-  if (cb > 32) cb = 32;
+int lines_per_cta(int len) {
+  int cb = (1 << Tot<R>::L) / len;
+  if (cb > 16) cb = 16;
   if (cb < 1) cb = 1;
   return cb;
 }
@@ -294,28 +460,19 @@ int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cu
     int inner = 1;
     for (int b = a + 1; b < 3; ++b) inner *= op->P[b];
     const int64_t nlines = total / len;
-    const int cb = cb_for<R>(len);
-    const size_t sm = 2 * (size_t)len * cb * sizeof(cx<R>);
+    const int cb = lines_per_cta<R>(len);
+    const size_t sm = (size_t)len * (cb + 1) * sizeof(cx<R>);
     const int blocks = (int)cdiv(nlines, cb);
     if (dir < 0) {
       CK(cudaFuncSetAttribute(k_fft_axis<R, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_fft_axis<R, -1><<<blocks, 256, sm, s>>>(data, len, inner, nlines, cb, tw[a]);
+      k_fft_axis<R, -1><<<blocks, FFT_THREADS, sm, s>>>(data, len, inner, nlines, cb, tw[a]);
     } else {
       CK(cudaFuncSetAttribute(k_fft_axis<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_fft_axis<R, 1><<<blocks, 256, sm, s>>>(data, len, inner, nlines, cb, tw[a]);
+      k_fft_axis<R, 1><<<blocks, FFT_THREADS, sm, s>>>(data, len, inner, nlines, cb, tw[a]);
     }
     CK(cudaGetLastError());
   }
   return SCABEM_OK;
-}
-
-// Columns per CTA for the axis-0 stages: 16 (complex64) or 8 (complex128),
-// halved until the two ping-pong buffers fit in 192 KB of shared memory.
-template <typename R>
-int axis0_cb(int P0) {
-  int cb = (sizeof(R) == 4) ? 16 : 8;
-  while (cb > 1 && 2 * (size_t)P0 * cb * sizeof(cx<R>) > 192 * 1024) cb /= 2;
-  return cb;
 }
 
 template <typename R>
@@ -323,34 +480,31 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
   const int P0 = op->P[0], P1 = op->P[1], P2 = op->P[2];
   const int C = n1 * n2;
+  const int cb = lines_per_cta<R>(P0);
+  const size_t sm0 = (size_t)P0 * (cb + 1) * sizeof(cx<R>);
   // stage A
-  {
-    const int cb = axis0_cb<R>(P0);
-    const size_t sm = 2 * (size_t)P0 * cb * sizeof(cx<R>);
-    CK(cudaFuncSetAttribute(k_axis0<R, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid((unsigned)cdiv(C, cb), NFIELD_IN);
-    k_axis0<R, -1><<<grid, 512, sm, s>>>(pd.src, pd.stA, n0, P0, P0, C, cb, pd.tw[0]);
-    CK(cudaGetLastError());
-  }
+  CK(cudaFuncSetAttribute(k_axis0<R, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+  k_axis0<R, -1><<<dim3((unsigned)cdiv(C, cb), NFIELD_IN), FFT_THREADS, sm0, s>>>(pd.src, pd.stA, n0, P0, P0, C, cb,
+                                                                                  pd.tw[0]);
+  CK(cudaGetLastError());
   prof_mark(op, s);
   // stage B
-  {
-    const size_t sm = 3 * (size_t)P1 * P2 * sizeof(cx<R>);
-    CK(cudaFuncSetAttribute(k_planes<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid(P0, NFIELD_IN);
-    k_planes<R><<<grid, 512, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, n1, n2, P1, P2, pd.tw[1], pd.tw[2]);
-    CK(cudaGetLastError());
+  const size_t sm1 = ((size_t)P1 + P2 + 2 * (size_t)P1 * (P2 + 2)) * sizeof(cx<R>);
+  PlanesFn<R> fn = planes_kernel<R>(ilog2(P1), ilog2(P2));
+  if (!fn) {
+    set_error("grid: the y and z transform sizes must be in [8, 128]");
+    return SCABEM_E_ARG;
   }
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  fn<<<dim3(P0, NFIELD_IN), PLANE_THREADS, sm1, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, n1, n2, pd.tw[1],
+                                                   pd.tw[2]);
+  CK(cudaGetLastError());
   prof_mark(op, s);
   // stage C
-  {
-    const int cb = axis0_cb<R>(P0);
-    const size_t sm = 2 * (size_t)P0 * cb * sizeof(cx<R>);
-    CK(cudaFuncSetAttribute(k_axis0<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid((unsigned)cdiv(C, cb), NFIELD_OUT);
-    k_axis0<R, 1><<<grid, 512, sm, s>>>(pd.stB, pd.grid, P0, n0, P0, C, cb, pd.tw[0]);
-    CK(cudaGetLastError());
-  }
+  CK(cudaFuncSetAttribute(k_axis0<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+  k_axis0<R, 1><<<dim3((unsigned)cdiv(C, cb), NFIELD_OUT), FFT_THREADS, sm0, s>>>(pd.stB, pd.grid, P0, n0, P0, C, cb,
+                                                                                  pd.tw[0]);
+  CK(cudaGetLastError());
   return SCABEM_OK;
 }
 
