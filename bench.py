@@ -163,8 +163,10 @@ def stage_bytes(info, case, b):
         "fft_axis0_fwd": b * 12 * (ng + P0 * C),
         "fft_planes_green": b * (12 * P0 * C + 16 * P0 * C + 2 * oct_),
         "fft_axis0_inv": b * 16 * (P0 * C + ng),
-        "near_field": b * (npairs * case.q * 2 * 10 + 2 * Q * 2 * 20 + nt * 12) + 4 * (nt + 1 + npairs),
-        "interpolation": b * (16 * ng + Q * 2 * 20),
+        # near records, the 16 potential grids, summaries, tested values out;
+        # per point: position, weight, stencil base and weights, conductivity
+        "points": b * (npairs * case.q * 2 * 10 + 16 * ng + nt * 12 + nt * 12) + 4 * (nt + 1 + npairs)
+        + Q * (24 + 8 + 12 + 2 * 3 * case.grid.p * b // 2 + b // 2) + nt * (16 + 3) * 8,
     }
 
 
@@ -259,7 +261,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": t_setup},
             "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
                     "d2h_bytes_per_step": int(N * 8)},
-            "gpu_launches": 9 * args.steps,
+            "gpu_launches": 8 * args.steps,
             "stages_ms_per_step": per,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -243,13 +243,13 @@ int scabem_reflection(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, c
                       const scabem_source* inc, double* out, void* stream);
 
 /* Stage timing of scabem_apply (instrumentation, not part of the paper's
- * method).  While enabled, every apply records CUDA events at its 8 stage
+ * method).  While enabled, every apply records CUDA events at its stage
  * boundaries on its own stream, for at most max_applies applies (events are
  * created here, so enable before any stream capture).  scabem_profile_read
  * waits for the recorded events, returns per-stage summed milliseconds in
- * stage_ms[8] = {summaries, projection, FFT axis-0 forward, FFT planes with
- * the Green multiply, FFT axis-0 inverse, interpolation, near field,
- * testing + rows} and the number of applies, and starts a new record.
+ * stage_ms[7] = {summaries, projection, FFT axis-0 forward, FFT planes with
+ * the Green multiply, FFT axis-0 inverse, points (interpolation + near field
+ * + testing), rows} and the number of applies, and starts a new record.
  * enable = 0 releases the events. */
 int scabem_profile(scabem_op_t op, int32_t enable, int32_t max_applies);
 int scabem_profile_read(scabem_op_t op, double* stage_ms, int64_t* n_applies);

@@ -7,10 +7,11 @@
 //                by the Lagrange stencils (12 fields)
 //  K3-5          fft_conv (fft.cu): 12 -> 16 grid potentials (A, phi, F, psi
 //                of each medium, Eqs. 15-16)
-//  K6 k_interp   potentials, gradients and curls at the quadrature points
-//  K7 k_near     near-field precorrection: exact minus grid panel moments
-//  K8 k_test     Galerkin testing of Eqs. 1-3 (weak form), Eq. 13 and Eq. 14
-//                (strong form, sigma-weighted, with the side-limit terms)
+//  K6-8 k_points per target triangle: potentials, gradients and curls at its
+//                quadrature points (interpolation), plus the near-field
+//                precorrection (exact minus grid panel moments), then the
+//                Galerkin testing of Eqs. 1-3 (weak form), Eq. 13 and Eq. 14
+//                (sigma-weighted, with the side-limit terms)
 //     k_rows     per-edge sum of the two triangles' tested values
 #include <cuda_runtime.h>
 
@@ -54,58 +55,85 @@ __global__ void k_summ(const cx<R>* __restrict__ x, const int32_t* __restrict__ 
   }
 }
 
+// K2a: one thread per quadrature point: the weighted point sources
+// qsrc[Qi*12 + set*4 + {x, y, z, div}] of the exterior J, interior J and
+// exterior M sets (J(r) = a (r - c) - beta, div J = 2a, times the weight).
 template <typename R>
-__device__ __forceinline__ void atomic_add_cx(cx<R>* p, cx<R> v);
-template <>
-__device__ __forceinline__ void atomic_add_cx<float>(cx<float>* p, cx<float> v) {
-  atomicAdd(reinterpret_cast<float2*>(p), make_float2(v.re, v.im));
-}
-template <>
-__device__ __forceinline__ void atomic_add_cx<double>(cx<double>* p, cx<double> v) {
-  atomicAdd(&p->re, v.re);
-  atomicAdd(&p->im, v.im);
-}
-
-// K2: one thread per (quadrature point, stencil node).  Source fields
-// [set*4 + {x, y, z, div}] of the exterior J, interior J and exterior M sets,
-// each point source weighted by its quadrature weight.
-template <typename R>
-__global__ void k_project(const cx<R>* __restrict__ summ, const double* __restrict__ qp, const double* __restrict__ qw,
-                          const double* __restrict__ tri, const int32_t* __restrict__ base, const R* __restrict__ L,
-                          int64_t Q, int q, int p, int n0, int n1, int n2, cx<R>* __restrict__ grids) {
-  const int p3 = p * p * p;
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= Q * p3) return;
-  const int64_t Qi = gid / p3;
-  const int sidx = (int)(gid - Qi * p3);
-  const int i = sidx / (p * p), j = (sidx / p) % p, k = sidx % p;
+__global__ void k_qsrc(const cx<R>* __restrict__ summ, const double* __restrict__ qp, const double* __restrict__ qw,
+                       const double* __restrict__ tri, int64_t Q, int q, cx<R>* __restrict__ qsrc) {
+  int64_t Qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (Qi >= Q) return;
   const int64_t t = Qi / q;
-  const R W = L[(3 * Qi + 0) * p + i] * L[(3 * Qi + 1) * p + j] * L[(3 * Qi + 2) * p + k] * (R)qw[Qi];
   const double* g = tri + 16 * t;
+  const R w = (R)qw[Qi];
   const R rel[3] = {(R)(qp[3 * Qi] - g[9]), (R)(qp[3 * Qi + 1] - g[10]), (R)(qp[3 * Qi + 2] - g[11])};
-  const int64_t gi =
-      ((int64_t)(base[3 * Qi] + i) * n1 + (base[3 * Qi + 1] + j)) * n2 + (base[3 * Qi + 2] + k);
-  const int64_t ng = (int64_t)n0 * n1 * n2;
+  cx<R>* o = qsrc + Qi * NFIELD_IN;
+#pragma unroll
   for (int set = 0; set < 3; ++set) {
     const cx<R>* s = summ + (3 * t + set) * 4;
     const cx<R> a = s[0];
-    for (int c = 0; c < 3; ++c) {
-      const cx<R> J = rel[c] * a - s[1 + c];
-      atomic_add_cx(grids + (set * 4 + c) * ng + gi, W * J);
-    }
-    atomic_add_cx(grids + (set * 4 + 3) * ng + gi, (R(2) * W) * a);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[set * 4 + c] = w * (rel[c] * a - s[1 + c]);
+    o[set * 4 + 3] = (R(2) * w) * a;
   }
 }
 
-// K6: one thread per (quadrature point, medium).  Output record (NREC):
-// A(3) phi grad phi(3) curl A(3) F(3) psi grad psi(3) curl F(3).
+// K2b: projection as a gather.  Eight lanes per grid point that some stencil
+// covers share its (point, stencil slot) entries, sum W_slot(point) *
+// qsrc[point], and reduce by shuffles; lane 0 writes the 12 fields.  Points
+// no stencil covers stay zero from set-up.  The sum order is fixed, so the
+// result does not depend on thread timing.
 template <typename R>
-__global__ void k_interp(const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
-                         const R* __restrict__ dL, int64_t Q, int p, int n0, int n1, int n2, cx<R>* __restrict__ fpt) {
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= Q * 2) return;
-  const int64_t Qi = gid >> 1;
-  const int med = (int)(gid & 1);
+__global__ void k_gather(const cx<R>* __restrict__ qsrc, const int32_t* __restrict__ gpt,
+                         const int32_t* __restrict__ goff, const int32_t* __restrict__ gent, const R* __restrict__ gw,
+                         int64_t ngnz, int p3, int64_t ng, cx<R>* __restrict__ grids) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  const int l8 = threadIdx.x & 7;
+  cx<R> acc[NFIELD_IN];
+#pragma unroll
+  for (int f = 0; f < NFIELD_IN; ++f) acc[f] = czero<R>();
+  if (i < ngnz) {
+    const int e1 = goff[i + 1];
+    for (int e = goff[i] + l8; e < e1; e += 8) {
+      const int64_t Qi = gent[e] / p3;
+      const R W = gw[e];
+      const cx<R>* src = qsrc + Qi * NFIELD_IN;
+#pragma unroll
+      for (int f = 0; f < NFIELD_IN; ++f) axpy(acc[f], W, src[f]);
+    }
+  }
+  // every lane reaches the shuffles (no early exit above)
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+    for (int f = 0; f < NFIELD_IN; ++f) {
+      acc[f].re += __shfl_xor_sync(0xffffffffu, acc[f].re, o);
+      acc[f].im += __shfl_xor_sync(0xffffffffu, acc[f].im, o);
+    }
+  if (i < ngnz && l8 == 0) {
+    const int64_t g = gpt[i];
+#pragma unroll
+    for (int f = 0; f < NFIELD_IN; ++f) grids[f * ng + g] = acc[f];
+  }
+}
+
+template <typename R>
+const R* gather_weights(scabem_op* op);
+template <>
+const float* gather_weights<float>(scabem_op* op) {
+  return op->gwf;
+}
+template <>
+const double* gather_weights<double>(scabem_op* op) {
+  return op->gwd;
+}
+
+// Interpolated potentials of one medium at quadrature point Qi.  Record
+// (NREC): A(3) phi grad phi(3) curl A(3) F(3) psi grad psi(3) curl F(3).
+template <typename R>
+__device__ __forceinline__ void interp_point(const cx<R>* __restrict__ grids, const int32_t* __restrict__ base,
+                                             const R* __restrict__ L, const R* __restrict__ dL, int64_t Qi, int med,
+                                             int p, int64_t ng, int n1, int n2, cx<R>* rec) {
   R Lx[MAXP], Ly[MAXP], Lz[MAXP], dx[MAXP], dy[MAXP], dz[MAXP];
   for (int i = 0; i < p; ++i) {
     Lx[i] = L[(3 * Qi + 0) * p + i];
@@ -116,44 +144,44 @@ __global__ void k_interp(const cx<R>* __restrict__ grids, const int32_t* __restr
     dz[i] = dL[(3 * Qi + 2) * p + i];
   }
   const int b0 = base[3 * Qi], b1 = base[3 * Qi + 1], b2 = base[3 * Qi + 2];
-  const int64_t ng = (int64_t)n0 * n1 * n2;
-  cx<R> v[8], gx[8], gy[8], gz[8];
-  for (int f = 0; f < 8; ++f) v[f] = gx[f] = gy[f] = gz[f] = czero<R>();
-  for (int i = 0; i < p; ++i)
-    for (int j = 0; j < p; ++j) {
-      const R wxy = Lx[i] * Ly[j], dxy = dx[i] * Ly[j], xdy = Lx[i] * dy[j];
-      const int64_t rowi = ((int64_t)(b0 + i) * n1 + (b1 + j)) * n2 + b2;
-      for (int k = 0; k < p; ++k) {
-        const R w = wxy * Lz[k], wx = dxy * Lz[k], wy = xdy * Lz[k], wz = wxy * dz[k];
-        for (int f = 0; f < 8; ++f) {
-          const cx<R> gv = grids[(med * 8 + f) * ng + rowi + k];
-          axpy(v[f], w, gv);
-          axpy(gx[f], wx, gv);
-          axpy(gy[f], wy, gv);
-          axpy(gz[f], wz, gv);
+  // two groups of 4 fields: (A, phi) of the J set, then (F, psi) of the M set
+  for (int h = 0; h < 2; ++h) {
+    cx<R> v[4], gx[4], gy[4], gz[4];
+    for (int f = 0; f < 4; ++f) v[f] = gx[f] = gy[f] = gz[f] = czero<R>();
+    const cx<R>* gm = grids + (int64_t)(med * 8 + 4 * h) * ng;
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) {
+        const R wxy = Lx[i] * Ly[j], dxy = dx[i] * Ly[j], xdy = Lx[i] * dy[j];
+        const int64_t rowi = ((int64_t)(b0 + i) * n1 + (b1 + j)) * n2 + b2;
+        for (int k = 0; k < p; ++k) {
+          const R w = wxy * Lz[k], wx = dxy * Lz[k], wy = xdy * Lz[k], wz = wxy * dz[k];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            const cx<R> gv = gm[f * ng + rowi + k];
+            axpy(v[f], w, gv);
+            axpy(gx[f], wx, gv);
+            axpy(gy[f], wy, gv);
+            axpy(gz[f], wz, gv);
+          }
         }
       }
-    }
-  cx<R>* o = fpt + gid * NREC;
-  for (int h = 0; h < 2; ++h) {
-    const int f0 = 4 * h;  // A (h=0) or F (h=1)
-    cx<R>* r = o + 10 * h;
-    r[0] = v[f0];
-    r[1] = v[f0 + 1];
-    r[2] = v[f0 + 2];
-    r[3] = v[f0 + 3];
-    r[4] = gx[f0 + 3];
-    r[5] = gy[f0 + 3];
-    r[6] = gz[f0 + 3];
-    r[7] = gy[f0 + 2] - gz[f0 + 1];
-    r[8] = gz[f0 + 0] - gx[f0 + 2];
-    r[9] = gx[f0 + 1] - gy[f0 + 0];
+    cx<R>* r = rec + 10 * h;
+    r[0] = v[0];
+    r[1] = v[1];
+    r[2] = v[2];
+    r[3] = v[3];
+    r[4] = gx[3];
+    r[5] = gy[3];
+    r[6] = gz[3];
+    r[7] = gy[2] - gz[1];
+    r[8] = gz[0] - gx[2];
+    r[9] = gx[1] - gy[0];
   }
 }
 
-// K7: one thread per (target point, medium).  Each near record (10 complex:
-// dP0, dP1, dQ, dC) is loaded once and applied to the J and the M source of
-// the pair; two pairs are kept in flight.
+// One near record (dP0, dP1, dQ, dC) applied to the J and the M source of a
+// pair: A += a dP1 - beta dP0, phi += 2a dP0, grad phi += 2a dQ,
+// curl A += a dC - dQ x beta.
 template <typename R>
 __device__ __forceinline__ void near_accumulate(const cx<R>* d, const cx<R>* sj, const cx<R>* sm, R sgnm,
                                                 cx<R>* accJ, cx<R>* accM) {
@@ -180,32 +208,30 @@ __device__ __forceinline__ void near_accumulate(const cx<R>* d, const cx<R>* sj,
   }
 }
 
+// Near-field precorrection of one (target point a of triangle t, medium).
 template <typename R>
-__global__ void __launch_bounds__(128) k_near(const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
-                                              const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ,
-                                              int64_t Q, int q, cx<R>* __restrict__ fpt) {
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= Q * 2) return;
-  const int64_t Qa = gid >> 1;
-  const int med = (int)(gid & 1);
-  const int64_t t = Qa / q;
-  const int a = (int)(Qa - t * q);
+__device__ __forceinline__ void near_point(const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
+                                           const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ,
+                                           int64_t t, int a, int med, int q, cx<R>* rec) {
   const R sgnm = med == 1 ? R(-1) : R(1);  // interior M = -M
-  cx<R> accJ[NCORR], accM[NCORR];
-  for (int c = 0; c < NCORR; ++c) accJ[c] = accM[c] = czero<R>();
+  cx<R>* accJ = rec;
+  cx<R>* accM = rec + 10;
   const int j0 = noff[t], j1 = noff[t + 1];
-  const int64_t rec = (int64_t)q * 2 * NCORR;  // complex per pair
-  const cx<R>* base = corr + ((int64_t)a * 2 + med) * NCORR;
+  // records are [pair][component][point][medium]: the 2q threads of a
+  // triangle read each component as one contiguous run
+  const int cs = 2 * q;                     // component stride
+  const int64_t stride = (int64_t)NCORR * cs;  // complex per pair
+  const cx<R>* base = corr + (int64_t)a * 2 + med;
   int j = j0;
   for (; j + 1 < j1; j += 2) {
     cx<R> dA[NCORR], dB[NCORR];
     const int64_t sA = nsrc[j], sB = nsrc[j + 1];
-    const cx<R>* pA = base + (int64_t)j * rec;
-    const cx<R>* pB = pA + rec;
+    const cx<R>* pA = base + (int64_t)j * stride;
+    const cx<R>* pB = pA + stride;
 #pragma unroll
     for (int c = 0; c < NCORR; ++c) {
-      dA[c] = pA[c];
-      dB[c] = pB[c];
+      dA[c] = pA[c * cs];
+      dB[c] = pB[c * cs];
     }
     near_accumulate(dA, summ + (3 * sA + med) * 4, summ + (3 * sA + 2) * 4, sgnm, accJ, accM);
     near_accumulate(dB, summ + (3 * sB + med) * 4, summ + (3 * sB + 2) * 4, sgnm, accJ, accM);
@@ -213,15 +239,10 @@ __global__ void __launch_bounds__(128) k_near(const cx<R>* __restrict__ corr, co
   if (j < j1) {
     cx<R> dA[NCORR];
     const int64_t sA = nsrc[j];
-    const cx<R>* pA = base + (int64_t)j * rec;
+    const cx<R>* pA = base + (int64_t)j * stride;
 #pragma unroll
-    for (int c = 0; c < NCORR; ++c) dA[c] = pA[c];
+    for (int c = 0; c < NCORR; ++c) dA[c] = pA[c * cs];
     near_accumulate(dA, summ + (3 * sA + med) * 4, summ + (3 * sA + 2) * 4, sgnm, accJ, accM);
-  }
-  cx<R>* o = fpt + gid * NREC;
-  for (int c = 0; c < NCORR; ++c) {
-    o[c] += accJ[c];
-    o[10 + c] += accM[c];
   }
 }
 
@@ -230,19 +251,17 @@ __device__ __forceinline__ cx<R> dot3(const R* X, const cx<R>* V) {
   return X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
 }
 
-// K8: one thread per (triangle, local edge k).  val[(t*3+k)*4 + type]:
-// type 0 <X, E_e - E_i>, 1 <X, H_e - H_i> (weak forms); 2 Eq. 13, 3 Eq. 14.
+// Tested values of local edge kk of triangle t from the records of its
+// points (recs[(a*2 + medium)*NREC]): type 0 <X, E_e - E_i>, 1 <X, H_e - H_i>
+// (weak forms), 2 Eq. 13, 3 Eq. 14.
 template <typename R>
-__global__ void k_test(const cx<R>* __restrict__ fpt, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
-                       const double* __restrict__ cX, const double* __restrict__ qp, const double* __restrict__ qw,
-                       const R* __restrict__ sig, int64_t nt, int q, R ke, R ki, R ze, R zi,
-                       cx<R>* __restrict__ val) {
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= nt * 3) return;
-  const int64_t t = gid / 3;
-  const int kk = (int)(gid - t * 3);
+__device__ __forceinline__ void test_edge(const cx<R>* recs, const cx<R>* __restrict__ summ,
+                                          const double* __restrict__ tri, const double* __restrict__ cX,
+                                          const double* __restrict__ qp, const double* __restrict__ qw,
+                                          const R* __restrict__ sig, int64_t t, int kk, int q, R ke, R ki, R ze,
+                                          R zi, cx<R>* out) {
   const double* g = tri + 16 * t;
-  const R cxk = (R)cX[gid];
+  const R cxk = (R)cX[3 * t + kk];
   const R divX = R(2) * cxk;
   const R nrm[3] = {(R)g[12], (R)g[13], (R)g[14]};
   const cx<R>* se = summ + (3 * t + 0) * 4;
@@ -263,7 +282,7 @@ __global__ void k_test(const cx<R>* __restrict__ fpt, const cx<R>* __restrict__ 
     cx<R> wE = czero<R>(), wH = czero<R>();
     for (int c = 0; c < 3; ++c) WE[c] = WH[c] = czero<R>();
     for (int m = 0; m < 2; ++m) {
-      const cx<R>* r = fpt + (Qa * 2 + m) * NREC;
+      const cx<R>* r = recs + (a * 2 + m) * NREC;
       const R k = kl[m], z = zl[m];
       const R sgm = m == 0 ? R(1) : R(-1);
       const cx<R> phi = r[3], psi = r[13];
@@ -300,11 +319,50 @@ __global__ void k_test(const cx<R>* __restrict__ fpt, const cx<R>* __restrict__ 
     // Eq. 14: <X, J_e + J_i> - <sigma X, E_i^->, side limit n x M / 2
     v3 += w * (XJ - sg * dot3(X, E[1]) - (R(0.5) * sg) * XnM);
   }
-  cx<R>* o = val + gid * 4;
-  o[0] = v0;
-  o[1] = v1;
-  o[2] = v2;
-  o[3] = v3;
+  out[0] = v0;
+  out[1] = v1;
+  out[2] = v2;
+  out[3] = v3;
+}
+
+// K6-8: one CTA per PT_TRI target triangles.  Phase 1: thread (triangle,
+// point, medium) interpolates its record and adds the near corrections, into
+// shared memory.  Phase 2: thread (triangle, local edge) tests.
+constexpr int PT_TRI = 16;
+
+template <typename R>
+__global__ void k_points(const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
+                         const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
+                         const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ,
+                         const double* __restrict__ tri, const double* __restrict__ cX, const double* __restrict__ qp,
+                         const double* __restrict__ qw, const R* __restrict__ sig, int64_t nt, int q, int p, int n0,
+                         int n1, int n2, R ke, R ki, R ze, R zi, int has_near, cx<R>* __restrict__ val) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* recs = reinterpret_cast<cx<R>*>(smem_raw);  // [PT_TRI][q][2][NREC]
+  const int64_t t0 = (int64_t)blockIdx.x * PT_TRI;
+  const int per = 2 * q;
+  const int tl = threadIdx.x / per;
+  const int rem = threadIdx.x - tl * per;
+  const int a = rem >> 1, med = rem & 1;
+  const int64_t t = t0 + tl;
+  const int64_t ng = (int64_t)n0 * n1 * n2;
+  if (tl < PT_TRI && t < nt) {
+    cx<R> rec[NREC];
+    interp_point(grids, base, L, dL, t * q + a, med, p, ng, n1, n2, rec);
+    if (has_near) near_point(corr, noff, nsrc, summ, t, a, med, q, rec);
+    cx<R>* o = recs + ((int64_t)tl * per + a * 2 + med) * NREC;
+#pragma unroll
+    for (int c = 0; c < NREC; ++c) o[c] = rec[c];
+  }
+  __syncthreads();
+  const int tt = threadIdx.x / 3, kk = threadIdx.x - (threadIdx.x / 3) * 3;
+  const int64_t t2 = t0 + tt;
+  if (tt < PT_TRI && t2 < nt) {
+    cx<R> o[4];
+    test_edge(recs + (int64_t)tt * per * NREC, summ, tri, cX, qp, qw, sig, t2, kk, q, ke, ki, ze, zi, o);
+    cx<R>* dst = val + (t2 * 3 + kk) * 4;
+    for (int c = 0; c < 4; ++c) dst[c] = o[c];
+  }
 }
 
 template <typename R>
@@ -334,30 +392,32 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   const int64_t nt = op->nt, Q = op->Q;
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
   const int64_t ng = (int64_t)n0 * n1 * n2;
-  const int p3 = op->p * op->p * op->p;
   prof_mark(op, s);
   k_summ<R><<<(int)cdiv(nt, 128), 128, 0, s>>>(x, op->unk, op->cX, op->tri, nt, pd.summ);
   CK(cudaGetLastError());
   prof_mark(op, s);
-  CK(cudaMemsetAsync(pd.src, 0, sizeof(cx<R>) * NFIELD_IN * ng, s));
-  k_project<R><<<(int)cdiv(Q * p3, 256), 256, 0, s>>>(pd.summ, op->qp, op->qw, op->tri, op->base, pd.L, Q, op->q,
-                                                       op->p, n0, n1, n2, pd.src);
+  k_qsrc<R><<<(int)cdiv(Q, 128), 128, 0, s>>>(pd.summ, op->qp, op->qw, op->tri, Q, op->q, pd.qsrc);
   CK(cudaGetLastError());
+  if (op->ngnz > 0) {
+    k_gather<R><<<(int)cdiv(op->ngnz * 8, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent,
+                                                             gather_weights<R>(op), op->ngnz,
+                                                             op->p * op->p * op->p, ng, pd.src);
+    CK(cudaGetLastError());
+  }
   prof_mark(op, s);
   int rc = fft_conv<R>(op, pd, s);
   if (rc) return rc;
   prof_mark(op, s);
-  k_interp<R><<<(int)cdiv(Q * 2, 128), 128, 0, s>>>(pd.grid, op->base, pd.L, pd.dL, Q, op->p, n0, n1, n2, pd.fpt);
-  CK(cudaGetLastError());
-  prof_mark(op, s);
-  if (op->npairs > 0) {
-    k_near<R><<<(int)cdiv(Q * 2, 128), 128, 0, s>>>(pd.near, op->noff, op->nsrc, pd.summ, Q, op->q, pd.fpt);
+  {
+    const int threads = PT_TRI * (2 * op->q > 3 ? 2 * op->q : 3);
+    const size_t sm = (size_t)PT_TRI * 2 * op->q * NREC * sizeof(cx<R>);
+    CK(cudaFuncSetAttribute(k_points<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_points<R><<<(int)cdiv(nt, PT_TRI), threads, sm, s>>>(
+        pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ, op->tri, op->cX, op->qp, op->qw, pd.sig,
+        nt, op->q, op->p, n0, n1, n2, (R)op->ke, (R)op->ki, (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, pd.val);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);
-  k_test<R><<<(int)cdiv(nt * 3, 128), 128, 0, s>>>(pd.fpt, pd.summ, op->tri, op->cX, op->qp, op->qw, pd.sig, nt,
-                                                    op->q, (R)op->ke, (R)op->ki, (R)op->ze, (R)op->zi, pd.val);
-  CK(cudaGetLastError());
   k_rows<R><<<(int)cdiv(op->N, 256), 256, 0, s>>>(pd.val, op->rowsrc, op->N, y);
   CK(cudaGetLastError());
   prof_mark(op, s);

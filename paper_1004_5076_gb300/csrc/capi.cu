@@ -73,6 +73,7 @@ void free_prec(PrecData<R>& pd) {
   cudaFree(pd.dL);
   cudaFree(pd.sig);
   cudaFree(pd.summ);
+  cudaFree(pd.qsrc);
   cudaFree(pd.src);
   cudaFree(pd.stA);
   cudaFree(pd.stB);
@@ -98,7 +99,10 @@ int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) 
     if ((rc = make_twiddles<R>(pd.tw[a], op->P[a], s))) return rc;
   }
   if ((rc = dalloc(&pd.summ, op->nt * 12))) return rc;
+  if ((rc = dalloc(&pd.qsrc, op->Q * 12))) return rc;
   if ((rc = dalloc(&pd.src, NFIELD_IN * ng))) return rc;
+  // grid points no stencil covers are never written by the projection
+  CK(cudaMemsetAsync(pd.src, 0, sizeof(cx<R>) * NFIELD_IN * ng, s));
   if ((rc = dalloc(&pd.stA, (int64_t)NFIELD_IN * op->P[0] * C))) return rc;
   if ((rc = dalloc(&pd.stB, (int64_t)NFIELD_OUT * op->P[0] * C))) return rc;
   if ((rc = dalloc(&pd.grid, NFIELD_OUT * ng))) return rc;
@@ -464,6 +468,7 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   TRY(upload(op->ecls, ecls.data(), sizeof(int32_t) * ecls.size()));
   TRY(upload(op->eunk, eunk.data(), sizeof(int32_t) * eunk.size()));
   TRY(setup_geometry(op, m, s));
+  TRY(setup_gather(op, s));
   TRY(setup_green(op, s));
   TRY(setup_near(op, s));
   TRY(setup_sigma_monomial(op, 0, nullptr, s));
@@ -535,6 +540,11 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->qp);
   cudaFree(op->qw);
   cudaFree(op->base);
+  cudaFree(op->goff);
+  cudaFree(op->gent);
+  cudaFree(op->gpt);
+  cudaFree(op->gwd);
+  cudaFree(op->gwf);
   cudaFree(op->sig64);
   cudaFree(op->noff);
   cudaFree(op->nsrc);

@@ -86,10 +86,10 @@ constexpr int NCORR = 10;  // per point and medium: dP0, dP1(3), dQ(3), dC(3)
 constexpr double ETA0 = 376.730313668;
 
 // ------------------------------------------------------------------ profiling
-// Stage boundaries of one apply: start, summaries, projection, FFT axis 0
-// forward, FFT planes with the Green multiply, FFT axis 0 inverse,
-// interpolation, near field, testing and rows.
-constexpr int NSTAGE = 8;
+// Stages of one apply: summaries, projection, FFT axis 0 forward, FFT planes
+// with the Green multiply, FFT axis 0 inverse, points (interpolation, near
+// field and testing), rows.
+constexpr int NSTAGE = 7;
 struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> ev;  // (NSTAGE + 1) per recorded apply
@@ -112,13 +112,14 @@ template <typename R>
 struct PrecData {
   bool built = false;
   cx<R>* ghat[2] = {nullptr, nullptr};  // octant spectra, scaled by 1/(P0 P1 P2)
-  cx<R>* near = nullptr;                // npairs * q * 2 * NCORR
+  cx<R>* near = nullptr;                // [npairs][NCORR][q][2]
   cx<R>* tw[3] = {nullptr, nullptr, nullptr};  // forward twiddles per axis length
   R* L = nullptr;                       // Q * 3 * p stencil weights
   R* dL = nullptr;                      // Q * 3 * p derivative weights [1/um]
   R* sig = nullptr;                     // Q normalised conductivity
   // workspaces
   cx<R>* summ = nullptr;  // nt * 3 sets * 4
+  cx<R>* qsrc = nullptr;  // Q * 12 weighted point sources
   cx<R>* src = nullptr;   // 12 * n0 n1 n2
   cx<R>* stA = nullptr;   // 12 * P0 * n1 n2
   cx<R>* stB = nullptr;   // 16 * P0 * n1 n2
@@ -149,6 +150,16 @@ struct scabem_op {
   double* qp = nullptr;       // Q * 3
   double* qw = nullptr;       // Q
   int32_t* base = nullptr;    // Q * 3
+  // projection as a gather over the ngnz grid points that some stencil
+  // covers: point gpt[i] sums entries goff[i] .. goff[i+1]-1 of gent, each
+  // (quadrature point * p^3 + stencil slot), in point order; gwd / gwf hold
+  // the entries' stencil weights
+  int64_t ngnz = 0;
+  int32_t* gpt = nullptr;   // ngnz
+  int32_t* goff = nullptr;  // ngnz + 1
+  int32_t* gent = nullptr;  // Q * p^3
+  double* gwd = nullptr;    // Q * p^3
+  float* gwf = nullptr;     // Q * p^3
   double* sig64 = nullptr;    // Q normalised (master copy)
   // near list
   int64_t npairs = 0;
@@ -192,6 +203,7 @@ int setup_near(scabem_op* op, cudaStream_t s);
 int setup_sigma_monomial(scabem_op* op, int nseg, const double* seg, cudaStream_t s);
 int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s);
 int setup_precond(scabem_op* op, cudaStream_t s);
+int setup_gather(scabem_op* op, cudaStream_t s);
 int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s);
 // apply.cu
 template <typename R>

@@ -257,7 +257,7 @@ __device__ void static_tri(const double* r, const double* v, const double* nrm, 
 // Near-field precorrection: one thread per (near pair, target point).  For
 // both media, exact potential moments (P0, P1, Q, C) of the source panel at
 // the target point minus the grid's version of the same interaction.
-// corr layout: [pair][a][medium][NCORR].
+// corr layout: [pair][NCORR component][target point][medium].
 template <typename RG>
 __global__ void k_near_corr(const double* __restrict__ tri, const double* __restrict__ qp, const double* __restrict__ qw,
                             const int32_t* __restrict__ base, const double* __restrict__ Ld,
@@ -398,10 +398,11 @@ __global__ void k_near_corr(const double* __restrict__ tri, const double* __rest
       o[4 + c] = Qe[c] - Qg[c];
       o[7 + c] = Ce[c] - Cg[c];
     }
-    const int64_t dst = ((j * q + a) * 2 + med) * NCORR;
+    // component-major within a pair: [pair][component][point][medium]
     for (int c = 0; c < NCORR; ++c) {
-      if (outd) outd[dst + c] = o[c];
-      if (outf) outf[dst + c] = mk((float)o[c].re, (float)o[c].im);
+      const int64_t dst = ((j * NCORR + c) * q + a) * 2 + med;
+      if (outd) outd[dst] = o[c];
+      if (outf) outf[dst] = mk((float)o[c].re, (float)o[c].im);
     }
   }
 }
@@ -434,6 +435,21 @@ __global__ void k_sigma_copy(const double* __restrict__ in, int64_t Q, double* _
   s64[i] = sig;
   if (sd) sd[i] = sig;
   if (sf) sf[i] = (float)sig;
+}
+
+// Stencil weight W_slot(point) = Lx[i] Ly[j] Lz[k] of every projection entry.
+__global__ void k_gather_weights(const int32_t* __restrict__ gent, const double* __restrict__ L, int64_t ne, int p,
+                                 double* __restrict__ wd, float* __restrict__ wf) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int p2 = p * p, p3 = p2 * p;
+  const int code = gent[e];
+  const int64_t Qi = code / p3;
+  const int sl = code - (int)Qi * p3;
+  const int i = sl / p2, j = (sl - i * p2) / p, k = sl - i * p2 - j * p;
+  const double W = L[(3 * Qi + 0) * p + i] * L[(3 * Qi + 1) * p + j] * L[(3 * Qi + 2) * p + k];
+  wd[e] = W;
+  wf[e] = (float)W;
 }
 
 // ---------------------------------------------------------------- block-diagonal preconditioner
@@ -676,6 +692,56 @@ __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __re
 }
 
 }  // namespace
+
+// Inverse of the projection stencil map: for every grid point, the list of
+// (quadrature point, stencil slot) pairs whose stencil covers it, in point
+// order (a counting sort on the host over the device-computed stencil bases).
+int setup_gather(scabem_op* op, cudaStream_t s) {
+  const int p = op->p, p3 = p * p * p;
+  const int64_t Q = op->Q;
+  const int64_t ng = (int64_t)op->n[0] * op->n[1] * op->n[2];
+  if (Q * p3 >= INT32_MAX || ng >= INT32_MAX) {
+    set_error("mesh too large for the projection map");
+    return SCABEM_E_ARG;
+  }
+  std::vector<int32_t> base(3 * Q);
+  CK(cudaMemcpyAsync(base.data(), op->base, sizeof(int32_t) * 3 * Q, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int n1 = op->n[1], n2 = op->n[2];
+  std::vector<int32_t> off(ng + 1, 0), ent(Q * p3);
+  auto grid_index = [&](int64_t qi, int sl) {
+    const int i = sl / (p * p), j = (sl / p) % p, k = sl % p;
+    return ((int64_t)(base[3 * qi] + i) * n1 + (base[3 * qi + 1] + j)) * n2 + (base[3 * qi + 2] + k);
+  };
+  for (int64_t qi = 0; qi < Q; ++qi)
+    for (int sl = 0; sl < p3; ++sl) ++off[grid_index(qi, sl) + 1];
+  for (int64_t g = 0; g < ng; ++g) off[g + 1] += off[g];
+  std::vector<int32_t> cur(off.begin(), off.end() - 1);
+  for (int64_t qi = 0; qi < Q; ++qi)
+    for (int sl = 0; sl < p3; ++sl) ent[cur[grid_index(qi, sl)]++] = (int32_t)(qi * p3 + sl);
+  // compact to the grid points that some stencil covers
+  std::vector<int32_t> pts, coff;
+  coff.push_back(0);
+  for (int64_t g = 0; g < ng; ++g)
+    if (off[g + 1] > off[g]) {
+      pts.push_back((int32_t)g);
+      coff.push_back(off[g + 1]);
+    }
+  op->ngnz = (int64_t)pts.size();
+  const int64_t ne = Q * p3;
+  CK(cudaMalloc(&op->gpt, sizeof(int32_t) * (pts.size() + 1)));
+  CK(cudaMalloc(&op->goff, sizeof(int32_t) * coff.size()));
+  CK(cudaMalloc(&op->gent, sizeof(int32_t) * ne));
+  CK(cudaMalloc(&op->gwd, sizeof(double) * ne));
+  CK(cudaMalloc(&op->gwf, sizeof(float) * ne));
+  CK(cudaMemcpyAsync(op->gpt, pts.data(), sizeof(int32_t) * pts.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(op->goff, coff.data(), sizeof(int32_t) * coff.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(op->gent, ent.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, s));
+  k_gather_weights<<<(int)cdiv(ne, 256), 256, 0, s>>>(op->gent, op->d.L, ne, p, op->gwd, op->gwf);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return SCABEM_OK;
+}
 
 int setup_precond(scabem_op* op, cudaStream_t s) {
   CK(cudaMemsetAsync(op->err, 0, sizeof(int), s));
