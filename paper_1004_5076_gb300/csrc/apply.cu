@@ -78,42 +78,85 @@ __global__ void k_qsrc(const cx<R>* __restrict__ summ, const double* __restrict_
   }
 }
 
-// K2b: projection as a gather.  Eight lanes per grid point that some stencil
-// covers share its (point, stencil slot) entries, sum W_slot(point) *
-// qsrc[point], and reduce by shuffles; lane 0 writes the 12 fields.  Points
-// no stencil covers stay zero from set-up.  The sum order is fixed, so the
+// K2b: projection as a gather.  Sixteen lanes per grid point that some
+// stencil covers share its entries (two in flight per lane), sum
+// W_slot(point) * qsrc[point] over 16-byte loads, and reduce the 24 real
+// sums by a reduce-scatter over shuffles (each round halves the values a
+// lane keeps); lanes with an even index then write three of them.  Points no
+// stencil covers stay zero from set-up.  The sum order is fixed, so the
 // result does not depend on thread timing.
+constexpr int GATHER_LANES = 16;
+
+// a[0..23] += w * (re, im of the 12 fields of row src)
+__device__ __forceinline__ void add_row(float* a, float w, const cx<float>* src) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float4 u = __ldg(s4 + i);
+    a[4 * i + 0] = fmaf(w, u.x, a[4 * i + 0]);
+    a[4 * i + 1] = fmaf(w, u.y, a[4 * i + 1]);
+    a[4 * i + 2] = fmaf(w, u.z, a[4 * i + 2]);
+    a[4 * i + 3] = fmaf(w, u.w, a[4 * i + 3]);
+  }
+}
+__device__ __forceinline__ void add_row(double* a, double w, const cx<double>* src) {
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const double2 u = __ldg(s2 + i);
+    a[2 * i + 0] = fma(w, u.x, a[2 * i + 0]);
+    a[2 * i + 1] = fma(w, u.y, a[2 * i + 1]);
+  }
+}
+
+// One reduce-scatter round over lanes l and l ^ M: the lane with bit M set
+// keeps the upper half of its H values, the other the lower half.
+template <int H, int M, typename R>
+__device__ __forceinline__ void rs_round(const R* a, R* b, bool up) {
+#pragma unroll
+  for (int i = 0; i < H / 2; ++i) {
+    const R send = up ? a[i] : a[i + H / 2];
+    const R keep = up ? a[i + H / 2] : a[i];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+  }
+}
+
 template <typename R>
 __global__ void k_gather(const cx<R>* __restrict__ qsrc, const int32_t* __restrict__ gpt,
-                         const int32_t* __restrict__ goff, const int32_t* __restrict__ gent, const R* __restrict__ gw,
-                         int64_t ngnz, int p3, int64_t ng, cx<R>* __restrict__ grids) {
-  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
-  const int l8 = threadIdx.x & 7;
-  cx<R> acc[NFIELD_IN];
+                         const int32_t* __restrict__ goff, const int32_t* __restrict__ gq, const R* __restrict__ gw,
+                         int64_t ngnz, int64_t ng, cx<R>* __restrict__ grids) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / GATHER_LANES;
+  const int l = threadIdx.x & (GATHER_LANES - 1);
+  R a[2 * NFIELD_IN];
 #pragma unroll
-  for (int f = 0; f < NFIELD_IN; ++f) acc[f] = czero<R>();
+  for (int f = 0; f < 2 * NFIELD_IN; ++f) a[f] = R(0);
   if (i < ngnz) {
     const int e1 = goff[i + 1];
-    for (int e = goff[i] + l8; e < e1; e += 8) {
-      const int64_t Qi = gent[e] / p3;
-      const R W = gw[e];
-      const cx<R>* src = qsrc + Qi * NFIELD_IN;
-#pragma unroll
-      for (int f = 0; f < NFIELD_IN; ++f) axpy(acc[f], W, src[f]);
+    for (int e = goff[i] + l; e < e1; e += 2 * GATHER_LANES) {
+      const int e2 = e + GATHER_LANES;
+      const int qa = gq[e];
+      const R wa = gw[e];
+      const int qb = e2 < e1 ? gq[e2] : qa;
+      const R wb = e2 < e1 ? gw[e2] : R(0);
+      add_row(a, wa, qsrc + (int64_t)qa * NFIELD_IN);
+      add_row(a, wb, qsrc + (int64_t)qb * NFIELD_IN);
     }
   }
   // every lane reaches the shuffles (no early exit above)
+  R b[12], c[6], d[3];
+  rs_round<24, 8>(a, b, l & 8);
+  rs_round<12, 4>(b, c, l & 4);
+  rs_round<6, 2>(c, d, l & 2);
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-    for (int f = 0; f < NFIELD_IN; ++f) {
-      acc[f].re += __shfl_xor_sync(0xffffffffu, acc[f].re, o);
-      acc[f].im += __shfl_xor_sync(0xffffffffu, acc[f].im, o);
-    }
-  if (i < ngnz && l8 == 0) {
+  for (int k = 0; k < 3; ++k) d[k] += __shfl_xor_sync(0xffffffffu, d[k], 1);
+  if (i < ngnz && (l & 1) == 0) {
     const int64_t g = gpt[i];
+    const int v0 = ((l & 8) ? 12 : 0) + ((l & 4) ? 6 : 0) + ((l & 2) ? 3 : 0);
 #pragma unroll
-    for (int f = 0; f < NFIELD_IN; ++f) grids[f * ng + g] = acc[f];
+    for (int k = 0; k < 3; ++k) {
+      const int v = v0 + k;  // real sum v = field v / 2, part v % 2
+      reinterpret_cast<R*>(grids + (v >> 1) * ng + g)[v & 1] = d[k];
+    }
   }
 }
 
@@ -399,9 +442,8 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   k_qsrc<R><<<(int)cdiv(Q, 128), 128, 0, s>>>(pd.summ, op->qp, op->qw, op->tri, Q, op->q, pd.qsrc);
   CK(cudaGetLastError());
   if (op->ngnz > 0) {
-    k_gather<R><<<(int)cdiv(op->ngnz * 8, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent,
-                                                             gather_weights<R>(op), op->ngnz,
-                                                             op->p * op->p * op->p, ng, pd.src);
+    k_gather<R><<<(int)cdiv(op->ngnz * GATHER_LANES, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent,
+                                                                        gather_weights<R>(op), op->ngnz, ng, pd.src);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);

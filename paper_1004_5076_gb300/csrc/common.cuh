@@ -111,7 +111,7 @@ struct scabem_mesh {
 template <typename R>
 struct PrecData {
   bool built = false;
-  cx<R>* ghat[2] = {nullptr, nullptr};  // octant spectra, scaled by 1/(P0 P1 P2)
+  cx<R>* ghat[2] = {nullptr, nullptr};  // octant spectra [q0][q2][q1], scaled by 1/(P0 P1 P2)
   cx<R>* near = nullptr;                // [npairs][NCORR][q][2]
   cx<R>* tw[3] = {nullptr, nullptr, nullptr};  // forward twiddles per axis length
   R* L = nullptr;                       // Q * 3 * p stencil weights
@@ -151,9 +151,9 @@ struct scabem_op {
   double* qw = nullptr;       // Q
   int32_t* base = nullptr;    // Q * 3
   // projection as a gather over the ngnz grid points that some stencil
-  // covers: point gpt[i] sums entries goff[i] .. goff[i+1]-1 of gent, each
-  // (quadrature point * p^3 + stencil slot), in point order; gwd / gwf hold
-  // the entries' stencil weights
+  // covers: point gpt[i] sums entries goff[i] .. goff[i+1]-1, entry e being
+  // quadrature point gent[e] with stencil weight gwd[e] / gwf[e]; entries
+  // are in (quadrature point, stencil slot) order within a grid point
   int64_t ngnz = 0;
   int32_t* gpt = nullptr;   // ngnz
   int32_t* goff = nullptr;  // ngnz + 1

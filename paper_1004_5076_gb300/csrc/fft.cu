@@ -340,10 +340,10 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_planes(const cx<R>* __restric
     for_warp_lines<L1>(P2, [&](int k2, int tl, bool act) {
       const cx<R>* scol = S + k2;
       cx<R>* wcol = W + k2;
-      const cx<R>* gcol = g0 + min(k2, P2 - k2);
+      const cx<R>* gcol = g0 + min(k2, P2 - k2) * h1;
       wline_fft<R, L1, 0, 1>(
           wcol, LS, tl, act, t1,
-          [&](int e) { return sgn * (scol[e * LS] * gcol[min(e, P1 - e) * h2]); },
+          [&](int e) { return sgn * (scol[e * LS] * gcol[min(e, P1 - e)]); },
           [&](int e, cx<R> v) {
             if (e < n1) wcol[e * LS] = v;
           });
@@ -382,6 +382,163 @@ PlanesFn<R> planes_row(int l2) {
     case 6: return planes_fn<R, L1, 6>();
     case 7: return planes_fn<R, L1, 7>();
     default: return nullptr;
+  }
+}
+
+// ---------------------------------------------------------------- stage B, 64 x 64 planes
+// The same plane step specialised to P1 = P2 = 64 (n1 = n2 = 32), the usual
+// cross-section of a guide grid.  A 64-point line belongs to eight lanes:
+// lane t holds elements t + 8r, transforms over r (radix 8), multiplies by
+// w64^(t k) and swaps through a per-line scratch so that lane k then holds
+// index k of every t; a second radix-8 transform leaves elements k + 8m in
+// lane k.  That is the layout the inverse transform starts from, so the
+// forward column transform, the Green multiply of each output and the
+// inverse column transform run back to back in registers.  Half-zero inputs
+// and half-kept outputs use pruned radix-8 transforms.
+//
+// Shared memory (8-byte words, 16 banks of 8 bytes per half-warp): a plane
+// holds rows 0..31 with row i, column k at i*64 + (k ^ g(i)), g(i) =
+// 2(i mod 8) ^ 8(i mod 2); row accesses (two rows per half-warp) and column
+// accesses (eight rows of two columns per half-warp) are then free of bank
+// conflicts.  The per-line scratch puts element (t, k) at 8t + (k + t) mod 8,
+// 72 words per line, for the same reason.
+constexpr int P64_THREADS = 256;  // 8 warps x 4 lines of 8 lanes: one pass over 32 rows
+constexpr int P64_SCR = 72;
+
+__device__ __forceinline__ int swz64(int i, int k) { return i * 64 + (k ^ ((2 * (i & 7)) ^ ((i & 1) << 3))); }
+
+// radix-8 transform of v[0..3] with v[4..7] = 0
+template <typename R, int DIR>
+__device__ __forceinline__ void dft8_hin(cx<R>* v) {
+  const R s = R(0.70710678118654752440);
+  cx<R> e0 = v[0], e1 = v[1], e2 = v[2], e3 = v[3];
+  cx<R> o0 = v[0], o1 = s * (v[1] + rot<R, DIR>(v[1])), o2 = rot<R, DIR>(v[2]), o3 = s * (rot<R, DIR>(v[3]) - v[3]);
+  dft4<R, DIR>(e0, e1, e2, e3);
+  dft4<R, DIR>(o0, o1, o2, o3);
+  v[0] = e0;
+  v[2] = e1;
+  v[4] = e2;
+  v[6] = e3;
+  v[1] = o0;
+  v[3] = o1;
+  v[5] = o2;
+  v[7] = o3;
+}
+
+// radix-8 transform keeping outputs 0..3
+template <typename R, int DIR>
+__device__ __forceinline__ void dft8_hout(cx<R>* v) {
+  cx<R> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  cx<R> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<R, DIR>(e0, e1, e2, e3);
+  dft4<R, DIR>(o0, o1, o2, o3);
+  const R s = R(0.70710678118654752440);
+  v[0] = e0 + o0;
+  v[1] = e1 + s * (o1 + rot<R, DIR>(o1));
+  v[2] = e2 + rot<R, DIR>(o2);
+  v[3] = e3 + s * (rot<R, DIR>(o3) - o3);
+}
+
+// 64-point transform of one line over its eight lanes (lane t, v[r] =
+// element t + 8r on entry, element t + 8m in v[m] on exit); w[k] = w64^(t k).
+template <typename R, int DIR, bool HALF_IN, bool HALF_OUT>
+__device__ __forceinline__ void line64(cx<R>* v, const cx<R>* w, cx<R>* scr, int t) {
+  if (HALF_IN)
+    dft8_hin<R, DIR>(v);
+  else
+    dft<R, 8, DIR>(v);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) v[k] = v[k] * (DIR < 0 ? w[k] : conj(w[k]));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) scr[t * 8 + ((k + t) & 7)] = v[k];
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = scr[i * 8 + ((t + i) & 7)];
+  __syncwarp();
+  if (HALF_OUT)
+    dft8_hout<R, DIR>(v);
+  else
+    dft<R, 8, DIR>(v);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
+    k_planes64(const cx<R>* __restrict__ A, cx<R>* __restrict__ B, const cx<R>* __restrict__ ghE,
+               const cx<R>* __restrict__ ghI, int P0, const cx<R>* __restrict__ tw64) {
+  constexpr int NP = 32, H = 33;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* W0 = reinterpret_cast<cx<R>*>(smem_raw);  // forward rows, then output 0
+  cx<R>* W1 = W0 + NP * 64;                        // output 1
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane & 7, sub = lane >> 3;
+  cx<R>* scr = W1 + NP * 64 + (warp * 4 + sub) * P64_SCR;
+  cx<R> w[8];
+  w[0] = mk(R(1), R(0));
+#pragma unroll
+  for (int k = 1; k < 8; ++k) w[k] = tw64[t * k];
+  const int k0 = blockIdx.x, f = blockIdx.y;
+  const int i1 = warp * 4 + sub;  // the row this lane works on in the row passes
+  {
+    // forward rows: the 32 physical rows, elements >= 32 are zero
+    const cx<R>* src = A + ((int64_t)f * P0 + k0) * (NP * NP) + i1 * NP;
+    cx<R> v[8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) v[r] = src[t + 8 * r];
+    line64<R, -1, true, false>(v, w, scr, t);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) W0[swz64(i1, t + 8 * m)] = v[m];
+  }
+  __syncthreads();
+
+  // source field -> output fields, media and signs (as in k_planes)
+  const int nout = f >= 8 ? 2 : 1;
+  const int q0 = min(k0, P0 - k0);
+  const cx<R>* ga = (f >= 4 && f < 8) ? ghI : ghE;  // output 0
+  const int foa = f < 4 ? f : (f < 8 ? 8 + (f - 4) : 4 + (f - 8));
+  const int fob = 12 + (f - 8);  // output 1 (f >= 8), interior medium, sign -1
+  ga += (int64_t)q0 * H * H;
+  const cx<R>* gb = ghI + (int64_t)q0 * H * H;
+
+  // columns: forward transform (rows >= 32 zero), Green multiply, inverse
+  // transform, rows < 32 kept in W0 / W1 (a column is read and rewritten by
+  // the same eight lanes)
+#pragma unroll 1
+  for (int it = 0; it < 2; ++it) {
+    const int c = it * 32 + warp * 4 + sub;
+    cx<R> x[8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) x[r] = W0[swz64(t + 8 * r, c)];
+    line64<R, -1, true, false>(x, w, scr, t);
+    const int cg = min(c, 64 - c) * H;
+#pragma unroll 1
+    for (int o = 0; o < nout; ++o) {
+      const cx<R>* gp = (o ? gb : ga) + cg;
+      cx<R> v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int e = t + 8 * m;
+        v[m] = x[m] * gp[min(e, 64 - e)];
+        if (o) v[m] = -v[m];
+      }
+      line64<R, 1, false, true>(v, w, scr, t);
+      cx<R>* Wo = o ? W1 : W0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Wo[swz64(t + 8 * m, c)] = v[m];
+    }
+  }
+  __syncthreads();
+
+  // inverse rows, the 32 physical columns written to global memory
+#pragma unroll 1
+  for (int o = 0; o < nout; ++o) {
+    const cx<R>* Wo = o ? W1 : W0;
+    cx<R> v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = Wo[swz64(i1, t + 8 * r)];
+    line64<R, 1, false, true>(v, w, scr, t);
+    cx<R>* dst = B + ((int64_t)(o ? fob : foa) * P0 + k0) * (NP * NP) + i1 * NP;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) dst[t + 8 * m] = v[m];
   }
 }
 
@@ -489,6 +646,18 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   CK(cudaGetLastError());
   prof_mark(op, s);
   // stage B
+  if (P1 == 64 && P2 == 64) {
+    const size_t sm = ((size_t)2 * 32 * 64 + (size_t)(P64_THREADS / 8) * P64_SCR) * sizeof(cx<R>);
+    CK(cudaFuncSetAttribute(k_planes64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_planes64<R><<<dim3(P0, NFIELD_IN), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1]);
+    CK(cudaGetLastError());
+    prof_mark(op, s);
+    CK(cudaFuncSetAttribute(k_axis0<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+    k_axis0<R, 1><<<dim3((unsigned)cdiv(C, cb), NFIELD_OUT), FFT_THREADS, sm0, s>>>(pd.stB, pd.grid, P0, n0, P0, C,
+                                                                                    cb, pd.tw[0]);
+    CK(cudaGetLastError());
+    return SCABEM_OK;
+  }
   const size_t sm1 = ((size_t)P1 + P2 + 2 * (size_t)P1 * (P2 + 2)) * sizeof(cx<R>);
   PlanesFn<R> fn = planes_kernel<R>(ilog2(P1), ilog2(P2));
   if (!fn) {

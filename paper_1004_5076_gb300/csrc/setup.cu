@@ -183,8 +183,10 @@ __global__ void k_octant(const cx<double>* __restrict__ F, cx<double>* __restric
   const double sc = 1.0 / ((double)P0 * P1 * P2);
   cx<double> v = F[((int64_t)q0 * P1 + q1) * P2 + q2];
   v = sc * v;
-  if (od) od[idx] = v;
-  if (of) of[idx] = mk((float)v.re, (float)v.im);
+  // stored [q0][q2][q1]: the plane kernels walk q1 along their lanes
+  const int64_t o = ((int64_t)q0 * h2 + q2) * h1 + q1;
+  if (od) od[o] = v;
+  if (of) of[o] = mk((float)v.re, (float)v.im);
 }
 
 // ---------------------------------------------------------------- near list
@@ -437,8 +439,9 @@ __global__ void k_sigma_copy(const double* __restrict__ in, int64_t Q, double* _
   if (sf) sf[i] = (float)sig;
 }
 
-// Stencil weight W_slot(point) = Lx[i] Ly[j] Lz[k] of every projection entry.
-__global__ void k_gather_weights(const int32_t* __restrict__ gent, const double* __restrict__ L, int64_t ne, int p,
+// Stencil weight W_slot(point) = Lx[i] Ly[j] Lz[k] of every projection entry;
+// the entry code (point * p^3 + slot) is then replaced by the point index.
+__global__ void k_gather_weights(int32_t* __restrict__ gent, const double* __restrict__ L, int64_t ne, int p,
                                  double* __restrict__ wd, float* __restrict__ wf) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= ne) return;
@@ -450,6 +453,7 @@ __global__ void k_gather_weights(const int32_t* __restrict__ gent, const double*
   const double W = L[(3 * Qi + 0) * p + i] * L[(3 * Qi + 1) * p + j] * L[(3 * Qi + 2) * p + k];
   wd[e] = W;
   wf[e] = (float)W;
+  gent[e] = (int32_t)Qi;
 }
 
 // ---------------------------------------------------------------- block-diagonal preconditioner

@@ -47,6 +47,13 @@ def guide_small(nx=40, ny=6, nz=3, length=2.0, absorber=0.6, padded=(64, 32, 16)
     return Case("guide_small", m, (12.1, 1.0, 2.1, 1.0, 1.55), grid, q, r_near, sigma_segments=segs, seed=12)
 
 
+def guide_planes64():
+    """guide_small on a 64 x 64 x 64 transform grid (64 x 64 cross-section planes)."""
+    c = guide_small(padded=(64, 64, 64))
+    c.name = "guide_planes64"
+    return c
+
+
 def plate_thin(padded=(32, 16, 8), p=2, q=3, r_near=0.3):
     """Flat thin box with a one-sided absorber: exercises p = 2 stencils and the 3-point rule."""
     m = synth.waveguide(1.5, 0.3, 0.1, 10, 3, 1, 0.4, 0.0)

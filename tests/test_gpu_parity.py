@@ -72,7 +72,7 @@ def oracle_apply(case, g, med, sig, x, key):
     return _oracle_y[key]
 
 
-CASES = [cases.sphere_mixed, cases.guide_small, cases.plate_thin]
+CASES = [cases.sphere_mixed, cases.guide_small, cases.plate_thin, cases.guide_planes64]
 
 
 @pytest.mark.parametrize("mk", CASES, ids=lambda f: f.__name__)
