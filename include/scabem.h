@@ -144,7 +144,11 @@ int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sigma);
  * (host buffers are staged through device copies on `stream`).  prec selects
  * complex64 or complex128 arithmetic; the operator must have been built with
  * that precision.  Stream-ordered: returns after enqueueing (device buffers)
- * or after completion (host buffers). */
+ * or after completion (host buffers).  The near-field stage waits on its
+ * own bulk copies with a time limit (about a second); if one expires, that
+ * launch's y is not valid and the next scabem_apply or scabem_solve on the
+ * operator returns SCABEM_E_TIMEOUT (scabem_solve also reports it for its own
+ * launches). */
 int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream);
 
 /* Excitation (Sec. II): kind 0 = plane wave (dir, pol), 1 = electric dipole

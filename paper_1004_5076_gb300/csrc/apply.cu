@@ -171,13 +171,38 @@ const double* gather_weights<double>(scabem_op* op) {
   return op->gwd;
 }
 
-// Interpolated potentials of one medium at quadrature point Qi.  Record
-// (NREC): A(3) phi grad phi(3) curl A(3) F(3) psi grad psi(3) curl F(3).
-template <typename R>
-__device__ __forceinline__ void interp_point(const cx<R>* __restrict__ grids, const int32_t* __restrict__ base,
+// The four potentials of one (grid point, medium, group) (32 contiguous bytes
+// in complex64).
+__device__ __forceinline__ void load_group(const cx<float>* p, cx<float>* v) {
+  const float4 u0 = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 u1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = mk(u0.x, u0.y);
+  v[1] = mk(u0.z, u0.w);
+  v[2] = mk(u1.x, u1.y);
+  v[3] = mk(u1.z, u1.w);
+}
+__device__ __forceinline__ void load_group(const cx<double>* p, cx<double>* v) {
+#pragma unroll
+  for (int f = 0; f < 4; ++f) v[f] = p[f];
+}
+
+// a += s * b on (re, im) as one packed FP32x2 FMA in complex64.
+__device__ __forceinline__ void axpy2(cx<float>& a, float s, cx<float> b) {
+  const float2 r = __ffma2_rn(make_float2(s, s), make_float2(b.re, b.im), make_float2(a.re, a.im));
+  a = mk(r.x, r.y);
+}
+__device__ __forceinline__ void axpy2(cx<double>& a, double s, cx<double> b) { axpy(a, s, b); }
+
+// Interpolated potentials of one medium at quadrature point Qi, group h of
+// the record (NREC = 2 x 10): h = 0 A(3) phi grad phi(3) curl A(3) from the
+// J fields, h = 1 F(3) psi grad psi(3) curl F(3) from the M fields.  The
+// grid is point-major: point g holds its 16 potentials at grids[16 g ..].
+template <typename R, int p>
+__device__ __forceinline__ void interp_group(const cx<R>* __restrict__ grids, const int32_t* __restrict__ base,
                                              const R* __restrict__ L, const R* __restrict__ dL, int64_t Qi, int med,
-                                             int p, int64_t ng, int n1, int n2, cx<R>* rec) {
-  R Lx[MAXP], Ly[MAXP], Lz[MAXP], dx[MAXP], dy[MAXP], dz[MAXP];
+                                             int h, int n1, int n2, cx<R>* r) {
+  R Lx[p], Ly[p], Lz[p], dx[p], dy[p], dz[p];
+#pragma unroll
   for (int i = 0; i < p; ++i) {
     Lx[i] = L[(3 * Qi + 0) * p + i];
     Ly[i] = L[(3 * Qi + 1) * p + i];
@@ -187,106 +212,103 @@ __device__ __forceinline__ void interp_point(const cx<R>* __restrict__ grids, co
     dz[i] = dL[(3 * Qi + 2) * p + i];
   }
   const int b0 = base[3 * Qi], b1 = base[3 * Qi + 1], b2 = base[3 * Qi + 2];
-  // two groups of 4 fields: (A, phi) of the J set, then (F, psi) of the M set
-  for (int h = 0; h < 2; ++h) {
-    cx<R> v[4], gx[4], gy[4], gz[4];
-    for (int f = 0; f < 4; ++f) v[f] = gx[f] = gy[f] = gz[f] = czero<R>();
-    const cx<R>* gm = grids + (int64_t)(med * 8 + 4 * h) * ng;
-    for (int i = 0; i < p; ++i)
-      for (int j = 0; j < p; ++j) {
-        const R wxy = Lx[i] * Ly[j], dxy = dx[i] * Ly[j], xdy = Lx[i] * dy[j];
-        const int64_t rowi = ((int64_t)(b0 + i) * n1 + (b1 + j)) * n2 + b2;
-        for (int k = 0; k < p; ++k) {
-          const R w = wxy * Lz[k], wx = dxy * Lz[k], wy = xdy * Lz[k], wz = wxy * dz[k];
+  cx<R> v[4], gx[4], gy[4], gz[4];
+  for (int f = 0; f < 4; ++f) v[f] = gx[f] = gy[f] = gz[f] = czero<R>();
+  const cx<R>* gm = grids + 4 * (med * 2 + h);
 #pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            const cx<R> gv = gm[f * ng + rowi + k];
-            axpy(v[f], w, gv);
-            axpy(gx[f], wx, gv);
-            axpy(gy[f], wy, gv);
-            axpy(gz[f], wz, gv);
-          }
+  for (int i = 0; i < p; ++i)
+#pragma unroll
+    for (int j = 0; j < p; ++j) {
+      const R wxy = Lx[i] * Ly[j], dxy = dx[i] * Ly[j], xdy = Lx[i] * dy[j];
+      const int64_t rowi = ((int64_t)(b0 + i) * n1 + (b1 + j)) * n2 + b2;
+#pragma unroll
+      for (int k = 0; k < p; ++k) {
+        const R w = wxy * Lz[k], wx = dxy * Lz[k], wy = xdy * Lz[k], wz = wxy * dz[k];
+        cx<R> gv[4];
+        load_group(gm + (rowi + k) * NFIELD_OUT, gv);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          axpy2(v[f], w, gv[f]);
+          axpy2(gx[f], wx, gv[f]);
+          axpy2(gy[f], wy, gv[f]);
+          axpy2(gz[f], wz, gv[f]);
         }
       }
-    cx<R>* r = rec + 10 * h;
-    r[0] = v[0];
-    r[1] = v[1];
-    r[2] = v[2];
-    r[3] = v[3];
-    r[4] = gx[3];
-    r[5] = gy[3];
-    r[6] = gz[3];
-    r[7] = gy[2] - gz[1];
-    r[8] = gz[0] - gx[2];
-    r[9] = gx[1] - gy[0];
-  }
+    }
+  r[0] = v[0];
+  r[1] = v[1];
+  r[2] = v[2];
+  r[3] = v[3];
+  r[4] = gx[3];
+  r[5] = gy[3];
+  r[6] = gz[3];
+  r[7] = gy[2] - gz[1];
+  r[8] = gz[0] - gx[2];
+  r[9] = gx[1] - gy[0];
 }
 
-// One near record (dP0, dP1, dQ, dC) applied to the J and the M source of a
-// pair: A += a dP1 - beta dP0, phi += 2a dP0, grad phi += 2a dQ,
-// curl A += a dC - dQ x beta.
+// a += x * B in complex64 with the factor B kept as (B, j B): two packed
+// FP32x2 FMAs, (x.re, x.re) * B + (x.im, x.im) * jB.
+struct Fac2 {
+  float2 b, jb;
+};
+__device__ __forceinline__ Fac2 fac2(cx<float> v, float s) {
+  Fac2 f;
+  f.b = make_float2(s * v.re, s * v.im);
+  f.jb = make_float2(-s * v.im, s * v.re);
+  return f;
+}
+__device__ __forceinline__ void cmac2(float2& acc, cx<float> x, const Fac2& f) {
+  acc = __ffma2_rn(make_float2(x.re, x.re), f.b, acc);
+  acc = __ffma2_rn(make_float2(x.im, x.im), f.jb, acc);
+}
+
+// complex64 form of near_part (the same sums, packed FP32x2 arithmetic)
+__device__ __forceinline__ void near_part(const cx<float>* d, const cx<float>* sv, cx<float>* acc) {
+  const Fac2 al = fac2(sv[0], 1.f), al2 = fac2(sv[0], 2.f);
+  const Fac2 be[3] = {fac2(sv[1], 1.f), fac2(sv[2], 1.f), fac2(sv[3], 1.f)};
+  const Fac2 nbe[3] = {fac2(sv[1], -1.f), fac2(sv[2], -1.f), fac2(sv[3], -1.f)};
+  float2 A[NREC / 2];
+#pragma unroll
+  for (int c = 0; c < NREC / 2; ++c) A[c] = make_float2(acc[c].re, acc[c].im);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cmac2(A[c], d[1 + c], al);     // A += a dP1
+    cmac2(A[c], d[0], nbe[c]);     //    - beta dP0
+    cmac2(A[4 + c], d[4 + c], al2);  // grad phi += 2a dQ
+    cmac2(A[7 + c], d[7 + c], al);   // curl A += a dC
+  }
+  cmac2(A[3], d[0], al2);  // phi += 2a dP0
+  // curl A -= dQ x beta
+  cmac2(A[7], d[5], nbe[2]);
+  cmac2(A[7], d[6], be[1]);
+  cmac2(A[8], d[6], nbe[0]);
+  cmac2(A[8], d[4], be[2]);
+  cmac2(A[9], d[4], nbe[1]);
+  cmac2(A[9], d[5], be[0]);
+#pragma unroll
+  for (int c = 0; c < NREC / 2; ++c) acc[c] = mk(A[c].x, A[c].y);
+}
+
+// One near record (dP0, dP1, dQ, dC) applied to source summary sv (a, beta):
+// A += a dP1 - beta dP0, phi += 2a dP0, grad phi += 2a dQ,
+// curl A += a dC - dQ x beta (the same for F, psi of an M source).
 template <typename R>
-__device__ __forceinline__ void near_accumulate(const cx<R>* d, const cx<R>* sj, const cx<R>* sm, R sgnm,
-                                                cx<R>* accJ, cx<R>* accM) {
+__device__ __forceinline__ void near_part(const cx<R>* d, const cx<R>* sv, cx<R>* acc) {
   const cx<R> d0 = d[0];
+  const cx<R> al = sv[0], al2 = R(2) * al;
+  const cx<R> be[3] = {sv[1], sv[2], sv[3]};
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const cx<R>* sv = h == 0 ? sj : sm;
-    const R sg = h == 0 ? R(1) : sgnm;
-    cx<R>* acc = h == 0 ? accJ : accM;
-    const cx<R> al = sg * sv[0];
-    const cx<R> be0 = sg * sv[1], be1 = sg * sv[2], be2 = sg * sv[3];
-    const cx<R> be[3] = {be0, be1, be2};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      cfma(acc[c], al, d[1 + c]);
-      acc[c] -= be[c] * d0;
-      cfma(acc[4 + c], R(2) * al, d[4 + c]);
-      cfma(acc[7 + c], al, d[7 + c]);
-    }
-    cfma(acc[3], R(2) * al, d0);
-    acc[7] -= d[5] * be2 - d[6] * be1;  // - dQ x beta
-    acc[8] -= d[6] * be0 - d[4] * be2;
-    acc[9] -= d[4] * be1 - d[5] * be0;
+  for (int c = 0; c < 3; ++c) {
+    cfma(acc[c], al, d[1 + c]);
+    acc[c] -= be[c] * d0;
+    cfma(acc[4 + c], al2, d[4 + c]);
+    cfma(acc[7 + c], al, d[7 + c]);
   }
-}
-
-// Near-field precorrection of one (target point a of triangle t, medium).
-template <typename R>
-__device__ __forceinline__ void near_point(const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
-                                           const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ,
-                                           int64_t t, int a, int med, int q, cx<R>* rec) {
-  const R sgnm = med == 1 ? R(-1) : R(1);  // interior M = -M
-  cx<R>* accJ = rec;
-  cx<R>* accM = rec + 10;
-  const int j0 = noff[t], j1 = noff[t + 1];
-  // records are [pair][component][point][medium]: the 2q threads of a
-  // triangle read each component as one contiguous run
-  const int cs = 2 * q;                     // component stride
-  const int64_t stride = (int64_t)NCORR * cs;  // complex per pair
-  const cx<R>* base = corr + (int64_t)a * 2 + med;
-  int j = j0;
-  for (; j + 1 < j1; j += 2) {
-    cx<R> dA[NCORR], dB[NCORR];
-    const int64_t sA = nsrc[j], sB = nsrc[j + 1];
-    const cx<R>* pA = base + (int64_t)j * stride;
-    const cx<R>* pB = pA + stride;
-#pragma unroll
-    for (int c = 0; c < NCORR; ++c) {
-      dA[c] = pA[c * cs];
-      dB[c] = pB[c * cs];
-    }
-    near_accumulate(dA, summ + (3 * sA + med) * 4, summ + (3 * sA + 2) * 4, sgnm, accJ, accM);
-    near_accumulate(dB, summ + (3 * sB + med) * 4, summ + (3 * sB + 2) * 4, sgnm, accJ, accM);
-  }
-  if (j < j1) {
-    cx<R> dA[NCORR];
-    const int64_t sA = nsrc[j];
-    const cx<R>* pA = base + (int64_t)j * stride;
-#pragma unroll
-    for (int c = 0; c < NCORR; ++c) dA[c] = pA[c * cs];
-    near_accumulate(dA, summ + (3 * sA + med) * 4, summ + (3 * sA + 2) * 4, sgnm, accJ, accM);
-  }
+  cfma(acc[3], al2, d0);
+  acc[7] -= d[5] * be[2] - d[6] * be[1];
+  acc[8] -= d[6] * be[0] - d[4] * be[2];
+  acc[9] -= d[4] * be[1] - d[5] * be[0];
 }
 
 template <typename R>
@@ -294,15 +316,15 @@ __device__ __forceinline__ cx<R> dot3(const R* X, const cx<R>* V) {
   return X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
 }
 
-// Tested values of local edge kk of triangle t from the records of its
-// points (recs[(a*2 + medium)*NREC]): type 0 <X, E_e - E_i>, 1 <X, H_e - H_i>
-// (weak forms), 2 Eq. 13, 3 Eq. 14.
+// Weighted contributions of quadrature point a to the tested values of local
+// edge kk of triangle t, from the point's records (recs[medium*NREC]):
+// type 0 <X, E_e - E_i>, 1 <X, H_e - H_i> (weak forms), 2 Eq. 13, 3 Eq. 14.
 template <typename R>
-__device__ __forceinline__ void test_edge(const cx<R>* recs, const cx<R>* __restrict__ summ,
-                                          const double* __restrict__ tri, const double* __restrict__ cX,
-                                          const double* __restrict__ qp, const double* __restrict__ qw,
-                                          const R* __restrict__ sig, int64_t t, int kk, int q, R ke, R ki, R ze,
-                                          R zi, cx<R>* out) {
+__device__ __forceinline__ void test_point(const cx<R>* recs, const cx<R>* __restrict__ summ,
+                                           const double* __restrict__ tri, const double* __restrict__ cX,
+                                           const double* __restrict__ qp, const double* __restrict__ qw,
+                                           const R* __restrict__ sig, int64_t t, int kk, int a, int q, R ke, R ki,
+                                           R ze, R zi, cx<R>* out) {
   const double* g = tri + 16 * t;
   const R cxk = (R)cX[3 * t + kk];
   const R divX = R(2) * cxk;
@@ -310,101 +332,241 @@ __device__ __forceinline__ void test_edge(const cx<R>* recs, const cx<R>* __rest
   const cx<R>* se = summ + (3 * t + 0) * 4;
   const cx<R>* si = summ + (3 * t + 1) * 4;
   const cx<R>* sM = summ + (3 * t + 2) * 4;
-  cx<R> v0 = czero<R>(), v1 = v0, v2 = v0, v3 = v0;
   const R kl[2] = {ke, ki}, zl[2] = {ze, zi};
-  for (int a = 0; a < q; ++a) {
-    const int64_t Qa = t * q + a;
-    const R w = (R)qw[Qa];
-    const R sg = sig[Qa];
-    R X[3], rel[3];
-    for (int c = 0; c < 3; ++c) {
-      X[c] = cxk * (R)(qp[3 * Qa + c] - g[3 * kk + c]);
-      rel[c] = (R)(qp[3 * Qa + c] - g[9 + c]);
-    }
-    cx<R> WE[3], WH[3], E[2][3];
-    cx<R> wE = czero<R>(), wH = czero<R>();
-    for (int c = 0; c < 3; ++c) WE[c] = WH[c] = czero<R>();
-    for (int m = 0; m < 2; ++m) {
-      const cx<R>* r = recs + (a * 2 + m) * NREC;
-      const R k = kl[m], z = zl[m];
-      const R sgm = m == 0 ? R(1) : R(-1);
-      const cx<R> phi = r[3], psi = r[13];
-      wE += (sgm * z / k) * mulj(phi);
-      wH += (sgm / (k * z)) * mulj(psi);
-      for (int c = 0; c < 3; ++c) {
-        const cx<R> A = r[c], gphi = r[4 + c], cA = r[7 + c], F = r[10 + c], cF = r[17 + c];
-        const cx<R> jA = mulj(A), jF = mulj(F);
-        WE[c] += sgm * ((-z * k) * jA - cF);
-        WH[c] += sgm * (cA - (k / z) * jF);
-        E[m][c] = -z * (k * jA + (R(1) / k) * mulj(gphi)) - cF;
-      }
-    }
-    cx<R> Js[3], M[3];  // J_e + J_i and M of this triangle at the point
-    for (int c = 0; c < 3; ++c) {
-      Js[c] = rel[c] * se[0] - se[1 + c] + rel[c] * si[0] - si[1 + c];
-      M[c] = rel[c] * sM[0] - sM[1 + c];
-    }
-    // n x (J_e + J_i), n x M and n x X
-    cx<R> nJ[3], nM[3];
-    nJ[0] = nrm[1] * Js[2] - nrm[2] * Js[1];
-    nJ[1] = nrm[2] * Js[0] - nrm[0] * Js[2];
-    nJ[2] = nrm[0] * Js[1] - nrm[1] * Js[0];
-    nM[0] = nrm[1] * M[2] - nrm[2] * M[1];
-    nM[1] = nrm[2] * M[0] - nrm[0] * M[2];
-    nM[2] = nrm[0] * M[1] - nrm[1] * M[0];
-    const R nX[3] = {nrm[1] * X[2] - nrm[2] * X[1], nrm[2] * X[0] - nrm[0] * X[2], nrm[0] * X[1] - nrm[1] * X[0]};
-    const cx<R> XJ = dot3(X, Js), XnM = dot3(X, nM);
-    const cx<R> hterm = dot3(X, WH) + divX * wH;
-    v0 += w * (dot3(X, WE) + divX * wE);
-    v1 += w * hterm;
-    // Eq. 13: <X, dH> - <sigma n x X, E_e^+>, side limits (J_e+J_i) x n / 2 and sigma M / 2
-    v2 += w * (hterm - R(0.5) * dot3(X, nJ) - sg * dot3(nX, E[0]) - (R(0.5) * sg) * dot3(X, M));
-    // Eq. 14: <X, J_e + J_i> - <sigma X, E_i^->, side limit n x M / 2
-    v3 += w * (XJ - sg * dot3(X, E[1]) - (R(0.5) * sg) * XnM);
+  const int64_t Qa = t * q + a;
+  const R w = (R)qw[Qa];
+  const R sg = sig[Qa];
+  R X[3], rel[3];
+  for (int c = 0; c < 3; ++c) {
+    X[c] = cxk * (R)(qp[3 * Qa + c] - g[3 * kk + c]);
+    rel[c] = (R)(qp[3 * Qa + c] - g[9 + c]);
   }
-  out[0] = v0;
-  out[1] = v1;
-  out[2] = v2;
-  out[3] = v3;
+  cx<R> WE[3], WH[3], E[2][3];
+  cx<R> wE = czero<R>(), wH = czero<R>();
+  for (int c = 0; c < 3; ++c) WE[c] = WH[c] = czero<R>();
+  for (int m = 0; m < 2; ++m) {
+    const cx<R>* r = recs + m * NREC;
+    const R k = kl[m], z = zl[m];
+    const R sgm = m == 0 ? R(1) : R(-1);
+    const cx<R> phi = r[3], psi = r[13];
+    wE += (sgm * z / k) * mulj(phi);
+    wH += (sgm / (k * z)) * mulj(psi);
+    for (int c = 0; c < 3; ++c) {
+      const cx<R> A = r[c], gphi = r[4 + c], cA = r[7 + c], F = r[10 + c], cF = r[17 + c];
+      const cx<R> jA = mulj(A), jF = mulj(F);
+      WE[c] += sgm * ((-z * k) * jA - cF);
+      WH[c] += sgm * (cA - (k / z) * jF);
+      E[m][c] = -z * (k * jA + (R(1) / k) * mulj(gphi)) - cF;
+    }
+  }
+  cx<R> Js[3], M[3];  // J_e + J_i and M of this triangle at the point
+  for (int c = 0; c < 3; ++c) {
+    Js[c] = rel[c] * se[0] - se[1 + c] + rel[c] * si[0] - si[1 + c];
+    M[c] = rel[c] * sM[0] - sM[1 + c];
+  }
+  // n x (J_e + J_i), n x M and n x X
+  cx<R> nJ[3], nM[3];
+  nJ[0] = nrm[1] * Js[2] - nrm[2] * Js[1];
+  nJ[1] = nrm[2] * Js[0] - nrm[0] * Js[2];
+  nJ[2] = nrm[0] * Js[1] - nrm[1] * Js[0];
+  nM[0] = nrm[1] * M[2] - nrm[2] * M[1];
+  nM[1] = nrm[2] * M[0] - nrm[0] * M[2];
+  nM[2] = nrm[0] * M[1] - nrm[1] * M[0];
+  const R nX[3] = {nrm[1] * X[2] - nrm[2] * X[1], nrm[2] * X[0] - nrm[0] * X[2], nrm[0] * X[1] - nrm[1] * X[0]};
+  const cx<R> XJ = dot3(X, Js), XnM = dot3(X, nM);
+  const cx<R> hterm = dot3(X, WH) + divX * wH;
+  out[0] = w * (dot3(X, WE) + divX * wE);
+  out[1] = w * hterm;
+  // Eq. 13: <X, dH> - <sigma n x X, E_e^+>, side limits (J_e+J_i) x n / 2 and sigma M / 2
+  out[2] = w * (hterm - R(0.5) * dot3(X, nJ) - sg * dot3(nX, E[0]) - (R(0.5) * sg) * dot3(X, M));
+  // Eq. 14: <X, J_e + J_i> - <sigma X, E_i^->, side limit n x M / 2
+  out[3] = w * (XJ - sg * dot3(X, E[1]) - (R(0.5) * sg) * XnM);
 }
 
-// K6-8: one CTA per PT_TRI target triangles.  Phase 1: thread (triangle,
-// point, medium) interpolates its record and adds the near corrections, into
-// shared memory.  Phase 2: thread (triangle, local edge) tests.
-constexpr int PT_TRI = 16;
-
-template <typename R>
-__global__ void k_points(const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
-                         const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
-                         const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ,
-                         const double* __restrict__ tri, const double* __restrict__ cX, const double* __restrict__ qp,
-                         const double* __restrict__ qw, const R* __restrict__ sig, int64_t nt, int q, int p, int n0,
-                         int n1, int n2, R ke, R ki, R ze, R zi, int has_near, cx<R>* __restrict__ val) {
-  extern __shared__ unsigned char smem_raw[];
-  cx<R>* recs = reinterpret_cast<cx<R>*>(smem_raw);  // [PT_TRI][q][2][NREC]
-  const int64_t t0 = (int64_t)blockIdx.x * PT_TRI;
-  const int per = 2 * q;
-  const int tl = threadIdx.x / per;
-  const int rem = threadIdx.x - tl * per;
-  const int a = rem >> 1, med = rem & 1;
-  const int64_t t = t0 + tl;
-  const int64_t ng = (int64_t)n0 * n1 * n2;
-  if (tl < PT_TRI && t < nt) {
-    cx<R> rec[NREC];
-    interp_point(grids, base, L, dL, t * q + a, med, p, ng, n1, n2, rec);
-    if (has_near) near_point(corr, noff, nsrc, summ, t, a, med, q, rec);
-    cx<R>* o = recs + ((int64_t)tl * per + a * 2 + med) * NREC;
-#pragma unroll
-    for (int c = 0; c < NREC; ++c) o[c] = rec[c];
+// Bulk asynchronous global -> shared copies (the TMA unit, cp.async.bulk)
+// completing on an mbarrier, and bounded waits on it.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// one arrival that also expects `bytes` of transaction, then the copy
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Wait for the phase of the given parity; false after about a second.
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (gtimer_ns() - t0 > WAIT_LIMIT_NS) return false;
   }
-  __syncthreads();
-  const int tt = threadIdx.x / 3, kk = threadIdx.x - (threadIdx.x / 3) * 3;
-  const int64_t t2 = t0 + tt;
-  if (tt < PT_TRI && t2 < nt) {
+}
+
+// K6-8: one warp per target triangle t, PT_WARPS triangles per CTA; warps
+// never wait on one another.
+//  Phase 1: lane (point a, medium, record group h), 4q lanes, interpolates
+//    its 10 record values, then adds the near corrections.  The triangle's
+//    near records are one contiguous run (pairs noff[t] .. noff[t+1]); they
+//    stream through a per-warp ring of PT_NSTG stages of PT_KP pairs, one
+//    bulk copy per stage issued by lane 0, the next stages in flight while
+//    one is consumed (the first ones during the interpolation).  A stage
+//    that does not arrive within the wait limit sets *tmo and ends the
+//    triangle's near loop after its copies in flight have landed.
+//  Phase 2: lane (local edge kk, point a), 3q lanes, forms the point's
+//    weighted tested values; phase 3: lane (kk, value type) sums them over the
+//    points in point order.
+constexpr int PT_WARPS = 4;
+constexpr int PT_NSTG = 4;
+constexpr int PT_KP = 2;
+
+// complex values of per-warp shared memory: the ring, which the records and
+// point parts of phases 2-3 reuse once the near loop is done
+__host__ __device__ constexpr int pt_warp_complex(int q) {
+  return PT_NSTG * PT_KP * NCORR * 2 * q > 2 * q * NREC + 3 * q * 4 ? PT_NSTG * PT_KP * NCORR * 2 * q
+                                                                     : 2 * q * NREC + 3 * q * 4;
+}
+// bytes of shared memory per CTA: rings, then one mbarrier per stage and warp
+__host__ __device__ constexpr size_t pt_smem_bytes(int q, size_t csize) {
+  return (size_t)PT_WARPS * pt_warp_complex(q) * csize + (size_t)PT_WARPS * PT_NSTG * sizeof(uint64_t);
+}
+
+template <typename R, int P>
+__global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 6) : 3) k_points(
+    const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
+    const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
+    const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
+    const double* __restrict__ cX, const double* __restrict__ qp, const double* __restrict__ qw,
+    const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki, R ze, R zi, int has_near,
+    cx<R>* __restrict__ val, int* __restrict__ tmo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
+  if (t >= nt) return;  // whole warp; no CTA-wide barrier below
+  const int pairc = NCORR * 2 * q;  // complex per pair: [component][point][medium]
+  cx<R>* ring = reinterpret_cast<cx<R>*>(smem_raw) + (int64_t)warp * pt_warp_complex(q);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<cx<R>*>(smem_raw) + PT_WARPS * pt_warp_complex(q)) +
+                   warp * PT_NSTG;
+  cx<R>* recs = ring;                 // [q][2][NREC], after the near loop
+  cx<R>* part = recs + 2 * q * NREC;  // [3][q][4]
+
+  const bool act = lane < 4 * q;
+  const int a = lane >> 2, med = (lane >> 1) & 1, h = lane & 1;
+  const int j0 = has_near ? noff[t] : 0, j1 = has_near ? noff[t + 1] : 0;
+  const int nst = (j1 - j0 + PT_KP - 1) / PT_KP;
+  const unsigned pair_bytes = (unsigned)(pairc * sizeof(cx<R>));
+  // stage st -> slot st % PT_NSTG, issued by lane 0
+  auto issue = [&](int st) {
+    const int pj = j0 + st * PT_KP;
+    const int np = min(PT_KP, j1 - pj);
+    fence_proxy_async();  // earlier reads of the slot come before the copy
+    bulk_load(ring + (st % PT_NSTG) * PT_KP * pairc, corr + (int64_t)pj * pairc, np * pair_bytes,
+              bars + st % PT_NSTG);
+  };
+  if (nst > 0) {
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < PT_NSTG; ++i) mbar_init(bars + i, 1);
+      mbar_init_fence();
+      for (int st = 0; st < PT_NSTG - 1 && st < nst; ++st) issue(st);
+    }
+    __syncwarp();
+  }
+  // source triangles of the pairs, 32 at a time in the lanes (one block ahead)
+  const int npair = j1 - j0;
+  int src_nxt = lane < npair ? nsrc[j0 + lane] : 0, src_cur = 0;
+  cx<R> acc[NREC / 2];
+  if (act) interp_group<R, P>(grids, base, L, dL, t * q + a, med, h, n1, n2, acc);
+  if (nst > 0) {
+    const int set = h ? 2 : med;  // source J of this medium, or M
+    // the interior medium sees -M: accumulate -acc + sum, then negate back
+    const bool neg = h && med;
+    if (neg)
+#pragma unroll
+      for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
+    int st = 0;
+    bool ok = true;
+    for (; st < nst; ++st) {
+      if (lane == 0 && st + PT_NSTG - 1 < nst) issue(st + PT_NSTG - 1);  // slot consumed at st - 1
+      ok = __all_sync(0xffffffffu, mbar_wait(bars + st % PT_NSTG, (st / PT_NSTG) & 1));
+      if (!ok) break;
+      const cx<R>* rs = ring + (st % PT_NSTG) * PT_KP * pairc + a * 2 + med;
+#pragma unroll
+      for (int k = 0; k < PT_KP; ++k) {
+        const int jj = st * PT_KP + k;  // pair within the triangle (warp-uniform)
+        if (jj < npair) {
+          if ((jj & 31) == 0) {
+            src_cur = src_nxt;
+            src_nxt = jj + 32 + lane < npair ? nsrc[j0 + jj + 32 + lane] : 0;
+          }
+          const int64_t sj = __shfl_sync(0xffffffffu, src_cur, jj & 31);
+          if (act) {
+            cx<R> d[NCORR], sv[4];
+            load_group(summ + (3 * sj + set) * 4, sv);
+#pragma unroll
+            for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
+            near_part(d, sv, acc);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (!ok) {
+      // stages st .. min(st + PT_NSTG - 1, nst - 1) were issued: let them land
+      for (int s2 = st; s2 < nst && s2 < st + PT_NSTG; ++s2) (void)mbar_wait(bars + s2 % PT_NSTG, (s2 / PT_NSTG) & 1);
+      if (lane == 0) atomicOr(tmo, 1);
+    }
+    __syncwarp();  // every lane is done with the ring before it holds records
+    if (neg)
+#pragma unroll
+      for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
+  }
+  if (act) {
+    cx<R>* o = recs + (a * 2 + med) * NREC + 10 * h;
+#pragma unroll
+    for (int c = 0; c < NREC / 2; ++c) o[c] = acc[c];
+  }
+  __syncwarp();
+  if (lane < 3 * q) {
+    const int kk = lane / q, pa = lane - kk * q;
     cx<R> o[4];
-    test_edge(recs + (int64_t)tt * per * NREC, summ, tri, cX, qp, qw, sig, t2, kk, q, ke, ki, ze, zi, o);
-    cx<R>* dst = val + (t2 * 3 + kk) * 4;
-    for (int c = 0; c < 4; ++c) dst[c] = o[c];
+    test_point(recs + pa * 2 * NREC, summ, tri, cX, qp, qw, sig, t, kk, pa, q, ke, ki, ze, zi, o);
+    cx<R>* d = part + (kk * q + pa) * 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[c] = o[c];
+  }
+  __syncwarp();
+  if (lane < 12) {
+    const int kk = lane >> 2, c = lane & 3;
+    const cx<R>* sp = part + kk * q * 4 + c;
+    cx<R> v = czero<R>();
+    for (int pa = 0; pa < q; ++pa) v += sp[pa * 4];
+    val[(t * 3 + kk) * 4 + c] = v;
   }
 }
 
@@ -415,6 +577,11 @@ __global__ void k_rows(const cx<R>* __restrict__ val, const int32_t* __restrict_
   if (i >= N) return;
   y[i] = val[rowsrc[2 * i]] + val[rowsrc[2 * i + 1]];
 }
+
+template <typename R>
+using PointsFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, const int32_t*,
+                          const int32_t*, const cx<R>*, const double*, const double*, const double*, const double*,
+                          const R*, int64_t, int, int, int, int, R, R, R, R, int, cx<R>*, int*);
 
 template <typename R>
 PrecData<R>& pdata(scabem_op* op);
@@ -451,12 +618,13 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   if (rc) return rc;
   prof_mark(op, s);
   {
-    const int threads = PT_TRI * (2 * op->q > 3 ? 2 * op->q : 3);
-    const size_t sm = (size_t)PT_TRI * 2 * op->q * NREC * sizeof(cx<R>);
-    CK(cudaFuncSetAttribute(k_points<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_points<R><<<(int)cdiv(nt, PT_TRI), threads, sm, s>>>(
-        pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ, op->tri, op->cX, op->qp, op->qw, pd.sig,
-        nt, op->q, op->p, n0, n1, n2, (R)op->ke, (R)op->ki, (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, pd.val);
+    const size_t sm = pt_smem_bytes(op->q, sizeof(cx<R>));
+    PointsFn<R> fn = op->p == 2 ? k_points<R, 2> : op->p == 3 ? k_points<R, 3> : k_points<R, 4>;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    fn<<<(int)cdiv(nt, PT_WARPS), PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
+                                                  op->tri, op->cX, op->qp, op->qw, pd.sig, nt, op->q, n0, n1, n2,
+                                                  (R)op->ke, (R)op->ki, (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0,
+                                                  pd.val, op->tmo_d);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);

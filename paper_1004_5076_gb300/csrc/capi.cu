@@ -454,6 +454,9 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   TRY(dalloc(&op->base, 3 * op->Q));
   TRY(dalloc(&op->sig64, op->Q));
   TRY(dalloc(&op->err, 1));
+  TRY(cudaHostAlloc(&op->tmo_h, sizeof(int), cudaHostAllocMapped) == cudaSuccess ? SCABEM_OK : SCABEM_E_NOMEM);
+  *op->tmo_h = 0;
+  TRY(cudaHostGetDevicePointer(&op->tmo_d, op->tmo_h, 0) == cudaSuccess ? SCABEM_OK : SCABEM_E_DEVICE);
   TRY(alloc_prec(op, op->d, (op->prec_mask & 2) != 0, s));
   TRY(alloc_prec(op, op->f, (op->prec_mask & 1) != 0, s));
   auto upload = [&](void* dst, const void* src, size_t bytes) -> int {
@@ -555,6 +558,7 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->eunk);
   cudaFree(op->pinv);
   cudaFree(op->err);
+  if (op->tmo_h) cudaFreeHost(op->tmo_h);
   free_prec(op->f);
   free_prec(op->d);
   delete op;
@@ -607,11 +611,24 @@ int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sg) {
   return SCABEM_E_ARG;
 }
 
+// Reports (once) that a bounded device wait of an earlier launch expired.
+static int take_timeout(scabem_op* op) {
+  volatile int* f = op->tmo_h;
+  if (f && *f) {
+    *f = 0;
+    set_error("a bounded device wait expired in an earlier launch (near-field record stream): "
+              "the results of the launches since the previous call are not valid");
+    return SCABEM_E_TIMEOUT;
+  }
+  return SCABEM_OK;
+}
+
 int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream) {
   if (!op || !x || !y || nrhs < 0 || ld < op->N) {
     set_error("scabem_apply: null argument, nrhs < 0 or ld < N");
     return SCABEM_E_ARG;
   }
+  if (int rc = take_timeout(op)) return rc;
   if (nrhs == 0) return SCABEM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (prec == SCABEM_C64) return apply_prec<float>(op, x, y, nrhs, ld, s);
@@ -661,8 +678,13 @@ int scabem_solve(scabem_op_t op, const void* b, void* x, int32_t nrhs, int64_t l
     return SCABEM_E_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = take_timeout(op)) return rc;
   const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
-  if (bd && xd) return solve_impl(op, b, x, nrhs, ld, o, s, info);
+  if (bd && xd) {
+    const int rc = solve_impl(op, b, x, nrhs, ld, o, s, info);
+    const int rt = take_timeout(op);  // solve_impl synchronises the stream
+    return rt ? rt : rc;
+  }
   const size_t bytes = sizeof(cx<double>) * ld * nrhs;
   void *db = nullptr, *dx = nullptr;
   CK(cudaMalloc(&db, bytes));
@@ -674,7 +696,8 @@ int scabem_solve(scabem_op_t op, const void* b, void* x, int32_t nrhs, int64_t l
   CK(cudaStreamSynchronize(s));
   cudaFree(db);
   cudaFree(dx);
-  return rc;
+  const int rt = take_timeout(op);
+  return rt ? rt : rc;
 }
 
 int scabem_fields(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const double* pts, int32_t npts,

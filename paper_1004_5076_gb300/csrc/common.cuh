@@ -123,7 +123,7 @@ struct PrecData {
   cx<R>* src = nullptr;   // 12 * n0 n1 n2
   cx<R>* stA = nullptr;   // 12 * P0 * n1 n2
   cx<R>* stB = nullptr;   // 16 * P0 * n1 n2
-  cx<R>* grid = nullptr;  // 16 * n0 n1 n2
+  cx<R>* grid = nullptr;  // n0 n1 n2 * 16, point-major: [point][medium][J, M set][A or F (3), phi or psi]
   cx<R>* fpt = nullptr;   // Q * 2 * NREC
   cx<R>* val = nullptr;   // nt * 3 * 4
   cx<R>* xs = nullptr;    // staging for host x/y: N * nrhs_cap
@@ -175,6 +175,10 @@ struct scabem_op {
   PrecData<float> f;
   PrecData<double> d;
   int* err = nullptr;  // device error flag
+  // set by a kernel whose bounded wait expired (host-mapped: readable
+  // without a synchronisation; reported as SCABEM_E_TIMEOUT by the next call)
+  int* tmo_h = nullptr;
+  int* tmo_d = nullptr;
   Profiler prof;
 };
 

@@ -9,7 +9,8 @@
 //   stage B: per k0 plane, forward 2-D FFT over (i1, i2) (input pruned to the
 //            physical n1 x n2 corner), multiply by the Green spectrum of the
 //            medium, inverse 2-D FFT, keep the physical corner: 12 -> 16 fields;
-//   stage C: inverse FFT along axis 0, keep i0 < n0.
+//   stage C: inverse FFT along axis 0, keep i0 < n0, written point-major
+//            [i0][i1][i2][16] for the interpolation gathers.
 // Every FFT is an in-place shared-memory Stockham transform (radix 8, then 4
 // or 2) with compile-time power-of-two lengths: each pass loads its
 // butterflies into registers, synchronises, and stores them at their sorted
@@ -183,6 +184,38 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis0(const cx<R>* __restrict__
   for (int idx = threadIdx.x; idx < n_out * CB; idx += FFT_THREADS) {
     const int k0 = idx >> lcb, l = idx & (CB - 1);
     if (c0 + l < C) out[fout + (int64_t)k0 * C + c0 + l] = b0[idx];
+  }
+}
+
+// Stage C with point-major output: one CTA owns NC columns of one group of 4
+// output fields over axis 0 (line l = field * NC + column) and writes
+// out[(i0 * C + c) * 16 + 4 * grp + f] for i0 < n_out, so the 16 potentials of
+// a grid point are contiguous and each group of 4 fills whole 32-byte sectors.
+template <typename R>
+__global__ void __launch_bounds__(FFT_THREADS) k_axis0_pm(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
+                                                          int n_out, int P0, int C, int NC,
+                                                          const cx<R>* __restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* b0 = tws + P0;
+  const int grp = blockIdx.y;
+  const int c0 = blockIdx.x * NC;
+  const int CB = 4 * NC;
+  const int lcb = ilog2(CB), lnc = ilog2(NC);
+  for (int i = threadIdx.x; i < P0; i += FFT_THREADS) tws[i] = tw[i];
+  for (int idx = threadIdx.x; idx < P0 * CB; idx += FFT_THREADS) {
+    const int i0 = idx >> lcb, l = idx & (CB - 1);
+    const int fl = l >> lnc, cl = l & (NC - 1);
+    cx<R> v = czero<R>();
+    if (c0 + cl < C) v = in[((int64_t)(4 * grp + fl) * P0 + i0) * C + c0 + cl];
+    b0[idx] = v;
+  }
+  __syncthreads();
+  fft_lines<R, 1, Tot<R>::L>(b0, ilog2(P0), lcb, 1, CB, tws);
+  for (int idx = threadIdx.x; idx < n_out * CB; idx += FFT_THREADS) {
+    const int k0 = idx >> lcb, l = idx & (CB - 1);
+    const int cl = l >> 2, fl = l & 3;  // field fastest: consecutive threads fill a sector
+    if (c0 + cl < C) out[((int64_t)k0 * C + c0 + cl) * NFIELD_OUT + 4 * grp + fl] = b0[(k0 << lcb) + fl * NC + cl];
   }
 }
 
@@ -632,6 +665,20 @@ int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cu
   return SCABEM_OK;
 }
 
+// stage C: 16 fields [field][k0][c] -> point-major grid [i0][c][16]
+template <typename R>
+static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
+  const int n0 = op->n[0], P0 = op->P[0];
+  const int C = op->n[1] * op->n[2];
+  const int nc = lines_per_cta<R>(P0) / 4;  // P0 <= 1024: at least one column
+  const size_t sm = (size_t)P0 * (4 * nc + 1) * sizeof(cx<R>);
+  CK(cudaFuncSetAttribute(k_axis0_pm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_axis0_pm<R><<<dim3((unsigned)cdiv(C, nc), NFIELD_OUT / 4), FFT_THREADS, sm, s>>>(pd.stB, pd.grid, n0, P0, C, nc,
+                                                                                    pd.tw[0]);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
 template <typename R>
 int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
@@ -652,11 +699,7 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
     k_planes64<R><<<dim3(P0, NFIELD_IN), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1]);
     CK(cudaGetLastError());
     prof_mark(op, s);
-    CK(cudaFuncSetAttribute(k_axis0<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
-    k_axis0<R, 1><<<dim3((unsigned)cdiv(C, cb), NFIELD_OUT), FFT_THREADS, sm0, s>>>(pd.stB, pd.grid, P0, n0, P0, C,
-                                                                                    cb, pd.tw[0]);
-    CK(cudaGetLastError());
-    return SCABEM_OK;
+    return axis0_inverse(op, pd, s);
   }
   const size_t sm1 = ((size_t)P1 + P2 + 2 * (size_t)P1 * (P2 + 2)) * sizeof(cx<R>);
   PlanesFn<R> fn = planes_kernel<R>(ilog2(P1), ilog2(P2));
@@ -669,12 +712,7 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
                                                    pd.tw[2]);
   CK(cudaGetLastError());
   prof_mark(op, s);
-  // stage C
-  CK(cudaFuncSetAttribute(k_axis0<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
-  k_axis0<R, 1><<<dim3((unsigned)cdiv(C, cb), NFIELD_OUT), FFT_THREADS, sm0, s>>>(pd.stB, pd.grid, P0, n0, P0, C, cb,
-                                                                                  pd.tw[0]);
-  CK(cudaGetLastError());
-  return SCABEM_OK;
+  return axis0_inverse(op, pd, s);
 }
 
 template int make_twiddles<float>(cx<float>*, int, cudaStream_t);
