@@ -78,7 +78,6 @@ void free_prec(PrecData<R>& pd) {
   cudaFree(pd.stA);
   cudaFree(pd.stB);
   cudaFree(pd.grid);
-  cudaFree(pd.fpt);
   cudaFree(pd.val);
   cudaFree(pd.xs);
   cudaFree(pd.ys);
@@ -104,9 +103,10 @@ int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) 
   // grid points no stencil covers are never written by the projection
   CK(cudaMemsetAsync(pd.src, 0, sizeof(cx<R>) * NFIELD_IN * ng, s));
   if ((rc = dalloc(&pd.stA, (int64_t)NFIELD_IN * op->P[0] * C))) return rc;
+  // the axis-0 transform writes only the columns some stencil covers
+  CK(cudaMemsetAsync(pd.stA, 0, sizeof(cx<R>) * NFIELD_IN * op->P[0] * C, s));
   if ((rc = dalloc(&pd.stB, (int64_t)NFIELD_OUT * op->P[0] * C))) return rc;
   if ((rc = dalloc(&pd.grid, NFIELD_OUT * ng))) return rc;
-  if ((rc = dalloc(&pd.fpt, op->Q * 2 * NREC))) return rc;
   if ((rc = dalloc(&pd.val, op->nt * 12))) return rc;
   pd.built = true;
   return SCABEM_OK;
@@ -558,6 +558,7 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->eunk);
   cudaFree(op->pinv);
   cudaFree(op->err);
+  cudaFree(op->acol);
   if (op->tmo_h) cudaFreeHost(op->tmo_h);
   free_prec(op->f);
   free_prec(op->d);

@@ -124,7 +124,6 @@ struct PrecData {
   cx<R>* stA = nullptr;   // 12 * P0 * n1 n2
   cx<R>* stB = nullptr;   // 16 * P0 * n1 n2
   cx<R>* grid = nullptr;  // n0 n1 n2 * 16, point-major: [point][medium][J, M set][A or F (3), phi or psi]
-  cx<R>* fpt = nullptr;   // Q * 2 * NREC
   cx<R>* val = nullptr;   // nt * 3 * 4
   cx<R>* xs = nullptr;    // staging for host x/y: N * nrhs_cap
   cx<R>* ys = nullptr;
@@ -160,6 +159,13 @@ struct scabem_op {
   int32_t* gent = nullptr;  // Q * p^3
   double* gwd = nullptr;    // Q * p^3
   float* gwf = nullptr;     // Q * p^3
+  // columns (i1, i2) of the grid that some stencil covers, ascending: the
+  // only ones whose sources are non-zero and whose potentials are read, so
+  // the axis-0 transforms run on these alone; rowmask bit i1 is set when row
+  // i1 holds one of them
+  int64_t nac = 0;
+  int32_t* acol = nullptr;  // nac
+  uint64_t rowmask = 0;
   double* sig64 = nullptr;    // Q normalised (master copy)
   // near list
   int64_t npairs = 0;

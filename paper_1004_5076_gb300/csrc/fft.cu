@@ -158,48 +158,50 @@ struct Tot {
 };
 
 // ---------------------------------------------------------------- stage A / C
-// Columns c in [0, C) of the [field][i0][c] layout; one CTA owns CB columns
-// of one field over the whole axis 0 (smem: [P0][CB], lines = columns).
-template <typename R, int DIR>
+// Stage A on the active columns acol[0 .. nac) of the [field][i0][c] layout
+// (C columns per i0); one CTA owns CB of them for one field over the whole
+// axis 0 (smem: [P0][CB], lines = columns).  Inputs i0 >= n_in are zero.
+template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS) k_axis0(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
-                                                       int n_in, int n_out, int P0, int C, int CB,
-                                                       const cx<R>* __restrict__ tw) {
+                                                       int n_in, int P0, int C, const int32_t* __restrict__ acol,
+                                                       int nac, int CB, const cx<R>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* b0 = tws + P0;
   const int f = blockIdx.y;
-  const int c0 = blockIdx.x * CB;
+  const int a0 = blockIdx.x * CB;
   const int lcb = ilog2(CB);
   for (int i = threadIdx.x; i < P0; i += FFT_THREADS) tws[i] = tw[i];
   const int64_t fin = (int64_t)f * n_in * C;
   for (int idx = threadIdx.x; idx < P0 * CB; idx += FFT_THREADS) {
     const int i0 = idx >> lcb, l = idx & (CB - 1);
     cx<R> v = czero<R>();
-    if (i0 < n_in && c0 + l < C) v = in[fin + (int64_t)i0 * C + c0 + l];
+    if (i0 < n_in && a0 + l < nac) v = in[fin + (int64_t)i0 * C + acol[a0 + l]];
     b0[idx] = v;
   }
   __syncthreads();
-  fft_lines<R, DIR, Tot<R>::L>(b0, ilog2(P0), lcb, 1, CB, tws);
-  const int64_t fout = (int64_t)f * n_out * C;
-  for (int idx = threadIdx.x; idx < n_out * CB; idx += FFT_THREADS) {
+  fft_lines<R, -1, Tot<R>::L>(b0, ilog2(P0), lcb, 1, CB, tws);
+  const int64_t fout = (int64_t)f * P0 * C;
+  for (int idx = threadIdx.x; idx < P0 * CB; idx += FFT_THREADS) {
     const int k0 = idx >> lcb, l = idx & (CB - 1);
-    if (c0 + l < C) out[fout + (int64_t)k0 * C + c0 + l] = b0[idx];
+    if (a0 + l < nac) out[fout + (int64_t)k0 * C + acol[a0 + l]] = b0[idx];
   }
 }
 
-// Stage C with point-major output: one CTA owns NC columns of one group of 4
+// Stage C with point-major output, on the active columns acol[0 .. nac)
+// only (the potentials are read nowhere else): one CTA owns NC of them for one group of 4
 // output fields over axis 0 (line l = field * NC + column) and writes
 // out[(i0 * C + c) * 16 + 4 * grp + f] for i0 < n_out, so the 16 potentials of
 // a grid point are contiguous and each group of 4 fills whole 32-byte sectors.
 template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS) k_axis0_pm(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
-                                                          int n_out, int P0, int C, int NC,
-                                                          const cx<R>* __restrict__ tw) {
+                                                          int n_out, int P0, int C, const int32_t* __restrict__ acol,
+                                                          int nac, int NC, const cx<R>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* b0 = tws + P0;
   const int grp = blockIdx.y;
-  const int c0 = blockIdx.x * NC;
+  const int a0 = blockIdx.x * NC;
   const int CB = 4 * NC;
   const int lcb = ilog2(CB), lnc = ilog2(NC);
   for (int i = threadIdx.x; i < P0; i += FFT_THREADS) tws[i] = tw[i];
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis0_pm(const cx<R>* __restric
     const int i0 = idx >> lcb, l = idx & (CB - 1);
     const int fl = l >> lnc, cl = l & (NC - 1);
     cx<R> v = czero<R>();
-    if (c0 + cl < C) v = in[((int64_t)(4 * grp + fl) * P0 + i0) * C + c0 + cl];
+    if (a0 + cl < nac) v = in[((int64_t)(4 * grp + fl) * P0 + i0) * C + acol[a0 + cl]];
     b0[idx] = v;
   }
   __syncthreads();
@@ -215,7 +217,8 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis0_pm(const cx<R>* __restric
   for (int idx = threadIdx.x; idx < n_out * CB; idx += FFT_THREADS) {
     const int k0 = idx >> lcb, l = idx & (CB - 1);
     const int cl = l >> 2, fl = l & 3;  // field fastest: consecutive threads fill a sector
-    if (c0 + cl < C) out[((int64_t)k0 * C + c0 + cl) * NFIELD_OUT + 4 * grp + fl] = b0[(k0 << lcb) + fl * NC + cl];
+    if (a0 + cl < nac)
+      out[((int64_t)k0 * C + acol[a0 + cl]) * NFIELD_OUT + 4 * grp + fl] = b0[(k0 << lcb) + fl * NC + cl];
   }
 }
 
@@ -497,7 +500,7 @@ __device__ __forceinline__ void line64(cx<R>* v, const cx<R>* w, cx<R>* scr, int
 template <typename R>
 __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_planes64(const cx<R>* __restrict__ A, cx<R>* __restrict__ B, const cx<R>* __restrict__ ghE,
-               const cx<R>* __restrict__ ghI, int P0, const cx<R>* __restrict__ tw64) {
+               const cx<R>* __restrict__ ghI, int P0, const cx<R>* __restrict__ tw64, uint64_t rowmask) {
   constexpr int NP = 32, H = 33;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* W0 = reinterpret_cast<cx<R>*>(smem_raw);  // forward rows, then output 0
@@ -511,13 +514,21 @@ __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
   for (int k = 1; k < 8; ++k) w[k] = tw64[t * k];
   const int k0 = blockIdx.x, f = blockIdx.y;
   const int i1 = warp * 4 + sub;  // the row this lane works on in the row passes
+  // rows no stencil covers are zero in and unused out; the test is per warp
+  // (its four rows) so that the line transforms' warp barriers see all lanes
+  const bool row_on = ((rowmask >> (warp * 4)) & 0xF) != 0;
   {
     // forward rows: the 32 physical rows, elements >= 32 are zero
-    const cx<R>* src = A + ((int64_t)f * P0 + k0) * (NP * NP) + i1 * NP;
     cx<R> v[8];
+    if (row_on) {
+      const cx<R>* src = A + ((int64_t)f * P0 + k0) * (NP * NP) + i1 * NP;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) v[r] = src[t + 8 * r];
-    line64<R, -1, true, false>(v, w, scr, t);
+      for (int r = 0; r < 4; ++r) v[r] = src[t + 8 * r];
+      line64<R, -1, true, false>(v, w, scr, t);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = czero<R>();
+    }
 #pragma unroll
     for (int m = 0; m < 8; ++m) W0[swz64(i1, t + 8 * m)] = v[m];
   }
@@ -563,7 +574,7 @@ __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
 
   // inverse rows, the 32 physical columns written to global memory
 #pragma unroll 1
-  for (int o = 0; o < nout; ++o) {
+  for (int o = 0; o < nout && row_on; ++o) {
     const cx<R>* Wo = o ? W1 : W0;
     cx<R> v[8];
 #pragma unroll
@@ -665,16 +676,24 @@ int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cu
   return SCABEM_OK;
 }
 
-// stage C: 16 fields [field][k0][c] -> point-major grid [i0][c][16]
+// Lines per CTA of the pruned axis-0 stages: at most 8, so that the few
+// active columns still spread over the SMs.
+template <typename R>
+int pruned_lines(int P0) {
+  const int l = lines_per_cta<R>(P0);
+  return l < 8 ? l : 8;
+}
+
+// stage C: 16 fields [field][k0][c] -> point-major grid [i0][c][16], active columns
 template <typename R>
 static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   const int n0 = op->n[0], P0 = op->P[0];
   const int C = op->n[1] * op->n[2];
-  const int nc = lines_per_cta<R>(P0) / 4;  // P0 <= 1024: at least one column
+  const int nc = pruned_lines<R>(P0) >= 4 ? pruned_lines<R>(P0) / 4 : 1;  // P0 <= 1024: 4 lines fit
   const size_t sm = (size_t)P0 * (4 * nc + 1) * sizeof(cx<R>);
   CK(cudaFuncSetAttribute(k_axis0_pm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_axis0_pm<R><<<dim3((unsigned)cdiv(C, nc), NFIELD_OUT / 4), FFT_THREADS, sm, s>>>(pd.stB, pd.grid, n0, P0, C, nc,
-                                                                                    pd.tw[0]);
+  k_axis0_pm<R><<<dim3((unsigned)cdiv(op->nac, nc), NFIELD_OUT / 4), FFT_THREADS, sm, s>>>(
+      pd.stB, pd.grid, n0, P0, C, op->acol, (int)op->nac, nc, pd.tw[0]);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }
@@ -684,19 +703,24 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
   const int P0 = op->P[0], P1 = op->P[1], P2 = op->P[2];
   const int C = n1 * n2;
-  const int cb = lines_per_cta<R>(P0);
+  if (op->nac == 0) {
+    set_error("grid: no grid point is covered by a stencil");
+    return SCABEM_E_ARG;
+  }
+  const int cb = pruned_lines<R>(P0);
   const size_t sm0 = (size_t)P0 * (cb + 1) * sizeof(cx<R>);
   // stage A
-  CK(cudaFuncSetAttribute(k_axis0<R, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
-  k_axis0<R, -1><<<dim3((unsigned)cdiv(C, cb), NFIELD_IN), FFT_THREADS, sm0, s>>>(pd.src, pd.stA, n0, P0, P0, C, cb,
-                                                                                  pd.tw[0]);
+  CK(cudaFuncSetAttribute(k_axis0<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+  k_axis0<R><<<dim3((unsigned)cdiv(op->nac, cb), NFIELD_IN), FFT_THREADS, sm0, s>>>(
+      pd.src, pd.stA, n0, P0, C, op->acol, (int)op->nac, cb, pd.tw[0]);
   CK(cudaGetLastError());
   prof_mark(op, s);
   // stage B
   if (P1 == 64 && P2 == 64) {
     const size_t sm = ((size_t)2 * 32 * 64 + (size_t)(P64_THREADS / 8) * P64_SCR) * sizeof(cx<R>);
     CK(cudaFuncSetAttribute(k_planes64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_planes64<R><<<dim3(P0, NFIELD_IN), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1]);
+    k_planes64<R><<<dim3(P0, NFIELD_IN), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1],
+                                                               op->rowmask);
     CK(cudaGetLastError());
     prof_mark(op, s);
     return axis0_inverse(op, pd, s);

@@ -732,6 +732,22 @@ int setup_gather(scabem_op* op, cudaStream_t s) {
       coff.push_back(off[g + 1]);
     }
   op->ngnz = (int64_t)pts.size();
+  // active columns and rows of the (i1, i2) cross-section
+  const int64_t C = (int64_t)n1 * n2;
+  std::vector<char> colact(C, 0);
+  for (int32_t g : pts) colact[g % C] = 1;
+  std::vector<int32_t> acol;
+  op->rowmask = 0;
+  for (int64_t c = 0; c < C; ++c)
+    if (colact[c]) {
+      acol.push_back((int32_t)c);
+      op->rowmask |= 1ull << (c / n2);
+    }
+  op->nac = (int64_t)acol.size();
+  if (op->nac > 0) {
+    CK(cudaMalloc(&op->acol, sizeof(int32_t) * op->nac));
+    CK(cudaMemcpyAsync(op->acol, acol.data(), sizeof(int32_t) * op->nac, cudaMemcpyHostToDevice, s));
+  }
   const int64_t ne = Q * p3;
   CK(cudaMalloc(&op->gpt, sizeof(int32_t) * (pts.size() + 1)));
   CK(cudaMalloc(&op->goff, sizeof(int32_t) * coff.size()));
