@@ -261,7 +261,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": t_setup},
             "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
                     "d2h_bytes_per_step": int(N * 8)},
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": 7 * args.steps,
             "stages_ms_per_step": per,
             "roofline": roof,
             "cpu_baseline": cpu,

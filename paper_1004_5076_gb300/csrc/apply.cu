@@ -1,10 +1,11 @@
 // The matvec y = A x of the grid-accelerated operator (one right-hand side).
 //
-//  K1 k_summ     RWG coefficients -> per-triangle current summaries
+//  K1 k_sources  RWG coefficients -> per-triangle current summaries
 //                J(r) = a (r - c_t) - beta for the exterior J, interior J and
-//                exterior M sets (current reduction, Eqs. 10-12)
-//  K2 k_project  point sources at the quadrature points spread onto the grid
-//                by the Lagrange stencils (12 fields)
+//                exterior M sets (current reduction, Eqs. 10-12), and the
+//                weighted point sources at the quadrature points
+//  K2 k_gather   point sources spread onto the grid by the Lagrange stencils
+//                (12 fields), as a gather over the covered grid points
 //  K3-5          fft_conv (fft.cu): 12 -> 16 grid potentials (A, phi, F, psi
 //                of each medium, Eqs. 15-16)
 //  K6-8 k_points per target triangle: potentials, gradients and curls at its
@@ -55,108 +56,124 @@ __global__ void k_summ(const cx<R>* __restrict__ x, const int32_t* __restrict__ 
   }
 }
 
-// K2a: one thread per quadrature point: the weighted point sources
-// qsrc[Qi*12 + set*4 + {x, y, z, div}] of the exterior J, interior J and
-// exterior M sets (J(r) = a (r - c) - beta, div J = 2a, times the weight).
+// a += s * b on (re, im) as one packed FP32x2 FMA in complex64.
+__device__ __forceinline__ void axpy2(cx<float>& a, float s, cx<float> b) {
+  const float2 r = __ffma2_rn(make_float2(s, s), make_float2(b.re, b.im), make_float2(a.re, a.im));
+  a = mk(r.x, r.y);
+}
+__device__ __forceinline__ void axpy2(cx<double>& a, double s, cx<double> b) { axpy(a, s, b); }
+
+// K1+K2a: one thread per quadrature point (point a of triangle t): the
+// current summaries of t (as k_summ; written by the thread of point 0) and
+// the point's weighted sources qsrc[Qi*12 + set*4 + {x, y, z, div}] of the
+// exterior J, interior J and exterior M sets (J(r) = a (r - c) - beta,
+// div J = 2a, times the quadrature weight).
 template <typename R>
-__global__ void k_qsrc(const cx<R>* __restrict__ summ, const double* __restrict__ qp, const double* __restrict__ qw,
-                       const double* __restrict__ tri, int64_t Q, int q, cx<R>* __restrict__ qsrc) {
-  int64_t Qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void k_sources(const cx<R>* __restrict__ x, const int32_t* __restrict__ unk,
+                          const double* __restrict__ cX, const double* __restrict__ tri,
+                          const double* __restrict__ qp, const double* __restrict__ qw, int64_t Q, int q,
+                          cx<R>* __restrict__ summ, cx<R>* __restrict__ qsrc) {
+  const int64_t Qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (Qi >= Q) return;
   const int64_t t = Qi / q;
+  const int a = (int)(Qi - t * q);
   const double* g = tri + 16 * t;
+  R rel[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) rel[k][c] = (R)(g[3 * k + c] - g[9 + c]);
+  R ck[3];
+  for (int k = 0; k < 3; ++k) ck[k] = (R)cX[3 * t + k];
   const R w = (R)qw[Qi];
-  const R rel[3] = {(R)(qp[3 * Qi] - g[9]), (R)(qp[3 * Qi + 1] - g[10]), (R)(qp[3 * Qi + 2] - g[11])};
+  const R rq[3] = {(R)(qp[3 * Qi] - g[9]), (R)(qp[3 * Qi + 1] - g[10]), (R)(qp[3 * Qi + 2] - g[11])};
   cx<R>* o = qsrc + Qi * NFIELD_IN;
 #pragma unroll
   for (int set = 0; set < 3; ++set) {
-    const cx<R>* s = summ + (3 * t + set) * 4;
-    const cx<R> a = s[0];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) o[set * 4 + c] = w * (rel[c] * a - s[1 + c]);
-    o[set * 4 + 3] = (R(2) * w) * a;
+    cx<R> al = czero<R>(), b0 = al, b1 = al, b2 = al;
+    for (int k = 0; k < 3; ++k) {
+      const cx<R> j = ck[k] * coef_of(x, unk[(3 * t + k) * 3 + set]);
+      al += j;
+      b0 += rel[k][0] * j;
+      b1 += rel[k][1] * j;
+      b2 += rel[k][2] * j;
+    }
+    if (a == 0) {
+      cx<R>* so = summ + (3 * t + set) * 4;
+      so[0] = al;
+      so[1] = b0;
+      so[2] = b1;
+      so[3] = b2;
+    }
+    o[set * 4 + 0] = w * (rq[0] * al - b0);
+    o[set * 4 + 1] = w * (rq[1] * al - b1);
+    o[set * 4 + 2] = w * (rq[2] * al - b2);
+    o[set * 4 + 3] = (R(2) * w) * al;
   }
 }
 
-// K2b: projection as a gather.  Sixteen lanes per grid point that some
-// stencil covers share its entries (two in flight per lane), sum
-// W_slot(point) * qsrc[point] over 16-byte loads, and reduce the 24 real
-// sums by a reduce-scatter over shuffles (each round halves the values a
-// lane keeps); lanes with an even index then write three of them.  Points no
-// stencil covers stay zero from set-up.  The sum order is fixed, so the
-// result does not depend on thread timing.
-constexpr int GATHER_LANES = 16;
-
-// a[0..23] += w * (re, im of the 12 fields of row src)
-__device__ __forceinline__ void add_row(float* a, float w, const cx<float>* src) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const float4 u = __ldg(s4 + i);
-    a[4 * i + 0] = fmaf(w, u.x, a[4 * i + 0]);
-    a[4 * i + 1] = fmaf(w, u.y, a[4 * i + 1]);
-    a[4 * i + 2] = fmaf(w, u.z, a[4 * i + 2]);
-    a[4 * i + 3] = fmaf(w, u.w, a[4 * i + 3]);
-  }
+// K2b: projection as a gather.  One warp per grid point that some stencil
+// covers: lane = portion * SL + slot reads 16-byte portion `portion` of the
+// rows qsrc[point] of entries slot, slot + SL, ... (SL rows per load
+// instruction, two in flight), weighted by W_slot(point); the SL slot sums
+// of a portion are then added by shuffles and the slot-0 lanes write their
+// portion.  Points no stencil covers stay zero from set-up.  The sum order
+// is fixed, so the result does not depend on thread timing.
+template <typename R>
+__device__ __forceinline__ void load_portion(const cx<R>* p, cx<R>* v);
+template <>
+__device__ __forceinline__ void load_portion<float>(const cx<float>* p, cx<float>* v) {
+  const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = mk(u.x, u.y);
+  v[1] = mk(u.z, u.w);
 }
-__device__ __forceinline__ void add_row(double* a, double w, const cx<double>* src) {
-  const double2* s2 = reinterpret_cast<const double2*>(src);
-#pragma unroll
-  for (int i = 0; i < 12; ++i) {
-    const double2 u = __ldg(s2 + i);
-    a[2 * i + 0] = fma(w, u.x, a[2 * i + 0]);
-    a[2 * i + 1] = fma(w, u.y, a[2 * i + 1]);
-  }
-}
-
-// One reduce-scatter round over lanes l and l ^ M: the lane with bit M set
-// keeps the upper half of its H values, the other the lower half.
-template <int H, int M, typename R>
-__device__ __forceinline__ void rs_round(const R* a, R* b, bool up) {
-#pragma unroll
-  for (int i = 0; i < H / 2; ++i) {
-    const R send = up ? a[i] : a[i + H / 2];
-    const R keep = up ? a[i + H / 2] : a[i];
-    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, M);
-  }
+template <>
+__device__ __forceinline__ void load_portion<double>(const cx<double>* p, cx<double>* v) {
+  v[0] = p[0];
 }
 
 template <typename R>
 __global__ void k_gather(const cx<R>* __restrict__ qsrc, const int32_t* __restrict__ gpt,
                          const int32_t* __restrict__ goff, const int32_t* __restrict__ gq, const R* __restrict__ gw,
                          int64_t ngnz, int64_t ng, cx<R>* __restrict__ grids) {
-  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / GATHER_LANES;
-  const int l = threadIdx.x & (GATHER_LANES - 1);
-  R a[2 * NFIELD_IN];
+  constexpr int CPP = 16 / (int)sizeof(cx<R>);  // complex per 16-byte portion
+  constexpr int NPOR = NFIELD_IN / CPP;          // portions per row: 6 or 12
+  constexpr int SL = 24 / NPOR;                  // rows per load instruction: 4 or 2
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int por = lane / SL, slot = lane - por * SL;
+  const bool act = lane < NPOR * SL && i < ngnz;
+  cx<R> acc[CPP];
 #pragma unroll
-  for (int f = 0; f < 2 * NFIELD_IN; ++f) a[f] = R(0);
-  if (i < ngnz) {
+  for (int c = 0; c < CPP; ++c) acc[c] = czero<R>();
+  if (act) {
     const int e1 = goff[i + 1];
-    for (int e = goff[i] + l; e < e1; e += 2 * GATHER_LANES) {
-      const int e2 = e + GATHER_LANES;
+    for (int e = goff[i] + slot; e < e1; e += 2 * SL) {
+      const int e2 = e + SL;
       const int qa = gq[e];
       const R wa = gw[e];
       const int qb = e2 < e1 ? gq[e2] : qa;
       const R wb = e2 < e1 ? gw[e2] : R(0);
-      add_row(a, wa, qsrc + (int64_t)qa * NFIELD_IN);
-      add_row(a, wb, qsrc + (int64_t)qb * NFIELD_IN);
+      cx<R> va[CPP], vb[CPP];
+      load_portion<R>(qsrc + (int64_t)qa * NFIELD_IN + por * CPP, va);
+      load_portion<R>(qsrc + (int64_t)qb * NFIELD_IN + por * CPP, vb);
+#pragma unroll
+      for (int c = 0; c < CPP; ++c) {
+        axpy2(acc[c], wa, va[c]);
+        axpy2(acc[c], wb, vb[c]);
+      }
     }
   }
   // every lane reaches the shuffles (no early exit above)
-  R b[12], c[6], d[3];
-  rs_round<24, 8>(a, b, l & 8);
-  rs_round<12, 4>(b, c, l & 4);
-  rs_round<6, 2>(c, d, l & 2);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) d[k] += __shfl_xor_sync(0xffffffffu, d[k], 1);
-  if (i < ngnz && (l & 1) == 0) {
-    const int64_t g = gpt[i];
-    const int v0 = ((l & 8) ? 12 : 0) + ((l & 4) ? 6 : 0) + ((l & 2) ? 3 : 0);
+  for (int o = 1; o < SL; o <<= 1)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int v = v0 + k;  // real sum v = field v / 2, part v % 2
-      reinterpret_cast<R*>(grids + (v >> 1) * ng + g)[v & 1] = d[k];
+    for (int c = 0; c < CPP; ++c) {
+      acc[c].re += __shfl_xor_sync(0xffffffffu, acc[c].re, o);
+      acc[c].im += __shfl_xor_sync(0xffffffffu, acc[c].im, o);
     }
+  if (act && slot == 0) {
+    const int64_t g = gpt[i];
+#pragma unroll
+    for (int c = 0; c < CPP; ++c) grids[(int64_t)(por * CPP + c) * ng + g] = acc[c];
   }
 }
 
@@ -185,13 +202,6 @@ __device__ __forceinline__ void load_group(const cx<double>* p, cx<double>* v) {
 #pragma unroll
   for (int f = 0; f < 4; ++f) v[f] = p[f];
 }
-
-// a += s * b on (re, im) as one packed FP32x2 FMA in complex64.
-__device__ __forceinline__ void axpy2(cx<float>& a, float s, cx<float> b) {
-  const float2 r = __ffma2_rn(make_float2(s, s), make_float2(b.re, b.im), make_float2(a.re, a.im));
-  a = mk(r.x, r.y);
-}
-__device__ __forceinline__ void axpy2(cx<double>& a, double s, cx<double> b) { axpy(a, s, b); }
 
 // Interpolated potentials of one medium at quadrature point Qi, group h of
 // the record (NREC = 2 x 10): h = 0 A(3) phi grad phi(3) curl A(3) from the
@@ -603,14 +613,13 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
   const int64_t ng = (int64_t)n0 * n1 * n2;
   prof_mark(op, s);
-  k_summ<R><<<(int)cdiv(nt, 128), 128, 0, s>>>(x, op->unk, op->cX, op->tri, nt, pd.summ);
+  k_sources<R><<<(int)cdiv(Q, 128), 128, 0, s>>>(x, op->unk, op->cX, op->tri, op->qp, op->qw, Q, op->q, pd.summ,
+                                                 pd.qsrc);
   CK(cudaGetLastError());
   prof_mark(op, s);
-  k_qsrc<R><<<(int)cdiv(Q, 128), 128, 0, s>>>(pd.summ, op->qp, op->qw, op->tri, Q, op->q, pd.qsrc);
-  CK(cudaGetLastError());
   if (op->ngnz > 0) {
-    k_gather<R><<<(int)cdiv(op->ngnz * GATHER_LANES, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent,
-                                                                        gather_weights<R>(op), op->ngnz, ng, pd.src);
+    k_gather<R><<<(int)cdiv(op->ngnz * 32, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent,
+                                                              gather_weights<R>(op), op->ngnz, ng, pd.src);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);

@@ -86,9 +86,9 @@ constexpr int NCORR = 10;  // per point and medium: dP0, dP1(3), dQ(3), dC(3)
 constexpr double ETA0 = 376.730313668;
 
 // ------------------------------------------------------------------ profiling
-// Stages of one apply: summaries, projection, FFT axis 0 forward, FFT planes
-// with the Green multiply, FFT axis 0 inverse, points (interpolation, near
-// field and testing), rows.
+// Stages of one apply: summaries (with the quadrature-point sources),
+// projection, FFT axis 0 forward, FFT planes with the Green multiply, FFT
+// axis 0 inverse, points (interpolation, near field and testing), rows.
 constexpr int NSTAGE = 7;
 struct Profiler {
   bool on = false;

@@ -30,13 +30,25 @@ __device__ __forceinline__ cx<R> rot(cx<R> a) {  // multiply by DIR * j
   return DIR < 0 ? mk(a.im, -a.re) : mk(-a.im, a.re);
 }
 
+// complex add / subtract; complex64 as one packed FP32x2 add
+__device__ __forceinline__ cx<float> padd(cx<float> a, cx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.re, a.im), make_float2(b.re, b.im));
+  return mk(r.x, r.y);
+}
+__device__ __forceinline__ cx<float> psub(cx<float> a, cx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.re, a.im), make_float2(-b.re, -b.im));
+  return mk(r.x, r.y);
+}
+__device__ __forceinline__ cx<double> padd(cx<double> a, cx<double> b) { return a + b; }
+__device__ __forceinline__ cx<double> psub(cx<double> a, cx<double> b) { return a - b; }
+
 template <typename R, int DIR>
 __device__ __forceinline__ void dft4(cx<R>& a0, cx<R>& a1, cx<R>& a2, cx<R>& a3) {
-  cx<R> t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, u = rot<R, DIR>(a1 - a3);
-  a0 = t0 + t2;
-  a2 = t0 - t2;
-  a1 = t1 + u;
-  a3 = t1 - u;
+  cx<R> t0 = padd(a0, a2), t1 = psub(a0, a2), t2 = padd(a1, a3), u = rot<R, DIR>(psub(a1, a3));
+  a0 = padd(t0, t2);
+  a2 = psub(t0, t2);
+  a1 = padd(t1, u);
+  a3 = psub(t1, u);
 }
 
 template <typename R, int RAD, int DIR>
@@ -58,14 +70,14 @@ __device__ __forceinline__ void dft(cx<R>* v) {
     const cx<R> w1 = s * (o1 + rot<R, DIR>(o1));
     const cx<R> w2 = rot<R, DIR>(o2);
     const cx<R> w3 = s * (rot<R, DIR>(o3) - o3);
-    v[0] = e0 + o0;
-    v[4] = e0 - o0;
-    v[1] = e1 + w1;
-    v[5] = e1 - w1;
-    v[2] = e2 + w2;
-    v[6] = e2 - w2;
-    v[3] = e3 + w3;
-    v[7] = e3 - w3;
+    v[0] = padd(e0, o0);
+    v[4] = psub(e0, o0);
+    v[1] = padd(e1, w1);
+    v[5] = psub(e1, w1);
+    v[2] = padd(e2, w2);
+    v[6] = psub(e2, w2);
+    v[3] = padd(e3, w3);
+    v[7] = psub(e3, w3);
   }
 }
 
@@ -469,10 +481,10 @@ __device__ __forceinline__ void dft8_hout(cx<R>* v) {
   dft4<R, DIR>(e0, e1, e2, e3);
   dft4<R, DIR>(o0, o1, o2, o3);
   const R s = R(0.70710678118654752440);
-  v[0] = e0 + o0;
-  v[1] = e1 + s * (o1 + rot<R, DIR>(o1));
-  v[2] = e2 + rot<R, DIR>(o2);
-  v[3] = e3 + s * (rot<R, DIR>(o3) - o3);
+  v[0] = padd(e0, o0);
+  v[1] = padd(e1, s * (o1 + rot<R, DIR>(o1)));
+  v[2] = padd(e2, rot<R, DIR>(o2));
+  v[3] = padd(e3, s * (rot<R, DIR>(o3) - o3));
 }
 
 // 64-point transform of one line over its eight lanes (lane t, v[r] =
