@@ -8,6 +8,12 @@ rows including the sigma-weighted absorber rows) on device-resident x.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
+After the timed region the same line also carries (unless --no-extras):
+the complex128 matvec rate, a 32-right-hand-side complex64 call, and the
+time of one GMRES solve (complex64 operator, FP64 Arnoldi and refinement to
+1e-8) with a Gaussian-beam excitation; a whole-matvec byte count beside the
+dominant kernel's roofline.
+
 N > 1 runs as N independent replicas (one per GPU, launched by
 torch.distributed.run); the only collective is the max-over-ranks of the
 timed region.  Prints one JSON line on rank 0.
@@ -89,7 +95,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
@@ -149,25 +155,44 @@ def barrier(ws):
 
 
 # ------------------------------------------------------------------ byte models
-def stage_bytes(info, case, b):
-    """Algorithmic HBM bytes per apply of each stage (one complex word = b bytes)."""
+def stage_bytes(info, ginfo, case, N, b):
+    """Algorithmic HBM bytes per apply of each stage (one complex word = b
+    bytes, one real word = b / 2).  Grid stages count only the covered grid
+    points and active columns that the pruned transforms need."""
     n0, n1, n2 = case.grid.n
     P0 = 2 * n0
-    C = n1 * n2
-    ng = n0 * C
+    nac, ngnz = ginfo["active_columns"], ginfo["covered_points"]
     oct_ = (P0 // 2 + 1) * (n1 + 1) * (n2 + 1)
-    Q = info["qpoints"]
-    nt = Q // case.q
+    Q, q, p = info["qpoints"], case.q, case.grid.p
+    nt = Q // q
     npairs = info["near_pairs"]
+    r = b // 2
     return {
-        "fft_axis0_fwd": b * 12 * (ng + P0 * C),
-        "fft_planes_green": b * (12 * P0 * C + 16 * P0 * C + 2 * oct_),
-        "fft_axis0_inv": b * 16 * (P0 * C + ng),
-        # near records, the 16 potential grids, summaries, tested values out;
-        # per point: position, weight, stencil base and weights, conductivity
-        "points": b * (npairs * case.q * 2 * 10 + 16 * ng + nt * 12 + nt * 12) + 4 * (nt + 1 + npairs)
-        + Q * (24 + 8 + 12 + 2 * 3 * case.grid.p * b // 2 + b // 2) + nt * (16 + 3) * 8,
+        # x in; summaries and point sources out; triangle and point geometry
+        "summaries": b * (N + nt * 12 + Q * 12) + 4 * nt * 9 + 8 * (nt * 15 + Q * 4),
+        # point sources in, the gather map (point, weight), 12 fields out
+        "projection": b * (Q * 12 + 12 * ngnz) + Q * p**3 * (4 + r) + 8 * ngnz,
+        "fft_axis0_fwd": b * 12 * nac * (n0 + P0),
+        "fft_planes_green": b * (12 * P0 * nac + 16 * P0 * nac + 2 * oct_),
+        "fft_axis0_inv": b * 16 * nac * (P0 + n0),
+        # near records, the 16 potentials at covered points, summaries, tested
+        # values out; per point: position, weight, stencil base and weights,
+        # conductivity; per triangle: geometry
+        "points": b * (npairs * q * 2 * 10 + 16 * ngnz + nt * 12 + nt * 12) + 4 * (nt + 1 + npairs)
+        + Q * (24 + 8 + 12 + 2 * 3 * p * r + r) + nt * (16 + 3) * 8,
+        "rows": b * 3 * N + 8 * N,
     }
+
+
+def survey_model_bytes(info, case, N, b):
+    """Whole-matvec bytes of the unpruned pFFT model: one round trip of each
+    half-transformed field of the full transform grid (12 in, 16 out), both
+    Green octants, the near records, the stencil data (read by projection and
+    interpolation), per-point geometry, x in and y out."""
+    n = 8 * case.grid.n[0] * case.grid.n[1] * case.grid.n[2]
+    Q, p = info["qpoints"], case.grid.p
+    nnz = info["near_pairs"] * case.q * 2 * 10
+    return b * (2 * 28 * n // 2 + 2 * n // 8) + b * nnz + 2 * Q * (4 + 3 * p * (b // 2)) + Q * 48 + 2 * N * b
 
 
 def run_gpu(args):
@@ -195,14 +220,20 @@ def run_gpu(args):
     t_setup = time.perf_counter()
     mh = sc.scabem_mesh_create(m.V, m.T, m.region)
     op = sc.scabem_op_create(mh, case.media, case.grid.n, case.grid.h, case.grid.origin, case.grid.p, case.q,
-                             case.r_near, 1, stream=stream)
+                             case.r_near, 1 if args.no_extras else 3, stream=stream)
     sc.scabem_set_sigma(op, segments=case.sigma_segments)
     t_setup = time.perf_counter() - t_setup
     info = sc.scabem_op_info(op)
+    ginfo = sc.scabem_op_grid_info(op)
     N = sc.scabem_mesh_info(mh)[2]
     gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
-    x = torch.complex(torch.randn(N, device="cuda", generator=gen), torch.randn(N, device="cuda", generator=gen))
-    x = (x / math.sqrt(2)).to(torch.complex64).contiguous()
+
+    def rand_x(shape, dtype):
+        z = torch.complex(torch.randn(shape, device="cuda", generator=gen), torch.randn(shape, device="cuda",
+                                                                                      generator=gen))
+        return (z / math.sqrt(2)).to(dtype).contiguous()
+
+    x = rand_x((N,), torch.complex64)
     y = torch.empty_like(x)
     for _ in range(args.warmup):
         sc.scabem_apply(op, x, y, prec=sc.SCABEM_C64, stream=stream)
@@ -237,16 +268,67 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws, device=torch.device("cuda", local))
     barrier(ws)
 
-    # roofline of the dominant kernel
-    hbm, src = peaks()
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    extras = None
+    if not args.no_extras:
+        # FP64 operator, single right-hand side
+        x2 = x.to(torch.complex128)
+        y2 = torch.empty_like(x2)
+        ms128 = timed(lambda: sc.scabem_apply(op, x2, y2, prec=sc.SCABEM_C128, stream=stream), max(3, args.steps // 10))
+        # complex64, 32 right-hand sides in one call (columns of a column-major N x 32 block)
+        nb = 32
+        X = rand_x((nb, N), torch.complex64)
+        Y = torch.empty_like(X)
+        msb = timed(lambda: sc.scabem_apply(op, X, Y, nrhs=nb, ld=N, prec=sc.SCABEM_C64, stream=stream), 3)
+        # GMRES solve: Gaussian beam launched inside the core, complex64 operator with FP64
+        # Arnoldi and FP64 iterative refinement to 1e-8
+        src = [sc.make_source("beam", side="i", pos=(6.0, 0.0, 0.0), dir=(1, 0, 0), pol=(0, 1, 0), b=0.15)]
+        bvec = torch.empty(N, dtype=torch.complex128, device="cuda")
+        sc.scabem_rhs(op, src, bvec, prec=sc.SCABEM_C128, stream=stream)
+        xs = torch.zeros_like(bvec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sinfo = sc.scabem_solve(op, bvec, xs, tol=1e-4, restart=100, maxit=20000, refine_tol=1e-8, max_refine=10,
+                                prec=sc.SCABEM_C64, stream=stream)[0]
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        extras = {
+            "c128": {"value": 1e3 / ms128, "unit": UNIT, "ms_per_step": ms128, "dtype": "c128"},
+            "batched_c64": {"value": nb * 1e3 / msb, "unit": UNIT, "nrhs": nb, "ms_per_call": msb},
+            "solve": {"seconds": t_solve, "iterations": sinfo["iters"], "refinements": sinfo["refinements"],
+                      "relres": sinfo["relres"], "status": sinfo["status"],
+                      "rhs": "Gaussian beam (waist 0.15 um) in the core at x = 6 um, y-polarised",
+                      "mode": "GMRES(100) on the complex64 operator to 1e-4 with FP64 Arnoldi (CGS2), FP64 refinement to 1e-8"},
+        }
+
+    # roofline of the dominant kernel, and of the whole matvec
+    hbm, src_peak = peaks()
     per = {k: v / max(napp, 1) for k, v in stages.items()}
-    bmodel = stage_bytes(info, case, 8)
+    bmodel = stage_bytes(info, ginfo, case, N, 8)
     dom = max(per, key=per.get)
     roof = None
     if dom in bmodel:
         ach = bmodel[dom] / (per[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": src, "algorithmic_bytes": bmodel[dom]}
+                "traffic": None, "peak_source": src_peak, "algorithmic_bytes": bmodel[dom]}
+    t_mv = ms_max / args.steps / 1e3
+    b_pruned = sum(bmodel.values())
+    b_full = survey_model_bytes(info, case, N, 8)
+    mv_roof = {
+        "pruned_bytes": b_pruned, "pruned_frac": b_pruned / t_mv / 1e9 / hbm,
+        "full_grid_model_bytes": b_full, "full_grid_model_frac": b_full / t_mv / 1e9 / hbm,
+        "peak": hbm, "unit": "GB/s",
+    }
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -257,6 +339,7 @@ def run_gpu(args):
                                    "absorbers at both ends, lambda 1.55 um",
                        "triangles": int(m.nt), "unknowns": int(N), "fft_grid": "512x64x64", "stencil_p": case.grid.p,
                        "q": case.q, "r_near_um": case.r_near, "near_pairs": info["near_pairs"],
+                       "covered_grid_points": ginfo["covered_points"], "active_columns": ginfo["active_columns"],
                        "l2": "working set per step > L2 (near data %.0f MB)" % (info["near_bytes_c64"] / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": t_setup},
             "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
@@ -264,9 +347,12 @@ def run_gpu(args):
             "gpu_launches": 7 * args.steps,
             "stages_ms_per_step": per,
             "roofline": roof,
+            "matvec_roofline": mv_roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }
+        if extras:
+            line.update(extras)
         print(json.dumps(line), flush=True)
     sc.scabem_op_destroy(op)
     sc.scabem_mesh_destroy(mh)
@@ -305,12 +391,13 @@ def run_reference(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the c128, batched and solve measurements")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

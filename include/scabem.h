@@ -121,6 +121,12 @@ int scabem_op_create(scabem_mesh_t mesh, const scabem_media* media, const scabem
 int scabem_op_info(scabem_op_t op, int64_t* n_near_pairs, int64_t* near_bytes_c64,
                    int64_t* near_bytes_c128, int64_t* n_qpoints);
 
+/* Sparsity of the grid (Appendix B's uniform grid): physical grid points
+ * that some projection stencil covers, and (i1, i2) columns holding one of
+ * them.  Sources are zero and potentials unused elsewhere, so the axis-0
+ * transforms run on the active columns only.  Any output pointer may be NULL. */
+int scabem_op_grid_info(scabem_op_t op, int64_t* n_covered_points, int64_t* n_active_columns);
+
 void scabem_op_destroy(scabem_op_t op);
 
 /* Conductivity profile (Sec. IV, Eq. 23).

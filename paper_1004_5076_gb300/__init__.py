@@ -95,6 +95,7 @@ def lib():
     L.scabem_mesh_destroy.restype = None
     L.scabem_op_create.argtypes = [vp, C.POINTER(Media), C.POINTER(GridOpts), vp, C.POINTER(vp)]
     L.scabem_op_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.scabem_op_grid_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     L.scabem_op_destroy.argtypes = [vp]
     L.scabem_op_destroy.restype = None
     L.scabem_set_sigma.argtypes = [vp, C.POINTER(Sigma)]
@@ -186,6 +187,12 @@ def scabem_op_info(op):
     a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().scabem_op_info(op, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
     return {"near_pairs": a.value, "near_bytes_c64": b.value, "near_bytes_c128": c.value, "qpoints": d.value}
+
+
+def scabem_op_grid_info(op):
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().scabem_op_grid_info(op, C.byref(a), C.byref(b)))
+    return {"covered_points": a.value, "active_columns": b.value}
 
 
 def scabem_op_destroy(op):

@@ -492,6 +492,16 @@ int scabem_op_info(scabem_op_t op, int64_t* npairs, int64_t* b64, int64_t* b128,
   return SCABEM_OK;
 }
 
+int scabem_op_grid_info(scabem_op_t op, int64_t* npts, int64_t* ncols) {
+  if (!op) {
+    set_error("null operator");
+    return SCABEM_E_ARG;
+  }
+  if (npts) *npts = op->ngnz;
+  if (ncols) *ncols = op->nac;
+  return SCABEM_OK;
+}
+
 int scabem_profile(scabem_op_t op, int32_t enable, int32_t max_applies) {
   if (!op || (enable && max_applies < 1)) {
     set_error("scabem_profile: null operator or max_applies < 1");

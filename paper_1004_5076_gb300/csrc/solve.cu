@@ -142,30 +142,49 @@ __global__ void k_rows_out(const cd* __restrict__ val, const int32_t* __restrict
 constexpr int DOT_THREADS = 256;
 constexpr int DOT_BLOCKS = 304;  // 2 x 152 SMs
 
-// part[b*nv + c] = sum over block b's rows of conj(V[:,c]) . w
-__global__ void k_dots(const cd* __restrict__ V, int64_t ldv, int nv, const cd* __restrict__ w, int64_t N,
-                       cd* __restrict__ part) {
-  __shared__ double sre[DOT_THREADS], sim[DOT_THREADS];
-  for (int c = 0; c < nv; ++c) {
-    const cd* v = V + (int64_t)c * ldv;
-    double ar = 0.0, ai = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-      const cd a = v[i], b = w[i];
-      ar += a.re * b.re + a.im * b.im;
-      ai += a.re * b.im - a.im * b.re;
-    }
-    sre[threadIdx.x] = ar;
-    sim[threadIdx.x] = ai;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) {
-        sre[threadIdx.x] += sre[threadIdx.x + st];
-        sim[threadIdx.x] += sim[threadIdx.x + st];
+// Tall-skinny dot products for the Arnoldi step: part[b * ldp + c] = sum
+// over row block b of conj(V[:, c]) . w, for the tile of DOT_TC columns
+// c0 = blockIdx.y * DOT_TC (w is read once per tile).
+constexpr int DOT_TC = 8;
+__global__ void __launch_bounds__(DOT_THREADS) k_dots(const cd* __restrict__ V, int64_t ldv, int nv,
+                                                      const cd* __restrict__ w, int64_t N, cd* __restrict__ part,
+                                                      int ldp) {
+  __shared__ double sm[DOT_THREADS / 32][2 * DOT_TC];
+  const int c0 = blockIdx.y * DOT_TC;
+  const int nc = min(DOT_TC, nv - c0);
+  double ar[DOT_TC], ai[DOT_TC];
+#pragma unroll
+  for (int c = 0; c < DOT_TC; ++c) ar[c] = ai[c] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const cd b = w[i];
+#pragma unroll
+    for (int c = 0; c < DOT_TC; ++c)
+      if (c < nc) {
+        const cd a = V[(int64_t)(c0 + c) * ldv + i];
+        ar[c] += a.re * b.re + a.im * b.im;
+        ai[c] += a.re * b.im - a.im * b.re;
       }
-      __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < DOT_TC; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar[c] += __shfl_xor_sync(0xffffffffu, ar[c], o);
+      ai[c] += __shfl_xor_sync(0xffffffffu, ai[c], o);
     }
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * nv + c] = mk(sre[0], sim[0]);
-    __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < DOT_TC; ++c) {
+      sm[wp][2 * c] = ar[c];
+      sm[wp][2 * c + 1] = ai[c];
+    }
+  __syncthreads();
+  if (threadIdx.x < 2 * nc) {
+    double v = 0.0;
+    for (int k = 0; k < DOT_THREADS / 32; ++k) v += sm[k][threadIdx.x];
+    double* o = reinterpret_cast<double*>(part + (int64_t)blockIdx.x * ldp + c0);
+    o[threadIdx.x] = v;
   }
 }
 
@@ -188,6 +207,55 @@ __global__ void k_reduce_parts(const cd* __restrict__ part, int nb, int nv, cd* 
     __syncthreads();
   }
   if (threadIdx.x == 0) out[c] = mk(sre[0], sim[0]);
+}
+
+// w -= V h, and nparts[b] = sum over block b's rows of |w|^2 (new w)
+__global__ void __launch_bounds__(DOT_THREADS) k_vsub_norm(const cd* __restrict__ V, int64_t ldv, int nv,
+                                                           const cd* __restrict__ h, cd* __restrict__ w, int64_t N,
+                                                           double* __restrict__ nparts) {
+  __shared__ double sm[DOT_THREADS / 32];
+  double nn = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    cd acc = w[i];
+    for (int c = 0; c < nv; ++c) {
+      const cd a = V[(int64_t)c * ldv + i], b = h[c];
+      acc.re -= a.re * b.re - a.im * b.im;
+      acc.im -= a.re * b.im + a.im * b.re;
+    }
+    w[i] = acc;
+    nn += acc.re * acc.re + acc.im * acc.im;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int k = 0; k < DOT_THREADS / 32; ++k) v += sm[k];
+    nparts[blockIdx.x] = v;
+  }
+}
+
+// out->re = sqrt(sum of nparts), out->im = 0 (one block)
+__global__ void k_norm_fin(const double* __restrict__ nparts, int nb, cd* __restrict__ out) {
+  __shared__ double sm[DOT_THREADS];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += nparts[b];
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = mk(sqrt(fmax(sm[0], 0.0)), 0.0);
+}
+
+// v = w / |w| with the norm read from the device (zero when it vanishes)
+__global__ void k_scale_dev(const cd* __restrict__ w, const cd* __restrict__ nrm, cd* __restrict__ v, int64_t N) {
+  const double n = nrm->re;
+  const double s = n > 1e-300 ? 1.0 / n : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = s * w[i];
 }
 
 // w -= V h   (h on the device, nv entries)
@@ -230,7 +298,8 @@ struct Work {
   cd* w = nullptr;     // N
   cd* t = nullptr;     // N
   cd* part = nullptr;  // DOT_BLOCKS x (m+1)
-  cd* h = nullptr;     // m+1
+  cd* h = nullptr;     // 2 (m+1) + 1: both Gram-Schmidt passes' coefficients, then the norm
+  double* nparts = nullptr;  // DOT_BLOCKS
   cd* z = nullptr;     // N, preconditioned Krylov vector
   cd* u = nullptr;     // N, solution in the preconditioned variables
   cx<float>* xf = nullptr;
@@ -243,16 +312,24 @@ struct Work {
     cudaFree(t);
     cudaFree(part);
     cudaFree(h);
+    cudaFree(nparts);
     cudaFree(xf);
     cudaFree(yf);
   }
 };
 
+// h_dev[c] = conj(V[:, c]) . w for c < nv, left on the device
+int dots_dev(const cd* V, int64_t ldv, int nv, const cd* w, int64_t N, Work& W, cd* h_dev, cudaStream_t s) {
+  k_dots<<<dim3(DOT_BLOCKS, (unsigned)cdiv(nv, DOT_TC)), DOT_THREADS, 0, s>>>(V, ldv, nv, w, N, W.part, nv);
+  CK(cudaGetLastError());
+  k_reduce_parts<<<nv, DOT_THREADS, 0, s>>>(W.part, DOT_BLOCKS, nv, h_dev);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
 int dots(const cd* V, int64_t ldv, int nv, const cd* w, int64_t N, Work& W, cudaStream_t s, std::vector<cd>& out) {
-  k_dots<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(V, ldv, nv, w, N, W.part);
-  CK(cudaGetLastError());
-  k_reduce_parts<<<nv, DOT_THREADS, 0, s>>>(W.part, DOT_BLOCKS, nv, W.h);
-  CK(cudaGetLastError());
+  int rc = dots_dev(V, ldv, nv, w, N, W, W.h, s);
+  if (rc) return rc;
   out.resize(nv);
   CK(cudaMemcpyAsync(out.data(), W.h, sizeof(cd) * nv, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -298,7 +375,7 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
   if (rn0 == 0.0) return SCABEM_OK;
   // working residual: t = r - A d (d accumulates over restarts)
   CK(cudaMemcpyAsync(W.t, r, sizeof(cd) * N, cudaMemcpyDeviceToDevice, s));
-  std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hv, hv2;
+  std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hv, hv2, hbuf;
   double beta = rn0;
   while (true) {
     k_scale_to<<<DOT_BLOCKS, 256, 0, s>>>(W.t, 1.0 / beta, W.V, N);
@@ -314,17 +391,31 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
       if (rc) return rc;
       rc = op_apply64(op, W.z, W.w, prec, W, s);
       if (rc) return rc;
-      rc = dots(W.V, N, j + 1, W.w, N, W, s, hv);
+      // classical Gram-Schmidt twice, the norm and the next basis vector on
+      // the device; one copy of the coefficients to the host
+      cd* h1 = W.h;
+      cd* h2 = W.h + (m + 1);
+      cd* hnd = W.h + 2 * (m + 1);
+      rc = dots_dev(W.V, N, j + 1, W.w, N, W, h1, s);
       if (rc) return rc;
-      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j + 1, W.h, W.w, N);
+      k_vsub<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h1, W.w, N);
       CK(cudaGetLastError());
-      rc = dots(W.V, N, j + 1, W.w, N, W, s, hv2);
+      rc = dots_dev(W.V, N, j + 1, W.w, N, W, h2, s);
       if (rc) return rc;
-      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j + 1, W.h, W.w, N);
+      k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h2, W.w, N, W.nparts);
       CK(cudaGetLastError());
-      double hn;
-      rc = norm2(W.w, N, W, s, hn);
-      if (rc) return rc;
+      k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, hnd);
+      CK(cudaGetLastError());
+      if (j + 1 < m) {
+        k_scale_dev<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.w, hnd, W.V + (int64_t)(j + 1) * N, N);
+        CK(cudaGetLastError());
+      }
+      hbuf.resize(2 * (m + 1) + 1);
+      CK(cudaMemcpyAsync(hbuf.data(), W.h, sizeof(cd) * hbuf.size(), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      hv.assign(hbuf.begin(), hbuf.begin() + j + 1);
+      hv2.assign(hbuf.begin() + (m + 1), hbuf.begin() + (m + 1) + j + 1);
+      const double hn = hbuf[2 * (m + 1)].re;
       if (!std::isfinite(hn)) {
         set_error("non-finite Krylov vector");
         return SCABEM_E_NONFINITE;
@@ -357,8 +448,6 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
         done = true;
         break;
       }
-      k_scale_to<<<DOT_BLOCKS, 256, 0, s>>>(W.w, 1.0 / hn, W.V + (int64_t)(j + 1) * N, N);
-      CK(cudaGetLastError());
     }
     // back substitution, d += V y
     std::vector<cd> y(j);
@@ -571,7 +660,8 @@ int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, co
   CK(cudaMalloc(&W.z, sizeof(cd) * N));
   CK(cudaMalloc(&W.u, sizeof(cd) * N));
   CK(cudaMalloc(&W.part, sizeof(cd) * DOT_BLOCKS * (m + 1)));
-  CK(cudaMalloc(&W.h, sizeof(cd) * (m + 1)));
+  CK(cudaMalloc(&W.h, sizeof(cd) * (2 * (m + 1) + 1)));
+  CK(cudaMalloc(&W.nparts, sizeof(double) * DOT_BLOCKS));
   if (prec == SCABEM_C64) {
     CK(cudaMalloc(&W.xf, sizeof(cx<float>) * N));
     CK(cudaMalloc(&W.yf, sizeof(cx<float>) * N));
