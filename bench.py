@@ -43,6 +43,23 @@ METRIC = "operator matvecs/sec and GMRES solve time at N unknowns (%HBM roofline
 UNIT = "matvec/s"
 
 
+def measured_traffic(stage):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu
+    capture, or None when there is none or the kernel source changed since."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "dram_traffic_guide_12um.json")
+    if not os.path.exists(p):
+        return None
+    k = json.load(open(p)).get("kernels", {}).get(stage)
+    if not k:
+        return None
+    src = os.path.join(ROOT, k["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != k["source_sha256_16"]:
+        return None
+    return int(k["dram_read_bytes"] + k["dram_write_bytes"])
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -320,7 +337,7 @@ def run_gpu(args):
     if dom in bmodel:
         ach = bmodel[dom] / (per[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": src_peak, "algorithmic_bytes": bmodel[dom]}
+                "traffic": measured_traffic(dom), "peak_source": src_peak, "algorithmic_bytes": bmodel[dom]}
     t_mv = ms_max / args.steps / 1e3
     b_pruned = sum(bmodel.values())
     b_full = survey_model_bytes(info, case, N, 8)
