@@ -383,3 +383,52 @@ def test_reflection_fit_recovers_two_waves():
     E = np.exp(-1j * beta * xs) + r * np.exp(1j * beta * xs)
     got, bt, res = post.fit_reflection(xs, E, betas=np.linspace(10, 12.5, 2501))
     assert abs(bt - beta) < 1e-3 and abs(got - r) < 1e-4 and res < 1e-3
+
+
+# ---------------------------------------------------------------- B-spline conductivity
+def _line_points(s, x0=1.0, L=2.0, axis=0):
+    pts = np.zeros((len(s), 3))
+    pts[:, axis] = x0 + L * np.asarray(s)
+    return pts
+
+
+def test_bspline_partition_of_unity_and_clamped_ends():
+    """Cubic B-splines on clamped knots sum to one on [0, 1] and interpolate
+    the end coefficients; the profile is zero outside [x0, x0 + L]."""
+    from oracle import sigma as osig
+
+    s = np.linspace(0.0, 1.0, 101)
+    ones = osig.bspline(_line_points(s), 1.0, 2.0, np.ones(16))
+    assert np.max(np.abs(ones - 1.0)) < 1e-14
+    c = np.random.default_rng(5).uniform(0.0, 1.0, 16)
+    v = osig.bspline(_line_points(np.array([0.0, 1.0])), 1.0, 2.0, c)
+    assert abs(v[0] - c[0]) < 1e-14 and abs(v[1] - c[-1]) < 1e-14
+    out = osig.bspline(_line_points(np.array([-0.01, 1.01])), 1.0, 2.0, c)
+    assert np.all(out == 0.0)
+
+
+def test_bspline_matches_library_routine():
+    """Against scipy's B-spline evaluation with the same knots and coefficients."""
+    from scipy.interpolate import BSpline
+
+    from oracle import sigma as osig
+
+    for n in (4, 7, 16):
+        c = np.random.default_rng(n).uniform(0.0, 2.0, n)
+        knots = osig.bspline_knots(n, 3)
+        s = np.random.default_rng(100 + n).uniform(0.0, 1.0, 200)
+        ref = BSpline(knots, c, 3)(s)
+        got = osig.bspline(_line_points(s, axis=2), 1.0, 2.0, c, axis=2)
+        assert np.max(np.abs(got - ref)) < 1e-13
+
+
+def test_bspline_reproduces_linear_function():
+    """Greville abscissae as coefficients reproduce s itself (linear precision)."""
+    from oracle import sigma as osig
+
+    n = 9
+    knots = osig.bspline_knots(n, 3)
+    grev = np.array([knots[k + 1 : k + 4].mean() for k in range(n)])
+    s = np.linspace(0.0, 1.0, 57)
+    got = osig.bspline(_line_points(s), 1.0, 2.0, grev)
+    assert np.max(np.abs(got - s)) < 1e-13
