@@ -79,7 +79,14 @@ typedef struct {
  *   q         quadrature points per triangle (1, 3, 6 or 7; Dunavant rules).
  *   r_near    near-field radius [um]: triangle pairs with centroid distance
  *             below it get the exact panel interaction (precorrection).
- *   prec_mask bit 0: build complex64 operator data, bit 1: complex128. */
+ *   prec_mask bit 0: build complex64 operator data, bit 1: complex128.
+ *   transverse how the (y, z) part of the grid convolution runs, per axis-0
+ *             frequency: 1 = 2-D FFTs of the zero-padded planes with the
+ *             Green spectrum; 2 = direct sum over the active (y, z) columns
+ *             (those a stencil covers) with the axis-0 transform of the
+ *             spatial Green table; 0 = automatic (direct when the active
+ *             columns are few: nac^2 <= 16 (2 n_y)(2 n_z)).  Both give the
+ *             same linear convolution up to rounding. */
 typedef struct {
   int32_t n[3];
   double h;
@@ -88,6 +95,7 @@ typedef struct {
   int32_t q;
   double r_near;
   int32_t prec_mask;
+  int32_t transverse;
 } scabem_grid_opts;
 
 /* Create a mesh from host arrays: xyz (nv x 3, um), tri (nt x 3, vertex
@@ -124,8 +132,11 @@ int scabem_op_info(scabem_op_t op, int64_t* n_near_pairs, int64_t* near_bytes_c6
 /* Sparsity of the grid (Appendix B's uniform grid): physical grid points
  * that some projection stencil covers, and (i1, i2) columns holding one of
  * them.  Sources are zero and potentials unused elsewhere, so the axis-0
- * transforms run on the active columns only.  Any output pointer may be NULL. */
-int scabem_op_grid_info(scabem_op_t op, int64_t* n_covered_points, int64_t* n_active_columns);
+ * transforms run on the active columns only.  transverse_direct = 1 when the
+ * (y, z) convolution runs as a direct sum over the active columns, 0 for 2-D
+ * FFT planes.  Any output pointer may be NULL. */
+int scabem_op_grid_info(scabem_op_t op, int64_t* n_covered_points, int64_t* n_active_columns,
+                        int32_t* transverse_direct);
 
 void scabem_op_destroy(scabem_op_t op);
 
@@ -136,13 +147,27 @@ void scabem_op_destroy(scabem_op_t op);
  *     seg[6*i .. 6*i+5] = {x0 [um], L [um], sigma0 [S], d, axis (0..2), dir (+1/-1)};
  *     d = 0 gives a step of height sigma0 at x0.
  *   SCABEM_SIGMA_PER_QPOINT: per_qpoint[t*q + a] [S], host array.
- * Conductivity enters only the Eq. 13 / Eq. 14 rows of absorber edges. */
-typedef enum { SCABEM_SIGMA_MONOMIAL = 0, SCABEM_SIGMA_PER_QPOINT = 1 } scabem_sigma_kind;
+ *   SCABEM_SIGMA_BSPLINE: sum_k coef[k] N_k(s) [S], s = (x_axis - x0) / L,
+ *     N_k the cubic B-splines on the clamped uniform knot vector of ncoef
+ *     (>= 4, <= 1024) coefficients over [0, 1]; zero for s outside [0, 1].
+ *     Uses x0 [um], L [um] (> 0), axis (0..2), ncoef and coef (host array,
+ *     finite, >= 0).  A smooth profile for gradient studies with respect to
+ *     the coefficients.
+ * Conductivity enters only the Eq. 13 / Eq. 14 rows of absorber edges.
+ * Fields a kind does not use are ignored. */
+typedef enum {
+  SCABEM_SIGMA_MONOMIAL = 0,
+  SCABEM_SIGMA_PER_QPOINT = 1,
+  SCABEM_SIGMA_BSPLINE = 2
+} scabem_sigma_kind;
 typedef struct {
   int32_t kind;
   int32_t nseg;
   const double* seg;
   const double* per_qpoint;
+  double x0, L;
+  int32_t axis, ncoef;
+  const double* coef;
 } scabem_sigma;
 int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sigma);
 

@@ -23,7 +23,7 @@ LIBPATH = os.path.join(_HERE, "libscabem.so")
 _lib = None
 
 SCABEM_C64, SCABEM_C128 = 0, 1
-SIGMA_MONOMIAL, SIGMA_PER_QPOINT = 0, 1
+SIGMA_MONOMIAL, SIGMA_PER_QPOINT, SIGMA_BSPLINE = 0, 1, 2
 STATUS = {
     0: "SCABEM_OK", -1: "SCABEM_E_ARG", -2: "SCABEM_E_MESH", -3: "SCABEM_E_DEVICE", -4: "SCABEM_E_NOMEM",
     -5: "SCABEM_E_NOCONV", -6: "SCABEM_E_BREAKDOWN", -7: "SCABEM_E_NONFINITE", -8: "SCABEM_E_TIMEOUT",
@@ -43,12 +43,13 @@ class Media(C.Structure):
 
 class GridOpts(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("h", C.c_double), ("origin", C.c_double * 3), ("p", C.c_int32),
-                ("q", C.c_int32), ("r_near", C.c_double), ("prec_mask", C.c_int32)]
+                ("q", C.c_int32), ("r_near", C.c_double), ("prec_mask", C.c_int32), ("transverse", C.c_int32)]
 
 
 class Sigma(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nseg", C.c_int32), ("seg", C.POINTER(C.c_double)),
-                ("per_qpoint", C.POINTER(C.c_double))]
+                ("per_qpoint", C.POINTER(C.c_double)), ("x0", C.c_double), ("L", C.c_double),
+                ("axis", C.c_int32), ("ncoef", C.c_int32), ("coef", C.POINTER(C.c_double))]
 
 
 class Source(C.Structure):
@@ -95,7 +96,7 @@ def lib():
     L.scabem_mesh_destroy.restype = None
     L.scabem_op_create.argtypes = [vp, C.POINTER(Media), C.POINTER(GridOpts), vp, C.POINTER(vp)]
     L.scabem_op_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
-    L.scabem_op_grid_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    L.scabem_op_grid_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]
     L.scabem_op_destroy.argtypes = [vp]
     L.scabem_op_destroy.restype = None
     L.scabem_set_sigma.argtypes = [vp, C.POINTER(Sigma)]
@@ -175,9 +176,13 @@ def scabem_mesh_destroy(mesh):
     lib().scabem_mesh_destroy(mesh)
 
 
-def scabem_op_create(mesh, media, n, h, origin, p=3, q=6, r_near=0.0, prec_mask=3, stream=None):
+TRANSVERSE = {"auto": 0, "fft": 1, "direct": 2}
+
+
+def scabem_op_create(mesh, media, n, h, origin, p=3, q=6, r_near=0.0, prec_mask=3, stream=None, transverse="auto"):
     md = Media(*media)
-    go = GridOpts((C.c_int32 * 3)(*n), h, (C.c_double * 3)(*origin), p, q, r_near, prec_mask)
+    tv = TRANSVERSE[transverse] if isinstance(transverse, str) else int(transverse)
+    go = GridOpts((C.c_int32 * 3)(*n), h, (C.c_double * 3)(*origin), p, q, r_near, prec_mask, tv)
     op = C.c_void_p()
     _check(lib().scabem_op_create(mesh, C.byref(md), C.byref(go), _stream(stream), C.byref(op)))
     return op
@@ -190,17 +195,25 @@ def scabem_op_info(op):
 
 
 def scabem_op_grid_info(op):
-    a, b = C.c_int64(), C.c_int64()
-    _check(lib().scabem_op_grid_info(op, C.byref(a), C.byref(b)))
-    return {"covered_points": a.value, "active_columns": b.value}
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib().scabem_op_grid_info(op, C.byref(a), C.byref(b), C.byref(c)))
+    return {"covered_points": a.value, "active_columns": b.value, "transverse_direct": bool(c.value)}
 
 
 def scabem_op_destroy(op):
     lib().scabem_op_destroy(op)
 
 
-def scabem_set_sigma(op, segments=None, per_qpoint=None):
-    """segments: list of (x0, L, sigma0 [S], d, axis, dir); or per_qpoint (nt*q) [S]."""
+def scabem_set_sigma(op, segments=None, per_qpoint=None, bspline=None):
+    """segments: list of (x0, L, sigma0 [S], d, axis, dir); or per_qpoint (nt*q) [S];
+    or bspline = (x0, L, axis, coef) with coef the cubic B-spline coefficients [S]."""
+    if bspline is not None:
+        x0, L, axis, coef = bspline
+        cf = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+        sg = Sigma(SIGMA_BSPLINE, 0, None, None, float(x0), float(L), int(axis), len(cf),
+                   cf.ctypes.data_as(C.POINTER(C.c_double)))
+        _check(lib().scabem_set_sigma(op, C.byref(sg)))
+        return
     if per_qpoint is not None:
         arr = np.ascontiguousarray(per_qpoint, dtype=np.float64).reshape(-1)
         sg = Sigma(SIGMA_PER_QPOINT, 0, None, arr.ctypes.data_as(C.POINTER(C.c_double)))

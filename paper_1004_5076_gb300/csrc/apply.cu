@@ -629,7 +629,7 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   {
     const size_t sm = pt_smem_bytes(op->q, sizeof(cx<R>));
     PointsFn<R> fn = op->p == 2 ? k_points<R, 2> : op->p == 3 ? k_points<R, 3> : k_points<R, 4>;
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm)) return rc_;
     fn<<<(int)cdiv(nt, PT_WARPS), PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
                                                   op->tri, op->cX, op->qp, op->qw, pd.sig, nt, op->q, n0, n1, n2,
                                                   (R)op->ke, (R)op->ki, (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0,

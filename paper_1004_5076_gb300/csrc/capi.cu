@@ -2,6 +2,9 @@
 // RWG edge table (host topology), and dispatch to the device kernels.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -15,6 +18,17 @@
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+int set_max_smem(int device, const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> done;
+  std::lock_guard<std::mutex> lock(mu);
+  int& have = done[{device, kernel}];
+  if (have >= bytes) return SCABEM_OK;
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  have = bytes;
+  return SCABEM_OK;
+}
 
 int cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
@@ -67,6 +81,8 @@ template <typename R>
 void free_prec(PrecData<R>& pd) {
   cudaFree(pd.ghat[0]);
   cudaFree(pd.ghat[1]);
+  cudaFree(pd.gt[0]);
+  cudaFree(pd.gt[1]);
   cudaFree(pd.near);
   for (int a = 0; a < 3; ++a) cudaFree(pd.tw[a]);
   cudaFree(pd.L);
@@ -344,8 +360,9 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
     return SCABEM_E_ARG;
   }
   if (o->p < 2 || o->p > MAXP || !(o->q == 1 || o->q == 3 || o->q == 6 || o->q == 7) || !(o->h > 0) ||
-      !(o->r_near >= 0) || o->prec_mask < 1 || o->prec_mask > 3) {
-    set_error("grid options: need p in 2..4, q in {1,3,6,7}, h > 0, r_near >= 0, prec_mask in 1..3");
+      !(o->r_near >= 0) || o->prec_mask < 1 || o->prec_mask > 3 || o->transverse < 0 || o->transverse > 2) {
+    set_error("grid options: need p in 2..4, q in {1,3,6,7}, h > 0, r_near >= 0, prec_mask in 1..3, "
+              "transverse in 0..2");
     return SCABEM_E_ARG;
   }
   scabem_op* op = new (std::nothrow) scabem_op();
@@ -366,6 +383,7 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   op->h = o->h;
   op->r_near = o->r_near;
   op->prec_mask = o->prec_mask;
+  op->transverse = o->transverse;
   for (int a = 0; a < 3; ++a) {
     op->n[a] = o->n[a];
     op->P[a] = 2 * o->n[a];
@@ -492,13 +510,14 @@ int scabem_op_info(scabem_op_t op, int64_t* npairs, int64_t* b64, int64_t* b128,
   return SCABEM_OK;
 }
 
-int scabem_op_grid_info(scabem_op_t op, int64_t* npts, int64_t* ncols) {
+int scabem_op_grid_info(scabem_op_t op, int64_t* npts, int64_t* ncols, int32_t* direct) {
   if (!op) {
     set_error("null operator");
     return SCABEM_E_ARG;
   }
   if (npts) *npts = op->ngnz;
   if (ncols) *ncols = op->nac;
+  if (direct) *direct = op->tdirect ? 1 : 0;
   return SCABEM_OK;
 }
 
@@ -569,6 +588,7 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->pinv);
   cudaFree(op->err);
   cudaFree(op->acol);
+  cudaFree(op->acoord);
   if (op->tmo_h) cudaFreeHost(op->tmo_h);
   free_prec(op->f);
   free_prec(op->d);
@@ -600,6 +620,27 @@ int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sg) {
       }
     }
     return setup_sigma_monomial(op, sg->nseg, sg->seg, s);
+  }
+  if (sg->kind == SCABEM_SIGMA_BSPLINE) {
+    if (!sg->coef || sg->ncoef < 4 || sg->ncoef > 1024 || !(sg->L > 0) || sg->axis < 0 || sg->axis > 2) {
+      set_error("B-spline profile: need coef, 4 <= ncoef <= 1024, L > 0, axis in {0,1,2}");
+      return SCABEM_E_ARG;
+    }
+    if (!std::isfinite(sg->x0) || !std::isfinite(sg->L)) {
+      set_error("B-spline profile: non-finite x0 or L");
+      return SCABEM_E_NONFINITE;
+    }
+    for (int i = 0; i < sg->ncoef; ++i) {
+      if (!std::isfinite(sg->coef[i])) {
+        set_error("B-spline profile: non-finite coefficient");
+        return SCABEM_E_NONFINITE;
+      }
+      if (sg->coef[i] < 0) {
+        set_error("B-spline profile: negative coefficient");
+        return SCABEM_E_ARG;
+      }
+    }
+    return setup_sigma_bspline(op, sg->x0, sg->L, sg->axis, sg->ncoef, sg->coef, s);
   }
   if (sg->kind == SCABEM_SIGMA_PER_QPOINT) {
     if (!sg->per_qpoint) {

@@ -112,6 +112,7 @@ template <typename R>
 struct PrecData {
   bool built = false;
   cx<R>* ghat[2] = {nullptr, nullptr};  // octant spectra [q0][q2][q1], scaled by 1/(P0 P1 P2)
+  cx<R>* gt[2] = {nullptr, nullptr};    // transverse tables [q0][|d1|][|d2|] (direct mode)
   cx<R>* near = nullptr;                // [npairs][NCORR][q][2]
   cx<R>* tw[3] = {nullptr, nullptr, nullptr};  // forward twiddles per axis length
   R* L = nullptr;                       // Q * 3 * p stencil weights
@@ -166,6 +167,14 @@ struct scabem_op {
   int64_t nac = 0;
   int32_t* acol = nullptr;  // nac
   uint64_t rowmask = 0;
+  // (y, z) convolution: direct sum over the active columns (tdirect) with
+  // gt[medium][q0][|d1|][|d2|] = (1/P0) x axis-0 transform of the spatial
+  // Green table for |d1| < R1, |d2| < R2 (the active box), or 2-D FFT planes
+  // with ghat.  acoord[j] = (i1 - b1) << 16 | (i2 - b2) of active column j.
+  int transverse = 0;
+  bool tdirect = false;
+  int R1 = 0, R2 = 0;
+  int32_t* acoord = nullptr;  // nac
   double* sig64 = nullptr;    // Q normalised (master copy)
   // near list
   int64_t npairs = 0;
@@ -205,6 +214,11 @@ int cuda_fail(cudaError_t e, const char* what);
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Raise a kernel's dynamic shared-memory limit on a device to at least
+// `bytes`, calling the runtime only the first time a larger size is needed
+// (the apply path then makes no attribute calls).
+int set_max_smem(int device, const void* kernel, int bytes);
+
 // ------------------------------------------------------------------ launchers
 // setup.cu
 int setup_geometry(scabem_op* op, const scabem_mesh* m, cudaStream_t s);
@@ -212,6 +226,7 @@ int setup_green(scabem_op* op, cudaStream_t s);
 int setup_near(scabem_op* op, cudaStream_t s);
 int setup_sigma_monomial(scabem_op* op, int nseg, const double* seg, cudaStream_t s);
 int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s);
+int setup_sigma_bspline(scabem_op* op, double x0, double L, int axis, int ncoef, const double* coef, cudaStream_t s);
 int setup_precond(scabem_op* op, cudaStream_t s);
 int setup_gather(scabem_op* op, cudaStream_t s);
 int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s);
@@ -223,6 +238,8 @@ template <typename R>
 int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s);
 template <typename R>
 int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cudaStream_t s);
+template <typename R>
+int fft_axis_full(scabem_op* op, cx<R>* data, int axis, const cx<R>* tw, int dir, cudaStream_t s);
 template <typename R>
 int make_twiddles(cx<R>* tw, int len, cudaStream_t s);
 // solve.cu

@@ -598,6 +598,100 @@ __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
   }
 }
 
+// ---------------------------------------------------------------- stage B, direct
+// Stage B as a direct sum over the active (i1, i2) columns: per (k0 plane,
+// medium) the 8 source fields of that medium (its J set and the M set) are
+// convolved with gt[q0][|d1|][|d2|] (the axis-0 transform of the spatial
+// Green table):  out_v(i) = sum over active j of gt(|i1 - j1|, |i2 - j2|)
+// src_v(j).  This is the linear convolution that the zero-padded 2-D FFTs
+// compute (offsets never reach the padding), evaluated only on the columns
+// that are read.  Medium 0: J_e (0..3), M (8..11) -> outputs 0..3, 4..7;
+// medium 1: J_i (4..7), M (8..11) -> outputs 8..11 and -(12..15).  One
+// thread per output column, 8 accumulators; each table value serves the 8
+// fields, and the source values are shared-memory broadcasts.
+constexpr int PD_THREADS = 128;
+
+// acc[v] += t * s[v], v < 8; complex64 keeps P + j Q parts (packed FP32x2)
+template <typename R>
+struct Acc8;
+template <>
+struct Acc8<float> {
+  float2 P[8], Q[8];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) P[v] = Q[v] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void mac(cx<float> t, const cx<float>* s) {
+    const float2 tr = make_float2(t.re, t.re), ti = make_float2(t.im, t.im);
+    const float4* s4 = reinterpret_cast<const float4*>(s);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 w = s4[u];
+      const float2 a = make_float2(w.x, w.y), b = make_float2(w.z, w.w);
+      P[2 * u] = __ffma2_rn(tr, a, P[2 * u]);
+      Q[2 * u] = __ffma2_rn(ti, a, Q[2 * u]);
+      P[2 * u + 1] = __ffma2_rn(tr, b, P[2 * u + 1]);
+      Q[2 * u + 1] = __ffma2_rn(ti, b, Q[2 * u + 1]);
+    }
+  }
+  __device__ __forceinline__ cx<float> get(int v) const { return mk(P[v].x - Q[v].y, P[v].y + Q[v].x); }
+};
+template <>
+struct Acc8<double> {
+  cx<double> a[8];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) a[v] = czero<double>();
+  }
+  __device__ __forceinline__ void mac(cx<double> t, const cx<double>* s) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) cfma(a[v], t, s[v]);
+  }
+  __device__ __forceinline__ cx<double> get(int v) const { return a[v]; }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __restrict__ A, cx<R>* __restrict__ B,
+                                                              const cx<R>* __restrict__ gtE,
+                                                              const cx<R>* __restrict__ gtI, int P0, int C,
+                                                              const int32_t* __restrict__ acol,
+                                                              const int32_t* __restrict__ acoord, int nac, int R1,
+                                                              int R2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* src = reinterpret_cast<cx<R>*>(smem_raw);  // [nac][8]
+  cx<R>* T = src + (int64_t)nac * 8;                 // [R1][R2]
+  int32_t* crd = reinterpret_cast<int32_t*>(T + R1 * R2);
+  const int k0 = blockIdx.x, med = blockIdx.y;
+  const int q0 = min(k0, P0 - k0);
+  const cx<R>* gt = (med ? gtI : gtE) + (int64_t)q0 * R1 * R2;
+  for (int i = threadIdx.x; i < R1 * R2; i += PD_THREADS) T[i] = gt[i];
+  for (int idx = threadIdx.x; idx < nac * 8; idx += PD_THREADS) {
+    const int v = idx / nac, j = idx - v * nac;  // consecutive threads: consecutive columns of one field
+    const int f = v < 4 ? (med ? 4 + v : v) : 8 + (v - 4);
+    src[j * 8 + v] = A[((int64_t)f * P0 + k0) * C + acol[j]];
+  }
+  for (int i = threadIdx.x; i < nac; i += PD_THREADS) crd[i] = acoord[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nac; i += PD_THREADS) {
+    const int ci = crd[i];
+    const int i1 = ci >> 16, i2 = ci & 0xffff;
+    Acc8<R> acc;
+    acc.zero();
+    for (int j = 0; j < nac; ++j) {
+      const int cj = crd[j];
+      const int d1 = abs(i1 - (cj >> 16)), d2 = abs(i2 - (cj & 0xffff));
+      acc.mac(T[d1 * R2 + d2], src + j * 8);
+    }
+    const int64_t c = acol[i];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int fo = med ? (v < 4 ? 8 + v : 12 + (v - 4)) : v;
+      const cx<R> val = acc.get(v);
+      B[((int64_t)fo * P0 + k0) * C + c] = (med && v >= 4) ? -val : val;
+    }
+  }
+}
+
 // Compiled plane sizes: (2^l1) x (2^l2) with 3 <= l1, l2 <= 7 and l1 + l2 <= 12.
 template <typename R>
 PlanesFn<R> planes_kernel(int l1, int l2) {
@@ -665,25 +759,33 @@ int make_twiddles(cx<R>* tw, int len, cudaStream_t s) {
   return SCABEM_OK;
 }
 
+// Full-length transform along one axis of a P0 x P1 x P2 array (set-up).
+template <typename R>
+int fft_axis_full(scabem_op* op, cx<R>* data, int a, const cx<R>* tw, int dir, cudaStream_t s) {
+  const int64_t total = (int64_t)op->P[0] * op->P[1] * op->P[2];
+  const int len = op->P[a];
+  int inner = 1;
+  for (int b = a + 1; b < 3; ++b) inner *= op->P[b];
+  const int64_t nlines = total / len;
+  const int cb = lines_per_cta<R>(len);
+  const size_t sm = (size_t)len * (cb + 1) * sizeof(cx<R>);
+  const int blocks = (int)cdiv(nlines, cb);
+  if (dir < 0) {
+    CK(cudaFuncSetAttribute(k_fft_axis<R, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fft_axis<R, -1><<<blocks, FFT_THREADS, sm, s>>>(data, len, inner, nlines, cb, tw);
+  } else {
+    CK(cudaFuncSetAttribute(k_fft_axis<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fft_axis<R, 1><<<blocks, FFT_THREADS, sm, s>>>(data, len, inner, nlines, cb, tw);
+  }
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
 template <typename R>
 int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cudaStream_t s) {
-  const int64_t total = (int64_t)op->P[0] * op->P[1] * op->P[2];
   for (int a = 0; a < 3; ++a) {
-    const int len = op->P[a];
-    int inner = 1;
-    for (int b = a + 1; b < 3; ++b) inner *= op->P[b];
-    const int64_t nlines = total / len;
-    const int cb = lines_per_cta<R>(len);
-    const size_t sm = (size_t)len * (cb + 1) * sizeof(cx<R>);
-    const int blocks = (int)cdiv(nlines, cb);
-    if (dir < 0) {
-      CK(cudaFuncSetAttribute(k_fft_axis<R, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_fft_axis<R, -1><<<blocks, FFT_THREADS, sm, s>>>(data, len, inner, nlines, cb, tw[a]);
-    } else {
-      CK(cudaFuncSetAttribute(k_fft_axis<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_fft_axis<R, 1><<<blocks, FFT_THREADS, sm, s>>>(data, len, inner, nlines, cb, tw[a]);
-    }
-    CK(cudaGetLastError());
+    int rc = fft_axis_full<R>(op, data, a, tw[a], dir, s);
+    if (rc) return rc;
   }
   return SCABEM_OK;
 }
@@ -703,7 +805,7 @@ static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   const int C = op->n[1] * op->n[2];
   const int nc = pruned_lines<R>(P0) >= 4 ? pruned_lines<R>(P0) / 4 : 1;  // P0 <= 1024: 4 lines fit
   const size_t sm = (size_t)P0 * (4 * nc + 1) * sizeof(cx<R>);
-  CK(cudaFuncSetAttribute(k_axis0_pm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  if (int rc_ = set_max_smem(op->device, (const void*)k_axis0_pm<R>, (int)sm)) return rc_;
   k_axis0_pm<R><<<dim3((unsigned)cdiv(op->nac, nc), NFIELD_OUT / 4), FFT_THREADS, sm, s>>>(
       pd.stB, pd.grid, n0, P0, C, op->acol, (int)op->nac, nc, pd.tw[0]);
   CK(cudaGetLastError());
@@ -722,15 +824,24 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   const int cb = pruned_lines<R>(P0);
   const size_t sm0 = (size_t)P0 * (cb + 1) * sizeof(cx<R>);
   // stage A
-  CK(cudaFuncSetAttribute(k_axis0<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+  if (int rc_ = set_max_smem(op->device, (const void*)k_axis0<R>, (int)sm0)) return rc_;
   k_axis0<R><<<dim3((unsigned)cdiv(op->nac, cb), NFIELD_IN), FFT_THREADS, sm0, s>>>(
       pd.src, pd.stA, n0, P0, C, op->acol, (int)op->nac, cb, pd.tw[0]);
   CK(cudaGetLastError());
   prof_mark(op, s);
   // stage B
+  if (op->tdirect) {
+    const size_t sm = ((size_t)op->nac * 8 + (size_t)op->R1 * op->R2) * sizeof(cx<R>) + sizeof(int32_t) * op->nac;
+    if (int rc_ = set_max_smem(op->device, (const void*)k_planes_direct<R>, (int)sm)) return rc_;
+    k_planes_direct<R><<<dim3(P0, 2), PD_THREADS, sm, s>>>(pd.stA, pd.stB, pd.gt[0], pd.gt[1], P0, C, op->acol,
+                                                           op->acoord, (int)op->nac, op->R1, op->R2);
+    CK(cudaGetLastError());
+    prof_mark(op, s);
+    return axis0_inverse(op, pd, s);
+  }
   if (P1 == 64 && P2 == 64) {
     const size_t sm = ((size_t)2 * 32 * 64 + (size_t)(P64_THREADS / 8) * P64_SCR) * sizeof(cx<R>);
-    CK(cudaFuncSetAttribute(k_planes64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (int rc_ = set_max_smem(op->device, (const void*)k_planes64<R>, (int)sm)) return rc_;
     k_planes64<R><<<dim3(P0, NFIELD_IN), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1],
                                                                op->rowmask);
     CK(cudaGetLastError());
@@ -743,7 +854,7 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
     set_error("grid: the y and z transform sizes must be in [8, 128]");
     return SCABEM_E_ARG;
   }
-  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm1)) return rc_;
   fn<<<dim3(P0, NFIELD_IN), PLANE_THREADS, sm1, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, n1, n2, pd.tw[1],
                                                    pd.tw[2]);
   CK(cudaGetLastError());
@@ -754,5 +865,6 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
 template int make_twiddles<float>(cx<float>*, int, cudaStream_t);
 template int make_twiddles<double>(cx<double>*, int, cudaStream_t);
 template int fft3d_full<double>(scabem_op*, cx<double>*, const cx<double>* const[3], int, cudaStream_t);
+template int fft_axis_full<double>(scabem_op*, cx<double>*, int, const cx<double>*, int, cudaStream_t);
 template int fft_conv<float>(scabem_op*, PrecData<float>&, cudaStream_t);
 template int fft_conv<double>(scabem_op*, PrecData<double>&, cudaStream_t);

@@ -3,6 +3,7 @@
 // precorrection, and the conductivity at the quadrature points.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -187,6 +188,23 @@ __global__ void k_octant(const cx<double>* __restrict__ F, cx<double>* __restric
   const int64_t o = ((int64_t)q0 * h2 + q2) * h1 + q1;
   if (od) od[o] = v;
   if (of) of[o] = mk((float)v.re, (float)v.im);
+}
+
+// Transverse tables of the direct (y, z) convolution: F holds the axis-0
+// transform of the padded spatial table, [k0][i1][i2]; keep k0 <= P0/2 (even
+// in k0) and offsets 0 <= d1 < R1, 0 <= d2 < R2 (even in d1, d2), scaled by
+// 1/P0 for the unnormalised inverse axis-0 transform.
+__global__ void k_transverse(const cx<double>* __restrict__ F, int P0, int P1, int P2, int R1, int R2,
+                             cx<double>* __restrict__ od, cx<float>* __restrict__ of) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)(P0 / 2 + 1) * R1 * R2;
+  if (idx >= tot) return;
+  const int d2 = (int)(idx % R2);
+  const int d1 = (int)((idx / R2) % R1);
+  const int q0 = (int)(idx / ((int64_t)R1 * R2));
+  const cx<double> v = (1.0 / P0) * F[((int64_t)q0 * P1 + d1) * P2 + d2];
+  if (od) od[idx] = v;
+  if (of) of[idx] = mk((float)v.re, (float)v.im);
 }
 
 // ---------------------------------------------------------------- near list
@@ -422,6 +440,45 @@ __global__ void k_sigma_monomial(const double* __restrict__ qp, int64_t Q, int n
     if (s < 0.0) continue;
     const double u = s > 1.0 ? 1.0 : s;
     sig += sgp[2] * pow(u, sgp[3]);
+  }
+  sig *= ETA0;
+  s64[i] = sig;
+  if (sd) sd[i] = sig;
+  if (sf) sf[i] = (float)sig;
+}
+
+// Cubic B-spline profile sum_k coef[k] N_k(s), s = (x_axis - x0) / L, on the
+// clamped uniform knots of ncoef coefficients over [0, 1] (interior knots
+// j / (ncoef - 3)), zero outside [0, 1]: the knot span of s and de Boor's
+// triangular scheme over the four coefficients that act there.
+__global__ void k_sigma_bspline(const double* __restrict__ qp, int64_t Q, double x0, double L, int axis, int ncoef,
+                                const double* __restrict__ coef, double* __restrict__ sd, float* __restrict__ sf,
+                                double* __restrict__ s64) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  const double s = (qp[3 * i + axis] - x0) / L;
+  double sig = 0.0;
+  if (s >= 0.0 && s <= 1.0) {
+    const int nspan = ncoef - 3;  // knot intervals of [0, 1]
+    int j = (int)(s * nspan);     // interval [j, j+1) / nspan; s = 1 joins the last
+    if (j >= nspan) j = nspan - 1;
+    // knot u(m) of the clamped vector, m = 0 .. ncoef + 3
+    auto knot = [&](int m) {
+      const int v = m - 3;
+      return v <= 0 ? 0.0 : (v >= nspan ? 1.0 : (double)v / nspan);
+    };
+    // span index in the full knot vector: knots[j + 3] <= s < knots[j + 4]
+    const int sp = j + 3;
+    double d[4];
+    for (int r = 0; r < 4; ++r) d[r] = coef[sp - 3 + r];
+    for (int lvl = 1; lvl <= 3; ++lvl)
+      for (int r = 3; r >= lvl; --r) {
+        const int m = sp - 3 + r;
+        const double den = knot(m + 4 - lvl) - knot(m);
+        const double al = den > 0.0 ? (s - knot(m)) / den : 0.0;
+        d[r] = (1.0 - al) * d[r - 1] + al * d[r];
+      }
+    sig = d[3];
   }
   sig *= ETA0;
   s64[i] = sig;
@@ -747,7 +804,24 @@ int setup_gather(scabem_op* op, cudaStream_t s) {
   if (op->nac > 0) {
     CK(cudaMalloc(&op->acol, sizeof(int32_t) * op->nac));
     CK(cudaMemcpyAsync(op->acol, acol.data(), sizeof(int32_t) * op->nac, cudaMemcpyHostToDevice, s));
+    // bounding box of the active columns and their coordinates in it
+    int lo1 = n1, hi1 = -1, lo2 = n2, hi2 = -1;
+    for (int32_t c : acol) {
+      const int i1 = c / n2, i2 = c % n2;
+      lo1 = std::min(lo1, i1);
+      hi1 = std::max(hi1, i1);
+      lo2 = std::min(lo2, i2);
+      hi2 = std::max(hi2, i2);
+    }
+    op->R1 = hi1 - lo1 + 1;
+    op->R2 = hi2 - lo2 + 1;
+    std::vector<int32_t> coord(op->nac);
+    for (int64_t j = 0; j < op->nac; ++j) coord[j] = ((acol[j] / n2 - lo1) << 16) | (acol[j] % n2 - lo2);
+    CK(cudaMalloc(&op->acoord, sizeof(int32_t) * op->nac));
+    CK(cudaMemcpyAsync(op->acoord, coord.data(), sizeof(int32_t) * op->nac, cudaMemcpyHostToDevice, s));
   }
+  op->tdirect = op->transverse == 2 ||
+                (op->transverse == 0 && op->nac * op->nac <= 16 * (int64_t)op->P[1] * op->P[2]);
   const int64_t ne = Q * p3;
   CK(cudaMalloc(&op->gpt, sizeof(int32_t) * (pts.size() + 1)));
   CK(cudaMalloc(&op->goff, sizeof(int32_t) * coff.size()));
@@ -831,6 +905,18 @@ int setup_green(scabem_op* op, cudaStream_t s) {
                                                      op->n[1], op->n[2], op->h, k);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(F, op->gspatial[med], sizeof(cx<double>) * tot, cudaMemcpyDeviceToDevice, s));
+    if (op->tdirect) {
+      // axis-0 transform only, then the active box of offsets
+      int rc = fft_axis_full<double>(op, F, 0, twd[0], -1, s);
+      if (rc) return rc;
+      const int64_t nt_ = (int64_t)(op->P[0] / 2 + 1) * op->R1 * op->R2;
+      if (op->prec_mask & 2) CK(cudaMalloc(&op->d.gt[med], sizeof(cx<double>) * nt_));
+      if (op->prec_mask & 1) CK(cudaMalloc(&op->f.gt[med], sizeof(cx<float>) * nt_));
+      k_transverse<<<(int)cdiv(nt_, 256), 256, 0, s>>>(F, op->P[0], op->P[1], op->P[2], op->R1, op->R2,
+                                                       op->d.gt[med], op->f.gt[med]);
+      CK(cudaGetLastError());
+      continue;
+    }
     const cx<double>* const tws[3] = {twd[0], twd[1], twd[2]};
     int rc = fft3d_full<double>(op, F, tws, -1, s);
     if (rc) return rc;
@@ -914,6 +1000,18 @@ int setup_sigma_monomial(scabem_op* op, int nseg, const double* seg, cudaStream_
   CK(cudaStreamSynchronize(s));
   if (dseg) cudaFree(dseg);
   return setup_precond(op, s);  // the absorber blocks depend on sigma
+}
+
+int setup_sigma_bspline(scabem_op* op, double x0, double L, int axis, int ncoef, const double* coef, cudaStream_t s) {
+  double* dc = nullptr;
+  CK(cudaMalloc(&dc, sizeof(double) * ncoef));
+  CK(cudaMemcpyAsync(dc, coef, sizeof(double) * ncoef, cudaMemcpyHostToDevice, s));
+  k_sigma_bspline<<<(int)cdiv(op->Q, 256), 256, 0, s>>>(op->qp, op->Q, x0, L, axis, ncoef, dc, op->d.sig, op->f.sig,
+                                                        op->sig64);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dc);
+  return setup_precond(op, s);
 }
 
 int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s) {

@@ -24,6 +24,7 @@ class Case:
     sigma_segments: list | None = None
     sigma_scale: float = 0.0  # random per-point conductivity [S] when > 0
     seed: int = 0
+    transverse: str = "auto"  # (y, z) convolution: "auto", "fft" planes or "direct" sums
 
 
 def sphere_mixed(level=2, padded=(32, 32, 32), p=3, q=6, r_near=0.5):
@@ -51,6 +52,22 @@ def guide_planes64():
     """guide_small on a 64 x 64 x 64 transform grid (64 x 64 cross-section planes)."""
     c = guide_small(padded=(64, 64, 64))
     c.name = "guide_planes64"
+    return c
+
+
+def guide_planes64_fft():
+    """guide_planes64 with the (y, z) convolution forced onto the 64 x 64 FFT planes."""
+    c = guide_planes64()
+    c.name = "guide_planes64_fft"
+    c.transverse = "fft"
+    return c
+
+
+def sphere_direct():
+    """sphere_mixed with the (y, z) convolution forced to direct sums over its active columns."""
+    c = sphere_mixed()
+    c.name = "sphere_direct"
+    c.transverse = "direct"
     return c
 
 

@@ -36,13 +36,15 @@ _cache = {}
 
 
 def build(case, prec_mask=3):
-    key = (case.name, prec_mask, case.grid.n, case.grid.p, case.q, case.r_near)
+    key = (case.name, prec_mask, case.grid.n, case.grid.p, case.q, case.r_near, case.transverse)
     if key in _cache:
         return _cache[key]
     m = case.mesh
     mh = sc.scabem_mesh_create(m.V, m.T, m.region)
     op = sc.scabem_op_create(mh, case.media, case.grid.n, case.grid.h, case.grid.origin, case.grid.p, case.q,
-                             case.r_near, prec_mask)
+                             case.r_near, prec_mask, transverse=case.transverse)
+    if case.transverse != "auto":
+        assert sc.scabem_op_grid_info(op)["transverse_direct"] == (case.transverse == "direct")
     g = mesh.build(m.V, m.T, m.region, q=case.q)
     sig = cases.sigma_points(case, g.qpts)
     if case.sigma_segments:
@@ -72,7 +74,8 @@ def oracle_apply(case, g, med, sig, x, key):
     return _oracle_y[key]
 
 
-CASES = [cases.sphere_mixed, cases.guide_small, cases.plate_thin, cases.guide_planes64]
+CASES = [cases.sphere_mixed, cases.guide_small, cases.plate_thin, cases.guide_planes64, cases.guide_planes64_fft,
+         cases.sphere_direct]
 
 
 @pytest.mark.parametrize("mk", CASES, ids=lambda f: f.__name__)
@@ -162,12 +165,15 @@ def test_solve_reaches_oracle_residual(prec):
     assert np.linalg.norm(r) / np.linalg.norm(bn) < 1e-8
 
 
-@pytest.mark.parametrize("prec", [sc.SCABEM_C64, sc.SCABEM_C128], ids=["c64", "c128"])
-def test_full_size_guide_sampled_rows(prec):
+@pytest.mark.parametrize("prec,transverse", [(sc.SCABEM_C64, "auto"), (sc.SCABEM_C128, "auto"), (sc.SCABEM_C64, "fft")],
+                         ids=["c64", "c128", "c64_fft_planes"])
+def test_full_size_guide_sampled_rows(prec, transverse):
     """The 12 um guide on the 512 x 64 x 64 grid, in the launch configuration
-    bench.py times: every row of 24 random edges (both triangles of each edge
-    as targets) against the oracle's grid operator at those rows."""
+    bench.py times (automatic choice: direct (y, z) sums), and with the FFT
+    planes: every row of 24 random edges (both triangles of each edge as
+    targets) against the oracle's grid operator at those rows."""
     case = cases.guide_full()
+    case.transverse = transverse
     mask = 1 if prec == sc.SCABEM_C64 else 3
     mh, op, g, med, sig = build(case, prec_mask=mask)
     x = cases.synth.complex_normal(g.N, seed=4242)
