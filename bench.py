@@ -325,7 +325,7 @@ def run_gpu(args):
             "solve": {"seconds": t_solve, "iterations": sinfo["iters"], "refinements": sinfo["refinements"],
                       "relres": sinfo["relres"], "status": sinfo["status"],
                       "rhs": "Gaussian beam (waist 0.15 um) in the core at x = 6 um, y-polarised",
-                      "mode": "GMRES(100) on the complex64 operator to 1e-4 with FP64 Arnoldi (CGS2), FP64 refinement to 1e-8"},
+                      "mode": "GMRES(100) on the complex64 operator to 1e-4 with FP64 Arnoldi (classical Gram-Schmidt, repeated when the DGKS test asks), FP64 refinement to 1e-8"},
         }
 
     # roofline of the dominant kernel, and of the whole matvec

@@ -318,11 +318,25 @@ struct Work {
   }
 };
 
-// h_dev[c] = conj(V[:, c]) . w for c < nv, left on the device
+// h_dev[c] = conj(V[:, c]) . w for c < nv, left on the device.  About
+// DOT_BLOCKS blocks in all: row blocks x column tiles, so that each thread
+// covers several rows before the block reduction.
 int dots_dev(const cd* V, int64_t ldv, int nv, const cd* w, int64_t N, Work& W, cd* h_dev, cudaStream_t s) {
-  k_dots<<<dim3(DOT_BLOCKS, (unsigned)cdiv(nv, DOT_TC)), DOT_THREADS, 0, s>>>(V, ldv, nv, w, N, W.part, nv);
+  const int tiles = (int)cdiv(nv, DOT_TC);
+  int rb = DOT_BLOCKS / tiles;
+  if (rb < 8) rb = 8;
+  k_dots<<<dim3(rb, tiles), DOT_THREADS, 0, s>>>(V, ldv, nv, w, N, W.part, nv);
   CK(cudaGetLastError());
-  k_reduce_parts<<<nv, DOT_THREADS, 0, s>>>(W.part, DOT_BLOCKS, nv, h_dev);
+  k_reduce_parts<<<nv, DOT_THREADS, 0, s>>>(W.part, rb, nv, h_dev);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
+// out->re = |w| (device)
+int norm_dev(const cd* w, int64_t N, Work& W, cd* out, cudaStream_t s) {
+  k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(nullptr, N, 0, nullptr, const_cast<cd*>(w), N, W.nparts);
+  CK(cudaGetLastError());
+  k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, out);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }
@@ -391,31 +405,50 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
       if (rc) return rc;
       rc = op_apply64(op, W.z, W.w, prec, W, s);
       if (rc) return rc;
-      // classical Gram-Schmidt twice, the norm and the next basis vector on
-      // the device; one copy of the coefficients to the host
+      // classical Gram-Schmidt on the device, repeated only when the first
+      // pass cancels most of w (|w'| < |w| / sqrt 2, the Daniel-Gragg-
+      // Kaufman-Stewart test); the norms and coefficients come to the host
+      // in one copy per pass, and the next basis vector is scaled on the device
       cd* h1 = W.h;
       cd* h2 = W.h + (m + 1);
-      cd* hnd = W.h + 2 * (m + 1);
+      cd* hn0 = W.h + 2 * (m + 1);  // |w| before, after pass 1, after pass 2
+      cd* hn1 = hn0 + 1;
+      cd* hn2 = hn0 + 2;
+      rc = norm_dev(W.w, N, W, hn0, s);
+      if (rc) return rc;
       rc = dots_dev(W.V, N, j + 1, W.w, N, W, h1, s);
       if (rc) return rc;
-      k_vsub<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h1, W.w, N);
+      k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h1, W.w, N, W.nparts);
       CK(cudaGetLastError());
-      rc = dots_dev(W.V, N, j + 1, W.w, N, W, h2, s);
-      if (rc) return rc;
-      k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h2, W.w, N, W.nparts);
+      k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, hn1);
       CK(cudaGetLastError());
-      k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, hnd);
-      CK(cudaGetLastError());
+      hbuf.resize(2 * (m + 1) + 3);
+      CK(cudaMemcpyAsync(hbuf.data(), W.h, sizeof(cd) * (j + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hbuf.data() + 2 * (m + 1), hn0, sizeof(cd) * 2, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      hv.assign(hbuf.begin(), hbuf.begin() + j + 1);
+      double hn = hbuf[2 * (m + 1) + 1].re;
+      const cd* hnd = hn1;
+      if (!(hn >= 0.70710678118654752 * hbuf[2 * (m + 1)].re)) {
+        rc = dots_dev(W.V, N, j + 1, W.w, N, W, h2, s);
+        if (rc) return rc;
+        k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h2, W.w, N, W.nparts);
+        CK(cudaGetLastError());
+        k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, hn2);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(hbuf.data() + (m + 1), h2, sizeof(cd) * (j + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hbuf.data() + 2 * (m + 1) + 2, hn2, sizeof(cd), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        hv2.assign(hbuf.begin() + (m + 1), hbuf.begin() + (m + 1) + j + 1);
+        hn = hbuf[2 * (m + 1) + 2].re;
+        hnd = hn2;
+      } else {
+        hv2.assign(j + 1, mk(0.0, 0.0));
+      }
       if (j + 1 < m) {
         k_scale_dev<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.w, hnd, W.V + (int64_t)(j + 1) * N, N);
         CK(cudaGetLastError());
       }
-      hbuf.resize(2 * (m + 1) + 1);
-      CK(cudaMemcpyAsync(hbuf.data(), W.h, sizeof(cd) * hbuf.size(), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      hv.assign(hbuf.begin(), hbuf.begin() + j + 1);
-      hv2.assign(hbuf.begin() + (m + 1), hbuf.begin() + (m + 1) + j + 1);
-      const double hn = hbuf[2 * (m + 1)].re;
       if (!std::isfinite(hn)) {
         set_error("non-finite Krylov vector");
         return SCABEM_E_NONFINITE;
@@ -660,7 +693,7 @@ int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, co
   CK(cudaMalloc(&W.z, sizeof(cd) * N));
   CK(cudaMalloc(&W.u, sizeof(cd) * N));
   CK(cudaMalloc(&W.part, sizeof(cd) * DOT_BLOCKS * (m + 1)));
-  CK(cudaMalloc(&W.h, sizeof(cd) * (2 * (m + 1) + 1)));
+  CK(cudaMalloc(&W.h, sizeof(cd) * (2 * (m + 1) + 3)));
   CK(cudaMalloc(&W.nparts, sizeof(double) * DOT_BLOCKS));
   if (prec == SCABEM_C64) {
     CK(cudaMalloc(&W.xf, sizeof(cx<float>) * N));
