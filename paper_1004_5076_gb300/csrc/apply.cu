@@ -113,10 +113,12 @@ __global__ void k_sources(const cx<R>* __restrict__ x, const int32_t* __restrict
 // K2b: projection as a gather.  One warp per grid point that some stencil
 // covers: lane = portion * SL + slot reads 16-byte portion `portion` of the
 // rows qsrc[point] of entries slot, slot + SL, ... (SL rows per load
-// instruction, two in flight), weighted by W_slot(point); the SL slot sums
+// instruction, GATHER_INFLIGHT in flight), weighted by W_slot(point); the SL slot sums
 // of a portion are then added by shuffles and the slot-0 lanes write their
 // portion.  Points no stencil covers stay zero from set-up.  The sum order
 // is fixed, so the result does not depend on thread timing.
+constexpr int GATHER_INFLIGHT = 4;
+
 template <typename R>
 __device__ __forceinline__ void load_portion(const cx<R>* p, cx<R>* v);
 template <>
@@ -146,20 +148,22 @@ __global__ void k_gather(const cx<R>* __restrict__ qsrc, const int32_t* __restri
   for (int c = 0; c < CPP; ++c) acc[c] = czero<R>();
   if (act) {
     const int e1 = goff[i + 1];
-    for (int e = goff[i] + slot; e < e1; e += 2 * SL) {
-      const int e2 = e + SL;
-      const int qa = gq[e];
-      const R wa = gw[e];
-      const int qb = e2 < e1 ? gq[e2] : qa;
-      const R wb = e2 < e1 ? gw[e2] : R(0);
-      cx<R> va[CPP], vb[CPP];
-      load_portion<R>(qsrc + (int64_t)qa * NFIELD_IN + por * CPP, va);
-      load_portion<R>(qsrc + (int64_t)qb * NFIELD_IN + por * CPP, vb);
+    for (int e = goff[i] + slot; e < e1; e += GATHER_INFLIGHT * SL) {
+      int qe[GATHER_INFLIGHT];
+      R we[GATHER_INFLIGHT];
 #pragma unroll
-      for (int c = 0; c < CPP; ++c) {
-        axpy2(acc[c], wa, va[c]);
-        axpy2(acc[c], wb, vb[c]);
+      for (int u = 0; u < GATHER_INFLIGHT; ++u) {
+        const int eu = e + u * SL;
+        qe[u] = eu < e1 ? gq[eu] : gq[e];
+        we[u] = eu < e1 ? gw[eu] : R(0);
       }
+      cx<R> v[GATHER_INFLIGHT][CPP];
+#pragma unroll
+      for (int u = 0; u < GATHER_INFLIGHT; ++u) load_portion<R>(qsrc + (int64_t)qe[u] * NFIELD_IN + por * CPP, v[u]);
+#pragma unroll
+      for (int u = 0; u < GATHER_INFLIGHT; ++u)
+#pragma unroll
+        for (int c = 0; c < CPP; ++c) axpy2(acc[c], we[u], v[u][c]);
     }
   }
   // every lane reaches the shuffles (no early exit above)
@@ -331,25 +335,24 @@ __device__ __forceinline__ cx<R> dot3(const R* X, const cx<R>* V) {
 // type 0 <X, E_e - E_i>, 1 <X, H_e - H_i> (weak forms), 2 Eq. 13, 3 Eq. 14.
 template <typename R>
 __device__ __forceinline__ void test_point(const cx<R>* recs, const cx<R>* __restrict__ summ,
-                                           const double* __restrict__ tri, const double* __restrict__ cX,
-                                           const double* __restrict__ qp, const double* __restrict__ qw,
+                                           const double* __restrict__ tri, const R* __restrict__ tp,
                                            const R* __restrict__ sig, int64_t t, int kk, int a, int q, R ke, R ki,
                                            R ze, R zi, cx<R>* out) {
   const double* g = tri + 16 * t;
-  const R cxk = (R)cX[3 * t + kk];
-  const R divX = R(2) * cxk;
   const R nrm[3] = {(R)g[12], (R)g[13], (R)g[14]};
   const cx<R>* se = summ + (3 * t + 0) * 4;
   const cx<R>* si = summ + (3 * t + 1) * 4;
   const cx<R>* sM = summ + (3 * t + 2) * 4;
   const R kl[2] = {ke, ki}, zl[2] = {ze, zi};
   const int64_t Qa = t * q + a;
-  const R w = (R)qw[Qa];
+  const R* tq = tp + 16 * Qa;
+  const R w = tq[3];
   const R sg = sig[Qa];
+  const R divX = tq[13 + kk];
   R X[3], rel[3];
   for (int c = 0; c < 3; ++c) {
-    X[c] = cxk * (R)(qp[3 * Qa + c] - g[3 * kk + c]);
-    rel[c] = (R)(qp[3 * Qa + c] - g[9 + c]);
+    X[c] = tq[4 + 3 * kk + c];
+    rel[c] = tq[c];
   }
   cx<R> WE[3], WH[3], E[2][3];
   cx<R> wE = czero<R>(), wH = czero<R>();
@@ -471,9 +474,8 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
     const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
     const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
     const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
-    const double* __restrict__ cX, const double* __restrict__ qp, const double* __restrict__ qw,
-    const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki, R ze, R zi, int has_near,
-    cx<R>* __restrict__ val, int* __restrict__ tmo) {
+    const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki,
+    R ze, R zi, int has_near, cx<R>* __restrict__ val, int* __restrict__ tmo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
   if (lane < 3 * q) {
     const int kk = lane / q, pa = lane - kk * q;
     cx<R> o[4];
-    test_point(recs + pa * 2 * NREC, summ, tri, cX, qp, qw, sig, t, kk, pa, q, ke, ki, ze, zi, o);
+    test_point(recs + pa * 2 * NREC, summ, tri, tp, sig, t, kk, pa, q, ke, ki, ze, zi, o);
     cx<R>* d = part + (kk * q + pa) * 4;
 #pragma unroll
     for (int c = 0; c < 4; ++c) d[c] = o[c];
@@ -590,8 +592,8 @@ __global__ void k_rows(const cx<R>* __restrict__ val, const int32_t* __restrict_
 
 template <typename R>
 using PointsFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, const int32_t*,
-                          const int32_t*, const cx<R>*, const double*, const double*, const double*, const double*,
-                          const R*, int64_t, int, int, int, int, R, R, R, R, int, cx<R>*, int*);
+                          const int32_t*, const cx<R>*, const double*, const R*, const R*, int64_t, int, int, int,
+                          int, R, R, R, R, int, cx<R>*, int*);
 
 template <typename R>
 PrecData<R>& pdata(scabem_op* op);
@@ -631,9 +633,8 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
     PointsFn<R> fn = op->p == 2 ? k_points<R, 2> : op->p == 3 ? k_points<R, 3> : k_points<R, 4>;
     if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm)) return rc_;
     fn<<<(int)cdiv(nt, PT_WARPS), PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
-                                                  op->tri, op->cX, op->qp, op->qw, pd.sig, nt, op->q, n0, n1, n2,
-                                                  (R)op->ke, (R)op->ki, (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0,
-                                                  pd.val, op->tmo_d);
+                                                  op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, (R)op->ke, (R)op->ki,
+                                                  (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, pd.val, op->tmo_d);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);

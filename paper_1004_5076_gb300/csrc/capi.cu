@@ -88,6 +88,7 @@ void free_prec(PrecData<R>& pd) {
   cudaFree(pd.L);
   cudaFree(pd.dL);
   cudaFree(pd.sig);
+  cudaFree(pd.tp);
   cudaFree(pd.summ);
   cudaFree(pd.qsrc);
   cudaFree(pd.src);
@@ -106,6 +107,7 @@ int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) 
   if ((rc = dalloc(&pd.L, op->Q * 3 * op->p))) return rc;
   if ((rc = dalloc(&pd.dL, op->Q * 3 * op->p))) return rc;
   if ((rc = dalloc(&pd.sig, op->Q))) return rc;
+  if ((rc = dalloc(&pd.tp, op->Q * 16))) return rc;
   if (!workspaces) return SCABEM_OK;
   const int64_t ng = (int64_t)op->n[0] * op->n[1] * op->n[2];
   const int64_t C = (int64_t)op->n[1] * op->n[2];

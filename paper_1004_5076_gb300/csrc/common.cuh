@@ -118,6 +118,7 @@ struct PrecData {
   R* L = nullptr;                       // Q * 3 * p stencil weights
   R* dL = nullptr;                      // Q * 3 * p derivative weights [1/um]
   R* sig = nullptr;                     // Q normalised conductivity
+  R* tp = nullptr;                      // Q * 16 testing geometry: rel (3), w, X_k (3 x 3), div X_k (3)
   // workspaces
   cx<R>* summ = nullptr;  // nt * 3 sets * 4
   cx<R>* qsrc = nullptr;  // Q * 12 weighted point sources

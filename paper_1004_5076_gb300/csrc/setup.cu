@@ -427,6 +427,30 @@ __global__ void k_near_corr(const double* __restrict__ tri, const double* __rest
   }
 }
 
+// Testing geometry per quadrature point Qi (point a of triangle t), formed in
+// FP64 and stored in each operator precision: the offset from the centroid
+// (3), the weight, the RWG test functions X_k(r) = cX_k (r - v_k) of the three
+// local edges (3 x 3) and their divergences 2 cX_k.
+__global__ void k_test_geometry(const double* __restrict__ tri, const double* __restrict__ cX,
+                                const double* __restrict__ qp, const double* __restrict__ qw, int64_t Q, int q,
+                                double* __restrict__ td, float* __restrict__ tf) {
+  const int64_t Qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (Qi >= Q) return;
+  const int64_t t = Qi / q;
+  const double* g = tri + 16 * t;
+  double v[16];
+  for (int c = 0; c < 3; ++c) v[c] = qp[3 * Qi + c] - g[9 + c];
+  v[3] = qw[Qi];
+  for (int k = 0; k < 3; ++k) {
+    for (int c = 0; c < 3; ++c) v[4 + 3 * k + c] = cX[3 * t + k] * (qp[3 * Qi + c] - g[3 * k + c]);
+    v[13 + k] = 2.0 * cX[3 * t + k];
+  }
+  for (int c = 0; c < 16; ++c) {
+    if (td) td[16 * Qi + c] = v[c];
+    if (tf) tf[16 * Qi + c] = (float)v[c];
+  }
+}
+
 // ---------------------------------------------------------------- conductivity
 __global__ void k_sigma_monomial(const double* __restrict__ qp, int64_t Q, int nseg, const double* __restrict__ seg,
                                  double* __restrict__ sd, float* __restrict__ sf, double* __restrict__ s64) {
@@ -872,6 +896,9 @@ int setup_geometry(scabem_op* op, const scabem_mesh* m, cudaStream_t s) {
                                                      op->origin[1], op->origin[2], op->n[0], op->n[1], op->n[2],
                                                      op->tri, op->cX, op->qp, op->qw, op->base, op->d.L, op->d.dL,
                                                      op->f.L, op->f.dL, op->err);
+  CK(cudaGetLastError());
+  k_test_geometry<<<(int)cdiv(op->Q, 256), 256, 0, s>>>(op->tri, op->cX, op->qp, op->qw, op->Q, op->q, op->d.tp,
+                                                        op->f.tp);
   CK(cudaGetLastError());
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, op->err, sizeof(int), cudaMemcpyDeviceToHost, s));
