@@ -196,8 +196,7 @@ def stage_bytes(info, ginfo, case, N, b):
         # values out; per point: position, weight, stencil base and weights,
         # conductivity; per triangle: geometry
         "points": b * (npairs * q * 2 * 10 + 16 * ngnz + nt * 12 + nt * 12) + 4 * (nt + 1 + npairs)
-        + Q * (24 + 8 + 12 + 2 * 3 * p * r + r) + nt * (16 + 3) * 8,
-        "rows": b * 3 * N + 8 * N,
+        + Q * (24 + 8 + 12 + 2 * 3 * p * r + r) + nt * (16 + 3) * 8 + b * N + 4 * 12 * nt,
     }
 
 
@@ -361,7 +360,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": t_setup},
             "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
                     "d2h_bytes_per_step": int(N * 8)},
-            "gpu_launches": 7 * args.steps,
+            "gpu_launches": 6 * args.steps,
             "stages_ms_per_step": per,
             "roofline": roof,
             "matvec_roofline": mv_roof,

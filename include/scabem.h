@@ -282,9 +282,10 @@ int scabem_reflection(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, c
  * boundaries on its own stream, for at most max_applies applies (events are
  * created here, so enable before any stream capture).  scabem_profile_read
  * waits for the recorded events, returns per-stage summed milliseconds in
- * stage_ms[7] = {summaries, projection, FFT axis-0 forward, FFT planes with
- * the Green multiply, FFT axis-0 inverse, points (interpolation + near field
- * + testing), rows} and the number of applies, and starts a new record.
+ * stage_ms[6] = {summaries and point sources, projection, FFT axis-0
+ * forward, (y, z) convolution with the Green functions (direct sums or FFT
+ * planes), FFT axis-0 inverse, points (interpolation + near field + testing
+ * + row sums)} and the number of applies, and starts a new record.
  * enable = 0 releases the events. */
 int scabem_profile(scabem_op_t op, int32_t enable, int32_t max_applies);
 int scabem_profile_read(scabem_op_t op, double* stage_ms, int64_t* n_applies);

@@ -292,7 +292,7 @@ def scabem_reflection(op, x, axis, comp, p0, t0, t1, npts, beta_lo, beta_hi, nbe
     return out
 
 
-STAGES = ["summaries", "projection", "fft_axis0_fwd", "fft_planes_green", "fft_axis0_inv", "points", "rows"]
+STAGES = ["summaries", "projection", "fft_axis0_fwd", "fft_planes_green", "fft_axis0_inv", "points"]
 
 
 def scabem_profile(op, enable=True, max_applies=1024):

@@ -13,7 +13,8 @@
 //                precorrection (exact minus grid panel moments), then the
 //                Galerkin testing of Eqs. 1-3 (weak form), Eq. 13 and Eq. 14
 //                (sigma-weighted, with the side-limit terms)
-//     k_rows     per-edge sum of the two triangles' tested values
+//                and the per-edge sums of the two triangles' tested values
+//                into the rows
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -67,14 +68,16 @@ __device__ __forceinline__ void axpy2(cx<double>& a, double s, cx<double> b) { a
 // current summaries of t (as k_summ; written by the thread of point 0) and
 // the point's weighted sources qsrc[Qi*12 + set*4 + {x, y, z, div}] of the
 // exterior J, interior J and exterior M sets (J(r) = a (r - c) - beta,
-// div J = 2a, times the quadrature weight).
+// div J = 2a, times the quadrature weight); it also zeroes the output y.
 template <typename R>
 __global__ void k_sources(const cx<R>* __restrict__ x, const int32_t* __restrict__ unk,
                           const double* __restrict__ cX, const double* __restrict__ tri,
                           const double* __restrict__ qp, const double* __restrict__ qw, int64_t Q, int q,
-                          cx<R>* __restrict__ summ, cx<R>* __restrict__ qsrc) {
+                          cx<R>* __restrict__ summ, cx<R>* __restrict__ qsrc, cx<R>* __restrict__ y, int64_t N) {
   const int64_t Qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (Qi >= Q) return;
+  // y is summed into by k_points (two terms per row)
+  for (int64_t r = Qi; r < N; r += Q) y[r] = czero<R>();
   const int64_t t = Qi / q;
   const int a = (int)(Qi - t * q);
   const double* g = tri + 16 * t;
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
     const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
     const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
     const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki,
-    R ze, R zi, int has_near, cx<R>* __restrict__ val, int* __restrict__ tmo) {
+    R ze, R zi, int has_near, const int32_t* __restrict__ valrow, cx<R>* __restrict__ y, int* __restrict__ tmo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
@@ -578,22 +581,22 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
     const cx<R>* sp = part + kk * q * 4 + c;
     cx<R> v = czero<R>();
     for (int pa = 0; pa < q; ++pa) v += sp[pa * 4];
-    val[(t * 3 + kk) * 4 + c] = v;
+    // each row is the sum of exactly two such values (the edge's two
+    // triangles) added to a zeroed word, so the result does not depend on
+    // which arrives first
+    const int row = valrow[(t * 3 + kk) * 4 + c];
+    if (row >= 0) {
+      atomicAdd(&y[row].re, v.re);
+      atomicAdd(&y[row].im, v.im);
+    }
   }
 }
 
-template <typename R>
-__global__ void k_rows(const cx<R>* __restrict__ val, const int32_t* __restrict__ rowsrc, int64_t N,
-                       cx<R>* __restrict__ y) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  y[i] = val[rowsrc[2 * i]] + val[rowsrc[2 * i + 1]];
-}
 
 template <typename R>
 using PointsFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, const int32_t*,
                           const int32_t*, const cx<R>*, const double*, const R*, const R*, int64_t, int, int, int,
-                          int, R, R, R, R, int, cx<R>*, int*);
+                          int, R, R, R, R, int, const int32_t*, cx<R>*, int*);
 
 template <typename R>
 PrecData<R>& pdata(scabem_op* op);
@@ -616,7 +619,7 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   const int64_t ng = (int64_t)n0 * n1 * n2;
   prof_mark(op, s);
   k_sources<R><<<(int)cdiv(Q, 128), 128, 0, s>>>(x, op->unk, op->cX, op->tri, op->qp, op->qw, Q, op->q, pd.summ,
-                                                 pd.qsrc);
+                                                 pd.qsrc, y, op->N);
   CK(cudaGetLastError());
   prof_mark(op, s);
   if (op->ngnz > 0) {
@@ -634,12 +637,10 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
     if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm)) return rc_;
     fn<<<(int)cdiv(nt, PT_WARPS), PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
                                                   op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, (R)op->ke, (R)op->ki,
-                                                  (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, pd.val, op->tmo_d);
+                                                  (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, op->valrow, y,
+                                                  op->tmo_d);
     CK(cudaGetLastError());
   }
-  prof_mark(op, s);
-  k_rows<R><<<(int)cdiv(op->N, 256), 256, 0, s>>>(pd.val, op->rowsrc, op->N, y);
-  CK(cudaGetLastError());
   prof_mark(op, s);
   return SCABEM_OK;
 }

@@ -440,6 +440,12 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
       rowsrc[2 * r3 + 1] = (int32_t)(src[1] + 3);
     }
   }
+  // row of each (triangle, local edge, type) tested value, -1 if none
+  std::vector<int32_t> valrow(12 * m->nt, -1);
+  for (int64_t r = 0; r < m->N; ++r) {
+    valrow[rowsrc[2 * r]] = (int32_t)r;
+    valrow[rowsrc[2 * r + 1]] = (int32_t)r;
+  }
   std::vector<int32_t> etk(4 * m->ne), ecls(m->ne), eunk(3 * m->ne, -1);
   for (int64_t e = 0; e < m->ne; ++e) {
     for (int side = 0; side < 2; ++side) {
@@ -469,6 +475,7 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   TRY(dalloc(&op->unk, 9 * op->nt));
   TRY(dalloc(&op->region, op->nt));
   TRY(dalloc(&op->rowsrc, 2 * op->N));
+  TRY(dalloc(&op->valrow, 12 * op->nt));
   TRY(dalloc(&op->qp, 3 * op->Q));
   TRY(dalloc(&op->qw, op->Q));
   TRY(dalloc(&op->base, 3 * op->Q));
@@ -486,6 +493,7 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   };
   TRY(upload(op->unk, unk.data(), sizeof(int32_t) * unk.size()));
   TRY(upload(op->rowsrc, rowsrc.data(), sizeof(int32_t) * rowsrc.size()));
+  TRY(upload(op->valrow, valrow.data(), sizeof(int32_t) * valrow.size()));
   TRY(upload(op->region, m->region.data(), sizeof(int32_t) * m->nt));
   TRY(upload(op->etk, etk.data(), sizeof(int32_t) * etk.size()));
   TRY(upload(op->ecls, ecls.data(), sizeof(int32_t) * ecls.size()));
@@ -570,6 +578,7 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->unk);
   cudaFree(op->region);
   cudaFree(op->trirow);
+  cudaFree(op->valrow);
   cudaFree(op->rowsrc);
   cudaFree(op->qp);
   cudaFree(op->qw);

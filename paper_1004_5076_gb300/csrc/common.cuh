@@ -87,9 +87,10 @@ constexpr double ETA0 = 376.730313668;
 
 // ------------------------------------------------------------------ profiling
 // Stages of one apply: summaries (with the quadrature-point sources),
-// projection, FFT axis 0 forward, FFT planes with the Green multiply, FFT
-// axis 0 inverse, points (interpolation, near field and testing), rows.
-constexpr int NSTAGE = 7;
+// projection, FFT axis 0 forward, (y, z) convolution with the Green
+// function, FFT axis 0 inverse, points (interpolation, near field, testing
+// and the row sums).
+constexpr int NSTAGE = 6;
 struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> ev;  // (NSTAGE + 1) per recorded apply
@@ -148,6 +149,7 @@ struct scabem_op {
   int32_t* region = nullptr;
   int32_t* trirow = nullptr;  // nt * 3 * 4: 1 if that (t,k,type) row exists
   int32_t* rowsrc = nullptr;  // N * 2 : ((t*3+k)*4+type) of T+ and T-
+  int32_t* valrow = nullptr;  // nt * 12: row of each (t, k, type) value, -1 if none
   double* qp = nullptr;       // Q * 3
   double* qw = nullptr;       // Q
   int32_t* base = nullptr;    // Q * 3
