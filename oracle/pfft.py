@@ -352,3 +352,24 @@ class PFFT:
         y = np.zeros((g.N, B), dtype=np.complex128)
         scatter_rows(g, tg, val, y)
         return y[:, 0] if squeeze else y
+
+
+# ---------------------------------------------------------------- transpose
+def dense(op: "PFFT", sigma_pts_S, chunk: int = 128):
+    """The O2 matrix, column by column (apply to blocks of unit vectors)."""
+    N = op.g.N
+    A = np.zeros((N, N), dtype=np.complex128)
+    for c0 in range(0, N, chunk):
+        c1 = min(N, c0 + chunk)
+        E = np.zeros((N, c1 - c0), dtype=np.complex128)
+        E[np.arange(c0, c1), np.arange(c1 - c0)] = 1.0
+        A[:, c0:c1] = op.apply(E, sigma_pts_S)
+    return A
+
+
+def apply_transpose(op: "PFFT", y, sigma_pts_S, A=None):
+    """A^T y for the O2 operator: the plain definition, the transposed matrix
+    (no conjugation).  Pass a precomputed ``dense(op, sigma)`` as A to reuse it."""
+    if A is None:
+        A = dense(op, sigma_pts_S)
+    return A.T @ np.asarray(y, dtype=np.complex128)

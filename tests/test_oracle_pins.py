@@ -432,3 +432,27 @@ def test_bspline_reproduces_linear_function():
     s = np.linspace(0.0, 1.0, 57)
     got = osig.bspline(_line_points(s), 1.0, 2.0, grev)
     assert np.max(np.abs(got - s)) < 1e-13
+
+
+def test_o2_transpose_pins():
+    """O2^T is the transposed O2 matrix: the chunked column assembly agrees
+    with single unit-vector applies, and y . (A x) = (A^T y) . x."""
+    import cases
+
+    case = cases.plate_thin()
+    g = mesh.build(case.mesh.V, case.mesh.T, case.mesh.region, q=case.q)
+    sig = cases.sigma_points(case, g.qpts)
+    med = operator.Media(*case.media)
+    op = pfft.PFFT(g, med, case.grid, case.r_near)
+    A2 = pfft.dense(op, sig, chunk=256)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)
+    y = rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N)
+    lhs = y @ op.apply(x, sig)
+    rhs = pfft.apply_transpose(op, y, sig, A=A2) @ x
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    # chunked assembly places each column where a single unit vector does
+    for c in (0, g.N // 2, g.N - 1):
+        e = np.zeros(g.N, dtype=np.complex128)
+        e[c] = 1.0
+        assert np.max(np.abs(A2[:, c] - op.apply(e, sig))) <= 1e-13 * np.max(np.abs(A2[:, c]))
