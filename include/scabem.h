@@ -182,6 +182,17 @@ int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sigma);
  * launches). */
 int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream);
 
+/* x = A^T y, the transpose (not the conjugate transpose) of the operator of
+ * scabem_apply, for adjoint solves and gradients (reciprocity of the
+ * Galerkin system).  The stages of scabem_apply run transposed in reverse
+ * order: testing and row sums, near-field precorrection (over the source
+ * triangles), interpolation (value and derivative stencils), the grid
+ * convolution (each potential field with its medium's Green function),
+ * projection and the current expansion.  Same arguments, layouts, host
+ * staging and errors as scabem_apply, with y the input and x the output. */
+int scabem_apply_adjoint(scabem_op_t op, const void* y, void* x, int32_t nrhs, int64_t ld, int32_t prec,
+                         void* stream);
+
 /* Excitation (Sec. II): kind 0 = plane wave (dir, pol), 1 = electric dipole
  * (pos, pol), 2 = complex-source-point beam at pos - j*b*dir radiating along
  * dir (pos, dir, b, pol).  side 0 = source in the interior medium (the

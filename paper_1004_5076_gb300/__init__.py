@@ -101,6 +101,7 @@ def lib():
     L.scabem_op_destroy.restype = None
     L.scabem_set_sigma.argtypes = [vp, C.POINTER(Sigma)]
     L.scabem_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
+    L.scabem_apply_adjoint.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_rhs.argtypes = [vp, C.POINTER(Source), i32, vp, i64, i32, vp]
     L.scabem_solve.argtypes = [vp, vp, vp, i32, i64, C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo)]
     L.scabem_fields.argtypes = [vp, vp, i32, i64, vp, i32, C.POINTER(Source), vp, vp]
@@ -229,6 +230,13 @@ def scabem_apply(op, x, y, nrhs=1, ld=None, prec=SCABEM_C128, stream=None):
     if ld is None:
         ld = x.shape[0]
     _check(lib().scabem_apply(op, _ptr(x), _ptr(y), nrhs, ld, prec, _stream(stream)))
+
+
+def scabem_apply_adjoint(op, y, x, nrhs=1, ld=None, prec=SCABEM_C128, stream=None):
+    """x = A^T y (transpose, no conjugation)."""
+    if ld is None:
+        ld = y.shape[0]
+    _check(lib().scabem_apply_adjoint(op, _ptr(y), _ptr(x), nrhs, ld, prec, _stream(stream)))
 
 
 def make_source(kind, side=0, pos=(0, 0, 0), dir=(1, 0, 0), pol=(0, 1, 0), b=0.0):

@@ -185,6 +185,17 @@ __global__ void k_gather(const cx<R>* __restrict__ qsrc, const int32_t* __restri
 }
 
 template <typename R>
+const R* gather_dweights(scabem_op* op);
+template <>
+const float* gather_dweights<float>(scabem_op* op) {
+  return op->gdf;
+}
+template <>
+const double* gather_dweights<double>(scabem_op* op) {
+  return op->gdd;
+}
+
+template <typename R>
 const R* gather_weights(scabem_op* op);
 template <>
 const float* gather_weights<float>(scabem_op* op) {
@@ -593,6 +604,330 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
 }
 
 
+// ================================================================ transposed apply
+// x_bar = A^T y_bar: the stages of the apply in reverse order, each the
+// transpose of its forward map (no conjugation):
+//   T1 k_points_adj   rows -> tested values -> record adjoints at every point
+//                     (Eqs. 1-3, 13, 14 testing transposed) and the
+//                     triangle's own side-limit terms -> its summary adjoints
+//   T2 k_near_adj     record adjoints of the targets -> summary adjoints of
+//                     each source triangle (near records transposed; one warp
+//                     per source over its reverse pair list, no atomics)
+//   T3 k_interp_adj   record adjoints -> 16 grid fields (value and derivative
+//                     stencils transposed), as a gather over covered points
+//   T4 fft_conv(adjoint): each field with its medium's Green function
+//   T5 k_proj_adj     grid -> point-source adjoints (value stencils
+//                     transposed) -> summary adjoints (source expansion
+//                     transposed), plus T1 + T2
+//   T6 k_x_adj        summary adjoints -> unknowns (current expansion transposed)
+
+// T1: one warp per triangle t.  Phase 1, lane (kk, a): the adjoints of the
+// point-a quantities that the tested values of local edge kk read
+// (u_type = w * ybar of the row, X = X_kk):
+//   WE: X u0, wE: divX u0, WH: X (u1 + u2), wH: divX (u1 + u2),
+//   E_e: -sg (n x X) u2, E_i: -sg X u3,
+//   J_e + J_i: (n x X) u2 / 2 + X u3, M: sg (-X u2 + (n x X) u3) / 2.
+// Phase 2, lane (a, medium, group): summed over kk, mapped to the 10 record
+// values of the group (the transposes of medium_fields' combinations).
+// Phase 3, lane (set, a | beta component): the own-summary adjoints summed
+// over the points.
+template <typename R>
+__global__ void __launch_bounds__(PT_WARPS * 32)
+    k_points_adj(const cx<R>* __restrict__ ybar, const int32_t* __restrict__ valrow, const double* __restrict__ tri,
+                 const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q, R ke, R ki, R ze, R zi,
+                 cx<R>* __restrict__ recb, cx<R>* __restrict__ sdir) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NA = 20;  // adjoint quantities per (kk, point)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
+  if (t >= nt) return;
+  cx<R>* part = reinterpret_cast<cx<R>*>(smem_raw) + (int64_t)warp * 3 * q * NA;  // [kk][a][NA]
+  const double* g = tri + 16 * t;
+  const R nrm[3] = {(R)g[12], (R)g[13], (R)g[14]};
+  if (lane < 3 * q) {
+    const int kk = lane / q, pa = lane - kk * q;
+    const int64_t Qa = t * q + pa;
+    const R* tq = tp + 16 * Qa;
+    const R w = tq[3], sg = sig[Qa], divX = tq[13 + kk];
+    const R X[3] = {tq[4 + 3 * kk], tq[5 + 3 * kk], tq[6 + 3 * kk]};
+    const R nX[3] = {nrm[1] * X[2] - nrm[2] * X[1], nrm[2] * X[0] - nrm[0] * X[2], nrm[0] * X[1] - nrm[1] * X[0]};
+    cx<R> u[4];
+#pragma unroll
+    for (int ty = 0; ty < 4; ++ty) {
+      const int row = valrow[(t * 3 + kk) * 4 + ty];
+      u[ty] = row >= 0 ? w * ybar[row] : czero<R>();
+    }
+    const cx<R> u12 = u[1] + u[2];
+    cx<R>* o = part + (int64_t)(kk * q + pa) * NA;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      o[c] = X[c] * u[0];
+      o[4 + c] = X[c] * u12;
+      o[8 + c] = (-sg * nX[c]) * u[2];
+      o[11 + c] = (-sg * X[c]) * u[3];
+      o[14 + c] = (R(0.5) * nX[c]) * u[2] + X[c] * u[3];
+      o[17 + c] = (R(0.5) * sg) * (nX[c] * u[3] - X[c] * u[2]);
+    }
+    o[3] = divX * u[0];
+    o[7] = divX * u12;
+  }
+  __syncwarp();
+  if (lane < 4 * q) {
+    const int pa = lane >> 2, m = (lane >> 1) & 1, h = lane & 1;
+    cx<R> ag[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) ag[i] = czero<R>();
+    for (int kk = 0; kk < 3; ++kk) {
+      const cx<R>* o = part + (int64_t)(kk * q + pa) * NA;
+#pragma unroll
+      for (int i = 0; i < 14; ++i) ag[i] += o[i];
+    }
+    const R k = m ? ki : ke, z = m ? zi : ze, sgm = m ? R(-1) : R(1);
+    const cx<R>* Eb = ag + (m ? 11 : 8);
+    cx<R> r[10];
+    if (h == 0) {  // A, phi, grad phi, curl A
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r[c] = (sgm * (-z * k)) * mulj(ag[c]) + (-z * k) * mulj(Eb[c]);
+        r[4 + c] = (-z / k) * mulj(Eb[c]);
+        r[7 + c] = sgm * ag[4 + c];
+      }
+      r[3] = (sgm * z / k) * mulj(ag[3]);
+    } else {  // F, psi, grad psi (unused by the rows), curl F
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r[c] = (-sgm * k / z) * mulj(ag[4 + c]);
+        r[4 + c] = czero<R>();
+        r[7 + c] = -(sgm * ag[c]) - Eb[c];
+      }
+      r[3] = (sgm / (k * z)) * mulj(ag[7]);
+    }
+    cx<R>* dst = recb + ((t * q + pa) * 2 + m) * NREC + 10 * h;
+#pragma unroll
+    for (int c = 0; c < 10; ++c) dst[c] = r[c];
+  }
+  __syncwarp();
+  if (lane < 12) {
+    const int set = lane >> 2, comp = lane & 3;
+    const int base = set < 2 ? 14 : 17;  // J_e + J_i feeds sets 0 and 1, M set 2
+    cx<R> acc = czero<R>();
+    for (int pa = 0; pa < q; ++pa) {
+      cx<R> v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        v[c] = part[(0 * q + pa) * NA + base + c] + part[(1 * q + pa) * NA + base + c] +
+               part[(2 * q + pa) * NA + base + c];
+      const R* tq = tp + 16 * (t * q + pa);
+      if (comp == 0)
+        acc += tq[0] * v[0] + tq[1] * v[1] + tq[2] * v[2];  // a: J = a (r - c) - beta
+      else
+        acc -= v[comp - 1];
+    }
+    sdir[(t * 3 + set) * 4 + comp] = acc;
+  }
+}
+
+// T2: one warp per source triangle s, over the pairs rpair[roff[s] ..) with
+// targets ptgt[j].  Lane (target point a, medium, group) transposes near_part:
+//   a_bar += r . dP1 + 2 phi_r dP0 + 2 grad_r . dQ + curl_r . dC,
+//   beta_bar += -A_r dP0 - (the dQ x beta term transposed),
+// the interior medium's M group with the sign of -M; the lanes' sums are
+// added in point order and to the triangle's own terms (sdir).
+template <typename R>
+__global__ void __launch_bounds__(PT_WARPS * 32)
+    k_near_adj(const cx<R>* __restrict__ corr, const int32_t* __restrict__ roff, const int32_t* __restrict__ rpair,
+               const int32_t* __restrict__ ptgt, const cx<R>* __restrict__ recb, const cx<R>* __restrict__ sdir,
+               int64_t nt, int q, cx<R>* __restrict__ snear) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t sidx = (int64_t)blockIdx.x * PT_WARPS + warp;
+  if (sidx >= nt) return;
+  cx<R>* red = reinterpret_cast<cx<R>*>(smem_raw) + (int64_t)warp * 32 * 4;  // [lane][4]
+  const bool act = lane < 4 * q;
+  const int a = lane >> 2, m = (lane >> 1) & 1, h = lane & 1;
+  const int pairc = NCORR * 2 * q;
+  const int r0 = roff[sidx], npair = roff[sidx + 1] - r0;
+  cx<R> al = czero<R>(), be[3] = {czero<R>(), czero<R>(), czero<R>()};
+  int jj = 0, tt = 0;
+  for (int i = 0; i < npair; ++i) {  // warp-uniform
+    if ((i & 31) == 0) {
+      jj = i + lane < npair ? rpair[r0 + i + lane] : 0;
+      tt = i + lane < npair ? ptgt[jj] : 0;
+    }
+    const int64_t j = __shfl_sync(0xffffffffu, jj, i & 31);
+    const int64_t tg = __shfl_sync(0xffffffffu, tt, i & 31);
+    if (act) {
+      const cx<R>* dp = corr + j * pairc + a * 2 + m;
+      const cx<R>* rb = recb + ((tg * q + a) * 2 + m) * NREC + 10 * h;
+      cx<R> d[NCORR], r[10];
+#pragma unroll
+      for (int c = 0; c < NCORR; ++c) d[c] = dp[c * 2 * q];
+#pragma unroll
+      for (int c = 0; c < 10; ++c) r[c] = rb[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cfma(al, r[c], d[1 + c]);
+        cfma(al, R(2) * r[4 + c], d[4 + c]);
+        cfma(al, r[7 + c], d[7 + c]);
+        be[c] -= r[c] * d[0];
+      }
+      cfma(al, R(2) * r[3], d[0]);
+      be[0] += r[9] * d[5] - r[8] * d[6];
+      be[1] += r[7] * d[6] - r[9] * d[4];
+      be[2] += r[8] * d[4] - r[7] * d[5];
+    }
+  }
+  red[lane * 4 + 0] = al;
+  red[lane * 4 + 1] = be[0];
+  red[lane * 4 + 2] = be[1];
+  red[lane * 4 + 3] = be[2];
+  __syncwarp();
+  if (lane < 12) {
+    const int set = lane >> 2, comp = lane & 3;
+    cx<R> acc = sdir[(sidx * 3 + set) * 4 + comp];
+    for (int pa = 0; pa < q; ++pa) {
+      if (set == 0) acc += red[((pa << 2) | 0) * 4 + comp];                  // J_e: (a, m=0, h=0)
+      else if (set == 1) acc += red[((pa << 2) | 2) * 4 + comp];             // J_i: (a, m=1, h=0)
+      else acc += red[((pa << 2) | 1) * 4 + comp] - red[((pa << 2) | 3) * 4 + comp];  // M: +exterior, -interior
+    }
+    snear[(sidx * 3 + set) * 4 + comp] = acc;
+  }
+}
+
+// T3: thread (covered grid point i, group g4 = 2 medium + h): the transposed
+// interpolation of the group's 10 record adjoints with the value weight W and
+// the derivative weights (Wx, Wy, Wz) of every entry:
+//   f0 += W r0 + Wz r8 - Wy r9,  f1 += W r1 - Wz r7 + Wx r9,
+//   f2 += W r2 + Wy r7 - Wx r8,  f3 += W r3 + Wx r4 + Wy r5 + Wz r6
+// into grid fields 4 g4 .. 4 g4 + 3 (field-major).
+template <typename R>
+__global__ void k_interp_adj(const cx<R>* __restrict__ recb, const int32_t* __restrict__ gpt,
+                             const int32_t* __restrict__ goff, const int32_t* __restrict__ gq,
+                             const R* __restrict__ gw, const R* __restrict__ gd, int64_t ngnz, int64_t ng,
+                             cx<R>* __restrict__ grids) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = idx >> 2;
+  if (i >= ngnz) return;
+  const int g4 = (int)(idx & 3), m = g4 >> 1, h = g4 & 1;
+  cx<R> o[4] = {czero<R>(), czero<R>(), czero<R>(), czero<R>()};
+  const int e1 = goff[i + 1];
+  for (int e = goff[i]; e < e1; ++e) {
+    const int64_t Qi = gq[e];
+    const R W = gw[e], Wx = gd[3 * (int64_t)e], Wy = gd[3 * (int64_t)e + 1], Wz = gd[3 * (int64_t)e + 2];
+    const cx<R>* r = recb + (Qi * 2 + m) * NREC + 10 * h;
+    cx<R> rr[10];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) rr[c] = r[c];
+    axpy(o[0], W, rr[0]);
+    axpy(o[0], Wz, rr[8]);
+    axpy(o[0], -Wy, rr[9]);
+    axpy(o[1], W, rr[1]);
+    axpy(o[1], -Wz, rr[7]);
+    axpy(o[1], Wx, rr[9]);
+    axpy(o[2], W, rr[2]);
+    axpy(o[2], Wy, rr[7]);
+    axpy(o[2], -Wx, rr[8]);
+    axpy(o[3], W, rr[3]);
+    axpy(o[3], Wx, rr[4]);
+    axpy(o[3], Wy, rr[5]);
+    axpy(o[3], Wz, rr[6]);
+  }
+  const int64_t gp = gpt[i];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) grids[(int64_t)(4 * g4 + f) * ng + gp] = o[f];
+}
+
+// T5: one warp per triangle t; lane (point a, set): the transposed value
+// interpolation of the convolved adjoint grid (point-major; J_e from fields
+// 0..3, J_i from 8..11, M from 4..7 minus 12..15), then the transposed point
+// sources (a_bar += w (r - c) . qb + 2 w qb_div, beta_bar -= w qb), summed
+// over the points in point order and added to snear.
+template <typename R, int P>
+__global__ void __launch_bounds__(PT_WARPS * 32)
+    k_proj_adj(const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
+               const R* __restrict__ tp, const cx<R>* __restrict__ snear, int64_t nt, int q, int n1, int n2,
+               cx<R>* __restrict__ stot) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
+  if (t >= nt) return;
+  cx<R>* red = reinterpret_cast<cx<R>*>(smem_raw) + (int64_t)warp * 32 * 4;  // [lane][4]
+  if (lane < 3 * q) {
+    const int pa = lane / 3, set = lane - pa * 3;
+    const int64_t Qi = t * q + pa;
+    R Lx[P], Ly[P], Lz[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      Lx[i] = L[(3 * Qi + 0) * P + i];
+      Ly[i] = L[(3 * Qi + 1) * P + i];
+      Lz[i] = L[(3 * Qi + 2) * P + i];
+    }
+    const int b0 = base[3 * Qi], b1 = base[3 * Qi + 1], b2 = base[3 * Qi + 2];
+    const int fa = set == 0 ? 0 : (set == 1 ? 8 : 4);
+    cx<R> qb[4] = {czero<R>(), czero<R>(), czero<R>(), czero<R>()};
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const R wxy = Lx[i] * Ly[j];
+        const int64_t rowi = ((int64_t)(b0 + i) * n1 + (b1 + j)) * n2 + b2;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          const R W = wxy * Lz[k];
+          cx<R> gv[4];
+          load_group(grids + (rowi + k) * NFIELD_OUT + fa, gv);
+          if (set == 2) {
+            cx<R> gi[4];
+            load_group(grids + (rowi + k) * NFIELD_OUT + 12, gi);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) gv[f] -= gi[f];
+          }
+#pragma unroll
+          for (int f = 0; f < 4; ++f) axpy(qb[f], W, gv[f]);
+        }
+      }
+    const R* tq = tp + 16 * Qi;
+    const R w = tq[3];
+    red[lane * 4 + 0] = w * (tq[0] * qb[0] + tq[1] * qb[1] + tq[2] * qb[2]) + (R(2) * w) * qb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) red[lane * 4 + 1 + c] = -(w * qb[c]);
+  }
+  __syncwarp();
+  if (lane < 12) {
+    const int set = lane >> 2, comp = lane & 3;
+    cx<R> acc = snear[(t * 3 + set) * 4 + comp];
+    for (int pa = 0; pa < q; ++pa) acc += red[(pa * 3 + set) * 4 + comp];
+    stot[(t * 3 + set) * 4 + comp] = acc;
+  }
+}
+
+// T6: thread per unknown: x_bar = sum over its uses (triangle t, local edge k,
+// set, sign) of sign cX_k (a_bar + (v_k - c) . beta_bar).
+template <typename R>
+__global__ void k_x_adj(const cx<R>* __restrict__ stot, const int32_t* __restrict__ xsrc,
+                        const double* __restrict__ tri, const double* __restrict__ cX, int64_t N,
+                        cx<R>* __restrict__ xbar) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  cx<R> acc = czero<R>();
+  for (int u = 0; u < 4; ++u) {
+    const int32_t code = xsrc[4 * i + u];
+    if (code == 0) break;
+    const int64_t c = (code > 0 ? code : -code) - 1;
+    const int set = (int)(c % 3);
+    const int64_t tk = c / 3, t = tk / 3;
+    const int k = (int)(tk - t * 3);
+    const double* g = tri + 16 * t;
+    const cx<R>* sb = stot + (t * 3 + set) * 4;
+    cx<R> v = sb[0];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) v += (R)(g[3 * k + cc] - g[9 + cc]) * sb[1 + cc];
+    const R f = (R)cX[3 * t + k] * (code > 0 ? R(1) : R(-1));
+    acc += f * v;
+  }
+  xbar[i] = acc;
+}
+
 template <typename R>
 using PointsFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, const int32_t*,
                           const int32_t*, const cx<R>*, const double*, const R*, const R*, int64_t, int, int, int,
@@ -628,7 +963,7 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
     CK(cudaGetLastError());
   }
   prof_mark(op, s);
-  int rc = fft_conv<R>(op, pd, s);
+  int rc = fft_conv<R>(op, pd, s, false);
   if (rc) return rc;
   prof_mark(op, s);
   {
@@ -645,6 +980,55 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   return SCABEM_OK;
 }
 
+template <typename R>
+using ProjAdjFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, int64_t, int, int, int,
+                           cx<R>*);
+
+// x_bar = A^T y_bar (one right-hand side), stages T1-T6.
+template <typename R>
+int apply_adjoint_one(scabem_op* op, const cx<R>* ybar, cx<R>* xbar, cudaStream_t s) {
+  PrecData<R>& pd = pdata<R>(op);
+  const int64_t nt = op->nt;
+  const int q = op->q;
+  const int64_t ng = (int64_t)op->n[0] * op->n[1] * op->n[2];
+  cx<R>* sdir = pd.sbar;
+  cx<R>* snear = pd.sbar + nt * 12;
+  const int blocks = (int)cdiv(nt, PT_WARPS);
+  {
+    const size_t sm = (size_t)PT_WARPS * 3 * q * 20 * sizeof(cx<R>);
+    if (int rc_ = set_max_smem(op->device, (const void*)k_points_adj<R>, (int)sm)) return rc_;
+    k_points_adj<R><<<blocks, PT_WARPS * 32, sm, s>>>(ybar, op->valrow, op->tri, pd.tp, pd.sig, nt, q, (R)op->ke,
+                                                      (R)op->ki, (R)op->ze, (R)op->zi, pd.recb, sdir);
+    CK(cudaGetLastError());
+  }
+  const cx<R>* s_after_near = sdir;
+  if (op->npairs > 0) {
+    const size_t sm = (size_t)PT_WARPS * 32 * 4 * sizeof(cx<R>);
+    k_near_adj<R><<<blocks, PT_WARPS * 32, sm, s>>>(pd.near, op->roff, op->rpair, op->ptgt, pd.recb, sdir, nt, q,
+                                                    snear);
+    CK(cudaGetLastError());
+    s_after_near = snear;
+  }
+  if (op->ngnz > 0) {
+    k_interp_adj<R><<<(int)cdiv(op->ngnz * 4, 256), 256, 0, s>>>(pd.recb, op->gpt, op->goff, op->gent,
+                                                                 gather_weights<R>(op), gather_dweights<R>(op),
+                                                                 op->ngnz, ng, pd.src);
+    CK(cudaGetLastError());
+  }
+  int rc = fft_conv<R>(op, pd, s, true);
+  if (rc) return rc;
+  {
+    const size_t sm = (size_t)PT_WARPS * 32 * 4 * sizeof(cx<R>);
+    ProjAdjFn<R> fn = op->p == 2 ? k_proj_adj<R, 2> : op->p == 3 ? k_proj_adj<R, 3> : k_proj_adj<R, 4>;
+    fn<<<blocks, PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.tp, s_after_near, nt, q, op->n[1], op->n[2],
+                                         sdir);
+    CK(cudaGetLastError());
+  }
+  k_x_adj<R><<<(int)cdiv(op->N, 256), 256, 0, s>>>(sdir, op->xsrc, op->tri, op->cX, op->N, xbar);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
 // Current summaries only (used by the field evaluation at probe points).
 template <typename R>
 int compute_summ(scabem_op* op, const cx<R>* x, cx<R>* summ, cudaStream_t s) {
@@ -655,4 +1039,6 @@ int compute_summ(scabem_op* op, const cx<R>* x, cx<R>* summ, cudaStream_t s) {
 
 template int compute_summ<double>(scabem_op*, const cx<double>*, cx<double>*, cudaStream_t);
 template int apply_one<float>(scabem_op*, const cx<float>*, cx<float>*, cudaStream_t);
+template int apply_adjoint_one<float>(scabem_op*, const cx<float>*, cx<float>*, cudaStream_t);
+template int apply_adjoint_one<double>(scabem_op*, const cx<double>*, cx<double>*, cudaStream_t);
 template int apply_one<double>(scabem_op*, const cx<double>*, cx<double>*, cudaStream_t);

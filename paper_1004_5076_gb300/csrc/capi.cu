@@ -96,6 +96,8 @@ void free_prec(PrecData<R>& pd) {
   cudaFree(pd.stB);
   cudaFree(pd.grid);
   cudaFree(pd.val);
+  cudaFree(pd.recb);
+  cudaFree(pd.sbar);
   cudaFree(pd.xs);
   cudaFree(pd.ys);
   pd = PrecData<R>();
@@ -117,12 +119,14 @@ int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) 
   }
   if ((rc = dalloc(&pd.summ, op->nt * 12))) return rc;
   if ((rc = dalloc(&pd.qsrc, op->Q * 12))) return rc;
-  if ((rc = dalloc(&pd.src, NFIELD_IN * ng))) return rc;
+  if ((rc = dalloc(&pd.src, NFIELD_OUT * ng))) return rc;
   // grid points no stencil covers are never written by the projection
-  CK(cudaMemsetAsync(pd.src, 0, sizeof(cx<R>) * NFIELD_IN * ng, s));
-  if ((rc = dalloc(&pd.stA, (int64_t)NFIELD_IN * op->P[0] * C))) return rc;
+  CK(cudaMemsetAsync(pd.src, 0, sizeof(cx<R>) * NFIELD_OUT * ng, s));
+  if ((rc = dalloc(&pd.stA, (int64_t)NFIELD_OUT * op->P[0] * C))) return rc;
   // the axis-0 transform writes only the columns some stencil covers
-  CK(cudaMemsetAsync(pd.stA, 0, sizeof(cx<R>) * NFIELD_IN * op->P[0] * C, s));
+  CK(cudaMemsetAsync(pd.stA, 0, sizeof(cx<R>) * NFIELD_OUT * op->P[0] * C, s));
+  if ((rc = dalloc(&pd.recb, op->Q * 2 * NREC))) return rc;
+  if ((rc = dalloc(&pd.sbar, 2 * op->nt * 12))) return rc;
   if ((rc = dalloc(&pd.stB, (int64_t)NFIELD_OUT * op->P[0] * C))) return rc;
   if ((rc = dalloc(&pd.grid, NFIELD_OUT * ng))) return rc;
   if ((rc = dalloc(&pd.val, op->nt * 12))) return rc;
@@ -140,7 +144,12 @@ bool is_device_ptr(const void* p) {
 }
 
 template <typename R>
-int apply_prec(scabem_op* op, const void* xv, void* yv, int nrhs, int64_t ld, cudaStream_t s) {
+int apply_col(scabem_op* op, const cx<R>* x, cx<R>* y, bool adjoint, cudaStream_t s) {
+  return adjoint ? apply_adjoint_one<R>(op, x, y, s) : apply_one<R>(op, x, y, s);
+}
+
+template <typename R>
+int apply_prec(scabem_op* op, const void* xv, void* yv, int nrhs, int64_t ld, cudaStream_t s, bool adjoint) {
   PrecData<R>& pd = *reinterpret_cast<PrecData<R>*>(sizeof(R) == 4 ? (void*)&op->f : (void*)&op->d);
   if (!pd.built) {
     set_error("operator was not built for this precision (prec_mask)");
@@ -150,7 +159,7 @@ int apply_prec(scabem_op* op, const void* xv, void* yv, int nrhs, int64_t ld, cu
   const int64_t N = op->N;
   if (xd && yd) {
     for (int c = 0; c < nrhs; ++c) {
-      int rc = apply_one<R>(op, (const cx<R>*)xv + c * ld, (cx<R>*)yv + c * ld, s);
+      int rc = apply_col<R>(op, (const cx<R>*)xv + c * ld, (cx<R>*)yv + c * ld, adjoint, s);
       if (rc) return rc;
     }
     return SCABEM_OK;
@@ -172,7 +181,7 @@ int apply_prec(scabem_op* op, const void* xv, void* yv, int nrhs, int64_t ld, cu
       xin = pd.xs;
     }
     cx<R>* yout = yd ? yc : pd.ys;
-    int rc = apply_one<R>(op, xin, yout, s);
+    int rc = apply_col<R>(op, xin, yout, adjoint, s);
     if (rc) return rc;
     if (!yd) CK(cudaMemcpyAsync(yc, pd.ys, sizeof(cx<R>) * N, cudaMemcpyDeviceToHost, s));
   }
@@ -440,6 +449,27 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
       rowsrc[2 * r3 + 1] = (int32_t)(src[1] + 3);
     }
   }
+  // uses of each unknown in the current expansion (transposed apply)
+  std::vector<int32_t> xsrc(4 * m->N, 0);
+  {
+    std::vector<int> nuse(m->N, 0);
+    for (int64_t t = 0; t < m->nt; ++t)
+      for (int k = 0; k < 3; ++k)
+        for (int set = 0; set < 3; ++set) {
+          const int32_t u = unk[(3 * t + k) * 3 + set];
+          if (u == 0) continue;
+          const int64_t idx = (u > 0 ? u : -u) - 1;
+          const int32_t code = (int32_t)((t * 3 + k) * 3 + set) + 1;
+          if (nuse[idx] < 4) xsrc[4 * idx + nuse[idx]] = u > 0 ? code : -code;
+          ++nuse[idx];
+        }
+    for (int64_t i = 0; i < m->N; ++i)
+      if (nuse[i] > 4) {
+        set_error("internal: an unknown has more than four current uses");
+        scabem_op_destroy(op);
+        return SCABEM_E_MESH;
+      }
+  }
   // row of each (triangle, local edge, type) tested value, -1 if none
   std::vector<int32_t> valrow(12 * m->nt, -1);
   for (int64_t r = 0; r < m->N; ++r) {
@@ -476,6 +506,7 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   TRY(dalloc(&op->region, op->nt));
   TRY(dalloc(&op->rowsrc, 2 * op->N));
   TRY(dalloc(&op->valrow, 12 * op->nt));
+  TRY(dalloc(&op->xsrc, 4 * op->N));
   TRY(dalloc(&op->qp, 3 * op->Q));
   TRY(dalloc(&op->qw, op->Q));
   TRY(dalloc(&op->base, 3 * op->Q));
@@ -494,6 +525,7 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   TRY(upload(op->unk, unk.data(), sizeof(int32_t) * unk.size()));
   TRY(upload(op->rowsrc, rowsrc.data(), sizeof(int32_t) * rowsrc.size()));
   TRY(upload(op->valrow, valrow.data(), sizeof(int32_t) * valrow.size()));
+  TRY(upload(op->xsrc, xsrc.data(), sizeof(int32_t) * xsrc.size()));
   TRY(upload(op->region, m->region.data(), sizeof(int32_t) * m->nt));
   TRY(upload(op->etk, etk.data(), sizeof(int32_t) * etk.size()));
   TRY(upload(op->ecls, ecls.data(), sizeof(int32_t) * ecls.size()));
@@ -599,6 +631,12 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->pinv);
   cudaFree(op->err);
   cudaFree(op->acol);
+  cudaFree(op->gdd);
+  cudaFree(op->gdf);
+  cudaFree(op->roff);
+  cudaFree(op->rpair);
+  cudaFree(op->ptgt);
+  cudaFree(op->xsrc);
   cudaFree(op->acoord);
   if (op->tmo_h) cudaFreeHost(op->tmo_h);
   free_prec(op->f);
@@ -694,9 +732,24 @@ int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t l
   if (int rc = take_timeout(op)) return rc;
   if (nrhs == 0) return SCABEM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (prec == SCABEM_C64) return apply_prec<float>(op, x, y, nrhs, ld, s);
-  if (prec == SCABEM_C128) return apply_prec<double>(op, x, y, nrhs, ld, s);
+  if (prec == SCABEM_C64) return apply_prec<float>(op, x, y, nrhs, ld, s, false);
+  if (prec == SCABEM_C128) return apply_prec<double>(op, x, y, nrhs, ld, s, false);
   set_error("scabem_apply: prec must be SCABEM_C64 or SCABEM_C128");
+  return SCABEM_E_ARG;
+}
+
+int scabem_apply_adjoint(scabem_op_t op, const void* y, void* x, int32_t nrhs, int64_t ld, int32_t prec,
+                         void* stream) {
+  if (!op || !x || !y || nrhs < 0 || ld < op->N) {
+    set_error("scabem_apply_adjoint: null argument, nrhs < 0 or ld < N");
+    return SCABEM_E_ARG;
+  }
+  if (int rc = take_timeout(op)) return rc;
+  if (nrhs == 0) return SCABEM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == SCABEM_C64) return apply_prec<float>(op, y, x, nrhs, ld, s, true);
+  if (prec == SCABEM_C128) return apply_prec<double>(op, y, x, nrhs, ld, s, true);
+  set_error("scabem_apply_adjoint: prec must be SCABEM_C64 or SCABEM_C128");
   return SCABEM_E_ARG;
 }
 

@@ -123,8 +123,10 @@ struct PrecData {
   // workspaces
   cx<R>* summ = nullptr;  // nt * 3 sets * 4
   cx<R>* qsrc = nullptr;  // Q * 12 weighted point sources
-  cx<R>* src = nullptr;   // 12 * n0 n1 n2
-  cx<R>* stA = nullptr;   // 12 * P0 * n1 n2
+  cx<R>* src = nullptr;   // 16 * n0 n1 n2 (12 sources; 16 in the transposed apply)
+  cx<R>* stA = nullptr;   // 16 * P0 * n1 n2 (12 fields in the apply, 16 in the transposed apply)
+  cx<R>* recb = nullptr;  // Q * 2 * NREC record adjoints (transposed apply)
+  cx<R>* sbar = nullptr;  // 2 * nt * 12: summary adjoints (near + direct, total)
   cx<R>* stB = nullptr;   // 16 * P0 * n1 n2
   cx<R>* grid = nullptr;  // n0 n1 n2 * 16, point-major: [point][medium][J, M set][A or F (3), phi or psi]
   cx<R>* val = nullptr;   // nt * 3 * 4
@@ -163,6 +165,8 @@ struct scabem_op {
   int32_t* gent = nullptr;  // Q * p^3
   double* gwd = nullptr;    // Q * p^3
   float* gwf = nullptr;     // Q * p^3
+  double* gdd = nullptr;    // Q * p^3 * 3 derivative weights of the entries (transposed interpolation)
+  float* gdf = nullptr;
   // columns (i1, i2) of the grid that some stencil covers, ascending: the
   // only ones whose sources are non-zero and whose potentials are read, so
   // the axis-0 transforms run on these alone; rowmask bit i1 is set when row
@@ -183,6 +187,14 @@ struct scabem_op {
   int64_t npairs = 0;
   int32_t* noff = nullptr;  // nt + 1
   int32_t* nsrc = nullptr;  // npairs
+  // reverse list: pairs rpair[roff[s] .. roff[s+1]) have source triangle s;
+  // ptgt[j] = target triangle of pair j
+  int32_t* roff = nullptr;   // nt + 1
+  int32_t* rpair = nullptr;  // npairs
+  int32_t* ptgt = nullptr;   // npairs
+  // unknown -> up to 4 (triangle, local edge, set) uses, (code + 1) * sign,
+  // code = (t * 3 + k) * 3 + set; 0 = unused (transposed current expansion)
+  int32_t* xsrc = nullptr;   // N * 4
   cx<double>* gspatial[2] = {nullptr, nullptr};  // padded G tables, set-up only
   // per-edge block-diagonal preconditioner (exact self blocks, inverted)
   int32_t* etk = nullptr;   // ne * 4: T+, k+, T-, k-
@@ -236,9 +248,14 @@ int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStre
 // apply.cu
 template <typename R>
 int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s);
-// fft.cu
+// x_bar = A^T y_bar (transpose, no conjugation)
 template <typename R>
-int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s);
+int apply_adjoint_one(scabem_op* op, const cx<R>* ybar, cx<R>* xbar, cudaStream_t s);
+// fft.cu
+// adjoint = false: 12 sources -> 16 potentials (the apply); true: 16 -> 16,
+// each field convolved with its medium's Green function (the transposed apply)
+template <typename R>
+int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint);
 template <typename R>
 int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cudaStream_t s);
 template <typename R>

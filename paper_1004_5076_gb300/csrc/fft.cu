@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_planes(const cx<R>* __restric
                                                           const cx<R>* __restrict__ ghE,
                                                           const cx<R>* __restrict__ ghI, int P0, int n1, int n2,
                                                           const cx<R>* __restrict__ tw1,
-                                                          const cx<R>* __restrict__ tw2) {
+                                                          const cx<R>* __restrict__ tw2, int ident) {
   extern __shared__ unsigned char smem_raw[];
   constexpr int P1 = 1 << L1, P2 = 1 << L2;
   constexpr int LS = P2 + 2;
@@ -364,12 +364,15 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_planes(const cx<R>* __restric
 
   const int h1 = P1 / 2 + 1, h2 = P2 / 2 + 1;
   const int q0 = min(k0, P0 - k0);
-  const int nout = (f >= 8) ? 2 : 1;
+  const int nout = (!ident && f >= 8) ? 2 : 1;
   for (int which = 0; which < nout; ++which) {
     int fo;
     const cx<R>* gh;
     R sgn = R(1);
-    if (f < 4) {
+    if (ident) {  // transposed apply: each of the 16 fields with its medium's function
+      fo = f;
+      gh = f < 8 ? ghE : ghI;
+    } else if (f < 4) {
       fo = f;
       gh = ghE;
     } else if (f < 8) {
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_planes(const cx<R>* __restric
 
 template <typename R>
 using PlanesFn = void (*)(const cx<R>*, cx<R>*, const cx<R>*, const cx<R>*, int, int, int, const cx<R>*,
-                          const cx<R>*);
+                          const cx<R>*, int);
 
 template <typename R, int L1, int L2>
 PlanesFn<R> planes_fn() {
@@ -512,7 +515,7 @@ __device__ __forceinline__ void line64(cx<R>* v, const cx<R>* w, cx<R>* scr, int
 template <typename R>
 __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_planes64(const cx<R>* __restrict__ A, cx<R>* __restrict__ B, const cx<R>* __restrict__ ghE,
-               const cx<R>* __restrict__ ghI, int P0, const cx<R>* __restrict__ tw64, uint64_t rowmask) {
+               const cx<R>* __restrict__ ghI, int P0, const cx<R>* __restrict__ tw64, uint64_t rowmask, int ident) {
   constexpr int NP = 32, H = 33;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* W0 = reinterpret_cast<cx<R>*>(smem_raw);  // forward rows, then output 0
@@ -547,10 +550,11 @@ __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
   __syncthreads();
 
   // source field -> output fields, media and signs (as in k_planes)
-  const int nout = f >= 8 ? 2 : 1;
+  // transposed apply (ident): each of the 16 fields with its medium's function
+  const int nout = (!ident && f >= 8) ? 2 : 1;
   const int q0 = min(k0, P0 - k0);
-  const cx<R>* ga = (f >= 4 && f < 8) ? ghI : ghE;  // output 0
-  const int foa = f < 4 ? f : (f < 8 ? 8 + (f - 4) : 4 + (f - 8));
+  const cx<R>* ga = ident ? (f < 8 ? ghE : ghI) : ((f >= 4 && f < 8) ? ghI : ghE);  // output 0
+  const int foa = ident ? f : (f < 4 ? f : (f < 8 ? 8 + (f - 4) : 4 + (f - 8)));
   const int fob = 12 + (f - 8);  // output 1 (f >= 8), interior medium, sign -1
   ga += (int64_t)q0 * H * H;
   const cx<R>* gb = ghI + (int64_t)q0 * H * H;
@@ -599,6 +603,8 @@ __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
 }
 
 // ---------------------------------------------------------------- stage B, direct
+// (In the transposed apply, ident = 1, medium m takes fields 8m .. 8m+7 to
+// the same fields, no sign.)
 // Stage B as a direct sum over the active (i1, i2) columns: per (k0 plane,
 // medium) the 8 source fields of that medium (its J set and the M set) are
 // convolved with gt[q0][|d1|][|d2|] (the axis-0 transform of the spatial
@@ -656,7 +662,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __res
                                                               const cx<R>* __restrict__ gtI, int P0, int C,
                                                               const int32_t* __restrict__ acol,
                                                               const int32_t* __restrict__ acoord, int nac, int R1,
-                                                              int R2) {
+                                                              int R2, int ident) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* src = reinterpret_cast<cx<R>*>(smem_raw);  // [nac][8]
   cx<R>* T = src + (int64_t)nac * 8;                 // [R1][R2]
@@ -667,7 +673,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __res
   for (int i = threadIdx.x; i < R1 * R2; i += PD_THREADS) T[i] = gt[i];
   for (int idx = threadIdx.x; idx < nac * 8; idx += PD_THREADS) {
     const int v = idx / nac, j = idx - v * nac;  // consecutive threads: consecutive columns of one field
-    const int f = v < 4 ? (med ? 4 + v : v) : 8 + (v - 4);
+    const int f = ident ? 8 * med + v : (v < 4 ? (med ? 4 + v : v) : 8 + (v - 4));
     src[j * 8 + v] = A[((int64_t)f * P0 + k0) * C + acol[j]];
   }
   for (int i = threadIdx.x; i < nac; i += PD_THREADS) crd[i] = acoord[i];
@@ -685,9 +691,9 @@ __global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __res
     const int64_t c = acol[i];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-      const int fo = med ? (v < 4 ? 8 + v : 12 + (v - 4)) : v;
+      const int fo = ident ? 8 * med + v : (med ? (v < 4 ? 8 + v : 12 + (v - 4)) : v);
       const cx<R> val = acc.get(v);
-      B[((int64_t)fo * P0 + k0) * C + c] = (med && v >= 4) ? -val : val;
+      B[((int64_t)fo * P0 + k0) * C + c] = (!ident && med && v >= 4) ? -val : val;
     }
   }
 }
@@ -813,8 +819,10 @@ static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
 }
 
 template <typename R>
-int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
+int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint) {
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
+  const int nf = adjoint ? NFIELD_OUT : NFIELD_IN;  // fields transformed along axis 0
+  const int id = adjoint ? 1 : 0;
   const int P0 = op->P[0], P1 = op->P[1], P2 = op->P[2];
   const int C = n1 * n2;
   if (op->nac == 0) {
@@ -825,7 +833,7 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   const size_t sm0 = (size_t)P0 * (cb + 1) * sizeof(cx<R>);
   // stage A
   if (int rc_ = set_max_smem(op->device, (const void*)k_axis0<R>, (int)sm0)) return rc_;
-  k_axis0<R><<<dim3((unsigned)cdiv(op->nac, cb), NFIELD_IN), FFT_THREADS, sm0, s>>>(
+  k_axis0<R><<<dim3((unsigned)cdiv(op->nac, cb), nf), FFT_THREADS, sm0, s>>>(
       pd.src, pd.stA, n0, P0, C, op->acol, (int)op->nac, cb, pd.tw[0]);
   CK(cudaGetLastError());
   prof_mark(op, s);
@@ -834,7 +842,7 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
     const size_t sm = ((size_t)op->nac * 8 + (size_t)op->R1 * op->R2) * sizeof(cx<R>) + sizeof(int32_t) * op->nac;
     if (int rc_ = set_max_smem(op->device, (const void*)k_planes_direct<R>, (int)sm)) return rc_;
     k_planes_direct<R><<<dim3(P0, 2), PD_THREADS, sm, s>>>(pd.stA, pd.stB, pd.gt[0], pd.gt[1], P0, C, op->acol,
-                                                           op->acoord, (int)op->nac, op->R1, op->R2);
+                                                           op->acoord, (int)op->nac, op->R1, op->R2, id);
     CK(cudaGetLastError());
     prof_mark(op, s);
     return axis0_inverse(op, pd, s);
@@ -842,8 +850,8 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
   if (P1 == 64 && P2 == 64) {
     const size_t sm = ((size_t)2 * 32 * 64 + (size_t)(P64_THREADS / 8) * P64_SCR) * sizeof(cx<R>);
     if (int rc_ = set_max_smem(op->device, (const void*)k_planes64<R>, (int)sm)) return rc_;
-    k_planes64<R><<<dim3(P0, NFIELD_IN), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1],
-                                                               op->rowmask);
+    k_planes64<R><<<dim3(P0, nf), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1],
+                                                        op->rowmask, id);
     CK(cudaGetLastError());
     prof_mark(op, s);
     return axis0_inverse(op, pd, s);
@@ -855,8 +863,8 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
     return SCABEM_E_ARG;
   }
   if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm1)) return rc_;
-  fn<<<dim3(P0, NFIELD_IN), PLANE_THREADS, sm1, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, n1, n2, pd.tw[1],
-                                                   pd.tw[2]);
+  fn<<<dim3(P0, nf), PLANE_THREADS, sm1, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, n1, n2, pd.tw[1], pd.tw[2],
+                                            id);
   CK(cudaGetLastError());
   prof_mark(op, s);
   return axis0_inverse(op, pd, s);
@@ -866,5 +874,5 @@ template int make_twiddles<float>(cx<float>*, int, cudaStream_t);
 template int make_twiddles<double>(cx<double>*, int, cudaStream_t);
 template int fft3d_full<double>(scabem_op*, cx<double>*, const cx<double>* const[3], int, cudaStream_t);
 template int fft_axis_full<double>(scabem_op*, cx<double>*, int, const cx<double>*, int, cudaStream_t);
-template int fft_conv<float>(scabem_op*, PrecData<float>&, cudaStream_t);
-template int fft_conv<double>(scabem_op*, PrecData<double>&, cudaStream_t);
+template int fft_conv<float>(scabem_op*, PrecData<float>&, cudaStream_t, bool);
+template int fft_conv<double>(scabem_op*, PrecData<double>&, cudaStream_t, bool);

@@ -520,10 +520,13 @@ __global__ void k_sigma_copy(const double* __restrict__ in, int64_t Q, double* _
   if (sf) sf[i] = (float)sig;
 }
 
-// Stencil weight W_slot(point) = Lx[i] Ly[j] Lz[k] of every projection entry;
-// the entry code (point * p^3 + slot) is then replaced by the point index.
-__global__ void k_gather_weights(int32_t* __restrict__ gent, const double* __restrict__ L, int64_t ne, int p,
-                                 double* __restrict__ wd, float* __restrict__ wf) {
+// Stencil weight W_slot(point) = Lx[i] Ly[j] Lz[k] of every projection entry
+// and its derivative weights (dLx Ly Lz, Lx dLy Lz, Lx Ly dLz: the
+// transposed interpolation of gradients and curls); the entry code
+// (point * p^3 + slot) is then replaced by the point index.
+__global__ void k_gather_weights(int32_t* __restrict__ gent, const double* __restrict__ L,
+                                 const double* __restrict__ dL, int64_t ne, int p, double* __restrict__ wd,
+                                 float* __restrict__ wf, double* __restrict__ gdd, float* __restrict__ gdf) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= ne) return;
   const int p2 = p * p, p3 = p2 * p;
@@ -531,9 +534,16 @@ __global__ void k_gather_weights(int32_t* __restrict__ gent, const double* __res
   const int64_t Qi = code / p3;
   const int sl = code - (int)Qi * p3;
   const int i = sl / p2, j = (sl - i * p2) / p, k = sl - i * p2 - j * p;
-  const double W = L[(3 * Qi + 0) * p + i] * L[(3 * Qi + 1) * p + j] * L[(3 * Qi + 2) * p + k];
+  const double lx = L[(3 * Qi + 0) * p + i], ly = L[(3 * Qi + 1) * p + j], lz = L[(3 * Qi + 2) * p + k];
+  const double W = lx * ly * lz;
   wd[e] = W;
   wf[e] = (float)W;
+  const double D[3] = {dL[(3 * Qi + 0) * p + i] * ly * lz, lx * dL[(3 * Qi + 1) * p + j] * lz,
+                       lx * ly * dL[(3 * Qi + 2) * p + k]};
+  for (int c = 0; c < 3; ++c) {
+    gdd[3 * e + c] = D[c];
+    gdf[3 * e + c] = (float)D[c];
+  }
   gent[e] = (int32_t)Qi;
 }
 
@@ -852,10 +862,13 @@ int setup_gather(scabem_op* op, cudaStream_t s) {
   CK(cudaMalloc(&op->gent, sizeof(int32_t) * ne));
   CK(cudaMalloc(&op->gwd, sizeof(double) * ne));
   CK(cudaMalloc(&op->gwf, sizeof(float) * ne));
+  CK(cudaMalloc(&op->gdd, sizeof(double) * 3 * ne));
+  CK(cudaMalloc(&op->gdf, sizeof(float) * 3 * ne));
   CK(cudaMemcpyAsync(op->gpt, pts.data(), sizeof(int32_t) * pts.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(op->goff, coff.data(), sizeof(int32_t) * coff.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(op->gent, ent.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, s));
-  k_gather_weights<<<(int)cdiv(ne, 256), 256, 0, s>>>(op->gent, op->d.L, ne, p, op->gwd, op->gwf);
+  k_gather_weights<<<(int)cdiv(ne, 256), 256, 0, s>>>(op->gent, op->d.L, op->d.dL, ne, p, op->gwd, op->gwf,
+                                                      op->gdd, op->gdf);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   return SCABEM_OK;
@@ -1012,6 +1025,24 @@ int setup_near(scabem_op* op, cudaStream_t s) {
   for (int med = 0; med < 2; ++med) {
     cudaFree(op->gspatial[med]);
     op->gspatial[med] = nullptr;
+  }
+  // reverse list for the transposed near field: the pairs of each source
+  // triangle (ascending pair index) and the target of every pair
+  if (acc > 0) {
+    std::vector<int32_t> hs(acc), rc(nt + 1, 0), rp(acc), pt(acc);
+    CK(cudaMemcpy(hs.data(), op->nsrc, sizeof(int32_t) * acc, cudaMemcpyDeviceToHost));
+    for (int64_t t = 0; t < nt; ++t)
+      for (int32_t j = ho[t]; j < ho[t + 1]; ++j) pt[j] = (int32_t)t;
+    for (int64_t j = 0; j < acc; ++j) ++rc[hs[j] + 1];
+    for (int64_t t = 0; t < nt; ++t) rc[t + 1] += rc[t];
+    std::vector<int32_t> cur(rc.begin(), rc.end() - 1);
+    for (int64_t j = 0; j < acc; ++j) rp[cur[hs[j]]++] = (int32_t)j;
+    CK(cudaMalloc(&op->roff, sizeof(int32_t) * (nt + 1)));
+    CK(cudaMalloc(&op->rpair, sizeof(int32_t) * acc));
+    CK(cudaMalloc(&op->ptgt, sizeof(int32_t) * acc));
+    CK(cudaMemcpy(op->roff, rc.data(), sizeof(int32_t) * (nt + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->rpair, rp.data(), sizeof(int32_t) * acc, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->ptgt, pt.data(), sizeof(int32_t) * acc, cudaMemcpyHostToDevice));
   }
   return SCABEM_OK;
 }
