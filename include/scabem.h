@@ -244,7 +244,10 @@ int scabem_rhs_noalloc(scabem_op_t op, const scabem_source* src, int32_t nsrc, v
  * blocks of A (the block-diagonal preconditioner of Appendix B), rebuilt on
  * every scabem_set_sigma.  x holds the initial guess on entry; info reports
  * iterations, refinement rounds and the final FP64 relative residual.
- * Returns SCABEM_E_NOCONV if refine_tol was not reached. */
+ * transpose = 1 solves A^T x = b instead (the adjoint system of gradients),
+ * with the transposed operator of scabem_apply_adjoint and the transposed
+ * preconditioner blocks.  Returns SCABEM_E_NOCONV if refine_tol was not
+ * reached. */
 typedef struct {
   double tol;        /* relative residual of each inner GMRES solve */
   int32_t restart;   /* Krylov dimension, <= 200 */
@@ -252,6 +255,7 @@ typedef struct {
   double refine_tol; /* outer FP64 relative residual */
   int32_t max_refine;
   int32_t prec;
+  int32_t transpose; /* 0: A x = b, 1: A^T x = b */
 } scabem_solve_opts;
 typedef struct {
   int32_t iters;
@@ -261,6 +265,24 @@ typedef struct {
 } scabem_solve_info;
 int scabem_solve(scabem_op_t op, const void* b, void* x, int32_t nrhs, int64_t ld, const scabem_solve_opts* opts,
                  void* stream, scabem_solve_info* info);
+
+/* Gradient of lam^T (A x - b) with respect to the parameters of a
+ * conductivity profile (A and b are affine in sigma: the sigma-weighted
+ * terms of the Eq. 13 / Eq. 14 rows and of their incident-field right-hand
+ * sides), summed over the quadrature points p:
+ *   g_i = sum_p (d sigma_p / d c_i) d(lam^T (A x - b)) / d sigma_p.
+ * x, lam: complex128, N each, device or host; src/nsrc: the excitation of b
+ * (as for scabem_rhs; nsrc = 0 when b does not depend on sigma).  `basis`
+ * names the parameters (only its shape is read):
+ *   SCABEM_SIGMA_PER_QPOINT: Q entries, the per-point derivative itself [1/S];
+ *   SCABEM_SIGMA_MONOMIAL:   nseg entries, d / d sigma0 of each segment;
+ *   SCABEM_SIGMA_BSPLINE:    ncoef entries, d / d coef of each coefficient.
+ * g_out: host, 2 * entries doubles (complex).  For x = A^-1 b and a real
+ * objective J with dJ = Re(v^H dx), solve A^T lam = conj(v) (scabem_solve
+ * with transpose = 1); then dJ/dc_i = -Re(g_i).  Needs the complex128
+ * operator; synchronises `stream`. */
+int scabem_sigma_gradient(scabem_op_t op, const void* x, const void* lam, const scabem_source* src, int32_t nsrc,
+                          const scabem_sigma* basis, double* g_out, void* stream);
 
 /* Interior electric field at npts host points (pts: npts x 3) from the
  * interior current set of x (complex128), plus the incident field of `inc`

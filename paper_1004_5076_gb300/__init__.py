@@ -59,7 +59,7 @@ class Source(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32), ("refine_tol", C.c_double),
-                ("max_refine", C.c_int32), ("prec", C.c_int32)]
+                ("max_refine", C.c_int32), ("prec", C.c_int32), ("transpose", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -102,6 +102,7 @@ def lib():
     L.scabem_set_sigma.argtypes = [vp, C.POINTER(Sigma)]
     L.scabem_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_apply_adjoint.argtypes = [vp, vp, vp, i32, i64, i32, vp]
+    L.scabem_sigma_gradient.argtypes = [vp, vp, vp, C.POINTER(Source), i32, C.POINTER(Sigma), vp, vp]
     L.scabem_rhs.argtypes = [vp, C.POINTER(Source), i32, vp, i64, i32, vp]
     L.scabem_solve.argtypes = [vp, vp, vp, i32, i64, C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo)]
     L.scabem_fields.argtypes = [vp, vp, i32, i64, vp, i32, C.POINTER(Source), vp, vp]
@@ -125,6 +126,8 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         if not a.is_contiguous():
             raise ValueError("buffer must be contiguous")
+        if (hasattr(a, "is_conj") and a.is_conj()) or (hasattr(a, "is_neg") and a.is_neg()):
+            raise ValueError("tensor has a pending conjugate/negation bit: call resolve_conj() / resolve_neg()")
         return C.c_void_p(a.data_ptr())
     a = np.asarray(a)
     if not a.flags["C_CONTIGUOUS"] and not a.flags["F_CONTIGUOUS"]:
@@ -267,16 +270,45 @@ def scabem_rhs_noalloc(op, sources, b, ld=None, prec=SCABEM_C128, stream=None):
 
 
 def scabem_solve(op, b, x, nrhs=1, ld=None, tol=1e-6, restart=60, maxit=2000, refine_tol=1e-8, max_refine=10,
-                 prec=SCABEM_C128, stream=None):
+                 prec=SCABEM_C128, stream=None, transpose=False):
+    """Solve A x = b (or A^T x = b with transpose=True); x holds the initial guess."""
     if ld is None:
         ld = b.shape[0]
-    o = SolveOpts(tol, restart, maxit, refine_tol, max_refine, prec)
+    o = SolveOpts(tol, restart, maxit, refine_tol, max_refine, prec, 1 if transpose else 0)
     info = (SolveInfo * max(nrhs, 1))()
     rc = lib().scabem_solve(op, _ptr(b), _ptr(x), nrhs, ld, C.byref(o), _stream(stream), info)
     out = [{"iters": i.iters, "refinements": i.refinements, "relres": i.relres, "status": i.status}
            for i in info[:nrhs]]
     _check(rc)
     return out
+
+
+def scabem_sigma_gradient(op, x, lam, sources=(), segments=None, bspline=None, per_qpoint=False, stream=None):
+    """g_i = sum_p dsigma_p/dc_i d(lam^T (A x - b))/dsigma_p for the parameters of
+    a profile: bspline = (x0, L, axis, ncoef) -> ncoef values; segments (the
+    monomial list) -> one value per segment (d / d sigma0); per_qpoint -> Q values."""
+    arr = (Source * max(len(sources), 1))(*sources)
+    if bspline is not None:
+        x0, L, axis, ncoef = bspline
+        basis = Sigma(SIGMA_BSPLINE, 0, None, None, float(x0), float(L), int(axis), int(ncoef), None)
+        n = int(ncoef)
+        keep = None
+    elif segments is not None:
+        seg = np.ascontiguousarray(np.asarray(segments, dtype=np.float64).reshape(-1))
+        basis = Sigma(SIGMA_MONOMIAL, len(seg) // 6, seg.ctypes.data_as(C.POINTER(C.c_double)), None)
+        n = len(seg) // 6
+        keep = seg
+    elif per_qpoint:
+        basis = Sigma(SIGMA_PER_QPOINT, 0, None, None)
+        n = scabem_op_info(op)["qpoints"]
+        keep = None
+    else:
+        raise ValueError("give bspline, segments or per_qpoint")
+    out = np.zeros(2 * max(n, 1), dtype=np.float64)
+    _check(lib().scabem_sigma_gradient(op, _ptr(x), _ptr(lam), arr, len(sources), C.byref(basis), _ptr(out),
+                                       _stream(stream)))
+    del keep
+    return out[0::2][:n] + 1j * out[1::2][:n]
 
 
 def scabem_fields(op, x, pts, inc=None, nrhs=1, ld=None, stream=None):

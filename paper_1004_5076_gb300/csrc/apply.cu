@@ -410,6 +410,42 @@ __device__ __forceinline__ void test_point(const cx<R>* recs, const cx<R>* __res
   out[3] = w * (XJ - sg * dot3(X, E[1]) - (R(0.5) * sg) * XnM);
 }
 
+// d out / d sg of the Eq. 13 and Eq. 14 tested values of local edge kk at
+// point a (sg the normalised conductivity): d2 = w (-(n x X) . E_e - X . M / 2),
+// d3 = w (-X . E_i - X . (n x M) / 2), from the point's records.
+template <typename R>
+__device__ __forceinline__ void test_point_sigma(const cx<R>* recs, const cx<R>* __restrict__ summ,
+                                                 const double* __restrict__ tri, const R* __restrict__ tp, int64_t t,
+                                                 int kk, int a, int q, R ke, R ki, R ze, R zi, cx<R>& d2,
+                                                 cx<R>& d3) {
+  const double* g = tri + 16 * t;
+  const R nrm[3] = {(R)g[12], (R)g[13], (R)g[14]};
+  const cx<R>* sM = summ + (3 * t + 2) * 4;
+  const R* tq = tp + 16 * (t * q + a);
+  const R w = tq[3];
+  R X[3], rel[3];
+  for (int c = 0; c < 3; ++c) {
+    X[c] = tq[4 + 3 * kk + c];
+    rel[c] = tq[c];
+  }
+  const R kl[2] = {ke, ki}, zl[2] = {ze, zi};
+  cx<R> E[2][3];
+  for (int m = 0; m < 2; ++m) {
+    const cx<R>* r = recs + m * NREC;
+    const R k = kl[m], z = zl[m];
+    for (int c = 0; c < 3; ++c)
+      E[m][c] = -z * (k * mulj(r[c]) + (R(1) / k) * mulj(r[4 + c])) - r[17 + c];
+  }
+  cx<R> M[3], nM[3];
+  for (int c = 0; c < 3; ++c) M[c] = rel[c] * sM[0] - sM[1 + c];
+  nM[0] = nrm[1] * M[2] - nrm[2] * M[1];
+  nM[1] = nrm[2] * M[0] - nrm[0] * M[2];
+  nM[2] = nrm[0] * M[1] - nrm[1] * M[0];
+  const R nX[3] = {nrm[1] * X[2] - nrm[2] * X[1], nrm[2] * X[0] - nrm[0] * X[2], nrm[0] * X[1] - nrm[1] * X[0]};
+  d2 = -w * (dot3(nX, E[0]) + R(0.5) * dot3(X, M));
+  d3 = -w * (dot3(X, E[1]) + R(0.5) * dot3(X, nM));
+}
+
 // Bulk asynchronous global -> shared copies (the TMA unit, cp.async.bulk)
 // completing on an mbarrier, and bounded waits on it.
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -483,13 +519,17 @@ __host__ __device__ constexpr size_t pt_smem_bytes(int q, size_t csize) {
   return (size_t)PT_WARPS * pt_warp_complex(q) * csize + (size_t)PT_WARPS * PT_NSTG * sizeof(uint64_t);
 }
 
-template <typename R, int P>
+// SENS = true (conductivity sensitivity): instead of testing into y, the
+// kernel writes hs[t q + a] = eta0 sum_kk (lam_row2 d2 + lam_row3 d3), the
+// derivative of lam^T A x with respect to the conductivity [S] at the point.
+template <typename R, int P, bool SENS = false>
 __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 6) : 3) k_points(
     const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
     const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
     const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
     const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki,
-    R ze, R zi, int has_near, const int32_t* __restrict__ valrow, cx<R>* __restrict__ y, int* __restrict__ tmo) {
+    R ze, R zi, int has_near, const int32_t* __restrict__ valrow, cx<R>* __restrict__ y, int* __restrict__ tmo,
+    const cx<R>* __restrict__ lam, cx<R>* __restrict__ hs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
@@ -578,6 +618,21 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
     for (int c = 0; c < NREC / 2; ++c) o[c] = acc[c];
   }
   __syncwarp();
+  if constexpr (SENS) {
+    if (lane < 3 * q) {
+      const int kk = lane / q, pa = lane - kk * q;
+      cx<R> d2, d3;
+      test_point_sigma(recs + pa * 2 * NREC, summ, tri, tp, t, kk, pa, q, ke, ki, ze, zi, d2, d3);
+      const int r2 = valrow[(t * 3 + kk) * 4 + 2], r3 = valrow[(t * 3 + kk) * 4 + 3];
+      cx<R> c = czero<R>();
+      if (r2 >= 0) c += lam[r2] * d2;
+      if (r3 >= 0) c += lam[r3] * d3;
+      part[kk * q + pa] = c;
+    }
+    __syncwarp();
+    if (lane < q) hs[t * q + lane] = R(ETA0) * (part[lane] + part[q + lane] + part[2 * q + lane]);
+    return;
+  }
   if (lane < 3 * q) {
     const int kk = lane / q, pa = lane - kk * q;
     cx<R> o[4];
@@ -931,7 +986,7 @@ __global__ void k_x_adj(const cx<R>* __restrict__ stot, const int32_t* __restric
 template <typename R>
 using PointsFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, const int32_t*,
                           const int32_t*, const cx<R>*, const double*, const R*, const R*, int64_t, int, int, int,
-                          int, R, R, R, R, int, const int32_t*, cx<R>*, int*);
+                          int, R, R, R, R, int, const int32_t*, cx<R>*, int*, const cx<R>*, cx<R>*);
 
 template <typename R>
 PrecData<R>& pdata(scabem_op* op);
@@ -973,7 +1028,7 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
     fn<<<(int)cdiv(nt, PT_WARPS), PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
                                                   op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, (R)op->ke, (R)op->ki,
                                                   (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, op->valrow, y,
-                                                  op->tmo_d);
+                                                  op->tmo_d, nullptr, nullptr);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);
@@ -1025,6 +1080,38 @@ int apply_adjoint_one(scabem_op* op, const cx<R>* ybar, cx<R>* xbar, cudaStream_
     CK(cudaGetLastError());
   }
   k_x_adj<R><<<(int)cdiv(op->N, 256), 256, 0, s>>>(sdir, op->xsrc, op->tri, op->cX, op->N, xbar);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
+// hs[p] = d(lam^T A x)/d sigma_p [per S] at every quadrature point
+// (complex128): the apply's stages up to the records, then the derivative
+// of the sigma-weighted testing (k_points in its sensitivity mode).  yscr:
+// N complex of scratch.
+int sigma_sensitivity_op(scabem_op* op, const cx<double>* x, const cx<double>* lam, cx<double>* hs,
+                         cx<double>* yscr, cudaStream_t s) {
+  PrecData<double>& pd = op->d;
+  const int64_t nt = op->nt, Q = op->Q;
+  const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
+  const int64_t ng = (int64_t)n0 * n1 * n2;
+  k_sources<double><<<(int)cdiv(Q, 128), 128, 0, s>>>(x, op->unk, op->cX, op->tri, op->qp, op->qw, Q, op->q,
+                                                      pd.summ, pd.qsrc, yscr, op->N);
+  CK(cudaGetLastError());
+  if (op->ngnz > 0) {
+    k_gather<double><<<(int)cdiv(op->ngnz * 32, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent, op->gwd,
+                                                                   op->ngnz, ng, pd.src);
+    CK(cudaGetLastError());
+  }
+  int rc = fft_conv<double>(op, pd, s, false);
+  if (rc) return rc;
+  const size_t sm = pt_smem_bytes(op->q, sizeof(cx<double>));
+  PointsFn<double> fn = op->p == 2 ? k_points<double, 2, true> : op->p == 3 ? k_points<double, 3, true>
+                                                                            : k_points<double, 4, true>;
+  if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm)) return rc_;
+  fn<<<(int)cdiv(nt, PT_WARPS), PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc,
+                                                        pd.summ, op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, op->ke,
+                                                        op->ki, op->ze, op->zi, op->npairs > 0 ? 1 : 0, op->valrow,
+                                                        yscr, op->tmo_d, lam, hs);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }

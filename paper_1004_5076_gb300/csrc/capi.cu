@@ -781,7 +781,7 @@ int scabem_rhs(scabem_op_t op, const scabem_source* src, int32_t nsrc, void* b, 
 int scabem_solve(scabem_op_t op, const void* b, void* x, int32_t nrhs, int64_t ld, const scabem_solve_opts* o,
                  void* stream, scabem_solve_info* info) {
   if (!op || !b || !x || !o || nrhs < 0 || ld < op->N || o->restart < 1 || o->restart > 200 || o->maxit < 1 ||
-      !(o->tol > 0) || (o->prec != SCABEM_C64 && o->prec != SCABEM_C128)) {
+      !(o->tol > 0) || (o->prec != SCABEM_C64 && o->prec != SCABEM_C128) || o->transpose < 0 || o->transpose > 1) {
     set_error("scabem_solve: bad argument");
     return SCABEM_E_ARG;
   }
@@ -812,6 +812,64 @@ int scabem_solve(scabem_op_t op, const void* b, void* x, int32_t nrhs, int64_t l
   CK(cudaStreamSynchronize(s));
   cudaFree(db);
   cudaFree(dx);
+  const int rt = take_timeout(op);
+  return rt ? rt : rc;
+}
+
+int scabem_sigma_gradient(scabem_op_t op, const void* x, const void* lam, const scabem_source* src, int32_t nsrc,
+                          const scabem_sigma* basis, double* g_out, void* stream) {
+  if (!op || !x || !lam || !basis || !g_out || nsrc < 0 || (nsrc > 0 && !src)) {
+    set_error("scabem_sigma_gradient: null argument or nsrc < 0");
+    return SCABEM_E_ARG;
+  }
+  if (!op->d.built) {
+    set_error("scabem_sigma_gradient needs the complex128 operator (prec_mask bit 1)");
+    return SCABEM_E_ARG;
+  }
+  if (basis->kind == SCABEM_SIGMA_BSPLINE) {
+    if (basis->ncoef < 4 || basis->ncoef > 1024 || !(basis->L > 0) || basis->axis < 0 || basis->axis > 2 ||
+        !std::isfinite(basis->x0)) {
+      set_error("scabem_sigma_gradient: B-spline basis needs 4 <= ncoef <= 1024, L > 0, axis in {0,1,2}");
+      return SCABEM_E_ARG;
+    }
+  } else if (basis->kind == SCABEM_SIGMA_MONOMIAL) {
+    if (basis->nseg < 0 || (basis->nseg > 0 && !basis->seg)) {
+      set_error("scabem_sigma_gradient: monomial basis needs its segments");
+      return SCABEM_E_ARG;
+    }
+    for (int i = 0; i < basis->nseg; ++i) {
+      const double* gsg = basis->seg + 6 * i;
+      if (!(gsg[1] > 0) || gsg[3] < 0 || (gsg[4] != 0 && gsg[4] != 1 && gsg[4] != 2) || (gsg[5] != 1 && gsg[5] != -1)) {
+        set_error("scabem_sigma_gradient: monomial segment needs L > 0, d >= 0, axis in {0,1,2}, dir = +-1");
+        return SCABEM_E_ARG;
+      }
+    }
+  } else if (basis->kind != SCABEM_SIGMA_PER_QPOINT) {
+    set_error("scabem_sigma_gradient: unknown basis kind");
+    return SCABEM_E_ARG;
+  }
+  for (int i = 0; i < nsrc; ++i)
+    if (src[i].kind < 0 || src[i].kind > 2 || src[i].side < 0 || src[i].side > 1) {
+      set_error("scabem_sigma_gradient: source kind must be 0..2 and side 0..1");
+      return SCABEM_E_ARG;
+    }
+  if (int rc = take_timeout(op)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(cx<double>) * op->N;
+  const bool xd = is_device_ptr(x), ld_ = is_device_ptr(lam);
+  void *dx = nullptr, *dl = nullptr;
+  if (!xd) {
+    CK(cudaMalloc(&dx, bytes));
+    CK(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, s));
+  }
+  if (!ld_) {
+    CK(cudaMalloc(&dl, bytes));
+    CK(cudaMemcpyAsync(dl, lam, bytes, cudaMemcpyHostToDevice, s));
+  }
+  int rc = sigma_gradient_impl(op, (const cx<double>*)(xd ? x : dx), (const cx<double>*)(ld_ ? lam : dl), src, nsrc,
+                               basis, g_out, s);
+  cudaFree(dx);
+  cudaFree(dl);
   const int rt = take_timeout(op);
   return rt ? rt : rc;
 }

@@ -244,10 +244,13 @@ int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s);
 int setup_sigma_bspline(scabem_op* op, double x0, double L, int axis, int ncoef, const double* coef, cudaStream_t s);
 int setup_precond(scabem_op* op, cudaStream_t s);
 int setup_gather(scabem_op* op, cudaStream_t s);
-int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s);
+int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed = false);
 // apply.cu
 template <typename R>
 int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s);
+// hs[p] = d(lam^T A x)/d sigma_p [per S] at every quadrature point (complex128)
+int sigma_sensitivity_op(scabem_op* op, const cx<double>* x, const cx<double>* lam, cx<double>* hs,
+                         cx<double>* yscr, cudaStream_t s);
 // x_bar = A^T y_bar (transpose, no conjugation)
 template <typename R>
 int apply_adjoint_one(scabem_op* op, const cx<R>* ybar, cx<R>* xbar, cudaStream_t s);
@@ -264,6 +267,8 @@ template <typename R>
 int make_twiddles(cx<R>* tw, int len, cudaStream_t s);
 // solve.cu
 int rhs_impl(scabem_op* op, const scabem_source* src, int nsrc, void* b, int64_t ld, int prec, cudaStream_t s);
+int sigma_gradient_impl(scabem_op* op, const cx<double>* x, const cx<double>* lam, const scabem_source* src, int nsrc,
+                        const scabem_sigma* basis, double* g_out, cudaStream_t s);
 int solve_impl(scabem_op* op, const void* b, void* x, int nrhs, int64_t ld, const scabem_solve_opts* o,
                cudaStream_t s, scabem_solve_info* info);
 int fields_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double* pts, int npts,

@@ -772,8 +772,9 @@ __global__ void k_precond(const double* __restrict__ tri, const double* __restri
 
 // out[unknowns of e] = Binv_e * in[rows of e] (rows and unknowns of an edge
 // share the same index set).
+// transposed = 1 applies (Binv_e)^T, the inverse blocks of A^T.
 __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __restrict__ eunk, int64_t ne,
-                                const cd* __restrict__ in, cd* __restrict__ out) {
+                                const cd* __restrict__ in, cd* __restrict__ out, int transposed) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= ne) return;
   const int nb = eunk[3 * e + 2] < 0 ? 2 : 3;
@@ -781,7 +782,7 @@ __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __re
   for (int i = 0; i < nb; ++i) v[i] = in[eunk[3 * e + i]];
   for (int i = 0; i < nb; ++i) {
     cd acc = mk(0.0, 0.0);
-    for (int j = 0; j < nb; ++j) acc += pinv[9 * e + 3 * i + j] * v[j];
+    for (int j = 0; j < nb; ++j) acc += pinv[9 * e + (transposed ? 3 * j + i : 3 * i + j)] * v[j];
     out[eunk[3 * e + i]] = acc;
   }
 }
@@ -886,8 +887,8 @@ int setup_precond(scabem_op* op, cudaStream_t s) {
   return SCABEM_OK;
 }
 
-int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s) {
-  k_precond_apply<<<(int)cdiv(op->ne, 256), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out);
+int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed) {
+  k_precond_apply<<<(int)cdiv(op->ne, 256), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out, transposed ? 1 : 0);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }

@@ -129,6 +129,104 @@ __global__ void k_rhs(scabem_source S, const double* __restrict__ tri, const dou
   }
 }
 
+// Right-hand-side part of the conductivity sensitivity, one thread per
+// quadrature point: hs[p] -= eta0 sum_kk lam_row d(rhs_row)/d sg, the
+// sigma-weighted incident-field terms of k_rhs (Eq. 14 rows for an interior
+// source, Eq. 13 rows for an exterior one).
+__global__ void k_rhs_sens(scabem_source S, const double* __restrict__ tri, const double* __restrict__ cX,
+                           const double* __restrict__ qp, const double* __restrict__ qw, const int32_t* __restrict__ valrow,
+                           const cd* __restrict__ lam, int64_t Q, int q, double k, double z, cd* __restrict__ hs) {
+  const int64_t Qa = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (Qa >= Q) return;
+  const int64_t t = Qa / q;
+  const double* g = tri + 16 * t;
+  const double r[3] = {qp[3 * Qa], qp[3 * Qa + 1], qp[3 * Qa + 2]};
+  cd E[3], H[3];
+  incident(S, k, z, r, E, H);
+  const double w = qw[Qa];
+  const double* n = g + 12;
+  cd acc = mk(0.0, 0.0);
+  for (int kk = 0; kk < 3; ++kk) {
+    double X[3];
+    for (int c = 0; c < 3; ++c) X[c] = cX[3 * t + kk] * (r[c] - g[3 * kk + c]);
+    const int row = valrow[(t * 3 + kk) * 4 + (S.side == 0 ? 3 : 2)];
+    if (row < 0) continue;
+    cd d;
+    if (S.side == 0) {
+      d = X[0] * E[0] + X[1] * E[1] + X[2] * E[2];
+    } else {
+      const double nX[3] = {n[1] * X[2] - n[2] * X[1], n[2] * X[0] - n[0] * X[2], n[0] * X[1] - n[1] * X[0]};
+      d = nX[0] * E[0] + nX[1] * E[1] + nX[2] * E[2];
+    }
+    acc += lam[row] * (w * d);
+  }
+  hs[Qa] -= ETA0 * acc;
+}
+
+// Gradient reductions over the quadrature points (one block per parameter,
+// fixed tree order): g[i] = sum_p dsigma_p/dc_i hs[p].
+constexpr int GRAD_THREADS = 256;
+__device__ void block_sum_store(cd v, cd* out) {
+  __shared__ double sr[GRAD_THREADS], si[GRAD_THREADS];
+  sr[threadIdx.x] = v.re;
+  si[threadIdx.x] = v.im;
+  __syncthreads();
+  for (int st = GRAD_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sr[threadIdx.x] += sr[threadIdx.x + st];
+      si[threadIdx.x] += si[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = mk(sr[0], si[0]);
+}
+
+// B-spline coefficient i: dsigma_p/dc_i = N_i(s_p), by de Boor's scheme on
+// the unit coefficient vector (the same knots as k_sigma_bspline).
+__global__ void k_grad_bspline(const double* __restrict__ qp, int64_t Q, double x0, double L, int axis, int ncoef,
+                               const cd* __restrict__ hs, cd* __restrict__ g) {
+  const int ci = blockIdx.x;
+  const int nspan = ncoef - 3;
+  cd acc = mk(0.0, 0.0);
+  for (int64_t p = threadIdx.x; p < Q; p += GRAD_THREADS) {
+    const double s = (qp[3 * p + axis] - x0) / L;
+    if (s < 0.0 || s > 1.0) continue;
+    int j = (int)(s * nspan);
+    if (j >= nspan) j = nspan - 1;
+    if (ci < j || ci > j + 3) continue;  // N_i vanishes outside its four spans
+    auto knot = [&](int m) {
+      const int v = m - 3;
+      return v <= 0 ? 0.0 : (v >= nspan ? 1.0 : (double)v / nspan);
+    };
+    const int sp = j + 3;
+    double d[4];
+    for (int r = 0; r < 4; ++r) d[r] = (sp - 3 + r == ci) ? 1.0 : 0.0;
+    for (int lvl = 1; lvl <= 3; ++lvl)
+      for (int r = 3; r >= lvl; --r) {
+        const int m = sp - 3 + r;
+        const double den = knot(m + 4 - lvl) - knot(m);
+        const double al = den > 0.0 ? (s - knot(m)) / den : 0.0;
+        d[r] = (1.0 - al) * d[r - 1] + al * d[r];
+      }
+    acc += d[3] * hs[p];
+  }
+  block_sum_store(acc, g + ci);
+}
+
+// Monomial segment i: dsigma_p/dsigma0_i = u(s_p)^d of that segment.
+__global__ void k_grad_monomial(const double* __restrict__ qp, int64_t Q, const double* __restrict__ seg,
+                                const cd* __restrict__ hs, cd* __restrict__ g) {
+  const double* sg = seg + 6 * blockIdx.x;
+  const int ax = (int)sg[4];
+  cd acc = mk(0.0, 0.0);
+  for (int64_t p = threadIdx.x; p < Q; p += GRAD_THREADS) {
+    const double s = sg[5] * (qp[3 * p + ax] - sg[0]) / sg[1];
+    if (s < 0.0) continue;
+    acc += pow(s > 1.0 ? 1.0 : s, sg[3]) * hs[p];
+  }
+  block_sum_store(acc, g + blockIdx.x);
+}
+
 template <typename R>
 __global__ void k_rows_out(const cd* __restrict__ val, const int32_t* __restrict__ rowsrc, int64_t N,
                            cx<R>* __restrict__ y) {
@@ -304,6 +402,7 @@ struct Work {
   cd* u = nullptr;     // N, solution in the preconditioned variables
   cx<float>* xf = nullptr;
   cx<float>* yf = nullptr;
+  bool tr = false;  // solve with A^T
   ~Work() {
     cudaFree(z);
     cudaFree(u);
@@ -361,10 +460,10 @@ int norm2(const cd* w, int64_t N, Work& W, cudaStream_t s, double& nrm) {
 // y = A v in FP64 storage, arithmetic in `prec`.
 int op_apply64(scabem_op* op, const cd* v, cd* y, int prec, Work& W, cudaStream_t s) {
   const int64_t N = op->N;
-  if (prec == SCABEM_C128) return apply_one<double>(op, v, y, s);
+  if (prec == SCABEM_C128) return W.tr ? apply_adjoint_one<double>(op, v, y, s) : apply_one<double>(op, v, y, s);
   k_to_f<<<DOT_BLOCKS, 256, 0, s>>>(v, W.xf, N);
   CK(cudaGetLastError());
-  int rc = apply_one<float>(op, W.xf, W.yf, s);
+  int rc = W.tr ? apply_adjoint_one<float>(op, W.xf, W.yf, s) : apply_one<float>(op, W.xf, W.yf, s);
   if (rc) return rc;
   k_from_f<<<DOT_BLOCKS, 256, 0, s>>>(W.yf, y, N);
   CK(cudaGetLastError());
@@ -401,7 +500,7 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
     for (; j < m && iters < maxit; ++j) {
       ++iters;
       // right preconditioning: w = A P^-1 v_j
-      rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s);
+      rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr);
       if (rc) return rc;
       rc = op_apply64(op, W.z, W.w, prec, W, s);
       if (rc) return rc;
@@ -497,7 +596,7 @@ int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int ma
       k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j, W.h, W.u, N);
       CK(cudaGetLastError());
     }
-    rc = precond_apply(op, W.u, d, s);  // d = P^-1 u
+    rc = precond_apply(op, W.u, d, s, W.tr);  // d = P^-1 u
     if (rc) return rc;
     if (done || iters >= maxit) break;
     // true residual for the restart
@@ -681,12 +780,64 @@ int rhs_impl(scabem_op* op, const scabem_source* src, int nsrc, void* b, int64_t
   return SCABEM_OK;
 }
 
+// Gradient of lam^T (A x - b) with respect to the parameters of `basis`
+// (x, lam: device complex128, N each).  g_out: host, 2 * entries doubles.
+int sigma_gradient_impl(scabem_op* op, const cd* x, const cd* lam, const scabem_source* src, int nsrc,
+                        const scabem_sigma* basis, double* g_out, cudaStream_t s) {
+  const int64_t Q = op->Q, N = op->N;
+  cd *hs = nullptr, *yscr = nullptr, *g = nullptr;
+  double* dseg = nullptr;
+  int64_t ng = basis->kind == SCABEM_SIGMA_PER_QPOINT ? Q
+               : basis->kind == SCABEM_SIGMA_BSPLINE   ? basis->ncoef
+                                                       : basis->nseg;
+  int rc = SCABEM_OK;
+  auto fail = [&](cudaError_t e, const char* what) { rc = cuda_fail(e, what); };
+  cudaError_t e;
+  if ((e = cudaMalloc(&hs, sizeof(cd) * Q)) != cudaSuccess) fail(e, "cudaMalloc");
+  if (!rc && (e = cudaMalloc(&yscr, sizeof(cd) * N)) != cudaSuccess) fail(e, "cudaMalloc");
+  if (!rc && (e = cudaMalloc(&g, sizeof(cd) * (ng > 0 ? ng : 1))) != cudaSuccess) fail(e, "cudaMalloc");
+  if (!rc) rc = sigma_sensitivity_op(op, x, lam, hs, yscr, s);
+  for (int i = 0; !rc && i < nsrc; ++i) {
+    const double k = src[i].side == 0 ? op->ki : op->ke, z = src[i].side == 0 ? op->zi : op->ze;
+    k_rhs_sens<<<(int)cdiv(Q, 256), 256, 0, s>>>(src[i], op->tri, op->cX, op->qp, op->qw, op->valrow, lam, Q,
+                                                 op->q, k, z, hs);
+    if ((e = cudaGetLastError()) != cudaSuccess) fail(e, "k_rhs_sens");
+  }
+  if (!rc && basis->kind == SCABEM_SIGMA_PER_QPOINT) {
+    if ((e = cudaMemcpyAsync(g_out, hs, sizeof(cd) * Q, cudaMemcpyDeviceToHost, s)) != cudaSuccess) fail(e, "copy");
+  } else if (!rc && basis->kind == SCABEM_SIGMA_BSPLINE) {
+    k_grad_bspline<<<basis->ncoef, GRAD_THREADS, 0, s>>>(op->qp, Q, basis->x0, basis->L, basis->axis, basis->ncoef,
+                                                         hs, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) fail(e, "k_grad_bspline");
+    if (!rc && (e = cudaMemcpyAsync(g_out, g, sizeof(cd) * ng, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      fail(e, "copy");
+  } else if (!rc && ng > 0) {
+    if ((e = cudaMalloc(&dseg, sizeof(double) * 6 * ng)) != cudaSuccess) fail(e, "cudaMalloc");
+    if (!rc && (e = cudaMemcpyAsync(dseg, basis->seg, sizeof(double) * 6 * ng, cudaMemcpyHostToDevice, s)) !=
+                   cudaSuccess)
+      fail(e, "copy");
+    if (!rc) {
+      k_grad_monomial<<<(int)ng, GRAD_THREADS, 0, s>>>(op->qp, Q, dseg, hs, g);
+      if ((e = cudaGetLastError()) != cudaSuccess) fail(e, "k_grad_monomial");
+    }
+    if (!rc && (e = cudaMemcpyAsync(g_out, g, sizeof(cd) * ng, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      fail(e, "copy");
+  }
+  if (!rc && (e = cudaStreamSynchronize(s)) != cudaSuccess) fail(e, "cudaStreamSynchronize");
+  cudaFree(hs);
+  cudaFree(yscr);
+  cudaFree(g);
+  cudaFree(dseg);
+  return rc;
+}
+
 int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, const scabem_solve_opts* o,
                cudaStream_t s, scabem_solve_info* info) {
   const int64_t N = op->N;
   const int m = o->restart;
   const int prec = o->prec;
   Work W;
+  W.tr = o->transpose != 0;
   CK(cudaMalloc(&W.V, sizeof(cd) * N * (m + 1)));
   CK(cudaMalloc(&W.w, sizeof(cd) * N));
   CK(cudaMalloc(&W.t, sizeof(cd) * N));
@@ -716,7 +867,7 @@ int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, co
     const double tol_out = o->refine_tol > 0 ? o->refine_tol : o->tol;
     int st = SCABEM_E_NOCONV;
     for (int it = 0; it <= outer; ++it) {
-      rc = apply_one<double>(op, x, W.w, s);
+      rc = W.tr ? apply_adjoint_one<double>(op, x, W.w, s) : apply_one<double>(op, x, W.w, s);
       if (rc) return rc;
       k_sub<<<DOT_BLOCKS, 256, 0, s>>>(b, W.w, r, N);
       CK(cudaGetLastError());
