@@ -221,6 +221,28 @@ __device__ __forceinline__ void load_group(const cx<double>* p, cx<double>* v) {
   for (int f = 0; f < 4; ++f) v[f] = p[f];
 }
 
+// Two consecutive complex values of shared memory on a 16-byte boundary.
+__device__ __forceinline__ void load_pair_smem(const cx<float>* p, cx<float>* v) {
+  const float4 u = *reinterpret_cast<const float4*>(p);
+  v[0] = mk(u.x, u.y);
+  v[1] = mk(u.z, u.w);
+}
+__device__ __forceinline__ void load_pair_smem(const cx<double>* p, cx<double>* v) {
+  v[0] = p[0];
+  v[1] = p[1];
+}
+
+// Two consecutive complex values starting on a 16-byte boundary.
+__device__ __forceinline__ void load_pair(const cx<float>* p, cx<float>* v) {
+  const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = mk(u.x, u.y);
+  v[1] = mk(u.z, u.w);
+}
+__device__ __forceinline__ void load_pair(const cx<double>* p, cx<double>* v) {
+  v[0] = p[0];
+  v[1] = p[1];
+}
+
 // Interpolated potentials of one medium at quadrature point Qi, group h of
 // the record (NREC = 2 x 10): h = 0 A(3) phi grad phi(3) curl A(3) from the
 // J fields, h = 1 F(3) psi grad psi(3) curl F(3) from the M fields.  The
@@ -465,6 +487,18 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// The arrival of one thread that expects `bytes` of copies on `bar`, and one
+// bulk copy completing its bytes there (several copies may share one arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -665,9 +699,10 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
 //   T1 k_points_adj   rows -> tested values -> record adjoints at every point
 //                     (Eqs. 1-3, 13, 14 testing transposed) and the
 //                     triangle's own side-limit terms -> its summary adjoints
-//   T2 k_near_adj     record adjoints of the targets -> summary adjoints of
-//                     each source triangle (near records transposed; one warp
-//                     per source over its reverse pair list, no atomics)
+//   T2 k_near_adj_*   record adjoints of the targets -> summary adjoints of
+//                     the source triangles (near records transposed): per
+//                     pair over each target's record run, then per source
+//                     over its reverse pair list (no atomics)
 //   T3 k_interp_adj   record adjoints -> 16 grid fields (value and derivative
 //                     stencils transposed), as a gather over covered points
 //   T4 fft_conv(adjoint): each field with its medium's Green function
@@ -782,114 +817,195 @@ __global__ void __launch_bounds__(PT_WARPS * 32)
   }
 }
 
-// T2: one warp per source triangle s, over the pairs rpair[roff[s] ..) with
-// targets ptgt[j].  Lane (target point a, medium, group) transposes near_part:
-//   a_bar += r . dP1 + 2 phi_r dP0 + 2 grad_r . dQ + curl_r . dC,
-//   beta_bar += -A_r dP0 - (the dQ x beta term transposed),
-// the interior medium's M group with the sign of -M; the lanes' sums are
-// added in point order and to the triangle's own terms (sdir).
+// T2a: one warp per target triangle t over its own near pairs (one
+// contiguous run of records).  The pairs stream through a per-warp ring of
+// NA_NSTG stages of NA_KP pairs (one bulk copy per pair into a slot padded to
+// na_slot(q) complex values, so that the 16 (pair, medium) rows a warp load
+// touches fall in distinct banks; bounded waits).  The target's record
+// adjoints (q points x 2 media x 20) sit in shared memory.  Lane (pair k,
+// medium m, group h) forms, for pair k of the stage, the transpose of
+// near_part summed over the target's points a:
+//   a_bar = sum_a r . dP1 + 2 phi_r dP0 + 2 grad_r . dQ + curl_r . dC,
+//   beta_bar = sum_a -A_r dP0 - (the dQ x beta term transposed),
+// and the pair's 12 contributions are the per-set values J_e = (exterior,
+// J), J_i = (interior, J), M = (exterior, M) - (interior, M).
+constexpr int NA_KP = 8;
+constexpr int NA_NSTG = 2;
+__host__ __device__ __forceinline__ int na_slot(int q) {
+  const int pc = NCORR * 2 * q;
+  return pc + (((2 - pc) % 16) + 16) % 16;
+}
+__host__ __device__ __forceinline__ int na_warp_cx(int q) { return NA_NSTG * NA_KP * na_slot(q) + 40 * q; }
 template <typename R>
-__global__ void __launch_bounds__(PT_WARPS * 32)
-    k_near_adj(const cx<R>* __restrict__ corr, const int32_t* __restrict__ roff, const int32_t* __restrict__ rpair,
-               const int32_t* __restrict__ ptgt, const cx<R>* __restrict__ recb, const cx<R>* __restrict__ sdir,
-               int64_t nt, int q, cx<R>* __restrict__ snear) {
+__global__ void __launch_bounds__(PT_WARPS * 32, 4)
+    k_near_adj_pairs(const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff, const cx<R>* __restrict__ recb,
+                     int64_t nt, int q, cx<R>* __restrict__ contrib, int* __restrict__ tmo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t sidx = (int64_t)blockIdx.x * PT_WARPS + warp;
-  if (sidx >= nt) return;
-  cx<R>* red = reinterpret_cast<cx<R>*>(smem_raw) + (int64_t)warp * 32 * 4;  // [lane][4]
-  const bool act = lane < 4 * q;
-  const int a = lane >> 2, m = (lane >> 1) & 1, h = lane & 1;
-  const int pairc = NCORR * 2 * q;
-  const int r0 = roff[sidx], npair = roff[sidx + 1] - r0;
-  cx<R> al = czero<R>(), be[3] = {czero<R>(), czero<R>(), czero<R>()};
-  int jj = 0, tt = 0;
-  for (int i = 0; i < npair; ++i) {  // warp-uniform
-    if ((i & 31) == 0) {
-      jj = i + lane < npair ? rpair[r0 + i + lane] : 0;
-      tt = i + lane < npair ? ptgt[jj] : 0;
-    }
-    const int64_t j = __shfl_sync(0xffffffffu, jj, i & 31);
-    const int64_t tg = __shfl_sync(0xffffffffu, tt, i & 31);
-    if (act) {
-      const cx<R>* dp = corr + j * pairc + a * 2 + m;
-      const cx<R>* rb = recb + ((tg * q + a) * 2 + m) * NREC + 10 * h;
-      cx<R> d[NCORR], r[10];
+  const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
+  if (t >= nt) return;  // whole warp
+  const int pairc = NCORR * 2 * q, slot = na_slot(q), wcx = na_warp_cx(q);
+  cx<R>* ring = reinterpret_cast<cx<R>*>(smem_raw) + (int64_t)warp * wcx;
+  cx<R>* rt = ring + NA_NSTG * NA_KP * slot;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<cx<R>*>(smem_raw) + PT_WARPS * wcx) + warp * NA_NSTG;
+  const int j0 = noff[t], j1 = noff[t + 1];
+  const int nst = (j1 - j0 + NA_KP - 1) / NA_KP;
+  if (nst == 0) return;
+  const unsigned pair_bytes = (unsigned)(pairc * sizeof(cx<R>));
+  auto issue = [&](int st) {
+    const int pj = j0 + st * NA_KP;
+    const int np = min(NA_KP, j1 - pj);
+    uint64_t* b = bars + st % NA_NSTG;
+    fence_proxy_async();
+    mbar_expect_tx(b, np * pair_bytes);
+    for (int k = 0; k < np; ++k)
+      bulk_copy(ring + ((st % NA_NSTG) * NA_KP + k) * slot, corr + (int64_t)(pj + k) * pairc, pair_bytes, b);
+  };
+  if (lane == 0) {
 #pragma unroll
-      for (int c = 0; c < NCORR; ++c) d[c] = dp[c * 2 * q];
-#pragma unroll
-      for (int c = 0; c < 10; ++c) r[c] = rb[c];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        cfma(al, r[c], d[1 + c]);
-        cfma(al, R(2) * r[4 + c], d[4 + c]);
-        cfma(al, r[7 + c], d[7 + c]);
-        be[c] -= r[c] * d[0];
-      }
-      cfma(al, R(2) * r[3], d[0]);
-      be[0] += r[9] * d[5] - r[8] * d[6];
-      be[1] += r[7] * d[6] - r[9] * d[4];
-      be[2] += r[8] * d[4] - r[7] * d[5];
-    }
+    for (int i = 0; i < NA_NSTG; ++i) mbar_init(bars + i, 1);
+    mbar_init_fence();
+    for (int st = 0; st < NA_NSTG - 1 && st < nst; ++st) issue(st);
   }
-  red[lane * 4 + 0] = al;
-  red[lane * 4 + 1] = be[0];
-  red[lane * 4 + 2] = be[1];
-  red[lane * 4 + 3] = be[2];
+  {
+    const cx<R>* rs = recb + t * q * 40;
+    for (int u = lane; u < 40 * q; u += 32) rt[u] = rs[u];
+  }
   __syncwarp();
-  if (lane < 12) {
-    const int set = lane >> 2, comp = lane & 3;
-    cx<R> acc = sdir[(sidx * 3 + set) * 4 + comp];
-    for (int pa = 0; pa < q; ++pa) {
-      if (set == 0) acc += red[((pa << 2) | 0) * 4 + comp];                  // J_e: (a, m=0, h=0)
-      else if (set == 1) acc += red[((pa << 2) | 2) * 4 + comp];             // J_i: (a, m=1, h=0)
-      else acc += red[((pa << 2) | 1) * 4 + comp] - red[((pa << 2) | 3) * 4 + comp];  // M: +exterior, -interior
+  const int k = lane >> 2, m = (lane >> 1) & 1, h = lane & 1;
+  const cx<R>* rl = rt + m * NREC + 10 * h;
+  int st = 0;
+  bool ok = true;
+  for (; st < nst; ++st) {
+    if (lane == 0 && st + NA_NSTG - 1 < nst) issue(st + NA_NSTG - 1);
+    ok = __all_sync(0xffffffffu, mbar_wait(bars + st % NA_NSTG, (st / NA_NSTG) & 1));
+    if (!ok) break;
+    const int j = j0 + st * NA_KP + k;
+    const cx<R>* dp = ring + ((st % NA_NSTG) * NA_KP + k) * slot + m;
+    cx<R> al = czero<R>(), be[3] = {czero<R>(), czero<R>(), czero<R>()};
+    if (j < j1) {
+      for (int a = 0; a < q; ++a) {
+        cx<R> r[10], d[NCORR];
+#pragma unroll
+        for (int c = 0; c < 10; c += 2) load_pair_smem(rl + a * 40 + c, r + c);
+#pragma unroll
+        for (int c = 0; c < NCORR; ++c) d[c] = dp[c * 2 * q + 2 * a];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cfma(al, r[c], d[1 + c]);
+          cfma(al, R(2) * r[4 + c], d[4 + c]);
+          cfma(al, r[7 + c], d[7 + c]);
+          be[c] -= r[c] * d[0];
+        }
+        cfma(al, R(2) * r[3], d[0]);
+        be[0] += r[9] * d[5] - r[8] * d[6];
+        be[1] += r[7] * d[6] - r[9] * d[4];
+        be[2] += r[8] * d[4] - r[7] * d[5];
+      }
     }
-    snear[(sidx * 3 + set) * 4 + comp] = acc;
+    // (exterior, M) - (interior, M): lanes h = 1 differ in bit 1 (medium)
+    cx<R> v[4] = {al, be[0], be[1], be[2]};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const cx<R> o = mk(__shfl_xor_sync(0xffffffffu, v[c].re, 2), __shfl_xor_sync(0xffffffffu, v[c].im, 2));
+      if (h) v[c] -= o;
+    }
+    if (j < j1 && (h == 0 || m == 0)) {
+      cx<R>* cj = contrib + (int64_t)j * 12 + (h ? 8 : 4 * m);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cj[c] = v[c];
+    }
+    __syncwarp();
+  }
+  if (!ok) {
+    for (int s2 = st; s2 < nst && s2 < st + NA_NSTG; ++s2) (void)mbar_wait(bars + s2 % NA_NSTG, (s2 / NA_NSTG) & 1);
+    if (lane == 0) atomicOr(tmo, 1);
   }
 }
 
-// T3: thread (covered grid point i, group g4 = 2 medium + h): the transposed
-// interpolation of the group's 10 record adjoints with the value weight W and
-// the derivative weights (Wx, Wy, Wz) of every entry:
-//   f0 += W r0 + Wz r8 - Wy r9,  f1 += W r1 - Wz r7 + Wx r9,
-//   f2 += W r2 + Wy r7 - Wx r8,  f3 += W r3 + Wx r4 + Wy r5 + Wz r6
-// into grid fields 4 g4 .. 4 g4 + 3 (field-major).
+// T2b: thread per (source triangle s, set, component): sdir plus the pair
+// contributions of the pairs whose source is s, in reverse-list order.
 template <typename R>
-__global__ void k_interp_adj(const cx<R>* __restrict__ recb, const int32_t* __restrict__ gpt,
-                             const int32_t* __restrict__ goff, const int32_t* __restrict__ gq,
-                             const R* __restrict__ gw, const R* __restrict__ gd, int64_t ngnz, int64_t ng,
-                             cx<R>* __restrict__ grids) {
+__global__ void k_near_adj_sum(const int32_t* __restrict__ roff, const int32_t* __restrict__ rpair,
+                               const cx<R>* __restrict__ contrib, const cx<R>* __restrict__ sdir, int64_t nt,
+                               cx<R>* __restrict__ snear) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t i = idx >> 2;
-  if (i >= ngnz) return;
-  const int g4 = (int)(idx & 3), m = g4 >> 1, h = g4 & 1;
-  cx<R> o[4] = {czero<R>(), czero<R>(), czero<R>(), czero<R>()};
-  const int e1 = goff[i + 1];
-  for (int e = goff[i]; e < e1; ++e) {
-    const int64_t Qi = gq[e];
-    const R W = gw[e], Wx = gd[3 * (int64_t)e], Wy = gd[3 * (int64_t)e + 1], Wz = gd[3 * (int64_t)e + 2];
-    const cx<R>* r = recb + (Qi * 2 + m) * NREC + 10 * h;
-    cx<R> rr[10];
+  if (idx >= nt * 12) return;
+  const int64_t sidx = idx / 12;
+  const int c = (int)(idx - sidx * 12);
+  cx<R> acc = sdir[idx];
+  for (int rp = roff[sidx]; rp < roff[sidx + 1]; ++rp) acc += contrib[(int64_t)rpair[rp] * 12 + c];
+  snear[idx] = acc;
+}
+
+// T3: one warp per covered grid point i.  Lane pr < 20 reads the 16-byte
+// portion pr of the 320-byte record-adjoint row of every entry of the point
+// (records 2 pr, 2 pr + 1 of the 40 = 2 media x 2 groups x 10; one coalesced
+// row per load instruction, IADJ_INFLIGHT rows in flight) and accumulates
+// each record against all four entry weights (value W, derivatives Wx, Wy,
+// Wz).  The transposed interpolation of one group (records r0..r9) is then a
+// fixed combination of those sums:
+//   f0 = W r0 + Wz r8 - Wy r9,  f1 = W r1 - Wz r7 + Wx r9,
+//   f2 = W r2 + Wy r7 - Wx r8,  f3 = W r3 + Wx r4 + Wy r5 + Wz r6,
+// formed by lanes 0..15 (group g4, field f) and written field-major.
+constexpr int IADJ_INFLIGHT = 4;
+template <typename R>
+__global__ void __launch_bounds__(256) k_interp_adj(const cx<R>* __restrict__ recb, const int32_t* __restrict__ gpt,
+                                                    const int32_t* __restrict__ goff, const int32_t* __restrict__ gq,
+                                                    const R* __restrict__ gw, const R* __restrict__ gd,
+                                                    int64_t ngnz, int64_t ng, cx<R>* __restrict__ grids) {
+  __shared__ cx<R> red[8][20][8];  // [warp in CTA][portion][record k * 4 + weight]
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const bool act = lane < 20 && i < ngnz;
+  cx<R> acc[8];
 #pragma unroll
-    for (int c = 0; c < 10; ++c) rr[c] = r[c];
-    axpy(o[0], W, rr[0]);
-    axpy(o[0], Wz, rr[8]);
-    axpy(o[0], -Wy, rr[9]);
-    axpy(o[1], W, rr[1]);
-    axpy(o[1], -Wz, rr[7]);
-    axpy(o[1], Wx, rr[9]);
-    axpy(o[2], W, rr[2]);
-    axpy(o[2], Wy, rr[7]);
-    axpy(o[2], -Wx, rr[8]);
-    axpy(o[3], W, rr[3]);
-    axpy(o[3], Wx, rr[4]);
-    axpy(o[3], Wy, rr[5]);
-    axpy(o[3], Wz, rr[6]);
+  for (int c = 0; c < 8; ++c) acc[c] = czero<R>();
+  if (act) {
+    const int e1 = goff[i + 1];
+    for (int e = goff[i]; e < e1; e += IADJ_INFLIGHT) {
+      int qe[IADJ_INFLIGHT];
+      R w[IADJ_INFLIGHT][4];
+#pragma unroll
+      for (int u = 0; u < IADJ_INFLIGHT; ++u) {
+        const int eu = e + u < e1 ? e + u : e;
+        const R on = e + u < e1 ? R(1) : R(0);
+        qe[u] = gq[eu];
+        w[u][0] = on * gw[eu];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[u][1 + c] = on * gd[3 * (int64_t)eu + c];
+      }
+      cx<R> v[IADJ_INFLIGHT][2];
+#pragma unroll
+      for (int u = 0; u < IADJ_INFLIGHT; ++u) load_pair(recb + (int64_t)qe[u] * (2 * NREC) + 2 * lane, v[u]);
+#pragma unroll
+      for (int u = 0; u < IADJ_INFLIGHT; ++u)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) axpy2(acc[k * 4 + c], w[u][c], v[u][k]);
+    }
   }
-  const int64_t gp = gpt[i];
+  if (lane < 20)
 #pragma unroll
-  for (int f = 0; f < 4; ++f) grids[(int64_t)(4 * g4 + f) * ng + gp] = o[f];
+    for (int c = 0; c < 8; ++c) red[wl][lane][c] = acc[c];
+  __syncwarp();
+  if (lane < 16 && i < ngnz) {
+    // record 10 h + r of group g4 = 2 m + h sits in portion 5 g4 + r / 2,
+    // slot (r & 1) * 4 + weight; weights 0 W, 1 Wx, 2 Wy, 3 Wz
+    const int g4 = lane >> 2, f = lane & 3;
+    const cx<R>(*rp)[8] = red[wl] + 5 * g4;
+#define RW(r, wt) rp[(r) >> 1][((r) & 1) * 4 + (wt)]
+    cx<R> o;
+    switch (f) {
+      case 0: o = RW(0, 0) + RW(8, 3) - RW(9, 2); break;
+      case 1: o = RW(1, 0) - RW(7, 3) + RW(9, 1); break;
+      case 2: o = RW(2, 0) + RW(7, 2) - RW(8, 1); break;
+      default: o = RW(3, 0) + RW(4, 1) + RW(5, 2) + RW(6, 3); break;
+    }
+#undef RW
+    grids[(int64_t)lane * ng + gpt[i]] = o;
+  }
 }
 
 // T5: one warp per triangle t; lane (point a, set): the transposed value
@@ -1058,14 +1174,16 @@ int apply_adjoint_one(scabem_op* op, const cx<R>* ybar, cx<R>* xbar, cudaStream_
   }
   const cx<R>* s_after_near = sdir;
   if (op->npairs > 0) {
-    const size_t sm = (size_t)PT_WARPS * 32 * 4 * sizeof(cx<R>);
-    k_near_adj<R><<<blocks, PT_WARPS * 32, sm, s>>>(pd.near, op->roff, op->rpair, op->ptgt, pd.recb, sdir, nt, q,
-                                                    snear);
+    const size_t sm = (size_t)PT_WARPS * na_warp_cx(q) * sizeof(cx<R>) + (size_t)PT_WARPS * NA_NSTG * sizeof(uint64_t);
+    if (int rc_ = set_max_smem(op->device, (const void*)k_near_adj_pairs<R>, (int)sm)) return rc_;
+    k_near_adj_pairs<R><<<blocks, PT_WARPS * 32, sm, s>>>(pd.near, op->noff, pd.recb, nt, q, pd.nadj, op->tmo_d);
+    CK(cudaGetLastError());
+    k_near_adj_sum<R><<<(int)cdiv(nt * 12, 256), 256, 0, s>>>(op->roff, op->rpair, pd.nadj, sdir, nt, snear);
     CK(cudaGetLastError());
     s_after_near = snear;
   }
   if (op->ngnz > 0) {
-    k_interp_adj<R><<<(int)cdiv(op->ngnz * 4, 256), 256, 0, s>>>(pd.recb, op->gpt, op->goff, op->gent,
+    k_interp_adj<R><<<(int)cdiv(op->ngnz * 32, 256), 256, 0, s>>>(pd.recb, op->gpt, op->goff, op->gent,
                                                                  gather_weights<R>(op), gather_dweights<R>(op),
                                                                  op->ngnz, ng, pd.src);
     CK(cudaGetLastError());

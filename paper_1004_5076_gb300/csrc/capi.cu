@@ -97,6 +97,7 @@ void free_prec(PrecData<R>& pd) {
   cudaFree(pd.grid);
   cudaFree(pd.val);
   cudaFree(pd.recb);
+  cudaFree(pd.nadj);
   cudaFree(pd.sbar);
   cudaFree(pd.xs);
   cudaFree(pd.ys);
@@ -635,7 +636,6 @@ void scabem_op_destroy(scabem_op_t op) {
   cudaFree(op->gdf);
   cudaFree(op->roff);
   cudaFree(op->rpair);
-  cudaFree(op->ptgt);
   cudaFree(op->xsrc);
   cudaFree(op->acoord);
   if (op->tmo_h) cudaFreeHost(op->tmo_h);

@@ -127,6 +127,7 @@ struct PrecData {
   cx<R>* stA = nullptr;   // 16 * P0 * n1 n2 (12 fields in the apply, 16 in the transposed apply)
   cx<R>* recb = nullptr;  // Q * 2 * NREC record adjoints (transposed apply)
   cx<R>* sbar = nullptr;  // 2 * nt * 12: summary adjoints (near + direct, total)
+  cx<R>* nadj = nullptr;  // npairs * 12: per-pair near contributions (transposed apply)
   cx<R>* stB = nullptr;   // 16 * P0 * n1 n2
   cx<R>* grid = nullptr;  // n0 n1 n2 * 16, point-major: [point][medium][J, M set][A or F (3), phi or psi]
   cx<R>* val = nullptr;   // nt * 3 * 4
@@ -187,11 +188,9 @@ struct scabem_op {
   int64_t npairs = 0;
   int32_t* noff = nullptr;  // nt + 1
   int32_t* nsrc = nullptr;  // npairs
-  // reverse list: pairs rpair[roff[s] .. roff[s+1]) have source triangle s;
-  // ptgt[j] = target triangle of pair j
+  // reverse list: pairs rpair[roff[s] .. roff[s+1]) have source triangle s
   int32_t* roff = nullptr;   // nt + 1
   int32_t* rpair = nullptr;  // npairs
-  int32_t* ptgt = nullptr;   // npairs
   // unknown -> up to 4 (triangle, local edge, set) uses, (code + 1) * sign,
   // code = (t * 3 + k) * 3 + set; 0 = unused (transposed current expansion)
   int32_t* xsrc = nullptr;   // N * 4

@@ -1014,6 +1014,9 @@ int setup_near(scabem_op* op, cudaStream_t s) {
       return SCABEM_E_NOMEM;
     }
   }
+  // per-pair buffer of the transposed near field
+  if (acc > 0 && op->f.built) CK(cudaMalloc(&op->f.nadj, sizeof(cx<float>) * acc * 12));
+  if (acc > 0 && op->d.built) CK(cudaMalloc(&op->d.nadj, sizeof(cx<double>) * acc * 12));
   const int64_t work = acc * op->q;
   if (work > 0) {
     k_near_corr<double><<<(int)cdiv(work, 128), 128, 0, s>>>(
@@ -1028,22 +1031,18 @@ int setup_near(scabem_op* op, cudaStream_t s) {
     op->gspatial[med] = nullptr;
   }
   // reverse list for the transposed near field: the pairs of each source
-  // triangle (ascending pair index) and the target of every pair
+  // triangle, ascending pair index
   if (acc > 0) {
-    std::vector<int32_t> hs(acc), rc(nt + 1, 0), rp(acc), pt(acc);
+    std::vector<int32_t> hs(acc), rc(nt + 1, 0), rp(acc);
     CK(cudaMemcpy(hs.data(), op->nsrc, sizeof(int32_t) * acc, cudaMemcpyDeviceToHost));
-    for (int64_t t = 0; t < nt; ++t)
-      for (int32_t j = ho[t]; j < ho[t + 1]; ++j) pt[j] = (int32_t)t;
     for (int64_t j = 0; j < acc; ++j) ++rc[hs[j] + 1];
     for (int64_t t = 0; t < nt; ++t) rc[t + 1] += rc[t];
     std::vector<int32_t> cur(rc.begin(), rc.end() - 1);
     for (int64_t j = 0; j < acc; ++j) rp[cur[hs[j]]++] = (int32_t)j;
     CK(cudaMalloc(&op->roff, sizeof(int32_t) * (nt + 1)));
     CK(cudaMalloc(&op->rpair, sizeof(int32_t) * acc));
-    CK(cudaMalloc(&op->ptgt, sizeof(int32_t) * acc));
     CK(cudaMemcpy(op->roff, rc.data(), sizeof(int32_t) * (nt + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->rpair, rp.data(), sizeof(int32_t) * acc, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(op->ptgt, pt.data(), sizeof(int32_t) * acc, cudaMemcpyHostToDevice));
   }
   return SCABEM_OK;
 }
