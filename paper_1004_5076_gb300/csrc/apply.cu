@@ -820,20 +820,22 @@ __global__ void __launch_bounds__(PT_WARPS * 32)
 // T2a: one warp per target triangle t over its own near pairs (one
 // contiguous run of records).  The pairs stream through a per-warp ring of
 // NA_NSTG stages of NA_KP pairs (one bulk copy per pair into a slot padded to
-// na_slot(q) complex values, so that the 16 (pair, medium) rows a warp load
-// touches fall in distinct banks; bounded waits).  The target's record
+// na_slot(q) complex values, so that the 16 (pair, point, medium) rows a warp
+// load touches fall in distinct banks; bounded waits).  The target's record
 // adjoints (q points x 2 media x 20) sit in shared memory.  Lane (pair k,
-// medium m, group h) forms, for pair k of the stage, the transpose of
-// near_part summed over the target's points a:
+// point half ah, medium m, group h) forms, for pair k of the stage, the
+// transpose of near_part summed over its points a = ah, ah + NA_AH, ...:
 //   a_bar = sum_a r . dP1 + 2 phi_r dP0 + 2 grad_r . dQ + curl_r . dC,
-//   beta_bar = sum_a -A_r dP0 - (the dQ x beta term transposed),
-// and the pair's 12 contributions are the per-set values J_e = (exterior,
-// J), J_i = (interior, J), M = (exterior, M) - (interior, M).
-constexpr int NA_KP = 8;
+//   beta_bar = sum_a -A_r dP0 - (the dQ x beta term transposed);
+// the point halves are summed by one xor shuffle, and the pair's 12
+// contributions are the per-set values J_e = (exterior, J), J_i = (interior,
+// J), M = (exterior, M) - (interior, M).
+constexpr int NA_AH = 2;  // lanes sharing one pair's points (1 or 2)
+constexpr int NA_KP = 8 / NA_AH;
 constexpr int NA_NSTG = 2;
 __host__ __device__ __forceinline__ int na_slot(int q) {
   const int pc = NCORR * 2 * q;
-  return pc + (((2 - pc) % 16) + 16) % 16;
+  return pc + (((2 * NA_AH - pc) % 16) + 16) % 16;
 }
 __host__ __device__ __forceinline__ int na_warp_cx(int q) { return NA_NSTG * NA_KP * na_slot(q) + 40 * q; }
 template <typename R>
@@ -872,7 +874,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, 4)
     for (int u = lane; u < 40 * q; u += 32) rt[u] = rs[u];
   }
   __syncwarp();
-  const int k = lane >> 2, m = (lane >> 1) & 1, h = lane & 1;
+  const int k = lane / (4 * NA_AH), ah = (lane >> 2) & (NA_AH - 1), m = (lane >> 1) & 1, h = lane & 1;
   const cx<R>* rl = rt + m * NREC + 10 * h;
   int st = 0;
   bool ok = true;
@@ -884,7 +886,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, 4)
     const cx<R>* dp = ring + ((st % NA_NSTG) * NA_KP + k) * slot + m;
     cx<R> al = czero<R>(), be[3] = {czero<R>(), czero<R>(), czero<R>()};
     if (j < j1) {
-      for (int a = 0; a < q; ++a) {
+      for (int a = ah; a < q; a += NA_AH) {
         cx<R> r[10], d[NCORR];
 #pragma unroll
         for (int c = 0; c < 10; c += 2) load_pair_smem(rl + a * 40 + c, r + c);
@@ -903,14 +905,18 @@ __global__ void __launch_bounds__(PT_WARPS * 32, 4)
         be[2] += r[8] * d[4] - r[7] * d[5];
       }
     }
-    // (exterior, M) - (interior, M): lanes h = 1 differ in bit 1 (medium)
     cx<R> v[4] = {al, be[0], be[1], be[2]};
+    if (NA_AH == 2)  // the two point halves (lane bit 2)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        v[c] += mk(__shfl_xor_sync(0xffffffffu, v[c].re, 4), __shfl_xor_sync(0xffffffffu, v[c].im, 4));
+    // (exterior, M) - (interior, M): lanes h = 1 differ in bit 1 (medium)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const cx<R> o = mk(__shfl_xor_sync(0xffffffffu, v[c].re, 2), __shfl_xor_sync(0xffffffffu, v[c].im, 2));
       if (h) v[c] -= o;
     }
-    if (j < j1 && (h == 0 || m == 0)) {
+    if (j < j1 && ah == 0 && (h == 0 || m == 0)) {
       cx<R>* cj = contrib + (int64_t)j * 12 + (h ? 8 : 4 * m);
 #pragma unroll
       for (int c = 0; c < 4; ++c) cj[c] = v[c];
