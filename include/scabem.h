@@ -182,6 +182,18 @@ int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sigma);
  * launches). */
 int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream);
 
+/* Self-test of the bounded device waits behind SCABEM_E_TIMEOUT.  One warp
+ * waits on an mbarrier that nothing ever completes, through the same wait
+ * routine and limit (about a second) as the near-field record streams, and
+ * reports the expiry through the operator's timeout flag as they do; the
+ * call synchronises `stream` and then reads and clears that flag.  Expected
+ * result: SCABEM_E_TIMEOUT, with the operator and the CUDA context still
+ * usable.  SCABEM_OK would mean that the wait did not report its expiry
+ * (a fault of the wait routine); SCABEM_E_ARG for a null operator;
+ * SCABEM_E_TIMEOUT is also
+ * returned (before launching) when an earlier launch had already expired. */
+int scabem_selftest_wait_limit(scabem_op_t op, void* stream);
+
 /* x = A^T y, the transpose (not the conjugate transpose) of the operator of
  * scabem_apply, for adjoint solves and gradients (reciprocity of the
  * Galerkin system).  The stages of scabem_apply run transposed in reverse

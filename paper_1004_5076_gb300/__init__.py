@@ -102,6 +102,7 @@ def lib():
     L.scabem_set_sigma.argtypes = [vp, C.POINTER(Sigma)]
     L.scabem_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_apply_adjoint.argtypes = [vp, vp, vp, i32, i64, i32, vp]
+    L.scabem_selftest_wait_limit.argtypes = [vp, vp]
     L.scabem_sigma_gradient.argtypes = [vp, vp, vp, C.POINTER(Source), i32, C.POINTER(Sigma), vp, vp]
     L.scabem_rhs.argtypes = [vp, C.POINTER(Source), i32, vp, i64, i32, vp]
     L.scabem_solve.argtypes = [vp, vp, vp, i32, i64, C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo)]
@@ -240,6 +241,11 @@ def scabem_apply_adjoint(op, y, x, nrhs=1, ld=None, prec=SCABEM_C128, stream=Non
     if ld is None:
         ld = y.shape[0]
     _check(lib().scabem_apply_adjoint(op, _ptr(y), _ptr(x), nrhs, ld, prec, _stream(stream)))
+
+
+def scabem_selftest_wait_limit(op, stream=None):
+    """Run the bounded-wait self-test; returns the status code (SCABEM_E_TIMEOUT expected)."""
+    return lib().scabem_selftest_wait_limit(op, _stream(stream))
 
 
 def make_source(kind, side=0, pos=(0, 0, 0), dir=(1, 0, 0), pol=(0, 1, 0), b=0.0):

@@ -525,6 +525,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   }
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier that no
+// arrival or copy ever completes, through the same mbar_wait as the record
+// rings; when the wait gives up it reports through *tmo exactly as they do.
+__global__ void k_wait_selftest(int* __restrict__ tmo) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar, 0));
+  if (!ok && threadIdx.x == 0) atomicOr(tmo, 1);
+}
+
 // K6-8: one warp per target triangle t, PT_WARPS triangles per CTA; warps
 // never wait on one another.
 //  Phase 1: lane (point a, medium, record group h), 4q lanes, interpolates
@@ -1237,6 +1251,13 @@ int sigma_sensitivity_op(scabem_op* op, const cx<double>* x, const cx<double>* l
                                                         op->ki, op->ze, op->zi, op->npairs > 0 ? 1 : 0, op->valrow,
                                                         yscr, op->tmo_d, lam, hs);
   CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
+int selftest_wait(scabem_op* op, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(op->tmo_d);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
   return SCABEM_OK;
 }
 

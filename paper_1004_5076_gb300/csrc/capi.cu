@@ -724,6 +724,16 @@ static int take_timeout(scabem_op* op) {
   return SCABEM_OK;
 }
 
+int scabem_selftest_wait_limit(scabem_op_t op, void* stream) {
+  if (!op) {
+    set_error("scabem_selftest_wait_limit: null operator");
+    return SCABEM_E_ARG;
+  }
+  if (int rc = take_timeout(op)) return rc;
+  if (int rc = selftest_wait(op, (cudaStream_t)stream)) return rc;
+  return take_timeout(op);
+}
+
 int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream) {
   if (!op || !x || !y || nrhs < 0 || ld < op->N) {
     set_error("scabem_apply: null argument, nrhs < 0 or ld < N");

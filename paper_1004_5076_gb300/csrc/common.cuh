@@ -232,6 +232,9 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // `bytes`, calling the runtime only the first time a larger size is needed
 // (the apply path then makes no attribute calls).
 int set_max_smem(int device, const void* kernel, int bytes);
+// One warp waits on an mbarrier that nothing completes, with the record
+// rings' wait limit, and reports the expiry through op->tmo_d (synchronous).
+int selftest_wait(scabem_op* op, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers
 // setup.cu

@@ -78,6 +78,20 @@ def plate_thin(padded=(32, 16, 8), p=2, q=3, r_near=0.3):
     return Case("plate_thin", m, (4.0, 1.0, 1.5, 1.0, 1.3), grid, q, r_near, sigma_scale=0.002, seed=13)
 
 
+def plate_p4_q7():
+    """plate_thin with p = 4 stencils (64 points) and the 7-point rule (28 lanes per triangle)."""
+    c = plate_thin(padded=(32, 16, 16), p=4, q=7, r_near=0.12)
+    c.name = "plate_p4_q7"
+    return c
+
+
+def plate_q1():
+    """plate_thin with p = 3 stencils and the 1-point rule (4 lanes per triangle)."""
+    c = plate_thin(p=3, q=1)
+    c.name = "plate_q1"
+    return c
+
+
 def guide_full(p=3, q=6, r_near=None):
     """The 12 um guide: 0.5 x 0.22 um core (eps 12.1) in eps 2.1, 4 um absorbers
     sigma0 (x/L)^3 at both ends, 19,420 triangles, FFT grid 512 x 64 x 64."""

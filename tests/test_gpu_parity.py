@@ -75,7 +75,7 @@ def oracle_apply(case, g, med, sig, x, key):
 
 
 CASES = [cases.sphere_mixed, cases.guide_small, cases.plate_thin, cases.guide_planes64, cases.guide_planes64_fft,
-         cases.sphere_direct]
+         cases.sphere_direct, cases.plate_p4_q7, cases.plate_q1]
 
 
 @pytest.mark.parametrize("mk", CASES, ids=lambda f: f.__name__)
@@ -100,6 +100,27 @@ def test_apply_complex64_matches_oracle(mk):
     rel = np.linalg.norm(y - y_or) / np.linalg.norm(y_or)
     assert rel < TOL32, rel
     assert np.max(np.abs(y - y_or)) <= TOL32 * np.max(np.abs(y_or))
+
+
+def test_apply_empty_batch_and_zero_input():
+    """nrhs = 0 touches nothing; x = 0 gives exactly 0 in both directions and precisions (every
+    stage is linear, and the row sums add exact zeros)."""
+    case = cases.plate_thin()
+    mh, op, g, med, sig = build(case)
+    N = g.N
+    y = torch.full((N,), complex(float("nan"), 0.0), dtype=torch.complex64, device="cuda")
+    x = torch.zeros(N, dtype=torch.complex64, device="cuda")
+    sc.scabem_apply(op, x, y, nrhs=0, ld=N, prec=sc.SCABEM_C64)
+    sc.scabem_apply_adjoint(op, x, y, nrhs=0, ld=N, prec=sc.SCABEM_C64)
+    torch.cuda.synchronize()
+    assert torch.isnan(y.real).all()
+    for prec, dt in ((sc.SCABEM_C64, torch.complex64), (sc.SCABEM_C128, torch.complex128)):
+        x = torch.zeros(N, dtype=dt, device="cuda")
+        for fn in (sc.scabem_apply, sc.scabem_apply_adjoint):
+            y = torch.full_like(x, 1.0 + 1.0j)
+            fn(op, x, y, prec=prec)
+            torch.cuda.synchronize()
+            assert int(torch.count_nonzero(y)) == 0, (fn.__name__, prec)
 
 
 def test_apply_batched_columns_and_host_buffers():
