@@ -185,6 +185,88 @@ def test_mie_catches_planted_jump_sign(monkeypatch):
     assert err > 0.10
 
 
+# ------------------------------------------------------------------ power balance (Sec. III-B)
+def _sphere_solution(region_R, sigma_S, planted=None, monkeypatch=None):
+    m = synth.icosphere(2, 1.0)
+    reg = np.ones(m.nt, int) if region_R else m.region
+    g = mesh.build(m.V, m.T, reg, q=6)
+    med = operator.Media(2.25, 1.0, 1.0, 1.0, 1.55)
+    sig = np.full((g.nt, g.q), sigma_S)
+    if planted is not None:
+        monkeypatch.setattr(operator, "test_rows", planted)
+    A = operator.assemble(g, med, sig)
+    b = excitation.rhs(g, med, sig, "e", "planewave", d=[0, 0, 1], e=[1, 0, 0])
+    return g, med, np.linalg.solve(A, b)
+
+
+def _power_terms(g, med, x, sigma_S):
+    """(extinguished, scattered, absorbed-in-the-sheet) power of the unit x-polarised plane wave
+    along +z, in units of |E0|^2 / eta0 (fields in the eta0 = 1 scaling).
+
+    Extinction by the forward-scattering amplitude (optical theorem; exp(+jwt), so the outgoing
+    field is F exp(-jkr)/r and P_ext = -(2 pi / (k Z)) Im(e . F(k^))); scattering by integrating
+    |F|^2 / (2 Z) over the sphere of directions (24 Gauss-Legendre nodes in cos(theta) x 48
+    uniform in phi); absorption as the Joule loss (1/2) sigma |E_tan|^2 of the sheet, with
+    E_tan = n x M, so |E_tan| = |M|, integrated by the mesh's quadrature rule."""
+    ke, ze = med.k[0], med.z[0]
+    f0 = post.far_field(g, x, ke, ze, np.array([[0.0, 0.0, 1.0]]))[0]
+    p_ext = -(2.0 * np.pi / (ke * ze)) * f0[0].imag
+    mu, wu = np.polynomial.legendre.leggauss(24)
+    nph = 48
+    ct, ph = np.meshgrid(mu, 2.0 * np.pi * np.arange(nph) / nph, indexing="ij")
+    st = np.sqrt(1.0 - ct**2)
+    rhat = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    wdir = np.repeat(wu, nph) * (2.0 * np.pi / nph)
+    F = post.far_field(g, x, ke, ze, rhat)
+    p_sca = np.sum(wdir * np.sum(np.abs(F) ** 2, 1)) / (2.0 * ze)
+    _, _, Ms = operator.current_sets(g, x[:, None])
+    M, _ = post._point_currents(g, Ms)
+    p_abs = 0.5 * sigma_S * ETA0 * np.sum(g.qw * np.sum(np.abs(M[..., 0]) ** 2, -1))
+    return p_ext, p_sca, p_abs
+
+
+def test_power_balance_lossless_and_absorbing_sheet():
+    """Poynting's theorem for the conductive surface (Sec. III-B): the power taken from the
+    incident wave minus the scattered power equals the Joule loss of the sheet.  A lossless
+    dielectric sphere absorbs nothing (P_ext = P_sca, the optical theorem with this time
+    convention); an all-absorber sphere with sigma = 0.2 / eta0 S absorbs exactly the sheet loss,
+    to the discretisation error of the 320-triangle mesh (the phase of the forward amplitude, which
+    the Mie magnitude pins do not see, enters through P_ext)."""
+    g, med, x = _sphere_solution(False, 0.0)
+    pe, ps, pa = _power_terms(g, med, x, 0.0)
+    assert pa == 0.0 and abs(pe - ps) < 1e-3 * pe, (pe, ps)
+    s = 0.2 / ETA0
+    g, med, x = _sphere_solution(True, s)
+    pe, ps, pa = _power_terms(g, med, x, s)
+    assert pa > 0.05 * pe, (pe, ps, pa)  # a real absorber, not a vanishing test
+    assert abs(pe - ps - pa) < 5e-3 * pe, (pe, ps, pa)
+
+
+def test_power_balance_catches_planted_mistakes(monkeypatch):
+    """Planted mistakes in the sigma-weighted rows (conductivity with the wrong sign, or the
+    n x M / 2 side-limit term with the wrong sign) break the balance by far more than the
+    discretisation error (< 1% of P_ext for the correct rows at sigma = 1 / eta0 S)."""
+    orig = operator.test_rows
+    s = 1.0 / ETA0
+
+    def wrong_sign(g, tris, fe, fi, Js, Ml, sig):
+        return orig(g, tris, fe, fi, Js, Ml, -sig)
+
+    def wrong_jump(g, tris, fe, fi, Js, Ml, sig):
+        val = orig(g, tris, fe, fi, Js, Ml, sig)
+        fz = {k: np.zeros_like(v) for k, v in fe.items()}
+        return val - 2.0 * orig(g, tris, fz, fz, np.zeros_like(Js), Ml, sig)
+
+    for plant in (wrong_sign, wrong_jump):
+        g, med, x = _sphere_solution(True, s, plant, monkeypatch)
+        pe, ps, pa = _power_terms(g, med, x, s)
+        assert abs(pe - ps - pa) > 0.3 * pe, (plant.__name__, pe, ps, pa)
+    monkeypatch.setattr(operator, "test_rows", orig)
+    g, med, x = _sphere_solution(True, s)
+    pe, ps, pa = _power_terms(g, med, x, s)
+    assert abs(pe - ps - pa) < 2e-2 * pe, (pe, ps, pa)
+
+
 def test_sigma_zero_absorber_rows_give_opposite_currents():
     """With sigma = 0, Eq. 14 reduces to <X, J_e + J_i> = 0, so J_e^R = -J_i^R exactly."""
     m = synth.icosphere(1, 1.0)
