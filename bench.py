@@ -43,15 +43,19 @@ METRIC = "operator matvecs/sec and GMRES solve time at N unknowns (%HBM roofline
 UNIT = "matvec/s"
 
 
-def measured_traffic(stage):
+def measured_traffic(stage, r_near_h=2.05):
     """DRAM bytes per launch of a stage's kernel from the committed ncu
-    capture, or None when there is none or the kernel source changed since."""
+    capture, or None when there is none, it was taken on another near radius,
+    or the kernel source changed since."""
     import hashlib
 
     p = os.path.join(ROOT, "profiles", "dram_traffic_guide_12um.json")
     if not os.path.exists(p):
         return None
-    k = json.load(open(p)).get("kernels", {}).get(stage)
+    d = json.load(open(p))
+    if abs(float(d.get("r_near_h", 2.05)) - r_near_h) > 1e-9:
+        return None
+    k = d.get("kernels", {}).get(stage)
     if not k:
         return None
     src = os.path.join(ROOT, k["source"])
@@ -70,8 +74,10 @@ def peaks():
 
 # ------------------------------------------------------------------ CPU oracle baseline
 def oracle_rate(case, seconds: float, max_tris: int | None = None):
-    """Time the oracle's direct matvec (O1) on a bounded sample of target
-    triangles and extrapolate to a full matvec.  Returns (matvec/s, sample text, threads)."""
+    """Time the oracle's direct matvec (O1) on a bounded sample of edges (both
+    triangles of each, so that their rows are complete) and extrapolate to a
+    full matvec.  Returns (matvec/s, sample text, threads, seconds, rows) with
+    rows = (x, row indices, O1 values at those rows) for the accuracy check."""
     from oracle import mesh, operator
 
     g = mesh.build(case.mesh.V, case.mesh.T, case.mesh.region, q=case.q)
@@ -81,21 +87,28 @@ def oracle_rate(case, seconds: float, max_tris: int | None = None):
     med = operator.Media(*case.media)
     x = cases.synth.complex_normal(g.N, seed=1)
     rng = np.random.default_rng(0)
-    order = rng.permutation(g.nt)
-    done, t0 = 0, time.perf_counter()
-    chunk = 2
+    order = rng.permutation(g.ne)
+    row_of = mesh.row_index(g)
+    done, ntri, t0 = 0, 0, time.perf_counter()
     threads = 1  # BLAS pools are pinned to one thread at start-up (see top of file)
+    rows, vals = [], []
     while True:
-        tris = order[done : done + chunk]
-        operator.matvec(g, med, x, sig, chunk=chunk, tris=tris)
-        done += len(tris)
+        e = order[done]
+        tris = g.edge_t[e]
+        y = operator.matvec(g, med, x, sig, chunk=2, tris=tris)
+        r = row_of[e][row_of[e] >= 0]
+        rows.append(r)
+        vals.append(y[r])
+        done += 1
+        ntri += len(tris)
         el = time.perf_counter() - t0
-        if el >= seconds or done >= g.nt or (max_tris and done >= max_tris):
+        if el >= seconds or done >= g.ne or (max_tris and ntri >= max_tris):
             break
-    per_tri = el / done
+    per_tri = el / ntri
     rate = 1.0 / (per_tri * g.nt)
-    sample = f"O1 direct matvec rows of {done} random target triangles of {g.nt} ({el:.1f} s), extrapolated"
-    return rate, sample, threads, el
+    sample = (f"O1 direct matvec rows of {done} random edges ({ntri} target triangles of {g.nt}, {el:.1f} s), "
+              "extrapolated")
+    return rate, sample, threads, el, (x, np.concatenate(rows), np.concatenate(vals))
 
 
 # ------------------------------------------------------------------ clocks
@@ -216,9 +229,11 @@ def run_gpu(args):
     import cases
 
     case = cases.guide_full()
+    case.r_near = args.near_radius_h * case.grid.h
     cpu = None
+    o1_rows = None
     if rank == 0 and not args.no_cpu:
-        rate, sample, threads, el = oracle_rate(case, args.cpu_seconds)
+        rate, sample, threads, el, o1_rows = oracle_rate(case, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
     import torch
 
@@ -249,6 +264,23 @@ def run_gpu(args):
                                                                                       generator=gen))
         return (z / math.sqrt(2)).to(dtype).contiguous()
 
+    # the GPU operator against the oracle's dense operator (O1) on complete
+    # sampled rows: the discretisation error of the grid method at (p, r_near)
+    accuracy = None
+    if o1_rows is not None:
+        xo, ro, vo = o1_rows
+        accuracy = {"rows": int(len(ro)), "reference": "oracle O1 (dense operator, direct matvec), same x",
+                    "meaning": "grid-method (pFFT) discretisation error at this stencil order and near radius"}
+        for name, prec, dt in (("c64", sc.SCABEM_C64, torch.complex64), ("c128", sc.SCABEM_C128, torch.complex128)):
+            if name == "c128" and args.no_extras:
+                continue
+            xd = torch.as_tensor(xo).to(dt).cuda().contiguous()
+            yd = torch.empty_like(xd)
+            sc.scabem_apply(op, xd, yd, prec=prec, stream=stream)
+            torch.cuda.synchronize()
+            d = yd.cpu().numpy().astype(np.complex128)[ro] - vo
+            accuracy["rel_l2_" + name] = float(np.linalg.norm(d) / np.linalg.norm(vo))
+            accuracy["max_rel_" + name] = float(np.max(np.abs(d)) / np.max(np.abs(vo)))
     x = rand_x((N,), torch.complex64)
     y = torch.empty_like(x)
     for _ in range(args.warmup):
@@ -354,7 +386,8 @@ def run_gpu(args):
     if dom in bmodel:
         ach = bmodel[dom] / (per[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": measured_traffic(dom), "peak_source": src_peak, "algorithmic_bytes": bmodel[dom]}
+                "traffic": measured_traffic(dom, args.near_radius_h), "peak_source": src_peak,
+                "algorithmic_bytes": bmodel[dom]}
     t_mv = ms_max / args.steps / 1e3
     b_pruned = sum(bmodel.values())
     b_full = survey_model_bytes(info, case, N, 8)
@@ -372,7 +405,8 @@ def run_gpu(args):
             "config": {"workload": "guide_12um: 0.5x0.22 um eps 12.1 core in eps 2.1, 12 um, 4 um sigma0 (x/L)^3 "
                                    "absorbers at both ends, lambda 1.55 um",
                        "triangles": int(m.nt), "unknowns": int(N), "fft_grid": "512x64x64", "stencil_p": case.grid.p,
-                       "q": case.q, "r_near_um": case.r_near, "near_pairs": info["near_pairs"],
+                       "q": case.q, "r_near_um": case.r_near, "r_near_h": args.near_radius_h,
+                       "near_pairs": info["near_pairs"],
                        "covered_grid_points": ginfo["covered_points"], "active_columns": ginfo["active_columns"],
                        "l2": "working set per step > L2 (near data %.0f MB)" % (info["near_bytes_c64"] / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": t_setup},
@@ -383,6 +417,7 @@ def run_gpu(args):
             "roofline": roof,
             "matvec_roofline": mv_roof,
             "cpu_baseline": cpu,
+            "accuracy_vs_dense": accuracy,
             "clocks": clocks,
         }
         if extras:
@@ -403,11 +438,12 @@ def run_reference(args):
     import cases
 
     case = cases.guide_full()
+    case.r_near = args.near_radius_h * case.grid.h
     per_step = []
     sample = None
     threads = 1
     for i in range(args.warmup + args.steps):
-        rate, sample, threads, el = oracle_rate(case, args.ref_seconds)
+        rate, sample, threads, el, _ = oracle_rate(case, args.ref_seconds)
         if i >= args.warmup:
             per_step.append(rate)
     value = float(np.mean(per_step))
@@ -428,7 +464,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--near-radius-h", type=float, default=2.05,
+                    help="near-field radius in grid steps (2.05: the headline configuration)")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the c128, batched and solve measurements")
