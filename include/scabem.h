@@ -322,6 +322,31 @@ typedef struct {
 int scabem_reflection(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_probe* probe,
                       const scabem_source* inc, double* out, void* stream);
 
+/* Decay-rate fit (Sec. III: the field inside a guide with uniform surface
+ * conductivity decays along the axis).  Least squares for
+ *   E(t) = a exp(-g tau) + c exp(g tau),  g = alpha + j beta,
+ *   tau = t - (t_first + t_last) / 2,
+ * both waves decaying along their direction of travel, over the uniform grid
+ * of nalpha x nbeta candidates (alpha in [alpha_lo, alpha_hi] [1/um], beta in
+ * [beta_lo, beta_hi] [rad/um], end points included; the low value alone when
+ * the count is 1).  For each candidate the amplitudes solve the 2 x 2 normal
+ * equations; the candidate with the smallest residual wins (ties: the first
+ * in alpha-major order).
+ *   scabem_decay_fit: given samples, host arrays t (npts, [um]) and E (npts
+ *   complex128, interleaved); npts >= 4, nalpha * nbeta <= 2^24;
+ *   SCABEM_E_NONFINITE for a non-finite sample, SCABEM_E_DEVICE without a
+ *   GB300.
+ *   scabem_decay_rate: the samples are the total interior field component
+ *   `comp` on the probe line of scabem_reflection (its beta range is used),
+ *   for each right-hand side; needs the complex128 operator.
+ * out (host, 6 per fit): {alpha, beta, relative residual, Re(c/a), Im(c/a),
+ * |a|}, with a and c referred to the midpoint of the samples. */
+int scabem_decay_fit(const double* t, const double* E, int32_t npts, double alpha_lo, double alpha_hi,
+                     int32_t nalpha, double beta_lo, double beta_hi, int32_t nbeta, double* out, void* stream);
+int scabem_decay_rate(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_probe* probe,
+                      double alpha_lo, double alpha_hi, int32_t nalpha, const scabem_source* inc, double* out,
+                      void* stream);
+
 /* Stage timing of scabem_apply (instrumentation, not part of the paper's
  * method).  While enabled, every apply records CUDA events at its stage
  * boundaries on its own stream, for at most max_applies applies (events are

@@ -8,6 +8,11 @@
 * Axis fit (reading of the paper's SWR measure): least squares for
   E(x_k) = a exp(-j beta x_k) + c exp(+j beta x_k); r = c/a, with beta fixed
   or scanned to minimise the residual.
+* Decay-rate fit (Sec. III): the field inside a guide with uniform surface
+  conductivity decays along the axis; least squares for
+  E(t) = a exp(-g tau) + c exp(g tau), g = alpha + j beta, tau = t - tm (tm the
+  midpoint of the samples), both waves decaying along their direction of
+  travel, over a grid of (alpha, beta) candidates.
 * Far field of the exterior currents, exp(+jwt):
   E ~ F exp(-jkr)/r,  F = -jk/(4 pi) [z (J^ - r (r.J^)) - r x M^],
   J^ = int J exp(jk r.r') dS'.
@@ -94,6 +99,28 @@ def fit_reflection(xs, E, beta=None, betas=None):
     else:
         coef, res = solve(beta)
     return coef[1] / coef[0], beta, res
+
+
+def fit_decay(ts, E, alphas, betas):
+    """Least-squares fit of E(t) = a exp(-g tau) + c exp(g tau), g = alpha + j beta,
+    tau = t - (t_first + t_last)/2, scanning every (alpha, beta) of the two 1-D grids.
+
+    Returns (alpha, beta, relative residual, a, c) of the candidate with the smallest
+    residual (the first in alpha-major order on a tie)."""
+    ts = np.asarray(ts, dtype=np.float64)
+    E = np.asarray(E, dtype=np.complex128)
+    tau = ts - 0.5 * (ts[0] + ts[-1])
+    best = None
+    for al in np.atleast_1d(alphas):
+        for bt in np.atleast_1d(betas):
+            g = al + 1j * bt
+            Mx = np.stack([np.exp(-g * tau), np.exp(g * tau)], axis=1)
+            coef, *_ = np.linalg.lstsq(Mx, E, rcond=None)
+            res = np.linalg.norm(Mx @ coef - E)
+            if best is None or res < best[2]:
+                best = (float(al), float(bt), res, coef[0], coef[1])
+    al, bt, res, a, c = best
+    return al, bt, res / np.linalg.norm(E), a, c
 
 
 def far_field(g: Geometry, x, k, z, rhat):

@@ -103,6 +103,9 @@ def lib():
     L.scabem_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_apply_adjoint.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_selftest_wait_limit.argtypes = [vp, vp]
+    L.scabem_decay_fit.argtypes = [vp, vp, i32, C.c_double, C.c_double, i32, C.c_double, C.c_double, i32, vp, vp]
+    L.scabem_decay_rate.argtypes = [vp, vp, i32, i64, C.POINTER(Probe), C.c_double, C.c_double, i32,
+                                    C.POINTER(Source), vp, vp]
     L.scabem_sigma_gradient.argtypes = [vp, vp, vp, C.POINTER(Source), i32, C.POINTER(Sigma), vp, vp]
     L.scabem_rhs.argtypes = [vp, C.POINTER(Source), i32, vp, i64, i32, vp]
     L.scabem_solve.argtypes = [vp, vp, vp, i32, i64, C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo)]
@@ -335,6 +338,29 @@ def scabem_reflection(op, x, axis, comp, p0, t0, t1, npts, beta_lo, beta_hi, nbe
     out = np.zeros((nrhs, 6), np.float64)
     _check(lib().scabem_reflection(op, _ptr(x), nrhs, ld, C.byref(pr), C.byref(inc) if inc else None, _ptr(out),
                                    _stream(stream)))
+    return out
+
+
+def scabem_decay_fit(t, E, alpha_lo, alpha_hi, nalpha, beta_lo, beta_hi, nbeta, stream=None):
+    """Decay-rate fit of samples E(t) (host arrays); returns
+    {alpha, beta, relative residual, Re(c/a), Im(c/a), |a|}."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.complex128)
+    out = np.zeros(6, np.float64)
+    _check(lib().scabem_decay_fit(t.ctypes.data, E.ctypes.data, len(t), alpha_lo, alpha_hi, nalpha, beta_lo,
+                                  beta_hi, nbeta, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def scabem_decay_rate(op, x, axis, comp, p0, t0, t1, npts, alpha_lo, alpha_hi, nalpha, beta_lo, beta_hi, nbeta,
+                      inc=None, nrhs=1, ld=None, stream=None):
+    """Decay-rate fit of the interior field component on a probe line, per right-hand side."""
+    if ld is None:
+        ld = x.shape[0]
+    pr = Probe(axis, comp, (C.c_double * 3)(*p0), t0, t1, npts, beta_lo, beta_hi, nbeta)
+    out = np.zeros((nrhs, 6), np.float64)
+    _check(lib().scabem_decay_rate(op, _ptr(x), nrhs, ld, C.byref(pr), alpha_lo, alpha_hi, nalpha,
+                                   C.byref(inc) if inc else None, _ptr(out), _stream(stream)))
     return out
 
 

@@ -905,6 +905,50 @@ int scabem_fields(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const
   return rc;
 }
 
+static bool decay_grid_ok(double alo, double ahi, int32_t na, double blo, double bhi, int32_t nb) {
+  return na >= 1 && nb >= 1 && (int64_t)na * nb <= (1 << 24) && std::isfinite(alo) && std::isfinite(ahi) &&
+         std::isfinite(blo) && std::isfinite(bhi);
+}
+
+int scabem_decay_fit(const double* t, const double* E, int32_t npts, double alpha_lo, double alpha_hi,
+                     int32_t nalpha, double beta_lo, double beta_hi, int32_t nbeta, double* out, void* stream) {
+  if (!t || !E || !out || npts < 4 || !decay_grid_ok(alpha_lo, alpha_hi, nalpha, beta_lo, beta_hi, nbeta)) {
+    set_error("scabem_decay_fit: bad argument (npts >= 4, nalpha, nbeta >= 1, nalpha * nbeta <= 2^24, finite ranges)");
+    return SCABEM_E_ARG;
+  }
+  for (int i = 0; i < npts; ++i)
+    if (!std::isfinite(t[i]) || !std::isfinite(E[2 * i]) || !std::isfinite(E[2 * i + 1])) {
+      set_error("scabem_decay_fit: non-finite sample");
+      return SCABEM_E_NONFINITE;
+    }
+  if (int rc = check_device()) return rc;
+  return decay_fit_impl(t, E, npts, alpha_lo, alpha_hi, nalpha, beta_lo, beta_hi, nbeta, out, (cudaStream_t)stream);
+}
+
+int scabem_decay_rate(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_probe* pr,
+                      double alpha_lo, double alpha_hi, int32_t nalpha, const scabem_source* inc, double* out,
+                      void* stream) {
+  if (!op || !x || !pr || !out || pr->npts < 4 || pr->axis < 0 || pr->axis > 2 || pr->comp < 0 || pr->comp > 2 ||
+      nrhs < 0 || ld < op->N || !decay_grid_ok(alpha_lo, alpha_hi, nalpha, pr->beta_lo, pr->beta_hi, pr->nbeta)) {
+    set_error("scabem_decay_rate: bad argument (npts >= 4, axis/comp in 0..2, nalpha, nbeta >= 1, "
+              "nalpha * nbeta <= 2^24)");
+    return SCABEM_E_ARG;
+  }
+  if (!op->d.built) {
+    set_error("scabem_decay_rate needs the complex128 operator");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (is_device_ptr(x)) return decay_rate_impl(op, x, nrhs, ld, pr, alpha_lo, alpha_hi, nalpha, inc, out, s);
+  void* dx = nullptr;
+  const size_t bytes = sizeof(cx<double>) * ld * nrhs;
+  CK(cudaMalloc(&dx, bytes));
+  CK(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, s));
+  int rc = decay_rate_impl(op, dx, nrhs, ld, pr, alpha_lo, alpha_hi, nalpha, inc, out, s);
+  cudaFree(dx);
+  return rc;
+}
+
 int scabem_reflection(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_probe* pr,
                       const scabem_source* inc, double* out, void* stream) {
   if (!op || !x || !pr || !out || pr->npts < 4 || pr->nbeta < 1 || pr->axis < 0 || pr->axis > 2 || pr->comp < 0 ||

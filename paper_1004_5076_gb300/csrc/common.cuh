@@ -277,3 +277,7 @@ int fields_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double
                 const scabem_source* inc, double* E, cudaStream_t s);
 int reflection_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_probe* pr,
                     const scabem_source* inc, double* out, cudaStream_t s);
+int decay_fit_impl(const double* t, const double* E, int npts, double alo, double ahi, int na, double blo, double bhi,
+                   int nb, double* out, cudaStream_t s);
+int decay_rate_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_probe* pr, double alo,
+                    double ahi, int na, const scabem_source* inc, double* out, cudaStream_t s);

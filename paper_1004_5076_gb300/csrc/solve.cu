@@ -756,6 +756,95 @@ __global__ void k_fit(const cd* __restrict__ E, const double* __restrict__ tt, i
   }
 }
 
+// Decay-rate fit (Sec. III): least squares for E(t) = a exp(-g tau) +
+// c exp(g tau), g = alpha + j beta, tau = t - tm with tm the midpoint of the
+// samples (both waves decay along their direction of travel).  With
+// phi1 = exp(-g tau), phi2 = exp(g tau) the normal equations are
+//   [g11 g12; conj(g12) g22] [a; c] = [r1; r2],
+//   g11 = sum exp(-2 alpha tau), g22 = sum exp(2 alpha tau),
+//   g12 = sum exp(2 j beta tau), r1 = sum conj(phi1) E, r2 = sum conj(phi2) E.
+// One block scans the nalpha x nbeta candidates (alpha-major), each with its
+// explicit residual; the smallest wins, ties to the lowest index.
+__device__ void decay_amplitudes(const cd* __restrict__ E, const double* __restrict__ tt, int npts, double tm,
+                                 double al, double be, cd& a, cd& c) {
+  double g11 = 0.0, g22 = 0.0;
+  cd g12 = mk(0.0, 0.0), r1 = g12, r2 = g12;
+  for (int i = 0; i < npts; ++i) {
+    const double tau = tt[i] - tm;
+    const double em = exp(-al * tau), ep = exp(al * tau);
+    double sn, cs;
+    sincos(be * tau, &sn, &cs);
+    g11 += em * em;
+    g22 += ep * ep;
+    g12 += mk(cs * cs - sn * sn, 2.0 * sn * cs);
+    r1 += mk(em * cs, em * sn) * E[i];   // conj(phi1) = exp(-alpha tau) exp(+j beta tau)
+    r2 += mk(ep * cs, -ep * sn) * E[i];  // conj(phi2) = exp(alpha tau) exp(-j beta tau)
+  }
+  const double det = g11 * g22 - (g12.re * g12.re + g12.im * g12.im);
+  a = (1.0 / det) * (g22 * r1 - g12 * r2);
+  c = (1.0 / det) * (g11 * r2 - conj(g12) * r1);
+}
+__device__ double decay_residual(const cd* __restrict__ E, const double* __restrict__ tt, int npts, double tm,
+                                 double al, double be, cd a, cd c) {
+  double res = 0.0;
+  for (int i = 0; i < npts; ++i) {
+    const double tau = tt[i] - tm;
+    const double em = exp(-al * tau), ep = exp(al * tau);
+    double sn, cs;
+    sincos(be * tau, &sn, &cs);
+    const cd f = a * mk(em * cs, -em * sn) + c * mk(ep * cs, ep * sn) - E[i];
+    res += f.re * f.re + f.im * f.im;
+  }
+  return res;
+}
+__global__ void k_fit_decay(const cd* __restrict__ E, const double* __restrict__ tt, int npts, double alo,
+                            double ahi, int na, double blo, double bhi, int nb, double* __restrict__ out) {
+  __shared__ double best_res[256];
+  __shared__ int best_i[256];
+  const double tm = 0.5 * (tt[0] + tt[npts - 1]);
+  double enorm = 0.0;
+  for (int i = 0; i < npts; ++i) enorm += E[i].re * E[i].re + E[i].im * E[i].im;
+  const int ncand = na * nb;
+  double bres = 1e300;
+  int bi = -1;
+  for (int ic = threadIdx.x; ic < ncand; ic += blockDim.x) {
+    const int ia = ic / nb, ib = ic - (ic / nb) * nb;
+    const double al = na > 1 ? alo + (ahi - alo) * ia / (na - 1) : alo;
+    const double be = nb > 1 ? blo + (bhi - blo) * ib / (nb - 1) : blo;
+    cd a, c;
+    decay_amplitudes(E, tt, npts, tm, al, be, a, c);
+    const double res = decay_residual(E, tt, npts, tm, al, be, a, c);
+    if (res < bres) {
+      bres = res;
+      bi = ic;
+    }
+  }
+  best_res[threadIdx.x] = bres;
+  best_i[threadIdx.x] = bi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = -1;
+    double r = 1e300;
+    for (int i = 0; i < blockDim.x; ++i)
+      if (best_i[i] >= 0 && (best_res[i] < r || (best_res[i] == r && best_i[i] < b))) {
+        r = best_res[i];
+        b = best_i[i];
+      }
+    const int ia = b / nb, ib = b - (b / nb) * nb;
+    const double al = na > 1 ? alo + (ahi - alo) * ia / (na - 1) : alo;
+    const double be = nb > 1 ? blo + (bhi - blo) * ib / (nb - 1) : blo;
+    cd a, c;
+    decay_amplitudes(E, tt, npts, tm, al, be, a, c);
+    const cd rr = cdivd(c, a);
+    out[0] = al;
+    out[1] = be;
+    out[2] = sqrt(r / enorm);
+    out[3] = rr.re;
+    out[4] = rr.im;
+    out[5] = sqrt(a.re * a.re + a.im * a.im);
+  }
+}
+
 }  // namespace
 
 int rhs_impl(scabem_op* op, const scabem_source* src, int nsrc, void* b, int64_t ld, int prec, cudaStream_t s) {
@@ -960,6 +1049,64 @@ int reflection_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const sc
     CK(cudaMemcpy2DAsync(dc, sizeof(cd), (const char*)dE + sizeof(cd) * pr->comp, 3 * sizeof(cd), sizeof(cd), npts,
                          cudaMemcpyDeviceToDevice, s));
     k_fit<<<1, 256, 0, s>>>(dc, dtt, npts, pr->beta_lo, pr->beta_hi, pr->nbeta, dout);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out + 6 * col, dout, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dpts);
+  cudaFree(dtt);
+  cudaFree(dE);
+  cudaFree(dc);
+  cudaFree(dout);
+  return SCABEM_OK;
+}
+
+// Decay-rate fit of given samples (host t, host complex128 E).
+int decay_fit_impl(const double* t, const double* E, int npts, double alo, double ahi, int na, double blo, double bhi,
+                   int nb, double* out, cudaStream_t s) {
+  double *dt = nullptr, *dout = nullptr;
+  cd* dE = nullptr;
+  CK(cudaMalloc(&dt, sizeof(double) * npts));
+  CK(cudaMalloc(&dE, sizeof(cd) * npts));
+  CK(cudaMalloc(&dout, sizeof(double) * 6));
+  CK(cudaMemcpyAsync(dt, t, sizeof(double) * npts, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dE, E, sizeof(cd) * npts, cudaMemcpyHostToDevice, s));
+  k_fit_decay<<<1, 256, 0, s>>>(dE, dt, npts, alo, ahi, na, blo, bhi, nb, dout);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, dout, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dt);
+  cudaFree(dE);
+  cudaFree(dout);
+  return SCABEM_OK;
+}
+
+// Decay rate along a probe line: the total interior field component there
+// (as for the reflection), then the decay-rate fit.
+int decay_rate_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_probe* pr, double alo,
+                    double ahi, int na, const scabem_source* inc, double* out, cudaStream_t s) {
+  const int npts = pr->npts;
+  std::vector<double> pts(3 * npts), tt(npts);
+  for (int i = 0; i < npts; ++i) {
+    const double t = npts > 1 ? pr->t0 + (pr->t1 - pr->t0) * i / (npts - 1) : pr->t0;
+    tt[i] = t;
+    for (int c = 0; c < 3; ++c) pts[3 * i + c] = pr->p0[c] + (c == pr->axis ? t : 0.0);
+  }
+  double *dpts = nullptr, *dtt = nullptr, *dout = nullptr;
+  cd *dE = nullptr, *dc = nullptr;
+  CK(cudaMalloc(&dpts, sizeof(double) * 3 * npts));
+  CK(cudaMalloc(&dtt, sizeof(double) * npts));
+  CK(cudaMalloc(&dE, sizeof(cd) * 3 * npts));
+  CK(cudaMalloc(&dc, sizeof(cd) * npts));
+  CK(cudaMalloc(&dout, sizeof(double) * 6));
+  CK(cudaMemcpyAsync(dpts, pts.data(), sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dtt, tt.data(), sizeof(double) * npts, cudaMemcpyHostToDevice, s));
+  for (int col = 0; col < nrhs; ++col) {
+    int rc = fields_dev(op, (const cd*)x + (int64_t)col * ld, dpts, npts, inc, dE, s);
+    if (rc) return rc;
+    CK(cudaMemcpy2DAsync(dc, sizeof(cd), (const char*)dE + sizeof(cd) * pr->comp, 3 * sizeof(cd), sizeof(cd), npts,
+                         cudaMemcpyDeviceToDevice, s));
+    k_fit_decay<<<1, 256, 0, s>>>(dc, dtt, npts, alo, ahi, na, pr->beta_lo, pr->beta_hi, pr->nbeta, dout);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out + 6 * col, dout, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
   }

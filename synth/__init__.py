@@ -201,6 +201,20 @@ def complex_normal(n: int, nrhs: int | None = None, seed: int = 0) -> np.ndarray
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2.0)
 
 
+def two_wave_samples(npts: int, t0: float, t1: float, alpha: float, beta: float, a: complex, c: complex,
+                     noise: float = 0.0, seed: int = 0):
+    """Samples t_k (uniform on [t0, t1]) and E_k = a exp(-g tau_k) + c exp(g tau_k) + noise, with
+    g = alpha + j beta and tau measured from the midpoint of [t0, t1]; the noise is complex normal
+    with standard deviation ``noise`` times the largest |E_k|."""
+    t = np.linspace(t0, t1, npts)
+    tau = t - 0.5 * (t0 + t1)
+    g = alpha + 1j * beta
+    E = a * np.exp(-g * tau) + c * np.exp(g * tau)
+    if noise > 0:
+        E = E + noise * np.max(np.abs(E)) * complex_normal(npts, seed=seed)
+    return t, E
+
+
 def random_sigma_qpoints(nt: int, q: int, region: np.ndarray, scale: float, seed: int = 0) -> np.ndarray:
     """Seeded non-negative conductivities [S], one per (triangle, quadrature point).
 

@@ -467,6 +467,33 @@ def test_reflection_fit_recovers_two_waves():
     assert abs(bt - beta) < 1e-3 and abs(got - r) < 1e-4 and res < 1e-3
 
 
+def test_decay_fit_recovers_decaying_waves():
+    """Two waves decaying along their directions of travel (Sec. III): an on-grid (alpha, beta) is
+    recovered exactly with both amplitudes; with 1e-3 noise, to one grid step."""
+    alpha, beta, a, c = 0.35, 11.3, 0.8 - 0.3j, 0.02 * np.exp(0.7j)
+    t, E = synth.two_wave_samples(48, 1.0, 4.0, alpha, beta, a, c)
+    alphas, betas = np.linspace(0.0, 1.0, 41), np.linspace(10.0, 12.5, 101)
+    al, bt, res, ga, gc = post.fit_decay(t, E, alphas, betas)
+    assert al == alphas[14] and abs(al - alpha) < 1e-12 and abs(bt - beta) < 1e-12
+    assert abs(ga - a) < 1e-10 and abs(gc - c) < 1e-10 and res < 1e-12
+    t, E = synth.two_wave_samples(48, 1.0, 4.0, alpha, beta, a, c, noise=1e-3, seed=3)
+    al, bt, res, ga, gc = post.fit_decay(t, E, alphas, betas)
+    assert abs(al - alpha) <= 0.025 + 1e-12 and abs(bt - beta) <= 0.025 + 1e-12 and res < 5e-3
+
+
+def test_decay_fit_without_decay_is_the_reflection_fit():
+    """With alpha fixed at 0 the decay fit is the two-wave reflection fit; its amplitudes are
+    referred to the midpoint tm, so c/a carries the factor exp(2 j beta tm)."""
+    xs = np.linspace(1.0, 3.0, 40)
+    E = np.exp(-1j * 11.3 * xs) + 0.0123 * np.exp(0.4j) * np.exp(1j * 11.3 * xs)
+    E = E + 1e-4 * synth.complex_normal(40, seed=8)
+    betas = np.linspace(10, 12.5, 501)
+    r, bt, res = post.fit_reflection(xs, E, betas=betas)
+    al, bt2, res2, a, c = post.fit_decay(xs, E, [0.0], betas)
+    assert al == 0.0 and bt2 == bt and abs(res2 - res) < 1e-12
+    assert abs(c / a - r * np.exp(2j * bt * 2.0)) < 1e-12
+
+
 # ---------------------------------------------------------------- B-spline conductivity
 def _line_points(s, x0=1.0, L=2.0, axis=0):
     pts = np.zeros((len(s), 3))
