@@ -22,8 +22,10 @@ Absorbers for Full-Wave Analysis of 3-D Nanophotonics"):
                  near-field precorrection.
 * ``excitation`` incident fields (plane wave, dipole, complex-source beam) and
                  the tested right-hand side b (Appendix A).
-* ``sigma``      conductivity profiles (the monomial of Eq. 23).
-* ``post``       SWR -> r, on-axis field fit, far field.
+* ``sigma``      conductivity profiles (the monomial of Eq. 23, and a cubic
+                 B-spline by the Cox-de Boor recursion).
+* ``post``       SWR -> r, fields at points, on-axis reflection fit, the
+                 decay-rate fit of Sec. III, far field.
 * ``mie``        Mie series for a dielectric sphere, optionally with a surface
                  conductivity sheet (textbook, derived from the boundary
                  conditions of Eq. 4).

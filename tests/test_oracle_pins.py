@@ -267,6 +267,39 @@ def test_power_balance_catches_planted_mistakes(monkeypatch):
     assert abs(pe - ps - pa) < 2e-2 * pe, (pe, ps, pa)
 
 
+def _shell_points(rng, r0, r1, n):
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    return v * rng.uniform(r0, r1, n)[:, None]
+
+
+def test_equivalence_principle_fields_of_the_solved_currents(monkeypatch):
+    """Equivalence principle (Sec. II, Eqs. 6-9) for the field evaluation at points: with the
+    solved currents of the dielectric sphere, the exterior currents radiating in the exterior
+    medium cancel the incident wave inside the sphere (extinction theorem), and the interior
+    currents radiating in the interior medium give no field outside, both to the discretisation
+    error of the 320-triangle mesh.  A planted sign error in the curl term must break it."""
+    g, med, x = _sphere_solution(False, 0.0)
+    rng = np.random.default_rng(2)
+    pin, pout = _shell_points(rng, 0.0, 0.6, 12), _shell_points(rng, 1.5, 2.0, 12)
+    (ke, ki), (ze, zi) = med.k, med.z
+    e_inc = excitation.plane_wave(pin, ke, ze, [0, 0, 1], [1, 0, 0])[0]
+
+    def gaps():
+        ext = np.linalg.norm(e_inc + post.radiated(g, x, pin, ke, ze, "e")) / np.linalg.norm(e_inc)
+        out = np.linalg.norm(post.radiated(g, x, pout, ki, zi, "i"))
+        inside = np.linalg.norm(post.radiated(g, x, pin, ki, zi, "i"))
+        return ext, out / inside
+
+    ext, leak = gaps()
+    assert ext < 0.02 and leak < 0.01, (ext, leak)
+    scat = np.linalg.norm(post.radiated(g, x, pout, ke, ze, "e"))
+    assert scat > 0.2 * np.linalg.norm(excitation.plane_wave(pout, ke, ze, [0, 0, 1], [1, 0, 0])[0])
+    monkeypatch.setattr(post, "_EPS", -post._EPS)
+    ext, leak = gaps()
+    assert ext > 0.2 or leak > 0.2, (ext, leak)
+
+
 def test_sigma_zero_absorber_rows_give_opposite_currents():
     """With sigma = 0, Eq. 14 reduces to <X, J_e + J_i> = 0, so J_e^R = -J_i^R exactly."""
     m = synth.icosphere(1, 1.0)
@@ -499,6 +532,24 @@ def _line_points(s, x0=1.0, L=2.0, axis=0):
     pts = np.zeros((len(s), 3))
     pts[:, axis] = x0 + L * np.asarray(s)
     return pts
+
+
+def test_monomial_profile_special_values_and_integral():
+    """Eq. 23 on the two-ended 12 um guide (cubic, 4 um absorbers): zero in the clean section,
+    sigma0 at both ends, sigma0 / 8 half-way into either absorber, the integral over one absorber
+    sigma0 L / (d + 1), and d = 0 a step of height sigma0 at x0."""
+    from oracle import sigma as osig
+
+    s0, L = 8e-3, 4.0
+    segs = [(12.0 - L, L, s0, 3, 0, 1.0), (L, L, s0, 3, 0, -1.0)]
+    x = np.array([6.0, 0.0, 12.0, 10.0, 2.0])
+    got = osig.monomial(_line_points(x, x0=0.0, L=1.0), segs)
+    assert np.allclose(got, [0.0, s0, s0, s0 / 8, s0 / 8], rtol=1e-14, atol=0.0)
+    xs = np.linspace(8.0, 12.0, 200001)
+    vals = osig.monomial(_line_points(xs, x0=0.0, L=1.0), segs)
+    assert abs(np.trapezoid(vals, xs) - s0 * L / 4) < 1e-9
+    step = osig.monomial(_line_points(np.array([0.99, 1.01, 5.0]), x0=0.0, L=1.0), [(1.0, 2.0, s0, 0, 0, 1.0)])
+    assert np.array_equal(step, [0.0, s0, s0])
 
 
 def test_bspline_partition_of_unity_and_clamped_ends():
