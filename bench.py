@@ -213,7 +213,7 @@ def stage_bytes(info, ginfo, case, N, b):
     }
 
 
-def survey_model_bytes(info, case, N, b):
+def full_grid_model_bytes(info, case, N, b):
     """Whole-matvec bytes of the unpruned pFFT model: one round trip of each
     half-transformed field of the full transform grid (12 in, 16 out), both
     Green octants, the near records, the stencil data (read by projection and
@@ -390,7 +390,7 @@ def run_gpu(args):
                 "algorithmic_bytes": bmodel[dom]}
     t_mv = ms_max / args.steps / 1e3
     b_pruned = sum(bmodel.values())
-    b_full = survey_model_bytes(info, case, N, 8)
+    b_full = full_grid_model_bytes(info, case, N, 8)
     mv_roof = {
         "pruned_bytes": b_pruned, "pruned_frac": b_pruned / t_mv / 1e9 / hbm,
         "full_grid_model_bytes": b_full, "full_grid_model_frac": b_full / t_mv / 1e9 / hbm,

@@ -4,7 +4,7 @@ Tolerances (stated by the target and used verbatim): complex128 operator
 1e-10 relative, complex64 operator 1e-5 relative, solved systems 1e-8
 relative residual after refinement.  Element-wise checks scale by the largest
 oracle entry (|y_gpu - y_orc|_inf <= tol * |y_orc|_inf) so tiny entries with
-cancellation are judged against the row scale of the operator.
+cancellation are measured against the row scale of the operator.
 """
 
 import numpy as np
