@@ -527,6 +527,25 @@ def test_decay_fit_without_decay_is_the_reflection_fit():
     assert abs(c / a - r * np.exp(2j * bt * 2.0)) < 1e-12
 
 
+def test_stored_decay_rate_study_has_the_shape_of_sec3():
+    """The oracle's decay rate under a uniform surface conductivity (tests/golden/
+    decay_rate_vs_sigma.txt, written by make_decay_rate_vs_sigma.py beside it, about six minutes
+    of oracle solves) has the behaviour Sec. III describes: no decay without conductivity, a rate
+    growing in proportion to a small conductivity (the lossy surface absorbs), and a maximum
+    followed by a decrease as the surface turns into a reflecting wall.  (On this 0.5 x 0.22 um
+    core the conducting-wall limit keeps an evanescent decay of about 2-3 /um: the y-polarised
+    field is at cut-off between walls 0.22 um apart at lambda_i = 0.45 um.)  This checks the stored
+    record of that study, not a fresh run."""
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "decay_rate_vs_sigma.txt"))
+    sig, alpha = rows[:, 0], rows[:, 1]
+    a = dict(zip(sig, alpha))
+    assert a[0.0] <= 0.1
+    assert a[1.0] > 0.2 and 1.6 <= a[2.0] / a[1.0] <= 2.4 and 1.6 <= a[4.0] / a[2.0] <= 2.4
+    k = int(np.argmax(alpha))
+    assert 0 < k < len(alpha) - 1
+    assert alpha[-1] < 0.7 * alpha[k]
+
+
 # ---------------------------------------------------------------- B-spline conductivity
 def _line_points(s, x0=1.0, L=2.0, axis=0):
     pts = np.zeros((len(s), 3))
