@@ -98,3 +98,24 @@ def test_operator_needs_a_gb300(lib):
         sc.scabem_op_create(h, (2.25, 1, 1, 1, 1.55), (16, 16, 16), 0.2, (-1.5, -1.5, -1.5), 3, 6, 0.3, 3)
     assert e.value.code == -3
     sc.scabem_mesh_destroy(h)
+
+
+def test_decay_fit_argument_checks_without_a_gpu(lib):
+    """scabem_decay_fit rejects a bad grid or sample count (SCABEM_E_ARG) and non-finite samples
+    (SCABEM_E_NONFINITE) before looking for a device; valid arguments then need a GB300
+    (SCABEM_E_DEVICE here): there is no host fallback."""
+    t, E = synth.two_wave_samples(16, 0.0, 1.0, 0.2, 6.0, 1.0, 0.1)
+    cases = [((t, E, 0.0, 1.0, 0, 4.0, 8.0, 11), -1), ((t[:3], E[:3], 0.0, 1.0, 5, 4.0, 8.0, 11), -1),
+             ((t, E, 0.0, 1.0, 4097, 4.0, 8.0, 4097), -1), ((t, E, 0.0, float("inf"), 5, 4.0, 8.0, 11), -1)]
+    for args, code in cases:
+        with pytest.raises(sc.ScabemError) as e:
+            sc.scabem_decay_fit(*args)
+        assert e.value.code == code, args
+    bad = E.copy()
+    bad[5] = complex(float("nan"), 0.0)
+    with pytest.raises(sc.ScabemError) as e:
+        sc.scabem_decay_fit(t, bad, 0.0, 1.0, 5, 4.0, 8.0, 11)
+    assert e.value.code == -7
+    with pytest.raises(sc.ScabemError) as e:
+        sc.scabem_decay_fit(t, E, 0.0, 1.0, 5, 4.0, 8.0, 11)
+    assert e.value.code == -3
