@@ -364,7 +364,21 @@ def run_gpu(args):
         t0 = time.perf_counter()
         sc.scabem_sigma_gradient(op, xs, lam, src, bspline=(0.0, 12.0, 0, 16), stream=stream)
         t_grad = time.perf_counter() - t0
+        # reflection of the solved field (the reflection configuration 2 asks for): E_y on the axis
+        # between the beam source (x = 6 um) and the right absorber (x in [8, 12] um), two-wave fit
+        refl = None
+        try:
+            t0 = time.perf_counter()
+            rr = sc.scabem_reflection(op, xs, 0, 1, (0.0, 0.01, -0.005), 6.3, 7.7, 48, 8.0, 13.0, 1001, inc=src[0],
+                                      stream=stream)[0]
+            refl = {"abs_r": math.hypot(rr[0], rr[1]), "r": [rr[0], rr[1]], "beta_rad_per_um": rr[2],
+                    "fit_residual": rr[3], "swr": rr[4], "r_from_swr": rr[5], "seconds": time.perf_counter() - t0,
+                    "probe": "E_y at 48 axis points, x in [6.3, 7.7] um, beta scanned over [8, 13] rad/um",
+                    "meaning": "reflection of the right-hand absorber seen by the beam launched at x = 6 um"}
+        except sc.ScabemError as e:
+            refl = {"error": str(e)}
         extras = {
+            "reflection": refl,
             "c128": {"value": 1e3 / ms128, "unit": UNIT, "ms_per_step": ms128, "dtype": "c128"},
             "batched_c64": {"value": nb * 1e3 / msb, "unit": UNIT, "nrhs": nb, "ms_per_call": msb},
             "solve": {"seconds": t_solve, "iterations": sinfo["iters"], "refinements": sinfo["refinements"],
