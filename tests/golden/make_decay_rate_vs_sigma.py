@@ -7,8 +7,9 @@ sigma the oracle's dense operator (O1, assembled once at sigma = 0 and once at s
 the operator is affine in sigma) is solved by LU, the interior field E_y is evaluated at 33 points
 of the axis between x = 0.6 and 1.4 um, and the decay-rate fit of Sec. III
 (a exp(-g tau) + c exp(g tau), g = alpha + j beta) is taken over alpha in [0, 12] /um (step 0.1)
-and beta in [4, 16] rad/um (step 0.2).  Calls only the oracle and the input generators; runs for
-about six minutes on one core.
+and beta in [4, 16] rad/um (step 0.2).  The decay rate by Poynting's theorem (Sec. III-B) is taken
+at the cross-section x = 1.025 um (the middle of one mesh slice) over the box |y| <= 0.6,
+|z| <= 0.5 um.  Calls only the oracle and the input generators; runs for about seven minutes.
 
     python tests/golden/make_decay_rate_vs_sigma.py
 """
@@ -46,15 +47,19 @@ def main():
         x = np.linalg.solve(A0 + (s * ETA0) * A1, excitation.rhs(g, med, z0 + s, "i", "beam", **src))
         E = post.radiated(g, x, pts, ki, zi, "i")[:, 1] + e_inc
         al, bt, res, a, c = post.fit_decay(ts, E, np.linspace(0.0, 12.0, 121), np.linspace(4.0, 16.0, 61))
-        rows.append((s_ms, al, bt, res, abs(c / a)))
+        ap = post.poynting_decay_rate(g, x, med, s, 1.025, (0.25, 0.11), (0.6, 0.5), 0.025,
+                                      inc=lambda q: excitation.beam(q, ki, zi, src["r0"], src["d"], src["b"],
+                                                                    src["p"]), n=8)[0]
+        rows.append((s_ms, al, ap, bt, res, abs(c / a)))
     with open(os.path.join(HERE, "decay_rate_vs_sigma.txt"), "w") as f:
         f.write("# Decay rate of the field in a guide with uniform surface conductivity (Sec. III of Zhang\n"
                 "# et al., arXiv 1004.5076), from the oracle; written by make_decay_rate_vs_sigma.py.\n"
                 f"# guide 2.4 um, 0.5 x 0.22 um core eps 12.1 in eps 2.1, lambda 1.55 um, {g.nt} triangles, "
                 f"N = {g.N}\n"
-                "# columns: sigma_mS  alpha_per_um  beta_rad_per_um  rel_residual  |c/a|\n")
+                "# columns: sigma_mS  alpha_fit_per_um  alpha_poynting_per_um  beta_rad_per_um  "
+                "fit_rel_residual  |c/a|\n")
         for r in rows:
-            f.write("%9.2f  %6.2f  %6.2f  %.4f  %.4f\n" % r)
+            f.write("%9.2f  %6.2f  %7.3f  %6.2f  %.4f  %.4f\n" % r)
 
 
 if __name__ == "__main__":

@@ -538,18 +538,54 @@ def test_decay_fit_without_decay_is_the_reflection_fit():
     assert abs(c / a - r * np.exp(2j * bt * 2.0)) < 1e-12
 
 
+def test_fields_at_points_satisfy_faraday(monkeypatch):
+    """The E and H of a current set at points off the surface (post.radiated_fields, Eqs. 15-16)
+    satisfy curl E = -j k Z H (exp(+jwt), eta0 = 1), by central differences, on both sides and
+    for random currents, to the quadrature's consistency of charge and current; E equals
+    post.radiated.  A planted sign error in the curl term must fail it."""
+    m = synth.icosphere(1, 1.0)
+    g = mesh.build(m.V, m.T, m.region, q=6)
+    x = synth.complex_normal(g.N, seed=3)
+    pts = np.array([[0.2, 0.1, -0.3], [1.6, 0.3, 0.2]])
+    h = 1e-4
+
+    def gap(side, k, z):
+        E, H = post.radiated_fields(g, x, pts, k, z, side)
+        worst = 0.0
+        for i, p in enumerate(pts):
+            d = [(post.radiated_fields(g, x, (p + h * e)[None], k, z, side)[0][0]
+                  - post.radiated_fields(g, x, (p - h * e)[None], k, z, side)[0][0]) / (2 * h) for e in np.eye(3)]
+            curl = np.array([d[1][2] - d[2][1], d[2][0] - d[0][2], d[0][1] - d[1][0]])
+            worst = max(worst, np.abs(curl + 1j * k * z * H[i]).max() / np.abs(curl).max())
+        return worst, E
+
+    for side, k, z in (("i", 2 * np.pi / 1.55 * 1.5, 1 / 1.5), ("e", 2 * np.pi / 1.55, 1.0)):
+        worst, E = gap(side, k, z)
+        assert worst < 5e-3, (side, worst)
+        assert np.abs(E - post.radiated(g, x, pts, k, z, side)).max() < 1e-12 * np.abs(E).max()
+    monkeypatch.setattr(post, "_EPS", -post._EPS)
+    worst, _ = gap("e", 2 * np.pi / 1.55, 1.0)
+    assert worst > 0.3, worst
+
+
 def test_stored_decay_rate_study_has_the_shape_of_sec3():
     """The oracle's decay rate under a uniform surface conductivity (tests/golden/
     decay_rate_vs_sigma.txt, written by make_decay_rate_vs_sigma.py beside it, about six minutes
     of oracle solves) has the behaviour Sec. III describes: no decay without conductivity, a rate
     growing in proportion to a small conductivity (the lossy surface absorbs), and a maximum
-    followed by a decrease as the surface turns into a reflecting wall.  (On this 0.5 x 0.22 um
+    followed by a decrease as the surface turns into a reflecting wall; for the absorbing range the
+    decay rate by Poynting's theorem (Sec. III-B) agrees with the fit.  (On this 0.5 x 0.22 um
     core the conducting-wall limit keeps an evanescent decay of about 2-3 /um: the y-polarised
     field is at cut-off between walls 0.22 um apart at lambda_i = 0.45 um.)  This checks the stored
     record of that study, not a fresh run."""
     rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "decay_rate_vs_sigma.txt"))
-    sig, alpha = rows[:, 0], rows[:, 1]
+    sig, alpha, alpha_p = rows[:, 0], rows[:, 1], rows[:, 2]
     a = dict(zip(sig, alpha))
+    # Sec. III-B: while the surface absorbs (sigma <= 4 mS), Poynting's theorem at one
+    # cross-section gives the fitted rate (fit grid step 0.1 /um)
+    for s_ms, a_fit, a_p in zip(sig, alpha, alpha_p):
+        if s_ms <= 4.0:
+            assert abs(a_p - a_fit) <= 0.1 + 0.15 * a_fit, (s_ms, a_fit, a_p)
     assert a[0.0] <= 0.1
     assert a[1.0] > 0.2 and 1.6 <= a[2.0] / a[1.0] <= 2.4 and 1.6 <= a[4.0] / a[2.0] <= 2.4
     k = int(np.argmax(alpha))
