@@ -129,6 +129,19 @@ int scabem_op_create(scabem_mesh_t mesh, const scabem_media* media, const scabem
 int scabem_op_info(scabem_op_t op, int64_t* n_near_pairs, int64_t* near_bytes_c64,
                    int64_t* near_bytes_c128, int64_t* n_qpoints);
 
+/* Grid plan for scabem_op_create (host only; a convenience, not part of the
+ * paper's method).  From the mesh's bounding box, picks per axis the smallest
+ * power-of-two transform size 2n within the limits of scabem_grid_opts whose
+ * physical grid holds the mesh and the stencil margin at a spacing no larger
+ * than h_max [um] (e.g. the wavelength in the densest medium over 10), takes
+ * the common spacing h = max over axes of extent / (n - p - 1.5) (so every
+ * stencil stays inside, with 1.25 cells to spare on either side), centres the
+ * mesh, and fills *opts: n, h, origin, p, q = 6, r_near = near_h * h (near_h
+ * in grid steps, e.g. 2.05 or 3.05), prec_mask = 3, transverse = 0 (auto).
+ * SCABEM_E_ARG for a null argument, h_max <= 0, p outside 2..4, near_h < 0,
+ * or an h_max too small for the transform or (y, z) plane limits. */
+int scabem_grid_plan(scabem_mesh_t mesh, double h_max, int32_t p, double near_h, scabem_grid_opts* opts);
+
 /* Sparsity of the grid (Appendix B's uniform grid): physical grid points
  * that some projection stencil covers, and (i1, i2) columns holding one of
  * them.  Sources are zero and potentials unused elsewhere, so the axis-0

@@ -103,6 +103,7 @@ def lib():
     L.scabem_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_apply_adjoint.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_selftest_wait_limit.argtypes = [vp, vp]
+    L.scabem_grid_plan.argtypes = [vp, C.c_double, i32, C.c_double, C.POINTER(GridOpts)]
     L.scabem_decay_fit.argtypes = [vp, vp, i32, C.c_double, C.c_double, i32, C.c_double, C.c_double, i32, vp, vp]
     L.scabem_decay_rate.argtypes = [vp, vp, i32, i64, C.POINTER(Probe), C.c_double, C.c_double, i32,
                                     C.POINTER(Source), vp, vp]
@@ -194,6 +195,14 @@ def scabem_op_create(mesh, media, n, h, origin, p=3, q=6, r_near=0.0, prec_mask=
     op = C.c_void_p()
     _check(lib().scabem_op_create(mesh, C.byref(md), C.byref(go), _stream(stream), C.byref(op)))
     return op
+
+
+def scabem_grid_plan(mesh, h_max, p=3, near_h=2.05):
+    """Grid options for scabem_op_create from the mesh's bounding box (see the header)."""
+    go = GridOpts()
+    _check(lib().scabem_grid_plan(mesh, h_max, p, near_h, C.byref(go)))
+    return {"n": tuple(go.n), "h": go.h, "origin": tuple(go.origin), "p": go.p, "q": go.q, "r_near": go.r_near,
+            "prec_mask": go.prec_mask, "transverse": go.transverse}
 
 
 def scabem_op_info(op):

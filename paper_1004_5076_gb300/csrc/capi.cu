@@ -553,6 +553,55 @@ int scabem_op_info(scabem_op_t op, int64_t* npairs, int64_t* b64, int64_t* b128,
   return SCABEM_OK;
 }
 
+int scabem_grid_plan(scabem_mesh_t mesh, double h_max, int32_t p, double near_h, scabem_grid_opts* opts) {
+  if (!mesh || !opts || !(h_max > 0.0) || !std::isfinite(h_max) || p < 2 || p > MAXP || !(near_h >= 0.0) ||
+      !std::isfinite(near_h) || mesh->nv < 1) {
+    set_error("scabem_grid_plan: null argument, h_max <= 0, p outside 2..4 or near_h < 0");
+    return SCABEM_E_ARG;
+  }
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) lo[a] = hi[a] = mesh->V[a];
+  for (int64_t v = 1; v < mesh->nv; ++v)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], mesh->V[3 * v + a]);
+      hi[a] = std::max(hi[a], mesh->V[3 * v + a]);
+    }
+  // usable stencil-base range on an axis of n points: u in [(p-2)/2, n - p/2), n - p + 1 cells;
+  // the mesh gets n - p - 1.5 of them, 1.25 cells of slack on either side
+  const int tmax[3] = {1024, 128, 128};
+  int n[3];
+  for (int a = 0; a < 3; ++a) {
+    const double need = (hi[a] - lo[a]) / h_max + p + 1.5;
+    int t = 8;
+    while (t < 2 * need && t <= tmax[a]) t *= 2;
+    if (t > tmax[a]) {
+      set_error("scabem_grid_plan: h_max too small for the transform limits along axis " + std::to_string(a));
+      return SCABEM_E_ARG;
+    }
+    n[a] = t / 2;
+  }
+  if (4 * n[1] * n[2] > 4096) {
+    set_error("scabem_grid_plan: h_max too small for the (y, z) plane limit (2 n_y)(2 n_z) <= 4096");
+    return SCABEM_E_ARG;
+  }
+  double h = 0.0;
+  for (int a = 0; a < 3; ++a) h = std::max(h, (hi[a] - lo[a]) / (n[a] - p - 1.5));
+  if (!(h > 0.0)) h = h_max;
+  // small fractions of a cell keep the points of structured meshes off cell boundaries
+  const double off[3] = {0.0731, 0.0419, 0.0257};
+  for (int a = 0; a < 3; ++a) {
+    opts->n[a] = n[a];
+    opts->origin[a] = 0.5 * (lo[a] + hi[a]) - h * (0.5 * (n[a] - 1) - off[a]);
+  }
+  opts->h = h;
+  opts->p = p;
+  opts->q = 6;
+  opts->r_near = near_h * h;
+  opts->prec_mask = 3;
+  opts->transverse = 0;
+  return SCABEM_OK;
+}
+
 int scabem_op_grid_info(scabem_op_t op, int64_t* npts, int64_t* ncols, int32_t* direct) {
   if (!op) {
     set_error("null operator");

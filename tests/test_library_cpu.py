@@ -119,3 +119,36 @@ def test_decay_fit_argument_checks_without_a_gpu(lib):
     with pytest.raises(sc.ScabemError) as e:
         sc.scabem_decay_fit(t, E, 0.0, 1.0, 5, 4.0, 8.0, 11)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("make,h_max,p", [(lambda: synth.waveguide(), 0.05, 3), (lambda: synth.icosphere(2), 0.1, 4),
+                                          (lambda: synth.waveguide(2.0, 0.5, 0.22, 20, 4, 2, 0.5, 0.5), 0.03, 2)])
+def test_grid_plan_keeps_every_stencil_inside(lib, make, h_max, p):
+    """scabem_grid_plan: power-of-two transform sizes within the limits, h <= h_max, and every
+    stencil base the set-up computes (floor(u - (p-2)/2) with u = (r - origin)/h) inside
+    [0, n - p] for the mesh's extreme points, so for every quadrature point."""
+    m = make()
+    h = sc.scabem_mesh_create(m.V, m.T, m.region)
+    plan = sc.scabem_grid_plan(h, h_max, p=p, near_h=3.05)
+    n, hh, org = np.array(plan["n"]), plan["h"], np.array(plan["origin"])
+    for a, tmax in enumerate((1024, 128, 128)):
+        t = 2 * n[a]
+        assert 8 <= t <= tmax and t & (t - 1) == 0
+    assert 4 * n[1] * n[2] <= 4096 and 0 < hh <= h_max
+    assert plan["p"] == p and abs(plan["r_near"] - 3.05 * hh) < 1e-15 and plan["q"] == 6
+    u = (m.V - org) / hh
+    b = np.floor(u - 0.5 * (p - 2))
+    assert b.min() >= 0 and np.all(b.max(axis=0) + p - 1 <= n - 1)
+    sc.scabem_mesh_destroy(h)
+
+
+def test_grid_plan_matches_the_guide_workload_and_rejects_bad_requests(lib):
+    m = synth.waveguide()
+    h = sc.scabem_mesh_create(m.V, m.T, m.region)
+    plan = sc.scabem_grid_plan(h, 0.05)
+    assert plan["n"] == (256, 16, 16) and abs(plan["h"] - 12.0 / (256 - 4.5)) < 1e-12
+    for args in ((0.005,), (0.05, 5), (-1.0,), (0.05, 3, -1.0)):
+        with pytest.raises(sc.ScabemError) as e:
+            sc.scabem_grid_plan(h, *args)
+        assert e.value.code == -1, args
+    sc.scabem_mesh_destroy(h)
