@@ -26,6 +26,8 @@ Absorbers for Full-Wave Analysis of 3-D Nanophotonics"):
                  B-spline by the Cox-de Boor recursion).
 * ``post``       SWR -> r, fields at points, on-axis reflection fit, the
                  decay-rate fit of Sec. III, far field.
+* ``toeplitz``   the exact block-Toeplitz product of O1 on a straight extruded
+                 guide (Appendix B), by circulant embedding along the slices.
 * ``mie``        Mie series for a dielectric sphere, optionally with a surface
                  conductivity sheet (textbook, derived from the boundary
                  conditions of Eq. 4).

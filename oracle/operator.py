@@ -331,16 +331,19 @@ def _unit_fields(P0, P1, Q, C):
     return (A.reshape(p, 3, S * 4), phi.reshape(p, S * 4), gphi.reshape(p, 3, S * 4), curl.reshape(p, 3, S * 4))
 
 
-def assemble(g: Geometry, media: Media, sigma_pts_S, chunk: int = 2) -> np.ndarray:
-    """Dense N x N matrix of O1 (for small meshes)."""
+def assemble(g: Geometry, media: Media, sigma_pts_S, chunk: int = 2, tris=None) -> np.ndarray:
+    """Dense N x N matrix of O1 (for small meshes).  ``tris`` restricts the assembly to the
+    rows those target triangles contribute to (a row is complete when both triangles of its edge
+    are included; the other rows stay zero or partial)."""
     (ke, ki), (ze, zi) = media.k, media.z
     S = g.nt
     smap = summary_map(g)
     sig = sigma_normalised(sigma_pts_S)
     A = np.zeros((g.N, g.N), dtype=np.complex128)
     rows = row_index(g)
-    for i in range(0, g.nt, chunk):
-        tc = np.arange(i, min(i + chunk, g.nt))
+    targets = np.arange(g.nt) if tris is None else np.asarray(tris)
+    for i in range(0, len(targets), chunk):
+        tc = targets[i : i + chunk]
         nq = len(tc) * g.q
         meds = []
         for k in (ke, ki):

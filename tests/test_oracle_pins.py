@@ -608,6 +608,44 @@ def test_stored_decay_rate_study_has_the_shape_of_sec3():
     assert alpha[-1] < 0.7 * alpha[k]
 
 
+def test_toeplitz_product_equals_direct_matvec():
+    """The paper's block-Toeplitz product (Appendix B) of the plain-surface operator on a straight
+    extruded guide equals O1's direct matvec on the rows of the regular slices, to rounding: the
+    end slices' blocks come straight from their rows, the interior ones only from translates."""
+    from oracle import toeplitz
+
+    nx, L = 20, 2.0
+    m = synth.waveguide(L, 0.5, 0.22, nx, 4, 2, 0.0, 0.0)
+    g = mesh.build(m.V, m.T, m.region, q=6)
+    med = operator.Media(12.1, 1.0, 2.1, 1.0, 1.55)
+    sig = np.zeros((g.nt, g.q))
+    lay = toeplitz.SliceLayout(g, 0.0, L / nx, nx)
+    T = toeplitz.blocks(g, med, sig, lay)
+    xs = synth.complex_normal(lay.count * lay.m, seed=4).reshape(lay.count, lay.m)
+    x = np.zeros(g.N, dtype=np.complex128)
+    for k in range(lay.count):
+        idx, sg = lay.unknowns(g, k)
+        x[idx] = sg * xs[k]
+    ys = toeplitz.apply(T, xs)
+    for k in (0, 5, 11, lay.count - 1):
+        idx, sg = lay.unknowns(g, k)
+        tris = np.unique(g.edge_t[lay.edges[k]].reshape(-1))
+        y = operator.matvec(g, med, x, sig, chunk=2, tris=tris)
+        assert np.linalg.norm(sg * y[idx] - ys[k]) < 1e-12 * np.linalg.norm(ys[k]), k
+
+
+def test_toeplitz_layout_rejects_a_non_periodic_mesh():
+    """A mesh whose slices are not translates (one node plane moved) is refused."""
+    from oracle import toeplitz
+
+    m = synth.waveguide(2.0, 0.5, 0.22, 20, 4, 2, 0.0, 0.0)
+    V = m.V.copy()
+    V[np.isclose(V[:, 0], 0.7), 0] += 0.013
+    g = mesh.build(V, m.T, m.region, q=1)
+    with pytest.raises(ValueError):
+        toeplitz.SliceLayout(g, 0.0, 0.1, 20)
+
+
 # ---------------------------------------------------------------- B-spline conductivity
 def _line_points(s, x0=1.0, L=2.0, axis=0):
     pts = np.zeros((len(s), 3))
