@@ -331,15 +331,23 @@ def _unit_fields(P0, P1, Q, C):
     return (A.reshape(p, 3, S * 4), phi.reshape(p, S * 4), gphi.reshape(p, 3, S * 4), curl.reshape(p, 3, S * 4))
 
 
-def assemble(g: Geometry, media: Media, sigma_pts_S, chunk: int = 2, tris=None) -> np.ndarray:
+def assemble(g: Geometry, media: Media, sigma_pts_S, chunk: int = 2, tris=None, rows_out=None) -> np.ndarray:
     """Dense N x N matrix of O1 (for small meshes).  ``tris`` restricts the assembly to the
     rows those target triangles contribute to (a row is complete when both triangles of its edge
-    are included; the other rows stay zero or partial)."""
+    are included; the other rows stay zero or partial).  With ``rows_out`` (row indices) only
+    those rows are kept, as a len(rows_out) x N matrix, so large meshes fit in memory."""
     (ke, ki), (ze, zi) = media.k, media.z
     S = g.nt
     smap = summary_map(g)
     sig = sigma_normalised(sigma_pts_S)
-    A = np.zeros((g.N, g.N), dtype=np.complex128)
+    if rows_out is None:
+        A = np.zeros((g.N, g.N), dtype=np.complex128)
+        keep = np.arange(g.N)
+    else:
+        rows_out = np.asarray(rows_out)
+        A = np.zeros((len(rows_out), g.N), dtype=np.complex128)
+        keep = -np.ones(g.N, dtype=np.int64)
+        keep[rows_out] = np.arange(len(rows_out))
     rows = row_index(g)
     targets = np.arange(g.nt) if tris is None else np.asarray(tris)
     for i in range(0, len(targets), chunk):
@@ -379,7 +387,9 @@ def assemble(g: Geometry, media: Media, sigma_pts_S, chunk: int = 2, tris=None) 
         rr = rows[e]
         m = rr >= 0
         contrib = np.asarray((smap.T @ val[m].T).T)
-        np.add.at(A, rr[m], contrib)
+        kr = keep[rr[m]]
+        sel = kr >= 0
+        np.add.at(A, kr[sel], contrib[sel])
     return A
 
 

@@ -11,8 +11,9 @@ gives the offsets of both signs.  Each product equals O1's direct matvec on thos
 
 Slices: an edge of a mesh built from uniform x-nodes x0 + i dx belongs to slice floor((m_x - x0)/dx)
 (m its midpoint).  Rings of edges at x_i and the edges between x_i and x_(i+1) both belong to slice
-i.  A slice is regular when it lies strictly between the end caps (slices 1 .. nslices - 1): its
-edges join lateral triangles only, and its edges are translates of the first regular slice's.
+i.  The regular slices (by default those strictly between the end caps, 1 .. nslices - 1; or a given
+range, such as the plain section between two absorbers) hold plain-surface edges joining lateral
+triangles only, and their edges are translates of the first regular slice's.
 Within a slice the edges are ordered by midpoint.  Each edge carries a sign, -1 where the
 translate has its two triangles in the opposite roles (its basis function is then the negated
 translate).
@@ -31,7 +32,7 @@ class SliceLayout:
     ``first + s`` in the common local order, ``sign[e]`` the orientation of edge e relative to the
     first regular slice."""
 
-    def __init__(self, g: Geometry, x0: float, dx: float, nslices: int):
+    def __init__(self, g: Geometry, x0: float, dx: float, nslices: int, first: int = 1, count: int | None = None):
         mid = 0.5 * (g.V[g.edge_v[:, 0]] + g.V[g.edge_v[:, 1]])
         u = (mid[:, 0] - x0) / dx
         s = np.floor(u + 1e-9).astype(np.int64)
@@ -39,8 +40,9 @@ class SliceLayout:
         tri_x = g.V[g.T][:, :, 0]
         cap = np.ptp(tri_x, axis=1) < 1e-12 * dx
         lateral = ~cap[g.edge_t[:, 0]] & ~cap[g.edge_t[:, 1]]
-        ok = (g.edge_class == 0) & lateral & (s >= 1) & (s <= nslices - 1)
-        self.first, self.count = 1, nslices - 1
+        self.first = first
+        self.count = nslices - first if count is None else count
+        ok = (g.edge_class == 0) & lateral & (s >= self.first) & (s < self.first + self.count)
         self.edges, self.sign = [], np.zeros(g.ne)
         ref_keys = ref_plus = None
         for k in range(self.count):
@@ -78,11 +80,11 @@ def blocks(g: Geometry, media, sigma_pts_S, lay: SliceLayout):
     T = {}
     for ref in (0, R - 1):
         tris = np.unique(g.edge_t[lay.edges[ref]].reshape(-1))
-        A = operator.assemble(g, media, sigma_pts_S, tris=tris)
         ri, rs = lay.unknowns(g, ref)
+        A = operator.assemble(g, media, sigma_pts_S, tris=tris, rows_out=ri)
         for j in range(R):
             ci, cs = lay.unknowns(g, j)
-            T[ref - j] = (rs[:, None] * A[np.ix_(ri, ci)]) * cs[None, :]
+            T[ref - j] = (rs[:, None] * A[:, ci]) * cs[None, :]
     return T
 
 
