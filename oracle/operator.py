@@ -336,16 +336,23 @@ def assemble(g: Geometry, media: Media, sigma_pts_S, chunk: int = 2, tris=None, 
     rows those target triangles contribute to (a row is complete when both triangles of its edge
     are included; the other rows stay zero or partial).  With ``rows_out`` (row indices) only
     those rows are kept, as a len(rows_out) x N matrix, so large meshes fit in memory."""
+    return assemble_many(g, media, [sigma_pts_S], chunk, tris, rows_out)[0]
+
+
+def assemble_many(g: Geometry, media: Media, sigmas, chunk: int = 2, tris=None, rows_out=None):
+    """``assemble`` for several conductivity profiles of one mesh at once: the panel moments
+    are computed once per target chunk and tested with each profile in turn.  Returns one
+    matrix per entry of ``sigmas`` (each a per-point conductivity [S], (nt, q))."""
     (ke, ki), (ze, zi) = media.k, media.z
     S = g.nt
     smap = summary_map(g)
-    sig = sigma_normalised(sigma_pts_S)
+    sigs = [sigma_normalised(s) for s in sigmas]
+    nrow = g.N if rows_out is None else len(rows_out)
+    As = [np.zeros((nrow, g.N), dtype=np.complex128) for _ in sigs]
     if rows_out is None:
-        A = np.zeros((g.N, g.N), dtype=np.complex128)
         keep = np.arange(g.N)
     else:
         rows_out = np.asarray(rows_out)
-        A = np.zeros((len(rows_out), g.N), dtype=np.complex128)
         keep = -np.ones(g.N, dtype=np.int64)
         keep[rows_out] = np.arange(len(rows_out))
     rows = row_index(g)
@@ -382,15 +389,16 @@ def assemble(g: Geometry, media: Media, sigma_pts_S, chunk: int = 2, tris=None, 
                 tgt[j, :, :, base] += rel
                 for c in range(3):
                     tgt[j, :, c, base + 1 + c] -= 1.0
-        val = test_rows(g, tc, fe, fi, Jsum, Ml, sig[tc])  # (nt_c, 3, 4, 12S)
         e = g.tri_edge[tc]
         rr = rows[e]
         m = rr >= 0
-        contrib = np.asarray((smap.T @ val[m].T).T)
         kr = keep[rr[m]]
         sel = kr >= 0
-        np.add.at(A, kr[sel], contrib[sel])
-    return A
+        for A, sig in zip(As, sigs):
+            val = test_rows(g, tc, fe, fi, Jsum, Ml, sig[tc])  # (nt_c, 3, 4, 12S)
+            contrib = np.asarray((smap.T @ val[m].T).T)
+            np.add.at(A, kr[sel], contrib[sel])
+    return As
 
 
 def solve_dense(A, b):

@@ -320,6 +320,19 @@ class PFFT:
             res.append(fields)
         return res
 
+    # -- near corrections ----------------------------------------------
+    def near(self, targets=None):
+        """Near pairs and their corrections (exact - grid moments) for the targets; those of the
+        whole mesh (targets None) are computed once and kept, since they do not depend on x or sigma."""
+        if targets is None and getattr(self, "_near_all", None) is not None:
+            return self._near_all
+        tg = np.arange(self.g.nt) if targets is None else np.asarray(targets)
+        pt, ps = near_pairs(self.g, self.r_near, tg)
+        corr = near_corrections(self.grid, self.g, self.media, self.Gpad, pt, ps)
+        if targets is None:
+            self._near_all = (pt, ps, corr)
+        return pt, ps, corr
+
     # -- full apply -----------------------------------------------------
     def apply(self, x, sigma_pts_S, targets=None):
         """y = A_fft x (rows of all triangles, or the rows touched by ``targets``)."""
@@ -330,8 +343,7 @@ class PFFT:
         sets = current_sets(g, X2)
         tg = np.arange(g.nt) if targets is None else np.asarray(targets)
         gf = self.grid_fields(sets, None if targets is None else tg)
-        pt, ps = near_pairs(g, self.r_near, tg)
-        corr = near_corrections(self.grid, g, media, self.Gpad, pt, ps)
+        pt, ps, corr = self.near(tg if targets is not None else None)
         (ke, ki), (ze, zi) = media.k, media.z
         B = X2.shape[1]
         q = g.q

@@ -40,8 +40,12 @@ class SliceLayout:
         tri_x = g.V[g.T][:, :, 0]
         cap = np.ptp(tri_x, axis=1) < 1e-12 * dx
         lateral = ~cap[g.edge_t[:, 0]] & ~cap[g.edge_t[:, 1]]
+        count = nslices - first if count is None else count
+        if not (1 <= first and count >= 1 and first + count <= nslices):
+            raise ValueError(f"regular slices {first} .. {first + count - 1} must lie within 1 .. {nslices - 1} "
+                             "(slice 0 and the end caps are not regular)")
         self.first = first
-        self.count = nslices - first if count is None else count
+        self.count = count
         ok = (g.edge_class == 0) & lateral & (s >= self.first) & (s < self.first + self.count)
         self.edges, self.sign = [], np.zeros(g.ne)
         ref_keys = ref_plus = None

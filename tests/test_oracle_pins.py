@@ -608,6 +608,57 @@ def test_stored_decay_rate_study_has_the_shape_of_sec3():
     assert alpha[-1] < 0.7 * alpha[k]
 
 
+def _transition_slopes(rows):
+    """Local log-log slopes of the Eq. 45 measure between consecutive absorber lengths, per d."""
+    out = {}
+    for d in sorted({int(r[0]) for r in rows}):
+        sel = rows[rows[:, 0] == d]
+        L, m = sel[:, 1], sel[:, 2]
+        out[d] = -np.diff(np.log(m)) / np.diff(np.log(L))
+    return out
+
+
+def _transition_law_holds(rows, band=0.5):
+    """The power law of Sec. IV-B (Eq. 45: |E(2L) - E(L)|^2 / |E(L)|^2 = O(L^-(2d+2))) in a record:
+    at the largest pair of lengths every slope is within `band` of 2d + 2, and the slopes grow
+    with d; the smoother profiles reflect far less (d >= 1 at least 1000 times below d = 0 at the
+    longest absorber)."""
+    sl = _transition_slopes(rows)
+    last = {d: v[-1] for d, v in sl.items()}
+    if any(abs(last[d] - (2 * d + 2)) > band for d in last):
+        return False
+    ds = sorted(last)
+    if any(last[a] >= last[b] for a, b in zip(ds, ds[1:])):
+        return False
+    mL = {d: rows[(rows[:, 0] == d)][-1, 2] for d in ds}
+    return all(mL[d] < 1e-3 * mL[0] for d in ds if d >= 1)
+
+
+def test_stored_transition_reflection_power_law():
+    """Sec. IV-B: the oracle's transition reflection falls with the absorber length L as
+    L^-(2d+2) for the monomial profiles sigma0 s^d (Eq. 23) at a fixed round trip
+    (tests/golden/transition_reflection.txt, written by make_transition_reflection.py beside it:
+    a guide with absorbers up to 16 um, dense LU, about six minutes on 8 cores).  At the largest
+    pair of lengths (6 and 8 um) the slopes are within 0.5 of 2, 4 and 6, and the d = 2 slope
+    climbs towards 6 as L grows (the approach to the asymptotic range).  Planted mistakes: a
+    record whose profiles ignore d (every d behaves like d = 0) and one with the d labels swapped
+    must both fail the same check.  Checks the stored record, not a fresh run."""
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "transition_reflection.txt"))
+    assert sorted({int(r[0]) for r in rows}) == [0, 1, 2]
+    assert _transition_law_holds(rows)
+    sl = _transition_slopes(rows)
+    assert np.all(np.diff(sl[2]) > 0), sl[2]
+    ignored = rows.copy()
+    for d in (1, 2):
+        ignored[ignored[:, 0] == d, 2:] = rows[rows[:, 0] == 0, 2:]
+    assert not _transition_law_holds(ignored)
+    swapped = rows.copy()
+    swapped[rows[:, 0] == 1, 0] = 2
+    swapped[rows[:, 0] == 2, 0] = 1
+    swapped = swapped[np.lexsort((swapped[:, 1], swapped[:, 0]))]
+    assert not _transition_law_holds(swapped)
+
+
 def test_toeplitz_product_equals_direct_matvec():
     """The paper's block-Toeplitz product (Appendix B) of the plain-surface operator on a straight
     extruded guide equals O1's direct matvec on the rows of the regular slices, to rounding: the
@@ -644,6 +695,65 @@ def test_toeplitz_layout_rejects_a_non_periodic_mesh():
     g = mesh.build(V, m.T, m.region, q=1)
     with pytest.raises(ValueError):
         toeplitz.SliceLayout(g, 0.0, 0.1, 20)
+
+
+def test_toeplitz_layout_rejects_slices_outside_the_regular_range():
+    """first / count must keep the regular slices off slice 0 and the far end cap."""
+    from oracle import toeplitz
+
+    m = synth.waveguide(1.2, 0.5, 0.22, 12, 4, 2, 0.0, 0.0)
+    g = mesh.build(m.V, m.T, m.region, q=1)
+    for first, count in ((0, 4), (1, 0), (1, -2), (9, 4), (12, 1)):
+        with pytest.raises(ValueError):
+            toeplitz.SliceLayout(g, 0.0, 0.1, 12, first=first, count=count)
+    assert toeplitz.SliceLayout(g, 0.0, 0.1, 12, first=8, count=4).count == 4
+
+
+def test_every_row_pipeline_on_a_short_guide():
+    """The pipeline behind the stored every-row record, live on a short guide with absorbers at
+    both ends: (1) the row-restricted assembly equals the full assembly's rows; (2) the
+    block-Toeplitz product over a given slice range (the plain section) equals O1's direct matvec
+    on every row of those slices; (3) the grid operator O2 against those exact rows improves as
+    the near radius grows (2.05, 3.05, 5.05 grid steps)."""
+    from oracle import toeplitz
+
+    nx, L = 12, 1.2
+    m = synth.waveguide(L, 0.5, 0.22, nx, 4, 2, 0.3, 0.3)
+    g = mesh.build(m.V, m.T, m.region, q=6)
+    med = operator.Media(12.1, 1.0, 2.1, 1.0, 1.55)
+    from oracle import sigma as osig
+
+    sig = osig.monomial(g.qpts, [(0.9, 0.3, 0.004, 2, 0, 1.0), (0.3, 0.3, 0.004, 2, 0, -1.0)])
+    lay = toeplitz.SliceLayout(g, 0.0, L / nx, nx, first=4, count=4)
+    # (1) row restriction
+    A = operator.assemble(g, med, sig)
+    idx, _ = lay.unknowns(g, 1)
+    tris = np.unique(g.edge_t[lay.edges[1]].reshape(-1))
+    Ar = operator.assemble(g, med, sig, tris=tris, rows_out=idx)
+    assert np.array_equal(Ar.shape, (len(idx), g.N))
+    assert np.max(np.abs(Ar - A[idx])) <= 1e-13 * np.max(np.abs(A[idx]))
+    # (2) exact rows of the plain section by the Toeplitz product
+    T = toeplitz.blocks(g, med, sig, lay)
+    xs = synth.complex_normal(lay.count * lay.m, seed=6).reshape(lay.count, lay.m)
+    x = np.zeros(g.N, dtype=np.complex128)
+    for k in range(lay.count):
+        i, sg = lay.unknowns(g, k)
+        x[i] = sg * xs[k]
+    ys = toeplitz.apply(T, xs)
+    y1 = A @ x
+    for k in range(lay.count):
+        i, sg = lay.unknowns(g, k)
+        assert np.linalg.norm(sg * y1[i] - ys[k]) < 1e-12 * np.linalg.norm(ys[k]), k
+    # (3) O2 on the same rows
+    grid = synth.grid_for_mesh(m.V, (32, 16, 16), p=3)
+    tt = np.unique(np.concatenate([g.edge_t[e].reshape(-1) for e in lay.edges]))
+    errs = []
+    for fh in (2.05, 3.05, 5.05):
+        y2 = pfft.PFFT(g, med, grid, fh * grid.h).apply(x, sig, targets=tt)
+        num = sum(np.linalg.norm(lay.unknowns(g, k)[1] * y2[lay.unknowns(g, k)[0]] - ys[k]) ** 2
+                  for k in range(lay.count))
+        errs.append(np.sqrt(num / sum(np.linalg.norm(v) ** 2 for v in ys)))
+    assert errs[0] < 0.2 and errs[1] < errs[0] and errs[2] < errs[1], errs
 
 
 def test_stored_every_row_accuracy_of_the_grid_operator():
