@@ -73,9 +73,17 @@ template <typename R>
 __global__ void k_sources(const cx<R>* __restrict__ x, const int32_t* __restrict__ unk,
                           const double* __restrict__ cX, const double* __restrict__ tri,
                           const double* __restrict__ qp, const double* __restrict__ qw, int64_t Q, int q,
-                          cx<R>* __restrict__ summ, cx<R>* __restrict__ qsrc, cx<R>* __restrict__ y, int64_t N) {
+                          cx<R>* __restrict__ summ, cx<R>* __restrict__ qsrc, cx<R>* __restrict__ y, int64_t N,
+                          int64_t ldx, int64_t ldy) {
   const int64_t Qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (Qi >= Q) return;
+  {  // right-hand side blockIdx.y of a batch: its columns and workspaces
+    const int64_t c = blockIdx.y;
+    x += c * ldx;
+    y += c * ldy;
+    summ += c * (Q / q) * 12;
+    qsrc += c * Q * 12;
+  }
   // y is summed into by k_points (two terms per row)
   for (int64_t r = Qi; r < N; r += Q) y[r] = czero<R>();
   const int64_t t = Qi / q;
@@ -138,8 +146,10 @@ __device__ __forceinline__ void load_portion<double>(const cx<double>* p, cx<dou
 template <typename R>
 __global__ void k_gather(const cx<R>* __restrict__ qsrc, const int32_t* __restrict__ gpt,
                          const int32_t* __restrict__ goff, const int32_t* __restrict__ gq, const R* __restrict__ gw,
-                         int64_t ngnz, int64_t ng, cx<R>* __restrict__ grids) {
+                         int64_t ngnz, int64_t ng, cx<R>* __restrict__ grids, int64_t cs_q, int64_t cs_g) {
   constexpr int CPP = 16 / (int)sizeof(cx<R>);  // complex per 16-byte portion
+  qsrc += blockIdx.y * cs_q;  // right-hand side blockIdx.y of a batch
+  grids += blockIdx.y * cs_g;
   constexpr int NPOR = NFIELD_IN / CPP;          // portions per row: 6 or 12
   constexpr int SL = 24 / NPOR;                  // rows per load instruction: 4 or 2
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -707,6 +717,145 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
 }
 
 
+// K6-8 for a batch of kc right-hand sides: one CTA of kc warps per target
+// triangle t = blockIdx.x, warp w working on right-hand side w exactly as a
+// warp of k_points does on its own.  The near records of t stream once
+// through one ring shared by the kc warps (PB_NSTG stages of PB_KP pairs,
+// filled by thread 0 with bulk copies), so each record leaves HBM once for
+// all kc columns.  After consuming a stage every warp joins a CTA barrier
+// that also combines the bounded waits' results: the slot is then free for
+// the next copy, and all warps leave the stage loop together when a wait
+// expired.  Interpolation, testing and the row sums are per warp (per
+// column); phases 2-3 use a per-warp area beside the ring.
+constexpr int PB_NSTG = 4;
+constexpr int PB_KP = 4;
+
+__host__ __device__ constexpr int pb_ring_complex(int q) { return PB_NSTG * PB_KP * NCORR * 2 * q; }
+__host__ __device__ constexpr int pb_warp_complex(int q) { return 2 * q * NREC + 3 * q * 4; }
+__host__ __device__ constexpr size_t pb_smem_bytes(int q, int kc, size_t csize) {
+  return ((size_t)pb_ring_complex(q) + (size_t)kc * pb_warp_complex(q)) * csize + PB_NSTG * sizeof(uint64_t);
+}
+
+template <typename R, int P>
+__global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3) : 1) k_points_batch(
+    const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
+    const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
+    const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
+    const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki,
+    R ze, R zi, int has_near, const int32_t* __restrict__ valrow, cx<R>* __restrict__ y, int* __restrict__ tmo,
+    int64_t cs_grid, int64_t cs_summ, int64_t ldy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kc = blockDim.x >> 5;
+  const int64_t t = blockIdx.x;
+  grids += warp * cs_grid;  // this warp's right-hand side
+  summ += warp * cs_summ;
+  y += warp * ldy;
+  const int pairc = NCORR * 2 * q;
+  cx<R>* ring = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* recs = ring + pb_ring_complex(q) + (int64_t)warp * pb_warp_complex(q);  // [q][2][NREC]
+  cx<R>* part = recs + 2 * q * NREC;                                              // [3][q][4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + pb_ring_complex(q) + (int64_t)kc * pb_warp_complex(q));
+
+  const bool act = lane < 4 * q;
+  const int a = lane >> 2, med = (lane >> 1) & 1, h = lane & 1;
+  const int j0 = has_near ? noff[t] : 0, j1 = has_near ? noff[t + 1] : 0;
+  const int nst = (j1 - j0 + PB_KP - 1) / PB_KP;  // the same for every warp of the CTA
+  const unsigned pair_bytes = (unsigned)(pairc * sizeof(cx<R>));
+  auto issue = [&](int st) {  // thread 0 only
+    const int pj = j0 + st * PB_KP;
+    const int np = min(PB_KP, j1 - pj);
+    fence_proxy_async();
+    bulk_load(ring + (st % PB_NSTG) * PB_KP * pairc, corr + (int64_t)pj * pairc, np * pair_bytes,
+              bars + st % PB_NSTG);
+  };
+  if (nst > 0) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < PB_NSTG; ++i) mbar_init(bars + i, 1);
+      mbar_init_fence();
+      for (int st = 0; st < PB_NSTG - 1 && st < nst; ++st) issue(st);
+    }
+    __syncthreads();  // the barriers are initialised before anyone waits on them
+  }
+  const int npair = j1 - j0;
+  int src_nxt = lane < npair ? nsrc[j0 + lane] : 0, src_cur = 0;
+  cx<R> acc[NREC / 2];
+  if (act) interp_group<R, P>(grids, base, L, dL, t * q + a, med, h, n1, n2, acc);
+  if (nst > 0) {
+    const int set = h ? 2 : med;
+    const bool neg = h && med;
+    if (neg)
+#pragma unroll
+      for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
+    int st = 0;
+    bool ok = true;
+    for (; st < nst; ++st) {
+      // slot (st - 1) % PB_NSTG was released by every warp at the barrier ending stage st - 1
+      if (threadIdx.x == 0 && st + PB_NSTG - 1 < nst) issue(st + PB_NSTG - 1);
+      const bool here = __all_sync(0xffffffffu, mbar_wait(bars + st % PB_NSTG, (st / PB_NSTG) & 1));
+      if (here) {
+        const cx<R>* rs = ring + (st % PB_NSTG) * PB_KP * pairc + a * 2 + med;
+#pragma unroll
+        for (int k = 0; k < PB_KP; ++k) {
+          const int jj = st * PB_KP + k;
+          if (jj < npair) {
+            if ((jj & 31) == 0) {
+              src_cur = src_nxt;
+              src_nxt = jj + 32 + lane < npair ? nsrc[j0 + jj + 32 + lane] : 0;
+            }
+            const int64_t sj = __shfl_sync(0xffffffffu, src_cur, jj & 31);
+            if (act) {
+              cx<R> d[NCORR], sv[4];
+              load_group(summ + (3 * sj + set) * 4, sv);
+#pragma unroll
+              for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
+              near_part(d, sv, acc);
+            }
+          }
+        }
+      }
+      ok = __syncthreads_and(here) != 0;
+      if (!ok) break;
+    }
+    if (!ok && threadIdx.x == 0) {
+      // stages st .. min(st + PB_NSTG - 1, nst - 1) may still be in flight: let them land
+      for (int s2 = st; s2 < nst && s2 < st + PB_NSTG; ++s2)
+        (void)mbar_wait(bars + s2 % PB_NSTG, (s2 / PB_NSTG) & 1);
+      atomicOr(tmo, 1);
+    }
+    if (neg)
+#pragma unroll
+      for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
+  }
+  if (act) {
+    cx<R>* o = recs + (a * 2 + med) * NREC + 10 * h;
+#pragma unroll
+    for (int c = 0; c < NREC / 2; ++c) o[c] = acc[c];
+  }
+  __syncwarp();
+  if (lane < 3 * q) {
+    const int kk = lane / q, pa = lane - kk * q;
+    cx<R> o[4];
+    test_point(recs + pa * 2 * NREC, summ, tri, tp, sig, t, kk, pa, q, ke, ki, ze, zi, o);
+    cx<R>* d = part + (kk * q + pa) * 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[c] = o[c];
+  }
+  __syncwarp();
+  if (lane < 12) {
+    const int kk = lane >> 2, c = lane & 3;
+    const cx<R>* sp = part + kk * q * 4 + c;
+    cx<R> v = czero<R>();
+    for (int pa = 0; pa < q; ++pa) v += sp[pa * 4];
+    const int row = valrow[(t * 3 + kk) * 4 + c];
+    if (row >= 0) {
+      atomicAdd(&y[row].re, v.re);
+      atomicAdd(&y[row].im, v.im);
+    }
+  }
+}
+
 // ================================================================ transposed apply
 // x_bar = A^T y_bar: the stages of the apply in reverse order, each the
 // transpose of its forward map (no conjugation):
@@ -1145,12 +1294,12 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   const int64_t ng = (int64_t)n0 * n1 * n2;
   prof_mark(op, s);
   k_sources<R><<<(int)cdiv(Q, 128), 128, 0, s>>>(x, op->unk, op->cX, op->tri, op->qp, op->qw, Q, op->q, pd.summ,
-                                                 pd.qsrc, y, op->N);
+                                                 pd.qsrc, y, op->N, 0, 0);
   CK(cudaGetLastError());
   prof_mark(op, s);
   if (op->ngnz > 0) {
     k_gather<R><<<(int)cdiv(op->ngnz * 32, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent,
-                                                              gather_weights<R>(op), op->ngnz, ng, pd.src);
+                                                              gather_weights<R>(op), op->ngnz, ng, pd.src, 0, 0);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);
@@ -1165,6 +1314,51 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
                                                   op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, (R)op->ke, (R)op->ki,
                                                   (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, op->valrow, y,
                                                   op->tmo_d, nullptr, nullptr);
+    CK(cudaGetLastError());
+  }
+  prof_mark(op, s);
+  return SCABEM_OK;
+}
+
+template <typename R>
+using PointsBatchFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, const int32_t*,
+                               const int32_t*, const cx<R>*, const double*, const R*, const R*, int64_t, int, int, int,
+                               int, R, R, R, R, int, const int32_t*, cx<R>*, int*, int64_t, int64_t, int64_t);
+
+template <typename R>
+int apply_batch(scabem_op* op, const cx<R>* x, int64_t ldx, cx<R>* y, int64_t ldy, int k, cudaStream_t s) {
+  PrecData<R>& pd = pdata<R>(op);
+  if (k < 1 || k > KBATCH || k > pd.kcap) {
+    set_error("apply_batch: batch size outside the workspace capacity");
+    return SCABEM_E_ARG;
+  }
+  const int64_t nt = op->nt, Q = op->Q;
+  const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
+  const int64_t ng = (int64_t)n0 * n1 * n2;
+  prof_mark(op, s);
+  k_sources<R><<<dim3((unsigned)cdiv(Q, 128), k), 128, 0, s>>>(x, op->unk, op->cX, op->tri, op->qp, op->qw, Q,
+                                                               op->q, pd.summ, pd.qsrc, y, op->N, ldx, ldy);
+  CK(cudaGetLastError());
+  prof_mark(op, s);
+  if (op->ngnz > 0) {
+    k_gather<R><<<dim3((unsigned)cdiv(op->ngnz * 32, 256), k), 256, 0, s>>>(
+        pd.qsrc, op->gpt, op->goff, op->gent, gather_weights<R>(op), op->ngnz, ng, pd.src, col_stride_qsrc(op),
+        col_stride_grid(op));
+    CK(cudaGetLastError());
+  }
+  prof_mark(op, s);
+  int rc = fft_conv<R>(op, pd, s, false, k);
+  if (rc) return rc;
+  prof_mark(op, s);
+  {
+    const size_t sm = pb_smem_bytes(op->q, k, sizeof(cx<R>));
+    PointsBatchFn<R> fn = op->p == 2 ? k_points_batch<R, 2> : op->p == 3 ? k_points_batch<R, 3> : k_points_batch<R, 4>;
+    if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)pb_smem_bytes(op->q, KBATCH, sizeof(cx<R>))))
+      return rc_;
+    fn<<<(unsigned)nt, 32 * k, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
+                                       op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, (R)op->ke, (R)op->ki,
+                                       (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, op->valrow, y, op->tmo_d,
+                                       col_stride_grid(op), col_stride_summ(op), ldy);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);
@@ -1233,11 +1427,11 @@ int sigma_sensitivity_op(scabem_op* op, const cx<double>* x, const cx<double>* l
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
   const int64_t ng = (int64_t)n0 * n1 * n2;
   k_sources<double><<<(int)cdiv(Q, 128), 128, 0, s>>>(x, op->unk, op->cX, op->tri, op->qp, op->qw, Q, op->q,
-                                                      pd.summ, pd.qsrc, yscr, op->N);
+                                                      pd.summ, pd.qsrc, yscr, op->N, 0, 0);
   CK(cudaGetLastError());
   if (op->ngnz > 0) {
     k_gather<double><<<(int)cdiv(op->ngnz * 32, 256), 256, 0, s>>>(pd.qsrc, op->gpt, op->goff, op->gent, op->gwd,
-                                                                   op->ngnz, ng, pd.src);
+                                                                   op->ngnz, ng, pd.src, 0, 0);
     CK(cudaGetLastError());
   }
   int rc = fft_conv<double>(op, pd, s, false);
@@ -1274,3 +1468,5 @@ template int apply_one<float>(scabem_op*, const cx<float>*, cx<float>*, cudaStre
 template int apply_adjoint_one<float>(scabem_op*, const cx<float>*, cx<float>*, cudaStream_t);
 template int apply_adjoint_one<double>(scabem_op*, const cx<double>*, cx<double>*, cudaStream_t);
 template int apply_one<double>(scabem_op*, const cx<double>*, cx<double>*, cudaStream_t);
+template int apply_batch<float>(scabem_op*, const cx<float>*, int64_t, cx<float>*, int64_t, int, cudaStream_t);
+template int apply_batch<double>(scabem_op*, const cx<double>*, int64_t, cx<double>*, int64_t, int, cudaStream_t);

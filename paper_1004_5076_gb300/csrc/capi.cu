@@ -135,6 +135,51 @@ int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) 
   return SCABEM_OK;
 }
 
+}  // namespace
+
+// Grow the forward workspaces of one precision to k right-hand sides side by
+// side (column c at c * col_stride_*): the summaries, point sources, source
+// grids, axis-0 intermediates and potential grids.  New source grids and
+// intermediates start at zero (stencils and active columns leave the rest
+// untouched), as at creation.
+template <typename R>
+int ensure_batch(scabem_op* op, int k, cudaStream_t s) {
+  PrecData<R>& pd = *reinterpret_cast<PrecData<R>*>(sizeof(R) == 4 ? (void*)&op->f : (void*)&op->d);
+  if (!pd.built) {
+    set_error("operator was not built for this precision (prec_mask)");
+    return SCABEM_E_ARG;
+  }
+  if (k <= pd.kcap) return SCABEM_OK;
+  CK(cudaStreamSynchronize(s));  // nothing in flight uses the old buffers
+  cx<R>* nb[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cx<R>** cur[6] = {&pd.summ, &pd.qsrc, &pd.src, &pd.stA, &pd.stB, &pd.grid};
+  const int64_t cs[6] = {col_stride_summ(op), col_stride_qsrc(op), col_stride_grid(op), col_stride_st(op),
+                         col_stride_st(op), col_stride_grid(op)};
+  for (int i = 0; i < 6; ++i) {
+    int rc = dalloc(&nb[i], cs[i] * k);
+    if (rc) {
+      for (int j = 0; j < i; ++j) cudaFree(nb[j]);
+      return rc;
+    }
+  }
+  // column 0 keeps its contents (the single-column paths use it); the others start at zero
+  for (int i = 0; i < 6; ++i) {
+    CK(cudaMemcpyAsync(nb[i], *cur[i], sizeof(cx<R>) * cs[i], cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(nb[i] + cs[i], 0, sizeof(cx<R>) * cs[i] * (k - 1), s));
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < 6; ++i) {
+    cudaFree(*cur[i]);
+    *cur[i] = nb[i];
+  }
+  pd.kcap = k;
+  return SCABEM_OK;
+}
+template int ensure_batch<float>(scabem_op*, int, cudaStream_t);
+template int ensure_batch<double>(scabem_op*, int, cudaStream_t);
+
+namespace {
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -158,6 +203,44 @@ int apply_prec(scabem_op* op, const void* xv, void* yv, int nrhs, int64_t ld, cu
   }
   const bool xd = is_device_ptr(xv), yd = is_device_ptr(yv);
   const int64_t N = op->N;
+  if (!adjoint && nrhs > 1) {
+    // batches of up to KBATCH columns: each stage runs once per batch and the
+    // point kernel reads the near records once per batch
+    const int kb = nrhs < KBATCH ? nrhs : KBATCH;
+    int rc = ensure_batch<R>(op, kb, s);
+    if (rc) return rc;
+    if (!xd || !yd) {
+      if (pd.stage_cap < N * kb) {
+        cudaFree(pd.xs);
+        cudaFree(pd.ys);
+        pd.xs = pd.ys = nullptr;
+        pd.stage_cap = 0;
+        if ((rc = dalloc(&pd.xs, N * kb)) || (rc = dalloc(&pd.ys, N * kb))) return rc;
+        pd.stage_cap = N * kb;
+      }
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += kb) {
+      const int k = nrhs - c0 < kb ? nrhs - c0 : kb;
+      const cx<R>* xin = (const cx<R>*)xv + c0 * ld;
+      int64_t ldx = ld, ldy = ld;
+      if (!xd) {
+        for (int c = 0; c < k; ++c)
+          CK(cudaMemcpyAsync(pd.xs + c * N, xin + c * ld, sizeof(cx<R>) * N, cudaMemcpyHostToDevice, s));
+        xin = pd.xs;
+        ldx = N;
+      }
+      cx<R>* yout = yd ? (cx<R>*)yv + c0 * ld : pd.ys;
+      if (!yd) ldy = N;
+      rc = apply_batch<R>(op, xin, ldx, yout, ldy, k, s);
+      if (rc) return rc;
+      if (!yd)
+        for (int c = 0; c < k; ++c)
+          CK(cudaMemcpyAsync((cx<R>*)yv + (c0 + c) * ld, pd.ys + c * N, sizeof(cx<R>) * N, cudaMemcpyDeviceToHost,
+                             s));
+    }
+    if (!xd || !yd) CK(cudaStreamSynchronize(s));
+    return SCABEM_OK;
+  }
   if (xd && yd) {
     for (int c = 0; c < nrhs; ++c) {
       int rc = apply_col<R>(op, (const cx<R>*)xv + c * ld, (cx<R>*)yv + c * ld, adjoint, s);
@@ -363,12 +446,15 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
       set_error("media parameters and wavelength must be finite and positive");
       return SCABEM_E_ARG;
     }
-  if (!pow2_in(2 * o->n[0], 8, 1024) || !pow2_in(2 * o->n[1], 8, 128) || !pow2_in(2 * o->n[2], 8, 128)) {
-    set_error("grid: 2*n must be a power of two, in [8, 1024] along x and in [8, 128] along y and z");
+  if (!pow2_in(2 * o->n[0], 8, 1024) || !pow2_in(2 * o->n[1], 8, 512) || !pow2_in(2 * o->n[2], 8, 512)) {
+    set_error("grid: 2*n must be a power of two, in [8, 1024] along x and in [8, 512] along y and z");
     return SCABEM_E_ARG;
   }
-  if (4 * o->n[1] * o->n[2] > 4096) {
-    set_error("grid: (2 n_y)(2 n_z) must not exceed 4096");
+  // the 2-D FFT plane kernels hold a whole (y, z) plane in shared memory
+  const bool planes_fit = 2 * o->n[1] <= 128 && 2 * o->n[2] <= 128 && 4 * o->n[1] * o->n[2] <= 4096;
+  if (!planes_fit && o->transverse == 1) {
+    set_error("grid: the FFT (y, z) planes need 2 n_y, 2 n_z <= 128 and (2 n_y)(2 n_z) <= 4096; larger planes "
+              "run as direct sums (transverse = 2 or 0)");
     return SCABEM_E_ARG;
   }
   if (o->p < 2 || o->p > MAXP || !(o->q == 1 || o->q == 3 || o->q == 6 || o->q == 7) || !(o->h > 0) ||
@@ -396,6 +482,7 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   op->r_near = o->r_near;
   op->prec_mask = o->prec_mask;
   op->transverse = o->transverse;
+  op->planes_fit = planes_fit;
   for (int a = 0; a < 3; ++a) {
     op->n[a] = o->n[a];
     op->P[a] = 2 * o->n[a];

@@ -134,6 +134,9 @@ struct PrecData {
   cx<R>* xs = nullptr;    // staging for host x/y: N * nrhs_cap
   cx<R>* ys = nullptr;
   int64_t stage_cap = 0;
+  // right-hand sides the forward workspaces (summ, qsrc, src, stA, stB, grid)
+  // hold side by side, at the column strides below
+  int kcap = 1;
 };
 
 struct scabem_op {
@@ -180,6 +183,7 @@ struct scabem_op {
   // Green table for |d1| < R1, |d2| < R2 (the active box), or 2-D FFT planes
   // with ghat.  acoord[j] = (i1 - b1) << 16 | (i2 - b2) of active column j.
   int transverse = 0;
+  bool planes_fit = true;  // the (y, z) plane fits the 2-D FFT plane kernels
   bool tdirect = false;
   int R1 = 0, R2 = 0;
   int32_t* acoord = nullptr;  // nac
@@ -210,6 +214,19 @@ struct scabem_op {
   int* tmo_d = nullptr;
   Profiler prof;
 };
+
+// Column strides of the forward workspaces (complex values per right-hand side).
+inline int64_t col_stride_grid(const scabem_op* op) {  // src and grid
+  return (int64_t)NFIELD_OUT * op->n[0] * op->n[1] * op->n[2];
+}
+inline int64_t col_stride_st(const scabem_op* op) {  // stA and stB
+  return (int64_t)NFIELD_OUT * op->P[0] * op->n[1] * op->n[2];
+}
+inline int64_t col_stride_summ(const scabem_op* op) { return op->nt * 12; }
+inline int64_t col_stride_qsrc(const scabem_op* op) { return op->Q * 12; }
+// Right-hand sides the batched apply handles per pass (one CTA of that many
+// warps shares each target triangle's near-record stream).
+constexpr int KBATCH = 8;
 
 // Record the next stage-boundary event when profiling is on.
 inline void prof_mark(scabem_op* op, cudaStream_t s) {
@@ -246,10 +263,20 @@ int setup_sigma_values(scabem_op* op, const double* per_q_host, cudaStream_t s);
 int setup_sigma_bspline(scabem_op* op, double x0, double L, int axis, int ncoef, const double* coef, cudaStream_t s);
 int setup_precond(scabem_op* op, cudaStream_t s);
 int setup_gather(scabem_op* op, cudaStream_t s);
-int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed = false);
+// k right-hand sides: column c of in / out starts at c * cs_in / c * cs_out
+int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed = false,
+                  int k = 1, int64_t cs_in = 0, int64_t cs_out = 0);
 // apply.cu
 template <typename R>
 int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s);
+// y[:, c] = A x[:, c] for c < k <= pd.kcap (k <= KBATCH), x and y column-major with
+// leading dimensions ldx, ldy; every stage runs once for all k columns and the
+// point kernel reads each near record once for all of them
+template <typename R>
+int apply_batch(scabem_op* op, const cx<R>* x, int64_t ldx, cx<R>* y, int64_t ldy, int k, cudaStream_t s);
+// grow the forward workspaces of precision R to k right-hand sides
+template <typename R>
+int ensure_batch(scabem_op* op, int k, cudaStream_t s);
 // hs[p] = d(lam^T A x)/d sigma_p [per S] at every quadrature point (complex128)
 int sigma_sensitivity_op(scabem_op* op, const cx<double>* x, const cx<double>* lam, cx<double>* hs,
                          cx<double>* yscr, cudaStream_t s);
@@ -259,8 +286,10 @@ int apply_adjoint_one(scabem_op* op, const cx<R>* ybar, cx<R>* xbar, cudaStream_
 // fft.cu
 // adjoint = false: 12 sources -> 16 potentials (the apply); true: 16 -> 16,
 // each field convolved with its medium's Green function (the transposed apply)
+// ncol right-hand sides at once: column c of each workspace starts at
+// c * col_stride_*(op) (the batched apply; ncol <= the batch capacity)
 template <typename R>
-int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint);
+int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint, int ncol = 1);
 template <typename R>
 int fft3d_full(scabem_op* op, cx<R>* data, const cx<R>* const tw[3], int dir, cudaStream_t s);
 template <typename R>

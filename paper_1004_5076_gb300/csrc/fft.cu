@@ -176,10 +176,13 @@ struct Tot {
 template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS) k_axis0(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
                                                        int n_in, int P0, int C, const int32_t* __restrict__ acol,
-                                                       int nac, int CB, const cx<R>* __restrict__ tw) {
+                                                       int nac, int CB, const cx<R>* __restrict__ tw,
+                                                       int64_t cs_in, int64_t cs_out) {
   extern __shared__ unsigned char smem_raw[];
   cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* b0 = tws + P0;
+  in += blockIdx.z * cs_in;  // right-hand side blockIdx.z
+  out += blockIdx.z * cs_out;
   const int f = blockIdx.y;
   const int a0 = blockIdx.x * CB;
   const int lcb = ilog2(CB);
@@ -208,10 +211,13 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis0(const cx<R>* __restrict__
 template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS) k_axis0_pm(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
                                                           int n_out, int P0, int C, const int32_t* __restrict__ acol,
-                                                          int nac, int NC, const cx<R>* __restrict__ tw) {
+                                                          int nac, int NC, const cx<R>* __restrict__ tw,
+                                                          int64_t cs_in, int64_t cs_out) {
   extern __shared__ unsigned char smem_raw[];
   cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* b0 = tws + P0;
+  in += blockIdx.z * cs_in;  // right-hand side blockIdx.z
+  out += blockIdx.z * cs_out;
   const int grp = blockIdx.y;
   const int a0 = blockIdx.x * NC;
   const int CB = 4 * NC;
@@ -329,9 +335,11 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_planes(const cx<R>* __restric
                                                           const cx<R>* __restrict__ ghE,
                                                           const cx<R>* __restrict__ ghI, int P0, int n1, int n2,
                                                           const cx<R>* __restrict__ tw1,
-                                                          const cx<R>* __restrict__ tw2, int ident) {
+                                                          const cx<R>* __restrict__ tw2, int ident, int64_t cs) {
   extern __shared__ unsigned char smem_raw[];
   constexpr int P1 = 1 << L1, P2 = 1 << L2;
+  A += blockIdx.z * cs;  // right-hand side blockIdx.z
+  B += blockIdx.z * cs;
   constexpr int LS = P2 + 2;
   constexpr int plane = P1 * LS;
   cx<R>* t1 = reinterpret_cast<cx<R>*>(smem_raw);
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_planes(const cx<R>* __restric
 
 template <typename R>
 using PlanesFn = void (*)(const cx<R>*, cx<R>*, const cx<R>*, const cx<R>*, int, int, int, const cx<R>*,
-                          const cx<R>*, int);
+                          const cx<R>*, int, int64_t);
 
 template <typename R, int L1, int L2>
 PlanesFn<R> planes_fn() {
@@ -515,8 +523,11 @@ __device__ __forceinline__ void line64(cx<R>* v, const cx<R>* w, cx<R>* scr, int
 template <typename R>
 __global__ void __launch_bounds__(P64_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_planes64(const cx<R>* __restrict__ A, cx<R>* __restrict__ B, const cx<R>* __restrict__ ghE,
-               const cx<R>* __restrict__ ghI, int P0, const cx<R>* __restrict__ tw64, uint64_t rowmask, int ident) {
+               const cx<R>* __restrict__ ghI, int P0, const cx<R>* __restrict__ tw64, uint64_t rowmask, int ident,
+               int64_t cs) {
   constexpr int NP = 32, H = 33;
+  A += blockIdx.z * cs;  // right-hand side blockIdx.z
+  B += blockIdx.z * cs;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* W0 = reinterpret_cast<cx<R>*>(smem_raw);  // forward rows, then output 0
   cx<R>* W1 = W0 + NP * 64;                        // output 1
@@ -662,8 +673,10 @@ __global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __res
                                                               const cx<R>* __restrict__ gtI, int P0, int C,
                                                               const int32_t* __restrict__ acol,
                                                               const int32_t* __restrict__ acoord, int nac, int R1,
-                                                              int R2, int ident) {
+                                                              int R2, int ident, int64_t cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  A += blockIdx.z * cs;  // right-hand side blockIdx.z
+  B += blockIdx.z * cs;
   cx<R>* src = reinterpret_cast<cx<R>*>(smem_raw);  // [nac][8]
   cx<R>* T = src + (int64_t)nac * 8;                 // [R1][R2]
   int32_t* crd = reinterpret_cast<int32_t*>(T + R1 * R2);
@@ -806,20 +819,20 @@ int pruned_lines(int P0) {
 
 // stage C: 16 fields [field][k0][c] -> point-major grid [i0][c][16], active columns
 template <typename R>
-static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
+static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s, int ncol) {
   const int n0 = op->n[0], P0 = op->P[0];
   const int C = op->n[1] * op->n[2];
   const int nc = pruned_lines<R>(P0) >= 4 ? pruned_lines<R>(P0) / 4 : 1;  // P0 <= 1024: 4 lines fit
   const size_t sm = (size_t)P0 * (4 * nc + 1) * sizeof(cx<R>);
   if (int rc_ = set_max_smem(op->device, (const void*)k_axis0_pm<R>, (int)sm)) return rc_;
-  k_axis0_pm<R><<<dim3((unsigned)cdiv(op->nac, nc), NFIELD_OUT / 4), FFT_THREADS, sm, s>>>(
-      pd.stB, pd.grid, n0, P0, C, op->acol, (int)op->nac, nc, pd.tw[0]);
+  k_axis0_pm<R><<<dim3((unsigned)cdiv(op->nac, nc), NFIELD_OUT / 4, ncol), FFT_THREADS, sm, s>>>(
+      pd.stB, pd.grid, n0, P0, C, op->acol, (int)op->nac, nc, pd.tw[0], col_stride_st(op), col_stride_grid(op));
   CK(cudaGetLastError());
   return SCABEM_OK;
 }
 
 template <typename R>
-int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint) {
+int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint, int ncol) {
   const int n0 = op->n[0], n1 = op->n[1], n2 = op->n[2];
   const int nf = adjoint ? NFIELD_OUT : NFIELD_IN;  // fields transformed along axis 0
   const int id = adjoint ? 1 : 0;
@@ -833,28 +846,29 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint) {
   const size_t sm0 = (size_t)P0 * (cb + 1) * sizeof(cx<R>);
   // stage A
   if (int rc_ = set_max_smem(op->device, (const void*)k_axis0<R>, (int)sm0)) return rc_;
-  k_axis0<R><<<dim3((unsigned)cdiv(op->nac, cb), nf), FFT_THREADS, sm0, s>>>(
-      pd.src, pd.stA, n0, P0, C, op->acol, (int)op->nac, cb, pd.tw[0]);
+  k_axis0<R><<<dim3((unsigned)cdiv(op->nac, cb), nf, ncol), FFT_THREADS, sm0, s>>>(
+      pd.src, pd.stA, n0, P0, C, op->acol, (int)op->nac, cb, pd.tw[0], col_stride_grid(op), col_stride_st(op));
   CK(cudaGetLastError());
   prof_mark(op, s);
   // stage B
   if (op->tdirect) {
     const size_t sm = ((size_t)op->nac * 8 + (size_t)op->R1 * op->R2) * sizeof(cx<R>) + sizeof(int32_t) * op->nac;
     if (int rc_ = set_max_smem(op->device, (const void*)k_planes_direct<R>, (int)sm)) return rc_;
-    k_planes_direct<R><<<dim3(P0, 2), PD_THREADS, sm, s>>>(pd.stA, pd.stB, pd.gt[0], pd.gt[1], P0, C, op->acol,
-                                                           op->acoord, (int)op->nac, op->R1, op->R2, id);
+    k_planes_direct<R><<<dim3(P0, 2, ncol), PD_THREADS, sm, s>>>(pd.stA, pd.stB, pd.gt[0], pd.gt[1], P0, C,
+                                                                 op->acol, op->acoord, (int)op->nac, op->R1, op->R2,
+                                                                 id, col_stride_st(op));
     CK(cudaGetLastError());
     prof_mark(op, s);
-    return axis0_inverse(op, pd, s);
+    return axis0_inverse(op, pd, s, ncol);
   }
   if (P1 == 64 && P2 == 64) {
     const size_t sm = ((size_t)2 * 32 * 64 + (size_t)(P64_THREADS / 8) * P64_SCR) * sizeof(cx<R>);
     if (int rc_ = set_max_smem(op->device, (const void*)k_planes64<R>, (int)sm)) return rc_;
-    k_planes64<R><<<dim3(P0, nf), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1],
-                                                        op->rowmask, id);
+    k_planes64<R><<<dim3(P0, nf, ncol), P64_THREADS, sm, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, pd.tw[1],
+                                                              op->rowmask, id, col_stride_st(op));
     CK(cudaGetLastError());
     prof_mark(op, s);
-    return axis0_inverse(op, pd, s);
+    return axis0_inverse(op, pd, s, ncol);
   }
   const size_t sm1 = ((size_t)P1 + P2 + 2 * (size_t)P1 * (P2 + 2)) * sizeof(cx<R>);
   PlanesFn<R> fn = planes_kernel<R>(ilog2(P1), ilog2(P2));
@@ -863,16 +877,16 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint) {
     return SCABEM_E_ARG;
   }
   if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm1)) return rc_;
-  fn<<<dim3(P0, nf), PLANE_THREADS, sm1, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, n1, n2, pd.tw[1], pd.tw[2],
-                                            id);
+  fn<<<dim3(P0, nf, ncol), PLANE_THREADS, sm1, s>>>(pd.stA, pd.stB, pd.ghat[0], pd.ghat[1], P0, n1, n2, pd.tw[1],
+                                                  pd.tw[2], id, col_stride_st(op));
   CK(cudaGetLastError());
   prof_mark(op, s);
-  return axis0_inverse(op, pd, s);
+  return axis0_inverse(op, pd, s, ncol);
 }
 
 template int make_twiddles<float>(cx<float>*, int, cudaStream_t);
 template int make_twiddles<double>(cx<double>*, int, cudaStream_t);
 template int fft3d_full<double>(scabem_op*, cx<double>*, const cx<double>* const[3], int, cudaStream_t);
 template int fft_axis_full<double>(scabem_op*, cx<double>*, int, const cx<double>*, int, cudaStream_t);
-template int fft_conv<float>(scabem_op*, PrecData<float>&, cudaStream_t, bool);
-template int fft_conv<double>(scabem_op*, PrecData<double>&, cudaStream_t, bool);
+template int fft_conv<float>(scabem_op*, PrecData<float>&, cudaStream_t, bool, int);
+template int fft_conv<double>(scabem_op*, PrecData<double>&, cudaStream_t, bool, int);

@@ -774,9 +774,12 @@ __global__ void k_precond(const double* __restrict__ tri, const double* __restri
 // share the same index set).
 // transposed = 1 applies (Binv_e)^T, the inverse blocks of A^T.
 __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __restrict__ eunk, int64_t ne,
-                                const cd* __restrict__ in, cd* __restrict__ out, int transposed) {
+                                const cd* __restrict__ in, cd* __restrict__ out, int transposed, int64_t cs_in,
+                                int64_t cs_out) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= ne) return;
+  in += blockIdx.y * cs_in;  // right-hand side blockIdx.y
+  out += blockIdx.y * cs_out;
   const int nb = eunk[3 * e + 2] < 0 ? 2 : 3;
   cd v[3];
   for (int i = 0; i < nb; ++i) v[i] = in[eunk[3 * e + i]];
@@ -833,7 +836,7 @@ int setup_gather(scabem_op* op, cudaStream_t s) {
   for (int64_t c = 0; c < C; ++c)
     if (colact[c]) {
       acol.push_back((int32_t)c);
-      op->rowmask |= 1ull << (c / n2);
+      if (c / n2 < 64) op->rowmask |= 1ull << (c / n2);  // read only by the 64 x 64 plane kernel
     }
   op->nac = (int64_t)acol.size();
   if (op->nac > 0) {
@@ -855,8 +858,18 @@ int setup_gather(scabem_op* op, cudaStream_t s) {
     CK(cudaMalloc(&op->acoord, sizeof(int32_t) * op->nac));
     CK(cudaMemcpyAsync(op->acoord, coord.data(), sizeof(int32_t) * op->nac, cudaMemcpyHostToDevice, s));
   }
-  op->tdirect = op->transverse == 2 ||
+  op->tdirect = op->transverse == 2 || !op->planes_fit ||
                 (op->transverse == 0 && op->nac * op->nac <= 16 * (int64_t)op->P[1] * op->P[2]);
+  if (op->tdirect) {
+    // one CTA of the direct (y, z) sums holds the active columns' sources and the table
+    const size_t csz = (op->prec_mask & 2) ? sizeof(cx<double>) : sizeof(cx<float>);
+    const size_t sm = ((size_t)op->nac * 8 + (size_t)op->R1 * op->R2) * csz + sizeof(int32_t) * op->nac;
+    if (sm > 227 * 1024) {
+      set_error("grid: " + std::to_string(op->nac) + " active (y, z) columns are too many for the direct sums (" +
+                std::to_string(sm) + " bytes of shared memory)");
+      return SCABEM_E_ARG;
+    }
+  }
   const int64_t ne = Q * p3;
   CK(cudaMalloc(&op->gpt, sizeof(int32_t) * (pts.size() + 1)));
   CK(cudaMalloc(&op->goff, sizeof(int32_t) * coff.size()));
@@ -887,8 +900,10 @@ int setup_precond(scabem_op* op, cudaStream_t s) {
   return SCABEM_OK;
 }
 
-int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed) {
-  k_precond_apply<<<(int)cdiv(op->ne, 256), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out, transposed ? 1 : 0);
+int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed, int k,
+                  int64_t cs_in, int64_t cs_out) {
+  k_precond_apply<<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out,
+                                                                       transposed ? 1 : 0, cs_in, cs_out);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }

@@ -17,6 +17,7 @@
 //   on-axis field into forward and backward waves (Table 1's reflection).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -236,63 +237,81 @@ __global__ void k_rows_out(const cd* __restrict__ val, const int32_t* __restrict
   y[i] = mk((R)v.re, (R)v.im);
 }
 
-// ---------------------------------------------------------------- BLAS-1 style kernels (FP64)
-constexpr int DOT_THREADS = 256;
-constexpr int DOT_BLOCKS = 304;  // 2 x 152 SMs
+// ---------------------------------------------------------------- batched GMRES (FP64 Krylov work)
+// K <= KBATCH right-hand sides run in lockstep.  One batched operator apply
+// per Arnoldi step serves all K (the point kernel reads the near records
+// once for them); everything else in the step stays on the device: the
+// norms, classical Gram-Schmidt whose second pass runs per column only when
+// the first one cancels most of w (|w'| < |w| / sqrt 2, the Daniel-Gragg-
+// Kaufman-Stewart test), the Givens update of the Hessenberg least squares
+// and the convergence test.  The host reads one host-mapped word per step,
+// one step behind the device, so the GPU never waits for it.  Column c of
+// every K-column work array starts at c * N; the basis of column c holds
+// m + 1 vectors of N from c * (m + 1) * N.
+constexpr int BG_THREADS = 256;
+constexpr int BG_BLOCKS = 152;  // row blocks per column of the reductions (one per SM)
+constexpr int BG_TC = 8;        // basis vectors per tile of the dot products
+constexpr int FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2;
 
-// Tall-skinny dot products for the Arnoldi step: part[b * ldp + c] = sum
-// over row block b of conj(V[:, c]) . w, for the tile of DOT_TC columns
-// c0 = blockIdx.y * DOT_TC (w is read once per tile).
-constexpr int DOT_TC = 8;
-__global__ void __launch_bounds__(DOT_THREADS) k_dots(const cd* __restrict__ V, int64_t ldv, int nv,
+// part[(c * rb + b) * ldp + col] = sum over row block b of conj(V_c[:, col]) . w_c,
+// col in the tile blockIdx.y; skipped for columns with need[c] == 0
+__global__ void __launch_bounds__(BG_THREADS) k_bdots(const cd* __restrict__ V, int64_t csV, int nv,
                                                       const cd* __restrict__ w, int64_t N, cd* __restrict__ part,
-                                                      int ldp) {
-  __shared__ double sm[DOT_THREADS / 32][2 * DOT_TC];
-  const int c0 = blockIdx.y * DOT_TC;
-  const int nc = min(DOT_TC, nv - c0);
-  double ar[DOT_TC], ai[DOT_TC];
+                                                      int ldp, const int* __restrict__ need) {
+  const int c = blockIdx.z;
+  if (need && !need[c]) return;  // the whole block
+  V += c * csV;
+  w += c * N;
+  __shared__ double sm[BG_THREADS / 32][2 * BG_TC];
+  const int c0 = blockIdx.y * BG_TC;
+  const int nc = min(BG_TC, nv - c0);
+  double ar[BG_TC], ai[BG_TC];
 #pragma unroll
-  for (int c = 0; c < DOT_TC; ++c) ar[c] = ai[c] = 0.0;
+  for (int k = 0; k < BG_TC; ++k) ar[k] = ai[k] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const cd b = w[i];
 #pragma unroll
-    for (int c = 0; c < DOT_TC; ++c)
-      if (c < nc) {
-        const cd a = V[(int64_t)(c0 + c) * ldv + i];
-        ar[c] += a.re * b.re + a.im * b.im;
-        ai[c] += a.re * b.im - a.im * b.re;
+    for (int k = 0; k < BG_TC; ++k)
+      if (k < nc) {
+        const cd a = V[(int64_t)(c0 + k) * N + i];
+        ar[k] += a.re * b.re + a.im * b.im;
+        ai[k] += a.re * b.im - a.im * b.re;
       }
   }
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-  for (int c = 0; c < DOT_TC; ++c)
+  for (int k = 0; k < BG_TC; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      ar[c] += __shfl_xor_sync(0xffffffffu, ar[c], o);
-      ai[c] += __shfl_xor_sync(0xffffffffu, ai[c], o);
+      ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
+      ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], o);
     }
   if (lane == 0)
 #pragma unroll
-    for (int c = 0; c < DOT_TC; ++c) {
-      sm[wp][2 * c] = ar[c];
-      sm[wp][2 * c + 1] = ai[c];
+    for (int k = 0; k < BG_TC; ++k) {
+      sm[wp][2 * k] = ar[k];
+      sm[wp][2 * k + 1] = ai[k];
     }
   __syncthreads();
   if (threadIdx.x < 2 * nc) {
     double v = 0.0;
-    for (int k = 0; k < DOT_THREADS / 32; ++k) v += sm[k][threadIdx.x];
-    double* o = reinterpret_cast<double*>(part + (int64_t)blockIdx.x * ldp + c0);
+    for (int k = 0; k < BG_THREADS / 32; ++k) v += sm[k][threadIdx.x];
+    double* o = reinterpret_cast<double*>(part + ((int64_t)c * gridDim.x + blockIdx.x) * ldp + c0);
     o[threadIdx.x] = v;
   }
 }
 
-__global__ void k_reduce_parts(const cd* __restrict__ part, int nb, int nv, cd* __restrict__ out) {
-  __shared__ double sre[DOT_THREADS], sim[DOT_THREADS];
-  const int c = blockIdx.x;
+// h[c * ldh + col] = sum over the rb row blocks (grid: nv x K)
+__global__ void k_breduce(const cd* __restrict__ part, int rb, int ldp, cd* __restrict__ h, int ldh,
+                          const int* __restrict__ need) {
+  const int col = blockIdx.x, c = blockIdx.y;
+  if (need && !need[c]) return;
+  __shared__ double sre[BG_THREADS], sim[BG_THREADS];
   double ar = 0.0, ai = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    ar += part[(int64_t)b * nv + c].re;
-    ai += part[(int64_t)b * nv + c].im;
+  for (int b = threadIdx.x; b < rb; b += blockDim.x) {
+    const cd v = part[((int64_t)c * rb + b) * ldp + col];
+    ar += v.re;
+    ai += v.im;
   }
   sre[threadIdx.x] = ar;
   sim[threadIdx.x] = ai;
@@ -304,23 +323,30 @@ __global__ void k_reduce_parts(const cd* __restrict__ part, int nb, int nv, cd* 
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[c] = mk(sre[0], sim[0]);
+  if (threadIdx.x == 0) h[(int64_t)c * ldh + col] = mk(sre[0], sim[0]);
 }
 
-// w -= V h, and nparts[b] = sum over block b's rows of |w|^2 (new w)
-__global__ void __launch_bounds__(DOT_THREADS) k_vsub_norm(const cd* __restrict__ V, int64_t ldv, int nv,
-                                                           const cd* __restrict__ h, cd* __restrict__ w, int64_t N,
-                                                           double* __restrict__ nparts) {
-  __shared__ double sm[DOT_THREADS / 32];
+// w_c -= V_c h_c (nv basis vectors; none for a plain norm), and the squared
+// norm of the new w_c per row block (grid: BG_BLOCKS x K)
+__global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cd* __restrict__ V, int64_t csV, int nv,
+                                                           const cd* __restrict__ h, int ldh, cd* __restrict__ w,
+                                                           int64_t N, double* __restrict__ nparts,
+                                                           const int* __restrict__ need) {
+  const int c = blockIdx.y;
+  if (need && !need[c]) return;
+  V += c * csV;
+  w += c * N;
+  h += (int64_t)c * ldh;
+  __shared__ double sm[BG_THREADS / 32];
   double nn = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     cd acc = w[i];
-    for (int c = 0; c < nv; ++c) {
-      const cd a = V[(int64_t)c * ldv + i], b = h[c];
+    for (int k = 0; k < nv; ++k) {
+      const cd a = V[(int64_t)k * N + i], b = h[k];
       acc.re -= a.re * b.re - a.im * b.im;
       acc.im -= a.re * b.im + a.im * b.re;
     }
-    w[i] = acc;
+    if (nv > 0) w[i] = acc;
     nn += acc.re * acc.re + acc.im * acc.im;
   }
 #pragma unroll
@@ -329,285 +355,408 @@ __global__ void __launch_bounds__(DOT_THREADS) k_vsub_norm(const cd* __restrict_
   __syncthreads();
   if (threadIdx.x == 0) {
     double v = 0.0;
-    for (int k = 0; k < DOT_THREADS / 32; ++k) v += sm[k];
-    nparts[blockIdx.x] = v;
+    for (int k = 0; k < BG_THREADS / 32; ++k) v += sm[k];
+    nparts[(int64_t)c * gridDim.x + blockIdx.x] = v;
   }
 }
 
-// out->re = sqrt(sum of nparts), out->im = 0 (one block)
-__global__ void k_norm_fin(const double* __restrict__ nparts, int nb, cd* __restrict__ out) {
-  __shared__ double sm[DOT_THREADS];
+// out[c * ostride] = sqrt(sum of column c's row-block parts) (grid: K).  With
+// set_need, also need[c] = (out < |w| before the pass / sqrt 2), |w| before
+// read from out[c * ostride - 1] (the DGKS test after the first pass).
+__global__ void k_bnorm_fin(const double* __restrict__ nparts, int nb, double* __restrict__ out, int ostride,
+                            const int* __restrict__ need, int* __restrict__ set_need) {
+  const int c = blockIdx.x;
+  if (need && !need[c]) return;
+  __shared__ double sm[BG_THREADS];
   double v = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += nparts[b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += nparts[(int64_t)c * nb + b];
   sm[threadIdx.x] = v;
   __syncthreads();
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = mk(sqrt(fmax(sm[0], 0.0)), 0.0);
-}
-
-// v = w / |w| with the norm read from the device (zero when it vanishes)
-__global__ void k_scale_dev(const cd* __restrict__ w, const cd* __restrict__ nrm, cd* __restrict__ v, int64_t N) {
-  const double n = nrm->re;
-  const double s = n > 1e-300 ? 1.0 / n : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = s * w[i];
-}
-
-// w -= V h   (h on the device, nv entries)
-__global__ void k_vsub(const cd* __restrict__ V, int64_t ldv, int nv, const cd* __restrict__ h, cd* __restrict__ w,
-                       int64_t N) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    cd acc = w[i];
-    for (int c = 0; c < nv; ++c) {
-      const cd a = V[(int64_t)c * ldv + i], b = h[c];
-      acc.re -= a.re * b.re - a.im * b.im;
-      acc.im -= a.re * b.im + a.im * b.re;
-    }
-    w[i] = acc;
+  if (threadIdx.x == 0) {
+    const double n = sqrt(fmax(sm[0], 0.0));
+    out[(int64_t)c * ostride] = n;
+    if (set_need) set_need[c] = !(n >= 0.70710678118654752 * out[(int64_t)c * ostride - 1]);
   }
 }
 
-__global__ void k_scale_to(const cd* __restrict__ w, double s, cd* __restrict__ v, int64_t N) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = s * w[i];
-}
-__global__ void k_sub(const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ o, int64_t N) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = a[i] - b[i];
-}
-__global__ void k_add(cd* __restrict__ x, const cd* __restrict__ d, int64_t N) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += d[i];
-}
-__global__ void k_to_f(const cd* __restrict__ a, cx<float>* __restrict__ o, int64_t N) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = mk((float)a[i].re, (float)a[i].im);
-}
-__global__ void k_from_f(const cx<float>* __restrict__ a, cd* __restrict__ o, int64_t N) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = mk((double)a[i].re, (double)a[i].im);
-}
-
-struct Work {
-  cd* V = nullptr;     // N x (m+1)
-  cd* w = nullptr;     // N
-  cd* t = nullptr;     // N
-  cd* part = nullptr;  // DOT_BLOCKS x (m+1)
-  cd* h = nullptr;     // 2 (m+1) + 1: both Gram-Schmidt passes' coefficients, then the norm
-  double* nparts = nullptr;  // DOT_BLOCKS
-  cd* z = nullptr;     // N, preconditioned Krylov vector
-  cd* u = nullptr;     // N, solution in the preconditioned variables
-  cx<float>* xf = nullptr;
-  cx<float>* yf = nullptr;
-  bool tr = false;  // solve with A^T
-  ~Work() {
-    cudaFree(z);
-    cudaFree(u);
-    cudaFree(V);
-    cudaFree(w);
-    cudaFree(t);
-    cudaFree(part);
-    cudaFree(h);
-    cudaFree(nparts);
-    cudaFree(xf);
-    cudaFree(yf);
-  }
+// Per-column state of the lockstep solver, on the device.
+struct BState {
+  cd* H;        // K * m * (m + 1): column j of column c's Hessenberg at (c m + j) (m + 1)
+  cd* cs;       // K * m Givens cosines
+  cd* sn;       // K * m Givens sines
+  cd* g;        // K * (m + 1) rotated right-hand side of the least squares
+  cd* y;        // K * m least-squares solution
+  cd* h1;       // K * (m + 1) first Gram-Schmidt pass
+  cd* h2;       // K * (m + 1) second pass
+  double* nrm;  // K * 4: |w| before, after pass 1, after pass 2; beta of the cycle
+  double* rn0;  // K initial residual norms
+  double* est;  // K residual estimates |g_{j+1}| / rn0
+  int* need;    // K second pass wanted
+  int* act;     // K still iterating in this cycle
+  int* jc;      // K basis vectors in this cycle's least squares
+  int* iters;   // K iterations so far
 };
 
-// h_dev[c] = conj(V[:, c]) . w for c < nv, left on the device.  About
-// DOT_BLOCKS blocks in all: row blocks x column tiles, so that each thread
-// covers several rows before the block reduction.
-int dots_dev(const cd* V, int64_t ldv, int nv, const cd* w, int64_t N, Work& W, cd* h_dev, cudaStream_t s) {
-  const int tiles = (int)cdiv(nv, DOT_TC);
-  int rb = DOT_BLOCKS / tiles;
-  if (rb < 8) rb = 8;
-  k_dots<<<dim3(rb, tiles), DOT_THREADS, 0, s>>>(V, ldv, nv, w, N, W.part, nv);
-  CK(cudaGetLastError());
-  k_reduce_parts<<<nv, DOT_THREADS, 0, s>>>(W.part, rb, nv, h_dev);
-  CK(cudaGetLastError());
-  return SCABEM_OK;
-}
-
-// out->re = |w| (device)
-int norm_dev(const cd* w, int64_t N, Work& W, cd* out, cudaStream_t s) {
-  k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(nullptr, N, 0, nullptr, const_cast<cd*>(w), N, W.nparts);
-  CK(cudaGetLastError());
-  k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, out);
-  CK(cudaGetLastError());
-  return SCABEM_OK;
-}
-
-int dots(const cd* V, int64_t ldv, int nv, const cd* w, int64_t N, Work& W, cudaStream_t s, std::vector<cd>& out) {
-  int rc = dots_dev(V, ldv, nv, w, N, W, W.h, s);
-  if (rc) return rc;
-  out.resize(nv);
-  CK(cudaMemcpyAsync(out.data(), W.h, sizeof(cd) * nv, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  return SCABEM_OK;
-}
-
-int norm2(const cd* w, int64_t N, Work& W, cudaStream_t s, double& nrm) {
-  std::vector<cd> d;
-  int rc = dots(w, N, 1, w, N, W, s, d);
-  if (rc) return rc;
-  nrm = std::sqrt(std::max(d[0].re, 0.0));
-  return SCABEM_OK;
-}
-
-// y = A v in FP64 storage, arithmetic in `prec`.
-int op_apply64(scabem_op* op, const cd* v, cd* y, int prec, Work& W, cudaStream_t s) {
-  const int64_t N = op->N;
-  if (prec == SCABEM_C128) return W.tr ? apply_adjoint_one<double>(op, v, y, s) : apply_one<double>(op, v, y, s);
-  k_to_f<<<DOT_BLOCKS, 256, 0, s>>>(v, W.xf, N);
-  CK(cudaGetLastError());
-  int rc = W.tr ? apply_adjoint_one<float>(op, W.xf, W.yf, s) : apply_one<float>(op, W.xf, W.yf, s);
-  if (rc) return rc;
-  k_from_f<<<DOT_BLOCKS, 256, 0, s>>>(W.yf, y, N);
-  CK(cudaGetLastError());
-  return SCABEM_OK;
-}
-
-// Restarted GMRES for A d = r from d = 0 (d, r on the device).  Returns the
-// status and accumulates iterations.
-int gmres(scabem_op* op, const cd* r, cd* d, int prec, double tol, int m, int maxit, Work& W, cudaStream_t s,
-          int& iters, double& relres_est) {
-  const int64_t N = op->N;
-  CK(cudaMemsetAsync(d, 0, sizeof(cd) * N, s));
-  CK(cudaMemsetAsync(W.u, 0, sizeof(cd) * N, s));
-  double rn0;
-  int rc = norm2(r, N, W, s, rn0);
-  if (rc) return rc;
-  if (!std::isfinite(rn0)) {
-    set_error("non-finite right-hand side");
-    return SCABEM_E_NONFINITE;
-  }
-  relres_est = 0.0;
-  if (rn0 == 0.0) return SCABEM_OK;
-  // working residual: t = r - A d (d accumulates over restarts)
-  CK(cudaMemcpyAsync(W.t, r, sizeof(cd) * N, cudaMemcpyDeviceToDevice, s));
-  std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hv, hv2, hbuf;
-  double beta = rn0;
-  while (true) {
-    k_scale_to<<<DOT_BLOCKS, 256, 0, s>>>(W.t, 1.0 / beta, W.V, N);
-    CK(cudaGetLastError());
-    for (auto& z : g) z = mk(0.0, 0.0);
-    g[0] = mk(beta, 0.0);
-    int j = 0;
-    bool done = false;
-    for (; j < m && iters < maxit; ++j) {
-      ++iters;
-      // right preconditioning: w = A P^-1 v_j
-      rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr);
-      if (rc) return rc;
-      rc = op_apply64(op, W.z, W.w, prec, W, s);
-      if (rc) return rc;
-      // classical Gram-Schmidt on the device, repeated only when the first
-      // pass cancels most of w (|w'| < |w| / sqrt 2, the Daniel-Gragg-
-      // Kaufman-Stewart test); the norms and coefficients come to the host
-      // in one copy per pass, and the next basis vector is scaled on the device
-      cd* h1 = W.h;
-      cd* h2 = W.h + (m + 1);
-      cd* hn0 = W.h + 2 * (m + 1);  // |w| before, after pass 1, after pass 2
-      cd* hn1 = hn0 + 1;
-      cd* hn2 = hn0 + 2;
-      rc = norm_dev(W.w, N, W, hn0, s);
-      if (rc) return rc;
-      rc = dots_dev(W.V, N, j + 1, W.w, N, W, h1, s);
-      if (rc) return rc;
-      k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h1, W.w, N, W.nparts);
-      CK(cudaGetLastError());
-      k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, hn1);
-      CK(cudaGetLastError());
-      hbuf.resize(2 * (m + 1) + 3);
-      CK(cudaMemcpyAsync(hbuf.data(), W.h, sizeof(cd) * (j + 1), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(hbuf.data() + 2 * (m + 1), hn0, sizeof(cd) * 2, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      hv.assign(hbuf.begin(), hbuf.begin() + j + 1);
-      double hn = hbuf[2 * (m + 1) + 1].re;
-      const cd* hnd = hn1;
-      if (!(hn >= 0.70710678118654752 * hbuf[2 * (m + 1)].re)) {
-        rc = dots_dev(W.V, N, j + 1, W.w, N, W, h2, s);
-        if (rc) return rc;
-        k_vsub_norm<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.V, N, j + 1, h2, W.w, N, W.nparts);
-        CK(cudaGetLastError());
-        k_norm_fin<<<1, DOT_THREADS, 0, s>>>(W.nparts, DOT_BLOCKS, hn2);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(hbuf.data() + (m + 1), h2, sizeof(cd) * (j + 1), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(hbuf.data() + 2 * (m + 1) + 2, hn2, sizeof(cd), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        hv2.assign(hbuf.begin() + (m + 1), hbuf.begin() + (m + 1) + j + 1);
-        hn = hbuf[2 * (m + 1) + 2].re;
-        hnd = hn2;
-      } else {
-        hv2.assign(j + 1, mk(0.0, 0.0));
-      }
-      if (j + 1 < m) {
-        k_scale_dev<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(W.w, hnd, W.V + (int64_t)(j + 1) * N, N);
-        CK(cudaGetLastError());
-      }
-      if (!std::isfinite(hn)) {
-        set_error("non-finite Krylov vector");
-        return SCABEM_E_NONFINITE;
-      }
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i] + hv2[i];
-      H[(size_t)(j + 1) * m + j] = mk(hn, 0.0);
-      // apply previous rotations
-      for (int i = 0; i < j; ++i) {
-        const cd a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = conj(cs[i]) * a + conj(sn[i]) * b;
-        H[(size_t)(i + 1) * m + j] = -(sn[i] * a) + cs[i] * b;
-      }
-      const cd a = H[(size_t)j * m + j];
-      const double bre = hn;
-      const double den = std::sqrt(a.re * a.re + a.im * a.im + bre * bre);
-      if (den == 0.0) {
-        set_error("GMRES breakdown");
-        return SCABEM_E_BREAKDOWN;
-      }
+// The Givens step of Arnoldi column j for every active column (one thread
+// per right-hand side): Hessenberg column j = h1 + h2 (the second pass when
+// taken) and |w|, the previous rotations, a new rotation, the rotated
+// right-hand side and the residual estimate; a column stops when the
+// estimate reaches tol or w vanishes.  word[0] = columns still active,
+// word[1] |= flags (host-mapped).
+__global__ void k_givens(BState S, int j, int m, int K, double tol, int* __restrict__ word) {
+  const int c = threadIdx.x;
+  bool on = false;
+  if (c < K && S.act[c]) {
+    const cd* a1 = S.h1 + (int64_t)c * (m + 1);
+    const cd* a2 = S.h2 + (int64_t)c * (m + 1);
+    const bool two = S.need[c] != 0;
+    const double hn = two ? S.nrm[4 * c + 2] : S.nrm[4 * c + 1];
+    cd* col = S.H + ((int64_t)c * m + j) * (m + 1);
+    cd* cs = S.cs + (int64_t)c * m;
+    cd* sn = S.sn + (int64_t)c * m;
+    cd* g = S.g + (int64_t)c * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = two ? a1[i] + a2[i] : a1[i];
+    for (int i = 0; i < j; ++i) {
+      const cd a = col[i], b = col[i + 1];
+      col[i] = conj(cs[i]) * a + conj(sn[i]) * b;
+      col[i + 1] = -(sn[i] * a) + cs[i] * b;
+    }
+    const cd a = col[j];
+    const double den = sqrt(a.re * a.re + a.im * a.im + hn * hn);
+    on = true;
+    if (!isfinite(hn) || !isfinite(den)) {
+      atomicOr(word + 1, FLAG_NONFINITE);
+      on = false;
+    } else if (den == 0.0) {
+      atomicOr(word + 1, FLAG_BREAKDOWN);
+      on = false;
+    } else {
       cs[j] = mk(a.re / den, a.im / den);
-      sn[j] = mk(bre / den, 0.0);
-      H[(size_t)j * m + j] = mk(den, 0.0);
-      H[(size_t)(j + 1) * m + j] = mk(0.0, 0.0);
+      sn[j] = mk(hn / den, 0.0);
+      col[j] = mk(den, 0.0);
+      col[j + 1] = mk(0.0, 0.0);
       const cd gj = g[j];
       g[j] = conj(cs[j]) * gj;
       g[j + 1] = -(sn[j] * gj);
-      relres_est = std::sqrt(g[j + 1].re * g[j + 1].re + g[j + 1].im * g[j + 1].im) / rn0;
-      if (hn <= 1e-300 || relres_est <= tol) {
-        ++j;
-        done = true;
-        break;
+      const double e = sqrt(g[j + 1].re * g[j + 1].re + g[j + 1].im * g[j + 1].im) / S.rn0[c];
+      S.est[c] = e;
+      S.jc[c] = j + 1;
+      S.iters[c] += 1;
+      if (hn <= 1e-300 || e <= tol) on = false;
+    }
+    if (!on) S.act[c] = 0;
+  }
+  const int n = __syncthreads_count(on);
+  if (threadIdx.x == 0) word[0] = n;
+}
+
+// v_c,j+1 = w_c / |w_c| (|w| after the last pass; zero when it vanishes)
+__global__ void k_bscale(const cd* __restrict__ w, cd* __restrict__ V, int64_t csV, int j1, const double* __restrict__ nrm,
+                         const int* __restrict__ need, int64_t N) {
+  const int c = blockIdx.y;
+  const double n = need[c] ? nrm[4 * c + 2] : nrm[4 * c + 1];
+  const double s = n > 1e-300 ? 1.0 / n : 0.0;
+  w += c * N;
+  V += c * csV + (int64_t)j1 * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    V[i] = s * w[i];
+}
+
+// start of a cycle for the active columns: v_c,0 = t_c / beta_c, g_c = beta_c e_1
+__global__ void k_bstart(const cd* __restrict__ t, cd* __restrict__ V, int64_t csV, BState S, int m, int64_t N) {
+  const int c = blockIdx.y;
+  if (!S.act[c]) return;
+  const double beta = S.nrm[4 * c + 3];
+  const double s = beta > 1e-300 ? 1.0 / beta : 0.0;
+  t += c * N;
+  V += c * csV;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    V[i] = s * t[i];
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) S.g[(int64_t)c * (m + 1) + i] = mk(i == 0 ? beta : 0.0, 0.0);
+    if (threadIdx.x == 0) S.jc[c] = 0;
+  }
+}
+
+// least squares of the cycle: y_c = R^-1 g_c over its jc[c] columns (one thread per column)
+__global__ void k_backsub(BState S, int m, int K) {
+  const int c = threadIdx.x;
+  if (c >= K) return;
+  const int j = S.jc[c];
+  const cd* H = S.H + (int64_t)c * m * (m + 1);
+  const cd* g = S.g + (int64_t)c * (m + 1);
+  cd* y = S.y + (int64_t)c * m;
+  for (int i = j - 1; i >= 0; --i) {
+    cd acc = g[i];
+    for (int l = i + 1; l < j; ++l) acc -= H[(int64_t)l * (m + 1) + i] * y[l];
+    const cd hd = H[(int64_t)i * (m + 1) + i];
+    const double dd = hd.re * hd.re + hd.im * hd.im;
+    y[i] = mk((acc.re * hd.re + acc.im * hd.im) / dd, (acc.im * hd.re - acc.re * hd.im) / dd);
+  }
+}
+
+// u_c += V_c y_c over the cycle's jc[c] basis vectors
+__global__ void k_bupdate(const cd* __restrict__ V, int64_t csV, BState S, int m, cd* __restrict__ u, int64_t N) {
+  const int c = blockIdx.y;
+  const int j = S.jc[c];
+  if (j == 0) return;
+  V += c * csV;
+  u += c * N;
+  const cd* y = S.y + (int64_t)c * m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    cd acc = u[i];
+    for (int l = 0; l < j; ++l) cfma(acc, V[(int64_t)l * N + i], y[l]);
+    u[i] = acc;
+  }
+}
+
+__global__ void k_sub(const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = a[i] - b[i];
+}
+__global__ void k_add(cd* __restrict__ x, const cd* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+__global__ void k_to_f(const cd* __restrict__ a, cx<float>* __restrict__ o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = mk((float)a[i].re, (float)a[i].im);
+}
+__global__ void k_from_f(const cx<float>* __restrict__ a, cd* __restrict__ o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = mk((double)a[i].re, (double)a[i].im);
+}
+
+constexpr int EW_BLOCKS = 4 * 152;  // element-wise kernels: 4 blocks of 256 threads per SM
+
+struct BWork {
+  int K = 0, m = 0;
+  int64_t N = 0;
+  bool tr = false;
+  cd* V = nullptr;           // K (m + 1) N basis
+  cd* w = nullptr;           // K N
+  cd* z = nullptr;           // K N preconditioned basis vector
+  cd* u = nullptr;           // K N solution in the preconditioned variables
+  cd* t = nullptr;           // K N working residual
+  cx<float>* zf = nullptr;   // K N complex64 operator input / output
+  cx<float>* wf = nullptr;
+  cd* part = nullptr;        // K BG_BLOCKS (m + 1)
+  double* nparts = nullptr;  // K BG_BLOCKS
+  BState S;
+  int* word_h = nullptr;     // host-mapped {active columns, flags}
+  int* word_d = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<void*> owned;
+  template <typename T>
+  int get(T** p, int64_t count) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (GMRES workspace)");
+    owned.push_back(*p);
+    return SCABEM_OK;
+  }
+  ~BWork() {
+    for (void* p : owned) cudaFree(p);
+    if (word_h) cudaFreeHost(word_h);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  int init(int k, int mm, int64_t n, bool c64) {
+    K = k;
+    m = mm;
+    N = n;
+    int rc;
+    if ((rc = get(&V, (int64_t)K * (m + 1) * N)) || (rc = get(&w, K * N)) || (rc = get(&z, K * N)) ||
+        (rc = get(&u, K * N)) || (rc = get(&t, K * N)) || (rc = get(&part, (int64_t)K * BG_BLOCKS * (m + 1))) ||
+        (rc = get(&nparts, (int64_t)K * BG_BLOCKS)) || (rc = get(&S.H, (int64_t)K * m * (m + 1))) ||
+        (rc = get(&S.cs, K * m)) || (rc = get(&S.sn, K * m)) || (rc = get(&S.g, K * (m + 1))) ||
+        (rc = get(&S.y, K * m)) || (rc = get(&S.h1, K * (m + 1))) || (rc = get(&S.h2, K * (m + 1))) ||
+        (rc = get(&S.nrm, 4 * K)) || (rc = get(&S.rn0, K)) || (rc = get(&S.est, K)) || (rc = get(&S.need, K)) ||
+        (rc = get(&S.act, K)) || (rc = get(&S.jc, K)) || (rc = get(&S.iters, K)))
+      return rc;
+    if (c64 && ((rc = get(&zf, K * N)) || (rc = get(&wf, K * N)))) return rc;
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&word_h), 2 * sizeof(int), cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&word_d), word_h, 0));
+    for (auto& e : ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return SCABEM_OK;
+  }
+};
+
+// out[c * ostride] = |x_c| for the K columns of x (c * N apart)
+int bnorms(const cd* x, BWork& W, double* out, int ostride, cudaStream_t s) {
+  k_bvsub_norm<<<dim3(BG_BLOCKS, W.K), BG_THREADS, 0, s>>>(nullptr, 0, 0, nullptr, 0, const_cast<cd*>(x), W.N,
+                                                           W.nparts, nullptr);
+  CK(cudaGetLastError());
+  k_bnorm_fin<<<W.K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, out, ostride, nullptr, nullptr);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
+// w = A z for the K columns (FP64 storage, operator arithmetic in prec; the
+// transposed operator when solving A^T)
+int bapply(scabem_op* op, const cd* z, cd* w, int prec, BWork& W, cudaStream_t s) {
+  const int64_t N = W.N;
+  const int K = W.K;
+  if (prec == SCABEM_C128) {
+    if (W.tr) {
+      for (int c = 0; c < K; ++c)
+        if (int rc = apply_adjoint_one<double>(op, z + c * N, w + c * N, s)) return rc;
+      return SCABEM_OK;
+    }
+    return K == 1 ? apply_one<double>(op, z, w, s) : apply_batch<double>(op, z, N, w, N, K, s);
+  }
+  k_to_f<<<EW_BLOCKS, 256, 0, s>>>(z, W.zf, K * N);
+  CK(cudaGetLastError());
+  int rc = SCABEM_OK;
+  if (W.tr) {
+    for (int c = 0; c < K && !rc; ++c) rc = apply_adjoint_one<float>(op, W.zf + c * N, W.wf + c * N, s);
+  } else {
+    rc = K == 1 ? apply_one<float>(op, W.zf, W.wf, s) : apply_batch<float>(op, W.zf, N, W.wf, N, K, s);
+  }
+  if (rc) return rc;
+  k_from_f<<<EW_BLOCKS, 256, 0, s>>>(W.wf, w, K * N);
+  CK(cudaGetLastError());
+  return SCABEM_OK;
+}
+
+// Restarted GMRES for A d_c = r_c, c < K in lockstep, from d = 0 (r, d: K N
+// on the device).  use[c] = false leaves column c out (d_c = 0).  iters[c]
+// accumulates column c's inner iterations; est[c] is its last relative
+// residual (estimate, or true residual at a restart).
+int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use, int prec, double tol, int maxit,
+                BWork& W, cudaStream_t s, std::vector<int>& iters, std::vector<double>& est) {
+  const int64_t N = W.N;
+  const int K = W.K, m = W.m;
+  const int64_t csV = (int64_t)(m + 1) * N;
+  BState& S = W.S;
+  CK(cudaMemsetAsync(d, 0, sizeof(cd) * K * N, s));
+  CK(cudaMemsetAsync(W.u, 0, sizeof(cd) * K * N, s));
+  CK(cudaMemsetAsync(S.iters, 0, sizeof(int) * K, s));
+  if (int rc = bnorms(r, W, S.rn0, 1, s)) return rc;
+  std::vector<double> rn0(K);
+  CK(cudaMemcpyAsync(rn0.data(), S.rn0, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int> act(K), it0(K, 0);
+  int nact = 0;
+  for (int c = 0; c < K; ++c) {
+    if (use[c] && !std::isfinite(rn0[c])) {
+      set_error("non-finite residual");
+      return SCABEM_E_NONFINITE;
+    }
+    act[c] = use[c] && rn0[c] > 0.0;
+    nact += act[c];
+    est[c] = 0.0;
+  }
+  if (nact == 0) return SCABEM_OK;
+  // the first cycle starts from t = r, beta = |r|
+  CK(cudaMemcpyAsync(W.t, r, sizeof(cd) * K * N, cudaMemcpyDeviceToDevice, s));
+  for (int c = 0; c < K; ++c)
+    CK(cudaMemcpyAsync(S.nrm + 4 * c + 3, S.rn0 + c, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int lock = 0;  // lockstep iterations
+  while (true) {
+    CK(cudaMemcpyAsync(S.act, act.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+    W.word_h[0] = nact;
+    W.word_h[1] = 0;
+    k_bstart<<<dim3(EW_BLOCKS / 4, K), 256, 0, s>>>(W.t, W.V, csV, S, m, N);
+    CK(cudaGetLastError());
+    for (int j = 0; j < m && lock < maxit; ++j, ++lock) {
+      // z = P^-1 v_j (right preconditioning), w = A z
+      if (int rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr, K, csV, N)) return rc;
+      if (int rc = bapply(op, W.z, W.w, prec, W, s)) return rc;
+      // |w|, first pass h1 = V^H w, w -= V h1, |w|; DGKS test; second pass when asked
+      k_bvsub_norm<<<dim3(BG_BLOCKS, K), BG_THREADS, 0, s>>>(nullptr, 0, 0, nullptr, 0, W.w, N, W.nparts, nullptr);
+      CK(cudaGetLastError());
+      k_bnorm_fin<<<K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 0, 4, nullptr, nullptr);
+      CK(cudaGetLastError());
+      const int tiles = (int)cdiv(j + 1, BG_TC);
+      const int rb = std::max(8, BG_BLOCKS / tiles);
+      for (int pass = 0; pass < 2; ++pass) {
+        const int* need = pass ? S.need : nullptr;
+        cd* h = pass ? S.h2 : S.h1;
+        k_bdots<<<dim3(rb, tiles, K), BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.w, N, W.part, m + 1, need);
+        CK(cudaGetLastError());
+        k_breduce<<<dim3(j + 1, K), BG_THREADS, 0, s>>>(W.part, rb, m + 1, h, m + 1, need);
+        CK(cudaGetLastError());
+        k_bvsub_norm<<<dim3(BG_BLOCKS, K), BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.w, N, W.nparts, need);
+        CK(cudaGetLastError());
+        k_bnorm_fin<<<K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 1 + pass, 4, need,
+                                             pass ? nullptr : S.need);
+        CK(cudaGetLastError());
+      }
+      k_givens<<<1, 32, 0, s>>>(S, j, m, K, tol, W.word_d);
+      CK(cudaGetLastError());
+      if (j + 1 < m) {
+        k_bscale<<<dim3(EW_BLOCKS / 4, K), 256, 0, s>>>(W.w, W.V, csV, j + 1, S.nrm, S.need, N);
+        CK(cudaGetLastError());
+      }
+      // the host stays one step ahead: wait for the previous step, read its word
+      CK(cudaEventRecord(W.ev[j & 1], s));
+      if (j > 0) {
+        CK(cudaEventSynchronize(W.ev[(j - 1) & 1]));
+        const int flags = reinterpret_cast<volatile int*>(W.word_h)[1];
+        if (flags & FLAG_NONFINITE) {
+          set_error("non-finite Krylov vector");
+          return SCABEM_E_NONFINITE;
+        }
+        if (flags & FLAG_BREAKDOWN) {
+          set_error("GMRES breakdown");
+          return SCABEM_E_BREAKDOWN;
+        }
+        if (reinterpret_cast<volatile int*>(W.word_h)[0] == 0) {
+          ++j, ++lock;
+          break;
+        }
       }
     }
-    // back substitution, d += V y
-    std::vector<cd> y(j);
-    for (int i = j - 1; i >= 0; --i) {
-      cd acc = g[i];
-      for (int l = i + 1; l < j; ++l) acc -= H[(size_t)i * m + l] * y[l];
-      const cd hd = H[(size_t)i * m + i];
-      const double dd = hd.re * hd.re + hd.im * hd.im;
-      y[i] = mk((acc.re * hd.re + acc.im * hd.im) / dd, (acc.im * hd.re - acc.re * hd.im) / dd);
-    }
-    for (auto& z : y) z = -z;
-    if (j > 0) {
-      CK(cudaMemcpyAsync(W.h, y.data(), sizeof(cd) * j, cudaMemcpyHostToDevice, s));
-      k_vsub<<<DOT_BLOCKS, 256, 0, s>>>(W.V, N, j, W.h, W.u, N);
-      CK(cudaGetLastError());
-    }
-    rc = precond_apply(op, W.u, d, s, W.tr);  // d = P^-1 u
-    if (rc) return rc;
-    if (done || iters >= maxit) break;
-    // true residual for the restart
-    rc = op_apply64(op, d, W.w, prec, W, s);
-    if (rc) return rc;
-    k_sub<<<DOT_BLOCKS, 256, 0, s>>>(r, W.w, W.t, N);
+    // least squares and d = P^-1 u for every column that took part in the cycle
+    k_backsub<<<1, 32, 0, s>>>(S, m, K);
     CK(cudaGetLastError());
-    rc = norm2(W.t, N, W, s, beta);
-    if (rc) return rc;
-    relres_est = beta / rn0;
-    if (relres_est <= tol) break;
+    k_bupdate<<<dim3(EW_BLOCKS / 4, K), 256, 0, s>>>(W.V, csV, S, m, W.u, N);
+    CK(cudaGetLastError());
+    if (int rc = precond_apply(op, W.u, d, s, W.tr, K, N, N)) return rc;
+    // columns that stopped inside the cycle (estimate at tol) are done; the
+    // others restart from their true residual
+    std::vector<int> still(K), nit(K);
+    std::vector<double> e(K);
+    CK(cudaMemcpyAsync(still.data(), S.act, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(nit.data(), S.iters, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(e.data(), S.est, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (W.word_h[1] & FLAG_NONFINITE) {
+      set_error("non-finite Krylov vector");
+      return SCABEM_E_NONFINITE;
+    }
+    if (W.word_h[1] & FLAG_BREAKDOWN) {
+      set_error("GMRES breakdown");
+      return SCABEM_E_BREAKDOWN;
+    }
+    nact = 0;
+    for (int c = 0; c < K; ++c) {
+      iters[c] += nit[c] - it0[c];
+      it0[c] = nit[c];
+      if (act[c]) est[c] = e[c];
+      act[c] = act[c] && still[c];
+      nact += act[c];
+    }
+    if (nact == 0 || lock >= maxit) break;
+    if (int rc = bapply(op, d, W.w, prec, W, s)) return rc;
+    k_sub<<<EW_BLOCKS, 256, 0, s>>>(r, W.w, W.t, K * N);
+    CK(cudaGetLastError());
+    if (int rc = bnorms(W.t, W, S.nrm + 3, 4, s)) return rc;
+    std::vector<double> nb(4 * K);
+    CK(cudaMemcpyAsync(nb.data(), S.nrm, sizeof(double) * 4 * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    nact = 0;
+    for (int c = 0; c < K; ++c) {
+      if (!act[c]) continue;
+      est[c] = nb[4 * c + 3] / rn0[c];
+      act[c] = est[c] > tol;
+      nact += act[c];
+    }
+    if (nact == 0) break;
   }
   return SCABEM_OK;
 }
@@ -925,72 +1074,84 @@ int solve_impl(scabem_op* op, const void* bv, void* xv, int nrhs, int64_t ld, co
   const int64_t N = op->N;
   const int m = o->restart;
   const int prec = o->prec;
-  Work W;
-  W.tr = o->transpose != 0;
-  CK(cudaMalloc(&W.V, sizeof(cd) * N * (m + 1)));
-  CK(cudaMalloc(&W.w, sizeof(cd) * N));
-  CK(cudaMalloc(&W.t, sizeof(cd) * N));
-  CK(cudaMalloc(&W.z, sizeof(cd) * N));
-  CK(cudaMalloc(&W.u, sizeof(cd) * N));
-  CK(cudaMalloc(&W.part, sizeof(cd) * DOT_BLOCKS * (m + 1)));
-  CK(cudaMalloc(&W.h, sizeof(cd) * (2 * (m + 1) + 3)));
-  CK(cudaMalloc(&W.nparts, sizeof(double) * DOT_BLOCKS));
-  if (prec == SCABEM_C64) {
-    CK(cudaMalloc(&W.xf, sizeof(cx<float>) * N));
-    CK(cudaMalloc(&W.yf, sizeof(cx<float>) * N));
+  const bool tr = o->transpose != 0;
+  if (nrhs == 0) return SCABEM_OK;
+  const int KB = nrhs < KBATCH ? nrhs : KBATCH;
+  if (KB > 1 && !tr) {
+    if (int rc = ensure_batch<double>(op, KB, s)) return rc;
+    if (prec == SCABEM_C64)
+      if (int rc = ensure_batch<float>(op, KB, s)) return rc;
   }
-  cd* r = nullptr;
-  cd* d = nullptr;
-  CK(cudaMalloc(&r, sizeof(cd) * N));
-  CK(cudaMalloc(&d, sizeof(cd) * N));
+  BWork W;
+  W.tr = tr;
+  if (int rc = W.init(KB, m, N, prec == SCABEM_C64)) return rc;
+  cd *B = nullptr, *X = nullptr, *R = nullptr, *D = nullptr;
+  if (int rc = W.get(&B, KB * N)) return rc;
+  if (int rc = W.get(&X, KB * N)) return rc;
+  if (int rc = W.get(&R, KB * N)) return rc;
+  if (int rc = W.get(&D, KB * N)) return rc;
+  const int outer = o->max_refine > 0 ? o->max_refine : 1;
+  const double tol_out = o->refine_tol > 0 ? o->refine_tol : o->tol;
   int status = SCABEM_OK;
-  for (int col = 0; col < nrhs; ++col) {
-    const cd* b = (const cd*)bv + (int64_t)col * ld;
-    cd* x = (cd*)xv + (int64_t)col * ld;
-    double bn;
-    int rc = norm2(b, N, W, s, bn);
-    if (rc) return rc;
-    int iters = 0, refs = 0;
-    double relres = 0.0;
-    const int outer = o->max_refine > 0 ? o->max_refine : 1;
-    const double tol_out = o->refine_tol > 0 ? o->refine_tol : o->tol;
-    int st = SCABEM_E_NOCONV;
+  for (int c0 = 0; c0 < nrhs; c0 += KB) {
+    const int k = nrhs - c0 < KB ? nrhs - c0 : KB;
+    W.K = k;
+    for (int c = 0; c < k; ++c) {
+      CK(cudaMemcpyAsync(B + c * N, (const cd*)bv + (c0 + c) * ld, sizeof(cd) * N, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(X + c * N, (const cd*)xv + (c0 + c) * ld, sizeof(cd) * N, cudaMemcpyDeviceToDevice, s));
+    }
+    std::vector<double> bn(k), rn(k), relres(k, 0.0), est(k, 0.0);
+    if (int rc = bnorms(B, W, W.S.rn0, 1, s)) return rc;
+    CK(cudaMemcpyAsync(bn.data(), W.S.rn0, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    std::vector<int> iters(k, 0), refs(k, 0), st(k, SCABEM_E_NOCONV);
+    std::vector<char> done(k, 0), use(k, 0);
     for (int it = 0; it <= outer; ++it) {
-      rc = W.tr ? apply_adjoint_one<double>(op, x, W.w, s) : apply_one<double>(op, x, W.w, s);
-      if (rc) return rc;
-      k_sub<<<DOT_BLOCKS, 256, 0, s>>>(b, W.w, r, N);
+      // FP64 residual r = b - A x with the complex128 operator
+      if (int rc = bapply(op, X, W.w, SCABEM_C128, W, s)) return rc;
+      k_sub<<<EW_BLOCKS, 256, 0, s>>>(B, W.w, R, k * N);
       CK(cudaGetLastError());
-      double rn;
-      rc = norm2(r, N, W, s, rn);
-      if (rc) return rc;
-      relres = bn > 0 ? rn / bn : 0.0;
-      if (!std::isfinite(relres)) {
-        st = SCABEM_E_NONFINITE;
-        break;
+      if (int rc = bnorms(R, W, W.S.nrm + 3, 4, s)) return rc;
+      std::vector<double> nb(4 * k);
+      CK(cudaMemcpyAsync(nb.data(), W.S.nrm, sizeof(double) * 4 * k, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      int left = 0;
+      for (int c = 0; c < k; ++c) {
+        if (done[c]) continue;
+        relres[c] = bn[c] > 0 ? nb[4 * c + 3] / bn[c] : 0.0;
+        if (!std::isfinite(relres[c])) {
+          st[c] = SCABEM_E_NONFINITE;
+          done[c] = 1;
+        } else if (relres[c] <= tol_out) {
+          st[c] = SCABEM_OK;
+          done[c] = 1;
+        } else if (it == outer || iters[c] >= o->maxit) {
+          done[c] = 1;
+        }
+        use[c] = !done[c];
+        left += use[c];
       }
-      if (relres <= tol_out) {
-        st = SCABEM_OK;
-        break;
-      }
-      if (it == outer || iters >= o->maxit) break;
-      double est;
-      rc = gmres(op, r, d, prec, o->tol, m, o->maxit, W, s, iters, est);
-      if (rc) return rc;
-      k_add<<<DOT_BLOCKS, 256, 0, s>>>(x, d, N);
+      if (left == 0) break;
+      int budget = 0;
+      for (int c = 0; c < k; ++c)
+        if (use[c]) budget = std::max(budget, o->maxit - iters[c]);
+      if (int rc = gmres_batch(op, R, D, use, prec, o->tol, budget, W, s, iters, est)) return rc;
+      k_add<<<EW_BLOCKS, 256, 0, s>>>(X, D, k * N);
       CK(cudaGetLastError());
-      ++refs;
+      for (int c = 0; c < k; ++c) refs[c] += use[c];
     }
-    if (info) {
-      info[col].iters = iters;
-      info[col].refinements = refs;
-      info[col].relres = relres;
-      info[col].status = st;
+    for (int c = 0; c < k; ++c)
+      CK(cudaMemcpyAsync((cd*)xv + (c0 + c) * ld, X + c * N, sizeof(cd) * N, cudaMemcpyDeviceToDevice, s));
+    for (int c = 0; c < k; ++c) {
+      if (info) {
+        info[c0 + c].iters = iters[c];
+        info[c0 + c].refinements = refs[c];
+        info[c0 + c].relres = relres[c];
+        info[c0 + c].status = st[c];
+      }
+      if (st[c] != SCABEM_OK && status == SCABEM_OK) status = st[c];
     }
-    if (st != SCABEM_OK && status == SCABEM_OK) status = st;
   }
   CK(cudaStreamSynchronize(s));
-  cudaFree(r);
-  cudaFree(d);
   if (status != SCABEM_OK) set_error("solver did not reach the requested residual");
   return status;
 }

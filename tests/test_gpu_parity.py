@@ -66,11 +66,21 @@ def gpu_apply(op, x, prec):
 
 
 _oracle_y = {}
+_oracle_ops = {}
+
+
+def oracle_op(case, g, med):
+    """The oracle's grid operator O2 of a case, built once per test session (it keeps its
+    whole-mesh near corrections, the costly part, after the first full apply)."""
+    key = (case.name, case.grid.n, case.grid.p, case.q, case.r_near, case.grid.h)
+    if key not in _oracle_ops:
+        _oracle_ops[key] = pfft.PFFT(g, med, case.grid, case.r_near)
+    return _oracle_ops[key]
 
 
 def oracle_apply(case, g, med, sig, x, key):
     if key not in _oracle_y:
-        _oracle_y[key] = pfft.PFFT(g, med, case.grid, case.r_near).apply(x, sig)
+        _oracle_y[key] = oracle_op(case, g, med).apply(x, sig)
     return _oracle_y[key]
 
 
@@ -126,8 +136,9 @@ def test_apply_empty_batch_and_zero_input():
 def test_apply_batched_columns_and_host_buffers():
     """nrhs > 1 with ld > N, from host (pinned-less numpy) buffers: same as column by column.
 
-    The projection accumulates with atomics, so two calls agree to rounding
-    (summation order), not bit for bit."""
+    The row sums add two terms per row with atomics (order-independent), so
+    the columns agree with single-column applies to rounding of the staging
+    path at most."""
     case = cases.sphere_mixed()
     mh, op, g, med, sig = build(case)
     N = g.N
@@ -182,7 +193,7 @@ def test_solve_reaches_oracle_residual(prec):
     assert info[0]["status"] == 0 and info[0]["relres"] < 1e-8, info
     xn = x.cpu().numpy()
     bn = b.cpu().numpy()
-    r = bn - pfft.PFFT(g, med, case.grid, case.r_near).apply(xn, sig)
+    r = bn - oracle_op(case, g, med).apply(xn, sig)
     assert np.linalg.norm(r) / np.linalg.norm(bn) < 1e-8
 
 
