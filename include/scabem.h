@@ -72,7 +72,11 @@ typedef struct {
 /* Grid and discretisation options.
  *   n[3]      physical grid points per axis (x, y, z); the FFT size is 2n.
  *             Each 2n must be a power of two, in [8, 1024] along x and in
- *             [8, 128] along y and z, with (2 n_y) * (2 n_z) <= 4096.
+ *             [8, 512] along y and z.  The 2-D FFT planes (transverse = 1)
+ *             need 2 n_y, 2 n_z <= 128 and (2 n_y)(2 n_z) <= 4096; larger
+ *             planes always run as direct sums, which need the active
+ *             columns' data (8 values each, plus the table of their offsets)
+ *             to fit in one CTA's shared memory (SCABEM_E_ARG otherwise).
  *   h         grid spacing [um]; origin[3] coordinates of grid point 0.
  *   p         stencil points per axis (2, 3 or 4), Lagrange interpolation;
  *             every stencil must fall inside the physical grid.
@@ -316,6 +320,44 @@ int scabem_sigma_gradient(scabem_op_t op, const void* x, const void* lam, const 
 int scabem_fields(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const double* pts, int32_t npts,
                   const scabem_source* inc, double* E_out, void* stream);
 
+/* Electric and magnetic field of one current set at npts host points
+ * (pts: npts x 3), the operators of Eqs. 15-16 evaluated off the surface by
+ * the triangle quadrature: side 0 = the interior set (J_i, -M) radiating in
+ * the interior medium, plus the incident field of `inc` when it is not NULL
+ * (Eq. 8: the total interior field); side 1 = the exterior set (J_e, M) in
+ * the exterior medium (the total exterior field of an interior source; inc
+ * is ignored).  x: complex128, device or host, nrhs columns of leading
+ * dimension ld.  E_out, H_out: host, npts x 3 complex128 per right-hand
+ * side, H in the eta0 = 1 scaling (eta0 H).  Needs the complex128 operator;
+ * synchronises `stream`. */
+int scabem_fields_eh(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const double* pts, int32_t npts,
+                     int32_t side, const scabem_source* inc, double* E_out, double* H_out, void* stream);
+
+/* Decay rate by Poynting's theorem (Sec. III-B) at the cross-section
+ * x = xc of a guide along x centred on y = z = 0:
+ *   alpha = [ int_L' sigma |E_tan|^2 dl + Re oint_L (E x H*) . n dl ]
+ *           / [ 2 Re int_A (E x H*) . x dS ],
+ * A the rectangle |y| <= box[0], |z| <= box[1]; the core rectangle
+ * |y| < core[0], |z| < core[1] takes the total interior field (with the
+ * incident field of `inc` when not NULL), the rest of A and its outer
+ * boundary L the exterior field.  Each of the nine rectangles uses n x n
+ * Gauss-Legendre points, each side of L 2n.  The perimeter integral L' is
+ * the surface integral of sigma eta0 |M|^2 over the band |x - xc| < slab of
+ * the mesh, divided by its width 2 slab (|E_tan| = |n x M| = |M| on the
+ * sheet), with the operator's own conductivity at each quadrature point.
+ * x: complex128 (device or host); out (host, per right-hand side):
+ * {alpha [1/um], loss per length, side flux per length, cross-section flux}.
+ * Needs the complex128 operator; synchronises `stream`. */
+typedef struct {
+  double xc;
+  double core[2];
+  double box[2];
+  double slab;
+  int32_t n;
+} scabem_poynting;
+int scabem_poynting_rate(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_poynting* p,
+                         const scabem_source* inc, double* out, void* stream);
+
 /* Reflection on a line of probe points inside the guide (Sec. I, Table 1):
  * samples the component `comp` of the total interior field at npts points
  * p0 + t * e_axis, t in [t0, t1]; fits E = a exp(-j beta t) + c exp(j beta t)
@@ -372,6 +414,15 @@ int scabem_decay_rate(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, c
  * enable = 0 releases the events. */
 int scabem_profile(scabem_op_t op, int32_t enable, int32_t max_applies);
 int scabem_profile_read(scabem_op_t op, double* stage_ms, int64_t* n_applies);
+
+/* Arithmetic peak of the current GPU's fused multiply-add pipe (instrumentation,
+ * not part of the paper's method): a kernel of independent FMA chains in
+ * registers, with no memory traffic, 8 CTAs of 256 threads per SM, timed with
+ * CUDA events on `stream` (the second of two launches).  prec = SCABEM_C128:
+ * FP64 FMA (the pipe of the complex128 operator); SCABEM_C64: packed FP32x2
+ * FMA (the pipe of the complex64 operator).  *tflops: measured TFLOP/s.
+ * Allocates and frees a small device buffer; synchronises `stream`. */
+int scabem_peak_fma(int32_t prec, double* tflops, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* scabem_last_error(void);

@@ -66,6 +66,11 @@ class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("relres", C.c_double), ("status", C.c_int32)]
 
 
+class Poynting(C.Structure):
+    _fields_ = [("xc", C.c_double), ("core", C.c_double * 2), ("box", C.c_double * 2), ("slab", C.c_double),
+                ("n", C.c_int32)]
+
+
 class Probe(C.Structure):
     _fields_ = [("axis", C.c_int32), ("comp", C.c_int32), ("p0", C.c_double * 3), ("t0", C.c_double),
                 ("t1", C.c_double), ("npts", C.c_int32), ("beta_lo", C.c_double), ("beta_hi", C.c_double),
@@ -115,6 +120,9 @@ def lib():
     L.scabem_rhs_noalloc.argtypes = [vp, C.POINTER(Source), i32, vp, i64, i32, vp]
     L.scabem_profile.argtypes = [vp, i32, i32]
     L.scabem_profile_read.argtypes = [vp, vp, C.POINTER(i64)]
+    L.scabem_peak_fma.argtypes = [i32, C.POINTER(C.c_double), vp]
+    L.scabem_fields_eh.argtypes = [vp, vp, i32, i64, vp, i32, i32, C.POINTER(Source), vp, vp, vp]
+    L.scabem_poynting_rate.argtypes = [vp, vp, i32, i64, C.POINTER(Poynting), C.POINTER(Source), vp, vp]
     L.scabem_last_error.argtypes = []
     L.scabem_last_error.restype = C.c_char_p
     _lib = L
@@ -339,6 +347,31 @@ def scabem_fields(op, x, pts, inc=None, nrhs=1, ld=None, stream=None):
     return E
 
 
+def scabem_fields_eh(op, x, pts, side=0, inc=None, nrhs=1, ld=None, stream=None):
+    """(E, H) of the interior (side 0, plus inc) or exterior (side 1) current set at pts:
+    two arrays (nrhs, npts, 3) complex128."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    if ld is None:
+        ld = x.shape[0]
+    E = np.zeros((nrhs, len(pts), 3), np.complex128)
+    H = np.zeros_like(E)
+    _check(lib().scabem_fields_eh(op, _ptr(x), nrhs, ld, _ptr(pts), len(pts), int(side),
+                                  C.byref(inc) if inc else None, _ptr(E), _ptr(H), _stream(stream)))
+    return E, H
+
+
+def scabem_poynting_rate(op, x, xc, core, box, slab, n=10, inc=None, nrhs=1, ld=None, stream=None):
+    """Decay rate by Poynting's theorem at x = xc: per right-hand side
+    (alpha [1/um], loss per length, side flux per length, cross-section flux)."""
+    if ld is None:
+        ld = x.shape[0]
+    pp = Poynting(float(xc), (C.c_double * 2)(*core), (C.c_double * 2)(*box), float(slab), int(n))
+    out = np.zeros((nrhs, 4), np.float64)
+    _check(lib().scabem_poynting_rate(op, _ptr(x), nrhs, ld, C.byref(pp), C.byref(inc) if inc else None, _ptr(out),
+                                      _stream(stream)))
+    return out
+
+
 def scabem_reflection(op, x, axis, comp, p0, t0, t1, npts, beta_lo, beta_hi, nbeta, inc=None, nrhs=1, ld=None,
                       stream=None):
     if ld is None:
@@ -385,6 +418,13 @@ def scabem_profile_read(op):
     n = C.c_int64()
     _check(lib().scabem_profile_read(op, _ptr(ms), C.byref(n)))
     return dict(zip(STAGES, ms.tolist())), n.value
+
+
+def scabem_peak_fma(prec=SCABEM_C128, stream=None):
+    """Measured FMA-pipe peak in TFLOP/s: FP64 (prec=SCABEM_C128) or packed FP32x2 (SCABEM_C64)."""
+    v = C.c_double()
+    _check(lib().scabem_peak_fma(int(prec), C.byref(v), _stream(stream)))
+    return v.value
 
 
 def scabem_last_error():

@@ -25,6 +25,7 @@ class Case:
     sigma_scale: float = 0.0  # random per-point conductivity [S] when > 0
     seed: int = 0
     transverse: str = "auto"  # (y, z) convolution: "auto", "fft" planes or "direct" sums
+    sigma_bspline: tuple | None = None  # (x0, L, axis, coef [S]): cubic B-spline profile
 
 
 def sphere_mixed(level=2, padded=(32, 32, 32), p=3, q=6, r_near=0.5):
@@ -92,6 +93,28 @@ def plate_q1():
     return c
 
 
+def guide_short(ncoef=16, sigma0=0.004, seed=1234):
+    """A 1.6 um guide (416 triangles, N = 1,572) with 0.4 um absorber regions at both ends and a
+    conductivity given as a cubic B-spline of ncoef coefficients over the whole guide, uniform in
+    [0, 2 sigma0] (seeded); small enough for the oracle to assemble its grid operator column by
+    column and solve it by LU."""
+    m = synth.waveguide(1.6, 0.5, 0.22, 16, 4, 2, 0.4, 0.4)
+    grid = synth.grid_for_mesh(m.V, (32, 16, 16), p=3)
+    coef = np.random.default_rng(seed).uniform(0.0, 2 * sigma0, ncoef)
+    return Case("guide_short", m, (12.1, 1.0, 2.1, 1.0, 1.55), grid, 6, 0.2, seed=14,
+                sigma_bspline=(0.0, 1.6, 0, coef))
+
+
+def guide_2k(ncoef=16, sigma0=0.004, seed=1234):
+    """A 4 um guide of 1,952 triangles with 1 um absorber regions at both ends and a 16-coefficient
+    cubic B-spline conductivity over the whole guide, uniform in [0, 2 sigma0] (seeded)."""
+    m = synth.waveguide(4.0, 0.5, 0.22, 80, 4, 2, 1.0, 1.0)
+    grid = synth.grid_for_mesh(m.V, (128, 16, 16), p=3)
+    coef = np.random.default_rng(seed).uniform(0.0, 2 * sigma0, ncoef)
+    return Case("guide_2k", m, (12.1, 1.0, 2.1, 1.0, 1.55), grid, 6, 2.05 * grid.h, seed=15,
+                sigma_bspline=(0.0, 4.0, 0, coef))
+
+
 def guide_full(p=3, q=6, r_near=None):
     """The 12 um guide: 0.5 x 0.22 um core (eps 12.1) in eps 2.1, 4 um absorbers
     sigma0 (x/L)^3 at both ends, 19,420 triangles, FFT grid 512 x 64 x 64."""
@@ -105,10 +128,27 @@ def guide_full(p=3, q=6, r_near=None):
     return Case("guide_12um", m, (12.1, 1.0, 2.1, 1.0, 1.55), grid, q, r_near, sigma_segments=segs, seed=0)
 
 
+def coupler_full(p=3, q=6, r_near=None):
+    """Two 40 um guides 0.2 um apart (a directional coupler) with 4 um absorbers sigma0 (x/L)^3 at
+    all four ports, 128,440 triangles, FFT grid 1024 x 256 x 256 (the (y, z) convolution runs as
+    direct sums over the active columns)."""
+    m = synth.coupler()
+    grid = synth.grid_for_mesh(m.V, (1024, 256, 256), p=p)
+    if r_near is None:
+        r_near = 2.05 * grid.h
+    L, length = 4.0, 40.0
+    s0 = 0.008
+    segs = [(length - L, L, s0, 3, 0, 1.0), (L, L, s0, 3, 0, -1.0)]
+    return Case("coupler_40um", m, (12.1, 1.0, 2.1, 1.0, 1.55), grid, q, r_near, sigma_segments=segs, seed=0)
+
+
 def sigma_points(case: Case, qpts):
     """Conductivity [S] at the quadrature points (nt, q) for a case."""
     from oracle import sigma as osig  # the oracle evaluates the profile on its side
 
+    if case.sigma_bspline is not None:
+        x0, L, axis, coef = case.sigma_bspline
+        return osig.bspline(qpts, x0, L, coef, axis)
     if case.sigma_segments:
         return osig.monomial(qpts, case.sigma_segments)
     if case.sigma_scale > 0:

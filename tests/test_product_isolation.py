@@ -52,4 +52,5 @@ def test_bench_imports_the_oracle_only_in_its_cpu_leg():
             visit(child, name)
 
     visit(tree, None)
-    assert where and set(where) == {"oracle_rate"}, where
+    # the CPU baselines: O1 on every host core (pool workers and driver) and O2 on one core
+    assert where and set(where) <= {"_o1_init", "_o1_edge", "oracle_rate_allcores", "o2_rate"}, where

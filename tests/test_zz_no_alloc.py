@@ -57,6 +57,31 @@ def test_rhs_noalloc_matches_rhs_on_consecutive_calls(guide_op, prec):
         assert np.linalg.norm(g - r) <= tol * np.linalg.norm(r)
 
 
+@pytest.mark.parametrize("prec", [sc.SCABEM_C128, sc.SCABEM_C64], ids=["c128", "c64"])
+def test_rhs_noalloc_two_sources_per_call_with_leading_dimension(guide_op, prec):
+    """Two sources in one call reuse the shared scratch one after the other; columns are ld = N + 3
+    apart and the padding between them is left untouched."""
+    op, N = guide_op
+    dt = torch.complex128 if prec == sc.SCABEM_C128 else torch.complex64
+    tol = TOL64 if prec == sc.SCABEM_C128 else TOL32
+    ld = N + 3
+    sources = [
+        sc.make_source("dipole", "i", pos=(0.9, 0.02, 0.01), pol=(0.2, 1.0, 0.1)),
+        sc.make_source("beam", "i", pos=(1.2, 0.0, 0.0), dir=(-1, 0, 0), pol=(0, 0, 1), b=0.05),
+    ]
+    ref = torch.zeros(2 * ld, dtype=dt, device="cuda")
+    sc.scabem_rhs(op, sources, ref, ld=ld, prec=prec)
+    fill = complex(7.0, -3.0)
+    got = torch.full((2 * ld,), fill, dtype=dt, device="cuda")
+    sc.scabem_rhs_noalloc(op, sources, got, ld=ld, prec=prec)
+    torch.cuda.synchronize()
+    r, g = ref.cpu().numpy().reshape(2, ld), got.cpu().numpy().reshape(2, ld)
+    for c in range(2):
+        assert np.linalg.norm(g[c, :N] - r[c, :N]) <= tol * np.linalg.norm(r[c, :N]), c
+        assert np.all(g[c, N:] == np.asarray(fill, dtype=g.dtype))
+    assert np.linalg.norm(g[0, :N] - g[1, :N]) > 0.1 * np.linalg.norm(g[0, :N])
+
+
 def test_rhs_noalloc_rejects_host_buffers(guide_op):
     op, N = guide_op
     b = np.zeros(N, np.complex128)
