@@ -199,6 +199,39 @@ int scabem_set_sigma(scabem_op_t op, const scabem_sigma* sigma);
  * launches). */
 int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t ld, int32_t prec, void* stream);
 
+/* Circulant preconditioner for the plain-surface block of a straight guide
+ * (Appendix B: A_LL of a mesh that repeats along the guide is block
+ * Toeplitz over its regular slices; a block circulant approximation of it is
+ * inverted with FFTs over the slice index, and the absorber rows keep the
+ * block-diagonal preconditioner).  Slice k of the mesh spans
+ * [x0 + k dx, x0 + (k + 1) dx) along `axis`; the plain-surface edges between
+ * lateral (not end-cap) triangles of slices first .. first + count - 1 must
+ * be translates of those of slice `first` (SCABEM_E_MESH otherwise).  Its
+ * blocks come from the operator's own columns for the unknowns of the middle
+ * slice (complex128 operator when built, else complex64), and Strang's
+ * circulant keeps the blocks of offsets up to count / 2 and wraps them.  The
+ * R = count DFT blocks (m x m, m = unknowns per slice) are inverted on the
+ * device by Gauss-Jordan elimination with partial pivoting
+ * (SCABEM_E_BREAKDOWN if one is singular).  From then on scabem_solve
+ * (forward, transpose = 0) preconditions those unknowns with it; transposed
+ * solves keep the block-diagonal preconditioner.  count = 0 removes it.
+ * `mesh` must be the mesh the operator was built from; synchronises `stream`;
+ * R m^2 complex128 values of device memory. */
+typedef struct {
+  int32_t axis;
+  double x0, dx;
+  int32_t first, count;
+} scabem_circulant;
+int scabem_set_precond_circulant(scabem_op_t op, scabem_mesh_t mesh, const scabem_circulant* c, void* stream);
+
+/* The preconditioner that scabem_solve applies, z = M^-1 v (the inverse
+ * per-edge diagonal blocks, and the circulant of scabem_set_precond_circulant
+ * on its periodic unknowns unless transpose = 1), for nrhs complex128 device
+ * columns of leading dimension ld; for tests and for callers that run their
+ * own Krylov method.  Stream-ordered. */
+int scabem_precond_apply(scabem_op_t op, const void* v, void* z, int32_t nrhs, int64_t ld, int32_t transpose,
+                         void* stream);
+
 /* Self-test of the bounded device waits behind SCABEM_E_TIMEOUT.  One warp
  * waits on an mbarrier that nothing ever completes, through the same wait
  * routine and limit (about a second) as the near-field record streams, and

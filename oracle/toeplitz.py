@@ -105,3 +105,38 @@ def apply(T, xs):
     Xp[:R] = xs
     Y = np.fft.ifft(np.einsum("kab,kb->ka", np.fft.fft(C, axis=0), np.fft.fft(Xp, axis=0)), axis=0)
     return Y[:R]
+
+
+# ---------------------------------------------------------------- circulant preconditioner
+def strang(T, R):
+    """Strang's circulant approximation of the block Toeplitz matrix with blocks T[d] (the
+    preconditioner of Appendix B for A_LL): the block circulant whose first block column is
+    c_k = T[k] for 0 <= k <= R/2 and c_k = T[k - R] for R/2 < k < R; an offset with no block in T
+    gives a zero block.  Returns c (R, m, m)."""
+    m = next(iter(T.values())).shape[0]
+    c = np.zeros((R, m, m), dtype=np.complex128)
+    for k in range(R):
+        d = k if k <= R // 2 else k - R
+        if d in T:
+            c[k] = T[d]
+    return c
+
+
+def circulant_apply(c, xs):
+    """y_i = sum_j c[(i - j) mod R] x_j for slice vectors xs (R, m), by the definition."""
+    R = len(c)
+    ys = np.zeros_like(np.asarray(xs, dtype=np.complex128))
+    for i in range(R):
+        for j in range(R):
+            ys[i] += c[(i - j) % R] @ xs[j]
+    return ys
+
+
+def circulant_solve(c, vs):
+    """x with circulant_apply(c, x) = vs: the block DFT over the slice index diagonalises the
+    circulant (block f = sum_k c_k exp(-2 pi i f k / R)); one dense solve per frequency."""
+    R = len(c)
+    ch = np.fft.fft(c, axis=0)
+    vh = np.fft.fft(np.asarray(vs, dtype=np.complex128), axis=0)
+    xh = np.stack([np.linalg.solve(ch[f], vh[f]) for f in range(R)])
+    return np.fft.ifft(xh, axis=0)

@@ -71,6 +71,11 @@ class Poynting(C.Structure):
                 ("n", C.c_int32)]
 
 
+class Circulant(C.Structure):
+    _fields_ = [("axis", C.c_int32), ("x0", C.c_double), ("dx", C.c_double), ("first", C.c_int32),
+                ("count", C.c_int32)]
+
+
 class Probe(C.Structure):
     _fields_ = [("axis", C.c_int32), ("comp", C.c_int32), ("p0", C.c_double * 3), ("t0", C.c_double),
                 ("t1", C.c_double), ("npts", C.c_int32), ("beta_lo", C.c_double), ("beta_hi", C.c_double),
@@ -122,6 +127,8 @@ def lib():
     L.scabem_profile_read.argtypes = [vp, vp, C.POINTER(i64)]
     L.scabem_peak_fma.argtypes = [i32, C.POINTER(C.c_double), vp]
     L.scabem_fields_eh.argtypes = [vp, vp, i32, i64, vp, i32, i32, C.POINTER(Source), vp, vp, vp]
+    L.scabem_set_precond_circulant.argtypes = [vp, vp, C.POINTER(Circulant), vp]
+    L.scabem_precond_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_poynting_rate.argtypes = [vp, vp, i32, i64, C.POINTER(Poynting), C.POINTER(Source), vp, vp]
     L.scabem_last_error.argtypes = []
     L.scabem_last_error.restype = C.c_char_p
@@ -345,6 +352,19 @@ def scabem_fields(op, x, pts, inc=None, nrhs=1, ld=None, stream=None):
     _check(lib().scabem_fields(op, _ptr(x), nrhs, ld, _ptr(pts), len(pts), C.byref(inc) if inc else None, _ptr(E),
                                _stream(stream)))
     return E
+
+
+def scabem_set_precond_circulant(op, mesh, axis=0, x0=0.0, dx=1.0, first=1, count=0, stream=None):
+    """Strang circulant preconditioner on regular slices first .. first+count-1 (count = 0 removes it)."""
+    c = Circulant(int(axis), float(x0), float(dx), int(first), int(count))
+    _check(lib().scabem_set_precond_circulant(op, mesh, C.byref(c), _stream(stream)))
+
+
+def scabem_precond_apply(op, v, z, nrhs=1, ld=None, transpose=False, stream=None):
+    """z = M^-1 v with the solver's preconditioner (complex128 device buffers)."""
+    if ld is None:
+        ld = v.shape[-1] if nrhs > 1 else v.shape[0]
+    _check(lib().scabem_precond_apply(op, _ptr(v), _ptr(z), nrhs, ld, 1 if transpose else 0, _stream(stream)))
 
 
 def scabem_fields_eh(op, x, pts, side=0, inc=None, nrhs=1, ld=None, stream=None):

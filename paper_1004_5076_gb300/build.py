@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libscabem.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["capi.cu", "setup.cu", "fft.cu", "apply.cu", "solve.cu", "measure.cu"]
+SOURCES = ["capi.cu", "setup.cu", "fft.cu", "apply.cu", "solve.cu", "measure.cu", "precond.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -104,6 +104,21 @@ void free_prec(PrecData<R>& pd) {
   pd = PrecData<R>();
 }
 
+// The axis-0 intermediates, once the active columns and the (y, z) mode are
+// known: compact (active columns only) for the direct sums, whole planes for
+// the FFT planes; the axis-0 transform writes only the active columns, so
+// the rest of a whole plane stays zero from here.
+template <typename R>
+int alloc_st(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
+  if (!pd.built) return SCABEM_OK;
+  const int64_t n = col_stride_st(op);
+  int rc;
+  if ((rc = dalloc(&pd.stA, n)) || (rc = dalloc(&pd.stB, n))) return rc;
+  CK(cudaMemsetAsync(pd.stA, 0, sizeof(cx<R>) * n, s));
+  CK(cudaMemsetAsync(pd.stB, 0, sizeof(cx<R>) * n, s));
+  return SCABEM_OK;
+}
+
 template <typename R>
 int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) {
   int rc;
@@ -113,7 +128,6 @@ int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) 
   if ((rc = dalloc(&pd.tp, op->Q * 16))) return rc;
   if (!workspaces) return SCABEM_OK;
   const int64_t ng = (int64_t)op->n[0] * op->n[1] * op->n[2];
-  const int64_t C = (int64_t)op->n[1] * op->n[2];
   for (int a = 0; a < 3; ++a) {
     if ((rc = dalloc(&pd.tw[a], op->P[a]))) return rc;
     if ((rc = make_twiddles<R>(pd.tw[a], op->P[a], s))) return rc;
@@ -123,12 +137,8 @@ int alloc_prec(scabem_op* op, PrecData<R>& pd, bool workspaces, cudaStream_t s) 
   if ((rc = dalloc(&pd.src, NFIELD_OUT * ng))) return rc;
   // grid points no stencil covers are never written by the projection
   CK(cudaMemsetAsync(pd.src, 0, sizeof(cx<R>) * NFIELD_OUT * ng, s));
-  if ((rc = dalloc(&pd.stA, (int64_t)NFIELD_OUT * op->P[0] * C))) return rc;
-  // the axis-0 transform writes only the columns some stencil covers
-  CK(cudaMemsetAsync(pd.stA, 0, sizeof(cx<R>) * NFIELD_OUT * op->P[0] * C, s));
   if ((rc = dalloc(&pd.recb, op->Q * 2 * NREC))) return rc;
   if ((rc = dalloc(&pd.sbar, 2 * op->nt * 12))) return rc;
-  if ((rc = dalloc(&pd.stB, (int64_t)NFIELD_OUT * op->P[0] * C))) return rc;
   if ((rc = dalloc(&pd.grid, NFIELD_OUT * ng))) return rc;
   if ((rc = dalloc(&pd.val, op->nt * 12))) return rc;
   pd.built = true;
@@ -187,6 +197,20 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Stage host x on the device when needed, then run fn(device x).
+template <typename F>
+int with_device_x(scabem_op* op, const void* x, int nrhs, int64_t ld, cudaStream_t s, F fn) {
+  if (is_device_ptr(x)) return fn(x);
+  void* dx = nullptr;
+  const size_t bytes = sizeof(cx<double>) * ld * nrhs;
+  CK(cudaMalloc(&dx, bytes));
+  CK(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, s));
+  const int rc = fn(dx);
+  cudaStreamSynchronize(s);
+  cudaFree(dx);
+  return rc;
 }
 
 template <typename R>
@@ -620,6 +644,9 @@ int scabem_op_create(scabem_mesh_t m, const scabem_media* md, const scabem_grid_
   TRY(upload(op->eunk, eunk.data(), sizeof(int32_t) * eunk.size()));
   TRY(setup_geometry(op, m, s));
   TRY(setup_gather(op, s));
+  op->cst = op->tdirect ? op->nac : (int64_t)op->n[1] * op->n[2];
+  TRY(alloc_st(op, op->d, s));
+  TRY(alloc_st(op, op->f, s));
   TRY(setup_green(op, s));
   TRY(setup_near(op, s));
   TRY(setup_sigma_monomial(op, 0, nullptr, s));
@@ -742,6 +769,7 @@ int scabem_profile_read(scabem_op_t op, double* stage_ms, int64_t* n_applies) {
 void scabem_op_destroy(scabem_op_t op) {
   if (!op) return;
   for (auto e : op->prof.ev) cudaEventDestroy(e);
+  circulant_release(op);
   cudaFree(op->tri);
   cudaFree(op->cX);
   cudaFree(op->unk);
@@ -1039,6 +1067,68 @@ int scabem_fields(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const
   int rc = fields_impl(op, dx, nrhs, ld, pts, npts, inc, E, s);
   cudaFree(dx);
   return rc;
+}
+
+int scabem_set_precond_circulant(scabem_op_t op, scabem_mesh_t mesh, const scabem_circulant* c, void* stream) {
+  if (!op || !mesh || !c || c->axis < 0 || c->axis > 2 || !(c->dx > 0) || !std::isfinite(c->x0) || c->first < 0 ||
+      c->count < 0 || (c->count > 0 && c->count < 2) || c->count > 4096 || mesh->nt != op->nt || mesh->N != op->N) {
+    set_error("scabem_set_precond_circulant: bad argument (axis 0..2, dx > 0, first >= 0, count 0 or 2..4096, "
+              "the operator's mesh)");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = take_timeout(op)) return rc;
+  const int rc = setup_circulant(op, mesh, c, s);
+  const int rt = take_timeout(op);
+  return rc ? rc : rt;
+}
+
+int scabem_precond_apply(scabem_op_t op, const void* v, void* z, int32_t nrhs, int64_t ld, int32_t transpose,
+                         void* stream) {
+  if (!op || !v || !z || nrhs < 0 || ld < op->N || transpose < 0 || transpose > 1) {
+    set_error("scabem_precond_apply: bad argument");
+    return SCABEM_E_ARG;
+  }
+  if (nrhs == 0) return SCABEM_OK;
+  if (!is_device_ptr(v) || !is_device_ptr(z)) {
+    set_error("scabem_precond_apply: v and z must be device memory");
+    return SCABEM_E_ARG;
+  }
+  return precond_apply(op, (const cx<double>*)v, (cx<double>*)z, (cudaStream_t)stream, transpose != 0, nrhs, ld, ld);
+}
+
+int scabem_fields_eh(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const double* pts, int32_t npts,
+                     int32_t side, const scabem_source* inc, double* E, double* H, void* stream) {
+  if (!op || !x || !pts || !E || !H || npts <= 0 || nrhs < 0 || ld < op->N || side < 0 || side > 1) {
+    set_error("scabem_fields_eh: bad argument (npts > 0, side 0 or 1, ld >= N)");
+    return SCABEM_E_ARG;
+  }
+  if (!op->d.built) {
+    set_error("scabem_fields_eh needs the complex128 operator");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  return with_device_x(op, x, nrhs, ld, s, [&](const void* dx) {
+    return fields_eh_impl(op, dx, nrhs, ld, pts, npts, side, inc, E, H, s);
+  });
+}
+
+int scabem_poynting_rate(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const scabem_poynting* p,
+                         const scabem_source* inc, double* out, void* stream) {
+  if (!op || !x || !p || !out || nrhs < 0 || ld < op->N || p->n < 1 || p->n > 64 || !(p->core[0] > 0) ||
+      !(p->core[1] > 0) || !(p->box[0] > p->core[0]) || !(p->box[1] > p->core[1]) || !(p->slab > 0) ||
+      !std::isfinite(p->xc)) {
+    set_error("scabem_poynting_rate: bad argument (1 <= n <= 64, 0 < core < box, slab > 0)");
+    return SCABEM_E_ARG;
+  }
+  if (!op->d.built) {
+    set_error("scabem_poynting_rate needs the complex128 operator");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  return with_device_x(op, x, nrhs, ld, s, [&](const void* dx) {
+    return poynting_impl(op, dx, nrhs, ld, p, inc, out, s);
+  });
 }
 
 static bool decay_grid_ok(double alo, double ahi, int32_t na, double blo, double bhi, int32_t nb) {

@@ -124,11 +124,11 @@ struct PrecData {
   cx<R>* summ = nullptr;  // nt * 3 sets * 4
   cx<R>* qsrc = nullptr;  // Q * 12 weighted point sources
   cx<R>* src = nullptr;   // 16 * n0 n1 n2 (12 sources; 16 in the transposed apply)
-  cx<R>* stA = nullptr;   // 16 * P0 * n1 n2 (12 fields in the apply, 16 in the transposed apply)
+  cx<R>* stA = nullptr;   // 16 * P0 * cst (12 fields in the apply, 16 in the transposed apply)
   cx<R>* recb = nullptr;  // Q * 2 * NREC record adjoints (transposed apply)
   cx<R>* sbar = nullptr;  // 2 * nt * 12: summary adjoints (near + direct, total)
   cx<R>* nadj = nullptr;  // npairs * 12: per-pair near contributions (transposed apply)
-  cx<R>* stB = nullptr;   // 16 * P0 * n1 n2
+  cx<R>* stB = nullptr;   // 16 * P0 * cst
   cx<R>* grid = nullptr;  // n0 n1 n2 * 16, point-major: [point][medium][J, M set][A or F (3), phi or psi]
   cx<R>* val = nullptr;   // nt * 3 * 4
   cx<R>* xs = nullptr;    // staging for host x/y: N * nrhs_cap
@@ -137,6 +137,17 @@ struct PrecData {
   // right-hand sides the forward workspaces (summ, qsrc, src, stA, stB, grid)
   // hold side by side, at the column strides below
   int kcap = 1;
+};
+
+// Circulant preconditioner of the plain-surface block over R regular slices
+// of m unknowns each (precond.cu); R = 0 when not set.
+struct Circulant {
+  int R = 0, m = 0;
+  int32_t* idx = nullptr;     // R * m unknown indices, slice-major, in the common local order
+  double* sgn = nullptr;      // R * m orientation signs
+  cx<double>* inv = nullptr;  // R * m * m inverses of the DFT blocks of Strang's circulant
+  cx<double>* work = nullptr;  // 2 * KBATCH * R * m spectra
+  cx<double>* tw = nullptr;   // R twiddles exp(-2 pi i k / R)
 };
 
 struct scabem_op {
@@ -184,6 +195,10 @@ struct scabem_op {
   // with ghat.  acoord[j] = (i1 - b1) << 16 | (i2 - b2) of active column j.
   int transverse = 0;
   bool planes_fit = true;  // the (y, z) plane fits the 2-D FFT plane kernels
+  // columns per (field, k0) of the axis-0 intermediates stA, stB: the nac
+  // active columns in order (compact) for the direct (y, z) sums, all n1 n2
+  // for the FFT planes
+  int64_t cst = 0;
   bool tdirect = false;
   int R1 = 0, R2 = 0;
   int32_t* acoord = nullptr;  // nac
@@ -205,6 +220,7 @@ struct scabem_op {
   int32_t* eunk = nullptr;  // ne * 3: unknown (= row) indices of the edge, -1 unused
   cx<double>* pinv = nullptr;  // ne * 9
   int precond_singular = 0;
+  Circulant circ;
   PrecData<float> f;
   PrecData<double> d;
   int* err = nullptr;  // device error flag
@@ -220,7 +236,7 @@ inline int64_t col_stride_grid(const scabem_op* op) {  // src and grid
   return (int64_t)NFIELD_OUT * op->n[0] * op->n[1] * op->n[2];
 }
 inline int64_t col_stride_st(const scabem_op* op) {  // stA and stB
-  return (int64_t)NFIELD_OUT * op->P[0] * op->n[1] * op->n[2];
+  return (int64_t)NFIELD_OUT * op->P[0] * op->cst;
 }
 inline int64_t col_stride_summ(const scabem_op* op) { return op->nt * 12; }
 inline int64_t col_stride_qsrc(const scabem_op* op) { return op->Q * 12; }
@@ -266,6 +282,11 @@ int setup_gather(scabem_op* op, cudaStream_t s);
 // k right-hand sides: column c of in / out starts at c * cs_in / c * cs_out
 int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed = false,
                   int k = 1, int64_t cs_in = 0, int64_t cs_out = 0);
+// precond.cu
+int setup_circulant(scabem_op* op, const scabem_mesh* mesh, const scabem_circulant* c, cudaStream_t s);
+int circulant_apply(scabem_op* op, const cx<double>* in, cx<double>* out, int k, int64_t cs_in, int64_t cs_out,
+                    cudaStream_t s);
+void circulant_release(scabem_op* op);
 // apply.cu
 template <typename R>
 int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s);
@@ -306,6 +327,10 @@ int fields_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double
                 const scabem_source* inc, double* E, cudaStream_t s);
 int reflection_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_probe* pr,
                     const scabem_source* inc, double* out, cudaStream_t s);
+int fields_eh_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double* pts, int npts, int side,
+                   const scabem_source* inc, double* E, double* H, cudaStream_t s);
+int poynting_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_poynting* P,
+                  const scabem_source* inc, double* out, cudaStream_t s);
 int decay_fit_impl(const double* t, const double* E, int npts, double alo, double ahi, int na, double blo, double bhi,
                    int nb, double* out, cudaStream_t s);
 int decay_rate_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_probe* pr, double alo,

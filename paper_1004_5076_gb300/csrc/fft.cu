@@ -173,11 +173,13 @@ struct Tot {
 // Stage A on the active columns acol[0 .. nac) of the [field][i0][c] layout
 // (C columns per i0); one CTA owns CB of them for one field over the whole
 // axis 0 (smem: [P0][CB], lines = columns).  Inputs i0 >= n_in are zero.
+// The output has Cout columns per (field, k0): active column j goes to
+// column j (compact, Cout = nac) or to acol[j] (whole planes, Cout = C).
 template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS) k_axis0(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
                                                        int n_in, int P0, int C, const int32_t* __restrict__ acol,
                                                        int nac, int CB, const cx<R>* __restrict__ tw,
-                                                       int64_t cs_in, int64_t cs_out) {
+                                                       int64_t cs_in, int64_t cs_out, int64_t Cout, int compact) {
   extern __shared__ unsigned char smem_raw[];
   cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* b0 = tws + P0;
@@ -196,15 +198,16 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis0(const cx<R>* __restrict__
   }
   __syncthreads();
   fft_lines<R, -1, Tot<R>::L>(b0, ilog2(P0), lcb, 1, CB, tws);
-  const int64_t fout = (int64_t)f * P0 * C;
+  const int64_t fout = (int64_t)f * P0 * Cout;
   for (int idx = threadIdx.x; idx < P0 * CB; idx += FFT_THREADS) {
     const int k0 = idx >> lcb, l = idx & (CB - 1);
-    if (a0 + l < nac) out[fout + (int64_t)k0 * C + acol[a0 + l]] = b0[idx];
+    if (a0 + l < nac) out[fout + (int64_t)k0 * Cout + (compact ? a0 + l : acol[a0 + l])] = b0[idx];
   }
 }
 
 // Stage C with point-major output, on the active columns acol[0 .. nac)
-// only (the potentials are read nowhere else): one CTA owns NC of them for one group of 4
+// only (the potentials are read nowhere else; the input holds Cin columns
+// per (field, k0), compact or whole planes as stage A wrote them): one CTA owns NC of them for one group of 4
 // output fields over axis 0 (line l = field * NC + column) and writes
 // out[(i0 * C + c) * 16 + 4 * grp + f] for i0 < n_out, so the 16 potentials of
 // a grid point are contiguous and each group of 4 fills whole 32-byte sectors.
@@ -212,7 +215,7 @@ template <typename R>
 __global__ void __launch_bounds__(FFT_THREADS) k_axis0_pm(const cx<R>* __restrict__ in, cx<R>* __restrict__ out,
                                                           int n_out, int P0, int C, const int32_t* __restrict__ acol,
                                                           int nac, int NC, const cx<R>* __restrict__ tw,
-                                                          int64_t cs_in, int64_t cs_out) {
+                                                          int64_t cs_in, int64_t cs_out, int64_t Cin, int compact) {
   extern __shared__ unsigned char smem_raw[];
   cx<R>* tws = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* b0 = tws + P0;
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis0_pm(const cx<R>* __restric
     const int i0 = idx >> lcb, l = idx & (CB - 1);
     const int fl = l >> lnc, cl = l & (NC - 1);
     cx<R> v = czero<R>();
-    if (a0 + cl < nac) v = in[((int64_t)(4 * grp + fl) * P0 + i0) * C + acol[a0 + cl]];
+    if (a0 + cl < nac) v = in[((int64_t)(4 * grp + fl) * P0 + i0) * Cin + (compact ? a0 + cl : acol[a0 + cl])];
     b0[idx] = v;
   }
   __syncthreads();
@@ -673,7 +676,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __res
                                                               const cx<R>* __restrict__ gtI, int P0, int C,
                                                               const int32_t* __restrict__ acol,
                                                               const int32_t* __restrict__ acoord, int nac, int R1,
-                                                              int R2, int ident, int64_t cs) {
+                                                              int R2, int ident, int64_t cs, int compact) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   A += blockIdx.z * cs;  // right-hand side blockIdx.z
   B += blockIdx.z * cs;
@@ -687,7 +690,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __res
   for (int idx = threadIdx.x; idx < nac * 8; idx += PD_THREADS) {
     const int v = idx / nac, j = idx - v * nac;  // consecutive threads: consecutive columns of one field
     const int f = ident ? 8 * med + v : (v < 4 ? (med ? 4 + v : v) : 8 + (v - 4));
-    src[j * 8 + v] = A[((int64_t)f * P0 + k0) * C + acol[j]];
+    src[j * 8 + v] = A[((int64_t)f * P0 + k0) * C + (compact ? j : acol[j])];
   }
   for (int i = threadIdx.x; i < nac; i += PD_THREADS) crd[i] = acoord[i];
   __syncthreads();
@@ -701,7 +704,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_planes_direct(const cx<R>* __res
       const int d1 = abs(i1 - (cj >> 16)), d2 = abs(i2 - (cj & 0xffff));
       acc.mac(T[d1 * R2 + d2], src + j * 8);
     }
-    const int64_t c = acol[i];
+    const int64_t c = compact ? i : acol[i];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
       const int fo = ident ? 8 * med + v : (med ? (v < 4 ? 8 + v : 12 + (v - 4)) : v);
@@ -826,7 +829,8 @@ static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s, int nco
   const size_t sm = (size_t)P0 * (4 * nc + 1) * sizeof(cx<R>);
   if (int rc_ = set_max_smem(op->device, (const void*)k_axis0_pm<R>, (int)sm)) return rc_;
   k_axis0_pm<R><<<dim3((unsigned)cdiv(op->nac, nc), NFIELD_OUT / 4, ncol), FFT_THREADS, sm, s>>>(
-      pd.stB, pd.grid, n0, P0, C, op->acol, (int)op->nac, nc, pd.tw[0], col_stride_st(op), col_stride_grid(op));
+      pd.stB, pd.grid, n0, P0, C, op->acol, (int)op->nac, nc, pd.tw[0], col_stride_st(op), col_stride_grid(op),
+      op->cst, op->tdirect ? 1 : 0);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }
@@ -847,16 +851,17 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint, int n
   // stage A
   if (int rc_ = set_max_smem(op->device, (const void*)k_axis0<R>, (int)sm0)) return rc_;
   k_axis0<R><<<dim3((unsigned)cdiv(op->nac, cb), nf, ncol), FFT_THREADS, sm0, s>>>(
-      pd.src, pd.stA, n0, P0, C, op->acol, (int)op->nac, cb, pd.tw[0], col_stride_grid(op), col_stride_st(op));
+      pd.src, pd.stA, n0, P0, C, op->acol, (int)op->nac, cb, pd.tw[0], col_stride_grid(op), col_stride_st(op),
+      op->cst, op->tdirect ? 1 : 0);
   CK(cudaGetLastError());
   prof_mark(op, s);
   // stage B
   if (op->tdirect) {
     const size_t sm = ((size_t)op->nac * 8 + (size_t)op->R1 * op->R2) * sizeof(cx<R>) + sizeof(int32_t) * op->nac;
     if (int rc_ = set_max_smem(op->device, (const void*)k_planes_direct<R>, (int)sm)) return rc_;
-    k_planes_direct<R><<<dim3(P0, 2, ncol), PD_THREADS, sm, s>>>(pd.stA, pd.stB, pd.gt[0], pd.gt[1], P0, C,
-                                                                 op->acol, op->acoord, (int)op->nac, op->R1, op->R2,
-                                                                 id, col_stride_st(op));
+    k_planes_direct<R><<<dim3(P0, 2, ncol), PD_THREADS, sm, s>>>(pd.stA, pd.stB, pd.gt[0], pd.gt[1], P0,
+                                                                 (int)op->cst, op->acol, op->acoord, (int)op->nac,
+                                                                 op->R1, op->R2, id, col_stride_st(op), 1);
     CK(cudaGetLastError());
     prof_mark(op, s);
     return axis0_inverse(op, pd, s, ncol);

@@ -905,6 +905,8 @@ int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStre
   k_precond_apply<<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out,
                                                                        transposed ? 1 : 0, cs_in, cs_out);
   CK(cudaGetLastError());
+  // the periodic plain-surface unknowns: the circulant preconditioner (forward solves)
+  if (op->circ.R > 0 && !transposed) return circulant_apply(op, in, out, k, cs_in, cs_out, s);
   return SCABEM_OK;
 }
 

@@ -237,6 +237,123 @@ __global__ void k_rows_out(const cd* __restrict__ val, const int32_t* __restrict
   y[i] = mk((R)v.re, (R)v.im);
 }
 
+// E and H of one current set at points (Eqs. 15-16 evaluated off the
+// surface, Eq. 8): side 0 = the interior set (J_i, -M) radiating in the
+// interior medium, plus the interior incident field when has_inc; side 1 =
+// the exterior set (J_e, M) in the exterior medium.  With A, phi of J and F,
+// psi of M (point-source quadrature over every source point):
+//   E = -z (jk A + (j/k) grad phi) - curl F,   H = curl A - (jk F + (j/k) grad psi) / z.
+// One block per point; the 18 complex sums are reduced by warp shuffles and
+// shared memory.
+__global__ void __launch_bounds__(256) k_fields_eh(const cd* __restrict__ summ, const double* __restrict__ tri,
+                                                   const double* __restrict__ qp, const double* __restrict__ qw,
+                                                   int64_t Q, int q, const double* __restrict__ pts, double k,
+                                                   double z, int side, scabem_source inc, int has_inc,
+                                                   cd* __restrict__ E, cd* __restrict__ H) {
+  const int pi = blockIdx.x;
+  const double r[3] = {pts[3 * pi], pts[3 * pi + 1], pts[3 * pi + 2]};
+  const double msign = side ? 1.0 : -1.0;
+  cd acc[18];  // A_J, grad phi_J, curl A_J, F_M, grad psi_M, curl F_M
+#pragma unroll
+  for (int v = 0; v < 18; ++v) acc[v] = mk(0.0, 0.0);
+  for (int64_t b = threadIdx.x; b < Q; b += blockDim.x) {
+    const int64_t t = b / q;
+    const double* g = tri + 16 * t;
+    const double rel[3] = {qp[3 * b] - g[9], qp[3 * b + 1] - g[10], qp[3 * b + 2] - g[11]};
+    const cd* sj = summ + (3 * t + (side ? 0 : 1)) * 4;
+    const cd* sm = summ + (3 * t + 2) * 4;
+    const double D[3] = {r[0] - qp[3 * b], r[1] - qp[3 * b + 1], r[2] - qp[3 * b + 2]};
+    const double R = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    double sn, cs;
+    sincos(k * R, &sn, &cs);
+    const double w = qw[b] / (4.0 * M_PI * R);
+    const cd G = mk(w * cs, -w * sn);
+    const cd dG = -(mk(1.0 / R, k) * G) * (1.0 / R);  // grad G = dG D
+    const cd gG[3] = {D[0] * dG, D[1] * dG, D[2] * dG};
+    cd J[3], M[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      J[c] = rel[c] * sj[0] - sj[1 + c];
+      M[c] = msign * (rel[c] * sm[0] - sm[1 + c]);
+    }
+    const cd rJ = 2.0 * sj[0], rM = (2.0 * msign) * sm[0];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+      acc[c] += G * J[c];
+      acc[3 + c] += gG[c] * rJ;
+      acc[6 + c] += gG[c1] * J[c2] - gG[c2] * J[c1];
+      acc[9 + c] += G * M[c];
+      acc[12 + c] += gG[c] * rM;
+      acc[15 + c] += gG[c1] * M[c2] - gG[c2] * M[c1];
+    }
+  }
+  __shared__ double red[8][36];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < 18; ++v)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[v].re += __shfl_xor_sync(0xffffffffu, acc[v].re, o);
+      acc[v].im += __shfl_xor_sync(0xffffffffu, acc[v].im, o);
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < 18; ++v) {
+      red[wp][2 * v] = acc[v].re;
+      red[wp][2 * v + 1] = acc[v].im;
+    }
+  __syncthreads();
+  __shared__ double tot[36];
+  if (threadIdx.x < 36) {
+    double v = 0.0;
+    for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) v += red[k2][threadIdx.x];
+    tot[threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cd Ei[3], Hi[3];
+    for (int c = 0; c < 3; ++c) Ei[c] = Hi[c] = mk(0.0, 0.0);
+    if (has_inc && side == 0) incident(inc, k, z, r, Ei, Hi);
+    for (int c = 0; c < 3; ++c) {
+      const cd AJ = mk(tot[2 * c], tot[2 * c + 1]), gJ = mk(tot[6 + 2 * c], tot[7 + 2 * c]);
+      const cd cJ = mk(tot[12 + 2 * c], tot[13 + 2 * c]), AM = mk(tot[18 + 2 * c], tot[19 + 2 * c]);
+      const cd gM = mk(tot[24 + 2 * c], tot[25 + 2 * c]), cM = mk(tot[30 + 2 * c], tot[31 + 2 * c]);
+      E[3 * pi + c] = Ei[c] - z * (k * mulj(AJ) + (1.0 / k) * mulj(gJ)) - cM;
+      H[3 * pi + c] = Hi[c] + cJ - (1.0 / z) * (k * mulj(AM) + (1.0 / k) * mulj(gM));
+    }
+  }
+}
+
+// Perimeter loss of a band of the surface (Sec. III-B): part[b] = sum over the
+// quadrature points of block b with |x_axis - xc| < slab of sigma eta0 w |M|^2
+// (|E_tan| = |n x M| = |M| on the sheet).
+__global__ void k_band_loss(const cd* __restrict__ summ, const double* __restrict__ tri, const double* __restrict__ qp,
+                            const double* __restrict__ qw, const double* __restrict__ sig, int64_t Q, int q, int axis,
+                            double xc, double slab, double* __restrict__ part) {
+  __shared__ double sm[256];
+  double v = 0.0;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < Q; b += (int64_t)gridDim.x * blockDim.x) {
+    if (fabs(qp[3 * b + axis] - xc) >= slab) continue;
+    const int64_t t = b / q;
+    const double* g = tri + 16 * t;
+    const cd* m = summ + (3 * t + 2) * 4;
+    double m2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const cd M = (qp[3 * b + c] - g[9 + c]) * m[0] - m[1 + c];
+      m2 += M.re * M.re + M.im * M.im;
+    }
+    v += sig[b] * qw[b] * m2;
+  }
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
 // ---------------------------------------------------------------- batched GMRES (FP64 Krylov work)
 // K <= KBATCH right-hand sides run in lockstep.  One batched operator apply
 // per Arnoldi step serves all K (the point kernel reads the near records
@@ -249,22 +366,23 @@ __global__ void k_rows_out(const cd* __restrict__ val, const int32_t* __restrict
 // every K-column work array starts at c * N; the basis of column c holds
 // m + 1 vectors of N from c * (m + 1) * N.
 constexpr int BG_THREADS = 256;
-constexpr int BG_BLOCKS = 152;  // row blocks per column of the reductions (one per SM)
+constexpr int BG_BLOCKS = 4 * 152;  // row blocks per column of the reductions (four per SM)
 constexpr int BG_TC = 8;        // basis vectors per tile of the dot products
 constexpr int FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2;
 
 // part[(c * rb + b) * ldp + col] = sum over row block b of conj(V_c[:, col]) . w_c,
-// col in the tile blockIdx.y; skipped for columns with need[c] == 0
+// col in the tile blockIdx.y; with self_col, column nv is w_c itself (its
+// squared norm); skipped for columns with need[c] == 0
 __global__ void __launch_bounds__(BG_THREADS) k_bdots(const cd* __restrict__ V, int64_t csV, int nv,
                                                       const cd* __restrict__ w, int64_t N, cd* __restrict__ part,
-                                                      int ldp, const int* __restrict__ need) {
+                                                      int ldp, const int* __restrict__ need, int self_col) {
   const int c = blockIdx.z;
   if (need && !need[c]) return;  // the whole block
   V += c * csV;
   w += c * N;
   __shared__ double sm[BG_THREADS / 32][2 * BG_TC];
   const int c0 = blockIdx.y * BG_TC;
-  const int nc = min(BG_TC, nv - c0);
+  const int nc = min(BG_TC, nv + self_col - c0);
   double ar[BG_TC], ai[BG_TC];
 #pragma unroll
   for (int k = 0; k < BG_TC; ++k) ar[k] = ai[k] = 0.0;
@@ -273,7 +391,7 @@ __global__ void __launch_bounds__(BG_THREADS) k_bdots(const cd* __restrict__ V, 
 #pragma unroll
     for (int k = 0; k < BG_TC; ++k)
       if (k < nc) {
-        const cd a = V[(int64_t)(c0 + k) * N + i];
+        const cd a = c0 + k < nv ? V[(int64_t)(c0 + k) * N + i] : b;
         ar[k] += a.re * b.re + a.im * b.im;
         ai[k] += a.re * b.im - a.im * b.re;
       }
@@ -364,9 +482,12 @@ __global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cd* __restrict_
 // set_need, also need[c] = (out < |w| before the pass / sqrt 2), |w| before
 // read from out[c * ostride - 1] (the DGKS test after the first pass).
 __global__ void k_bnorm_fin(const double* __restrict__ nparts, int nb, double* __restrict__ out, int ostride,
-                            const int* __restrict__ need, int* __restrict__ set_need) {
+                            const int* __restrict__ need, int* __restrict__ set_need, const cd* __restrict__ selfdot,
+                            int ldh) {
   const int c = blockIdx.x;
   if (need && !need[c]) return;
+  // |w| before the pass, from the self column of the first pass's dot products
+  if (selfdot && threadIdx.x == 0) out[(int64_t)c * ostride - 1] = sqrt(fmax(selfdot[(int64_t)c * ldh].re, 0.0));
   __shared__ double sm[BG_THREADS];
   double v = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) v += nparts[(int64_t)c * nb + b];
@@ -399,6 +520,7 @@ struct BState {
   int* act;     // K still iterating in this cycle
   int* jc;      // K basis vectors in this cycle's least squares
   int* iters;   // K iterations so far
+  int* col;     // K the right-hand side (column of r, d, u, t) that slot c works on
 };
 
 // The Givens step of Arnoldi column j for every active column (one thread
@@ -466,13 +588,14 @@ __global__ void k_bscale(const cd* __restrict__ w, cd* __restrict__ V, int64_t c
     V[i] = s * w[i];
 }
 
-// start of a cycle for the active columns: v_c,0 = t_c / beta_c, g_c = beta_c e_1
-__global__ void k_bstart(const cd* __restrict__ t, cd* __restrict__ V, int64_t csV, BState S, int m, int64_t N) {
+// start of a cycle in slot c (the slot's right-hand side is column col[c]
+// of t): v_c,0 = t / beta_c, g_c = beta_c e_1
+__global__ void k_bstart(const cd* __restrict__ t, const int* __restrict__ col, cd* __restrict__ V, int64_t csV,
+                         BState S, int m, int64_t N) {
   const int c = blockIdx.y;
-  if (!S.act[c]) return;
   const double beta = S.nrm[4 * c + 3];
   const double s = beta > 1e-300 ? 1.0 / beta : 0.0;
-  t += c * N;
+  t += col[c] * N;
   V += c * csV;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     V[i] = s * t[i];
@@ -499,13 +622,14 @@ __global__ void k_backsub(BState S, int m, int K) {
   }
 }
 
-// u_c += V_c y_c over the cycle's jc[c] basis vectors
-__global__ void k_bupdate(const cd* __restrict__ V, int64_t csV, BState S, int m, cd* __restrict__ u, int64_t N) {
+// u (column col[c]) += V_c y_c over slot c's jc[c] basis vectors
+__global__ void k_bupdate(const cd* __restrict__ V, int64_t csV, BState S, int m, const int* __restrict__ col,
+                          cd* __restrict__ u, int64_t N) {
   const int c = blockIdx.y;
   const int j = S.jc[c];
   if (j == 0) return;
   V += c * csV;
-  u += c * N;
+  u += col[c] * N;
   const cd* y = S.y + (int64_t)c * m;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     cd acc = u[i];
@@ -575,7 +699,7 @@ struct BWork {
         (rc = get(&S.cs, K * m)) || (rc = get(&S.sn, K * m)) || (rc = get(&S.g, K * (m + 1))) ||
         (rc = get(&S.y, K * m)) || (rc = get(&S.h1, K * (m + 1))) || (rc = get(&S.h2, K * (m + 1))) ||
         (rc = get(&S.nrm, 4 * K)) || (rc = get(&S.rn0, K)) || (rc = get(&S.est, K)) || (rc = get(&S.need, K)) ||
-        (rc = get(&S.act, K)) || (rc = get(&S.jc, K)) || (rc = get(&S.iters, K)))
+        (rc = get(&S.act, K)) || (rc = get(&S.jc, K)) || (rc = get(&S.iters, K)) || (rc = get(&S.col, K)))
       return rc;
     if (c64 && ((rc = get(&zf, K * N)) || (rc = get(&wf, K * N)))) return rc;
     CK(cudaHostAlloc(reinterpret_cast<void**>(&word_h), 2 * sizeof(int), cudaHostAllocMapped));
@@ -590,7 +714,7 @@ int bnorms(const cd* x, BWork& W, double* out, int ostride, cudaStream_t s) {
   k_bvsub_norm<<<dim3(BG_BLOCKS, W.K), BG_THREADS, 0, s>>>(nullptr, 0, 0, nullptr, 0, const_cast<cd*>(x), W.N,
                                                            W.nparts, nullptr);
   CK(cudaGetLastError());
-  k_bnorm_fin<<<W.K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, out, ostride, nullptr, nullptr);
+  k_bnorm_fin<<<W.K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, out, ostride, nullptr, nullptr, nullptr, 0);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }
@@ -625,7 +749,10 @@ int bapply(scabem_op* op, const cd* z, cd* w, int prec, BWork& W, cudaStream_t s
 // Restarted GMRES for A d_c = r_c, c < K in lockstep, from d = 0 (r, d: K N
 // on the device).  use[c] = false leaves column c out (d_c = 0).  iters[c]
 // accumulates column c's inner iterations; est[c] is its last relative
-// residual (estimate, or true residual at a restart).
+// residual (estimate, or true residual at a restart).  Every restart cycle
+// runs only the columns still above tol, packed into the first slots (the
+// Krylov work of slot s belongs to column col[s]), so that converged
+// columns cost nothing in the batched apply.
 int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use, int prec, double tol, int maxit,
                 BWork& W, cudaStream_t s, std::vector<int>& iters, std::vector<double>& est) {
   const int64_t N = W.N;
@@ -634,62 +761,79 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
   BState& S = W.S;
   CK(cudaMemsetAsync(d, 0, sizeof(cd) * K * N, s));
   CK(cudaMemsetAsync(W.u, 0, sizeof(cd) * K * N, s));
-  CK(cudaMemsetAsync(S.iters, 0, sizeof(int) * K, s));
   if (int rc = bnorms(r, W, S.rn0, 1, s)) return rc;
-  std::vector<double> rn0(K);
+  std::vector<double> rn0(K), beta(K);
   CK(cudaMemcpyAsync(rn0.data(), S.rn0, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  std::vector<int> act(K), it0(K, 0);
-  int nact = 0;
+  std::vector<int> act(K);
   for (int c = 0; c < K; ++c) {
     if (use[c] && !std::isfinite(rn0[c])) {
       set_error("non-finite residual");
       return SCABEM_E_NONFINITE;
     }
     act[c] = use[c] && rn0[c] > 0.0;
-    nact += act[c];
     est[c] = 0.0;
+    beta[c] = rn0[c];
   }
-  if (nact == 0) return SCABEM_OK;
   // the first cycle starts from t = r, beta = |r|
   CK(cudaMemcpyAsync(W.t, r, sizeof(cd) * K * N, cudaMemcpyDeviceToDevice, s));
-  for (int c = 0; c < K; ++c)
-    CK(cudaMemcpyAsync(S.nrm + 4 * c + 3, S.rn0 + c, sizeof(double), cudaMemcpyDeviceToDevice, s));
   int lock = 0;  // lockstep iterations
+  std::vector<int> col, h_int(4 * K);
+  std::vector<double> h_slot(4 * K);
   while (true) {
-    CK(cudaMemcpyAsync(S.act, act.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
-    W.word_h[0] = nact;
+    col.clear();
+    for (int c = 0; c < K; ++c)
+      if (act[c]) col.push_back(c);
+    const int Ka = (int)col.size();
+    if (Ka == 0) break;
+    // slot state: column map, initial norms (rn0 for the estimate, beta for the start)
+    for (int a = 0; a < Ka; ++a) {
+      h_int[a] = col[a];
+      h_int[K + a] = 1;  // act
+      h_int[2 * K + a] = 0;  // iters
+      h_slot[a] = rn0[col[a]];
+      h_slot[K + a] = beta[col[a]];
+    }
+    CK(cudaMemcpyAsync(S.col, h_int.data(), sizeof(int) * Ka, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(S.act, h_int.data() + K, sizeof(int) * Ka, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(S.iters, h_int.data() + 2 * K, sizeof(int) * Ka, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(S.rn0, h_slot.data(), sizeof(double) * Ka, cudaMemcpyHostToDevice, s));
+    for (int a = 0; a < Ka; ++a)
+      CK(cudaMemcpyAsync(S.nrm + 4 * a + 3, h_slot.data() + K + a, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // the pageable sources above are read before they change
+    W.word_h[0] = Ka;
     W.word_h[1] = 0;
-    k_bstart<<<dim3(EW_BLOCKS / 4, K), 256, 0, s>>>(W.t, W.V, csV, S, m, N);
+    W.K = Ka;
+    k_bstart<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.t, S.col, W.V, csV, S, m, N);
     CK(cudaGetLastError());
     for (int j = 0; j < m && lock < maxit; ++j, ++lock) {
       // z = P^-1 v_j (right preconditioning), w = A z
-      if (int rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr, K, csV, N)) return rc;
+      if (int rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr, Ka, csV, N)) return rc;
       if (int rc = bapply(op, W.z, W.w, prec, W, s)) return rc;
-      // |w|, first pass h1 = V^H w, w -= V h1, |w|; DGKS test; second pass when asked
-      k_bvsub_norm<<<dim3(BG_BLOCKS, K), BG_THREADS, 0, s>>>(nullptr, 0, 0, nullptr, 0, W.w, N, W.nparts, nullptr);
-      CK(cudaGetLastError());
-      k_bnorm_fin<<<K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 0, 4, nullptr, nullptr);
-      CK(cudaGetLastError());
-      const int tiles = (int)cdiv(j + 1, BG_TC);
+      // first pass h1 = V^H w with |w|^2 in its column j + 1, w -= V h1, |w|; the
+      // DGKS test; the second pass only where it asks
+      const int tiles = (int)cdiv(j + 2, BG_TC);
       const int rb = std::max(8, BG_BLOCKS / tiles);
       for (int pass = 0; pass < 2; ++pass) {
         const int* need = pass ? S.need : nullptr;
         cd* h = pass ? S.h2 : S.h1;
-        k_bdots<<<dim3(rb, tiles, K), BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.w, N, W.part, m + 1, need);
+        const int tl = pass ? (int)cdiv(j + 1, BG_TC) : tiles;
+        const int rbp = pass ? std::max(8, BG_BLOCKS / tl) : rb;
+        k_bdots<<<dim3(rbp, tl, Ka), BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.w, N, W.part, m + 1, need,
+                                                         pass ? 0 : 1);
         CK(cudaGetLastError());
-        k_breduce<<<dim3(j + 1, K), BG_THREADS, 0, s>>>(W.part, rb, m + 1, h, m + 1, need);
+        k_breduce<<<dim3(j + 1 + (pass ? 0 : 1), Ka), BG_THREADS, 0, s>>>(W.part, rbp, m + 1, h, m + 1, need);
         CK(cudaGetLastError());
-        k_bvsub_norm<<<dim3(BG_BLOCKS, K), BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.w, N, W.nparts, need);
+        k_bvsub_norm<<<dim3(BG_BLOCKS, Ka), BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.w, N, W.nparts, need);
         CK(cudaGetLastError());
-        k_bnorm_fin<<<K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 1 + pass, 4, need,
-                                             pass ? nullptr : S.need);
+        k_bnorm_fin<<<Ka, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 1 + pass, 4, need,
+                                              pass ? nullptr : S.need, pass ? nullptr : S.h1 + (j + 1), m + 1);
         CK(cudaGetLastError());
       }
-      k_givens<<<1, 32, 0, s>>>(S, j, m, K, tol, W.word_d);
+      k_givens<<<1, 32, 0, s>>>(S, j, m, Ka, tol, W.word_d);
       CK(cudaGetLastError());
       if (j + 1 < m) {
-        k_bscale<<<dim3(EW_BLOCKS / 4, K), 256, 0, s>>>(W.w, W.V, csV, j + 1, S.nrm, S.need, N);
+        k_bscale<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.w, W.V, csV, j + 1, S.nrm, S.need, N);
         CK(cudaGetLastError());
       }
       // the host stays one step ahead: wait for the previous step, read its word
@@ -706,24 +850,25 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
           return SCABEM_E_BREAKDOWN;
         }
         if (reinterpret_cast<volatile int*>(W.word_h)[0] == 0) {
-          ++j, ++lock;
+          ++lock;
           break;
         }
       }
     }
-    // least squares and d = P^-1 u for every column that took part in the cycle
-    k_backsub<<<1, 32, 0, s>>>(S, m, K);
+    // least squares of the cycle into u (at each slot's column), then d = P^-1 u for all columns
+    k_backsub<<<1, 32, 0, s>>>(S, m, Ka);
     CK(cudaGetLastError());
-    k_bupdate<<<dim3(EW_BLOCKS / 4, K), 256, 0, s>>>(W.V, csV, S, m, W.u, N);
+    k_bupdate<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.V, csV, S, m, S.col, W.u, N);
     CK(cudaGetLastError());
+    W.K = K;
     if (int rc = precond_apply(op, W.u, d, s, W.tr, K, N, N)) return rc;
-    // columns that stopped inside the cycle (estimate at tol) are done; the
+    // slots that stopped inside the cycle (estimate at tol) are done; the
     // others restart from their true residual
-    std::vector<int> still(K), nit(K);
-    std::vector<double> e(K);
-    CK(cudaMemcpyAsync(still.data(), S.act, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(nit.data(), S.iters, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(e.data(), S.est, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    std::vector<int> still(Ka), nit(Ka);
+    std::vector<double> e(Ka);
+    CK(cudaMemcpyAsync(still.data(), S.act, sizeof(int) * Ka, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(nit.data(), S.iters, sizeof(int) * Ka, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(e.data(), S.est, sizeof(double) * Ka, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (W.word_h[1] & FLAG_NONFINITE) {
       set_error("non-finite Krylov vector");
@@ -733,12 +878,12 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
       set_error("GMRES breakdown");
       return SCABEM_E_BREAKDOWN;
     }
-    nact = 0;
-    for (int c = 0; c < K; ++c) {
-      iters[c] += nit[c] - it0[c];
-      it0[c] = nit[c];
-      if (act[c]) est[c] = e[c];
-      act[c] = act[c] && still[c];
+    int nact = 0;
+    for (int a = 0; a < Ka; ++a) {
+      const int c = col[a];
+      iters[c] += nit[a];
+      est[c] = e[a];
+      act[c] = still[a];
       nact += act[c];
     }
     if (nact == 0 || lock >= maxit) break;
@@ -749,15 +894,14 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
     std::vector<double> nb(4 * K);
     CK(cudaMemcpyAsync(nb.data(), S.nrm, sizeof(double) * 4 * K, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    nact = 0;
     for (int c = 0; c < K; ++c) {
       if (!act[c]) continue;
-      est[c] = nb[4 * c + 3] / rn0[c];
+      beta[c] = nb[4 * c + 3];
+      est[c] = beta[c] / rn0[c];
       act[c] = est[c] > tol;
-      nact += act[c];
     }
-    if (nact == 0) break;
   }
+  W.K = K;
   return SCABEM_OK;
 }
 
@@ -1183,6 +1327,160 @@ int fields_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double
   CK(cudaStreamSynchronize(s));
   cudaFree(dpts);
   cudaFree(dE);
+  return SCABEM_OK;
+}
+
+// E and H of one current set at host points (see k_fields_eh), per right-hand side.
+int fields_eh_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const double* pts, int npts, int side,
+                   const scabem_source* inc, double* E, double* H, cudaStream_t s) {
+  double* dpts = nullptr;
+  cd* dE = nullptr;
+  CK(cudaMalloc(&dpts, sizeof(double) * 3 * npts));
+  CK(cudaMalloc(&dE, sizeof(cd) * 6 * npts));
+  CK(cudaMemcpyAsync(dpts, pts, sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, s));
+  scabem_source S{};
+  if (inc) S = *inc;
+  const double k = side ? op->ke : op->ki, z = side ? op->ze : op->zi;
+  for (int col = 0; col < nrhs; ++col) {
+    int rc = compute_summ<double>(op, (const cd*)x + (int64_t)col * ld, op->d.summ, s);
+    if (rc) return rc;
+    k_fields_eh<<<npts, 256, 0, s>>>(op->d.summ, op->tri, op->qp, op->qw, op->Q, op->q, dpts, k, z, side, S,
+                                     inc ? 1 : 0, dE, dE + 3 * npts);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(E + (int64_t)col * 6 * npts, dE, sizeof(cd) * 3 * npts, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(H + (int64_t)col * 6 * npts, dE + 3 * npts, sizeof(cd) * 3 * npts, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  cudaFree(dpts);
+  cudaFree(dE);
+  return SCABEM_OK;
+}
+
+namespace {
+// Gauss-Legendre rule on [-1, 1]: the roots of P_n by Newton's method from
+// the estimate cos(pi (i - 1/4) / (n + 1/2)), weights 2 / ((1 - x^2) P_n'(x)^2).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int m = 2; m <= n; ++m) {
+        const double p2 = ((2.0 * m - 1.0) * t * p1 - (m - 1.0) * p0) / m;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);  // p1 = P_n(t), p0 = P_{n-1}(t)
+      const double dt = p1 / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    x[i] = t;
+    w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+struct QPoint {
+  double y, z, w;
+};
+// n x n Gauss-Legendre points of the rectangle [y0, y1] x [z0, z1]
+void gl_rect(double y0, double y1, double z0, double z1, int n, std::vector<QPoint>& out) {
+  std::vector<double> u, wu;
+  gauss_legendre(n, u, wu);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      out.push_back({0.5 * (y1 - y0) * u[i] + 0.5 * (y1 + y0), 0.5 * (z1 - z0) * u[j] + 0.5 * (z1 + z0),
+                     wu[i] * wu[j] * 0.25 * (y1 - y0) * (z1 - z0)});
+}
+}  // namespace
+
+// Decay rate by Poynting's theorem (Sec. III-B) at the cross-section
+// x = xc of a guide along x centred on y = z = 0.
+int poynting_impl(scabem_op* op, const void* x, int nrhs, int64_t ld, const scabem_poynting* P,
+                  const scabem_source* inc, double* out, cudaStream_t s) {
+  const int n = P->n;
+  const double hy = P->core[0], hz = P->core[1], Y = P->box[0], Z = P->box[1];
+  // cross-section: the core (interior field) and the eight rectangles around it (exterior field)
+  std::vector<QPoint> core, outer;
+  gl_rect(-hy, hy, -hz, hz, n, core);
+  const double ys[4] = {-Y, -hy, hy, Y}, zs[4] = {-Z, -hz, hz, Z};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      if (!(a == 1 && b == 1)) gl_rect(ys[a], ys[a + 1], zs[b], zs[b + 1], n, outer);
+  // outer boundary: lines y = +-Y (z in [-Z, Z]) and z = +-Z (y in [-Y, Y]), 2n points each;
+  // weight = Gauss weight x half length x the sign of the outward normal
+  std::vector<double> u, wu;
+  gauss_legendre(2 * n, u, wu);
+  std::vector<QPoint> side;
+  std::vector<int> side_comp;
+  for (int ax = 0; ax < 2; ++ax)
+    for (int sg = 1; sg >= -1; sg -= 2) {
+      const double half = ax == 0 ? Z : Y;
+      for (int i = 0; i < 2 * n; ++i) {
+        const double l = u[i] * half;
+        side.push_back(ax == 0 ? QPoint{sg * Y, l, wu[i] * half * sg} : QPoint{l, sg * Z, wu[i] * half * sg});
+        side_comp.push_back(1 + ax);
+      }
+    }
+  const int ni = (int)core.size(), ne = (int)(outer.size() + side.size());
+  std::vector<double> pi(3 * ni), pe(3 * ne);
+  for (int i = 0; i < ni; ++i) {
+    pi[3 * i] = P->xc;
+    pi[3 * i + 1] = core[i].y;
+    pi[3 * i + 2] = core[i].z;
+  }
+  for (int i = 0; i < ne; ++i) {
+    const QPoint& qq = i < (int)outer.size() ? outer[i] : side[i - outer.size()];
+    pe[3 * i] = P->xc;
+    pe[3 * i + 1] = qq.y;
+    pe[3 * i + 2] = qq.z;
+  }
+  std::vector<double> Ei(6 * ni), Hi(6 * ni), Ee(6 * ne), He(6 * ne);
+  const int nb = 152;
+  double* part = nullptr;
+  CK(cudaMalloc(&part, sizeof(double) * nb));
+  std::vector<double> hp(nb);
+  for (int col = 0; col < nrhs; ++col) {
+    const void* xcol = (const cd*)x + (int64_t)col * ld;
+    int rc = fields_eh_impl(op, xcol, 1, ld, pi.data(), ni, 0, inc, Ei.data(), Hi.data(), s);
+    if (rc) return rc;
+    rc = fields_eh_impl(op, xcol, 1, ld, pe.data(), ne, 1, nullptr, Ee.data(), He.data(), s);
+    if (rc) return rc;
+    auto sx = [](const double* E, const double* H) {  // Re (E x H*) . x
+      return (E[2] * H[4] + E[3] * H[5]) - (E[4] * H[2] + E[5] * H[3]);
+    };
+    double flux = 0.0, sidef = 0.0;
+    for (int i = 0; i < ni; ++i) flux += core[i].w * sx(&Ei[6 * i], &Hi[6 * i]);
+    for (int i = 0; i < (int)outer.size(); ++i) flux += outer[i].w * sx(&Ee[6 * i], &He[6 * i]);
+    for (int i = 0; i < (int)side.size(); ++i) {
+      const int j = (int)outer.size() + i;
+      const double* E = &Ee[6 * j];
+      const double* H = &He[6 * j];
+      // Re (E x H*) component 1 (y) or 2 (z)
+      const int c = side_comp[i], c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+      const double S = (E[2 * c1] * H[2 * c2] + E[2 * c1 + 1] * H[2 * c2 + 1]) -
+                       (E[2 * c2] * H[2 * c1] + E[2 * c2 + 1] * H[2 * c1 + 1]);
+      sidef += side[i].w * S;
+    }
+    // the sheet's loss around the perimeter: the band |x - xc| < slab over its width
+    rc = compute_summ<double>(op, (const cd*)xcol, op->d.summ, s);
+    if (rc) return rc;
+    k_band_loss<<<nb, 256, 0, s>>>(op->d.summ, op->tri, op->qp, op->qw, op->sig64, op->Q, op->q, 0, P->xc, P->slab,
+                                   part);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double loss = 0.0;
+    for (double v : hp) loss += v;
+    loss /= 2.0 * P->slab;
+    double* o = out + 4 * col;
+    o[0] = (loss + sidef) / (2.0 * flux);
+    o[1] = loss;
+    o[2] = sidef;
+    o[3] = flux;
+  }
+  cudaFree(part);
   return SCABEM_OK;
 }
 
