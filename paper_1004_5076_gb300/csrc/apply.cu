@@ -350,6 +350,73 @@ __device__ __forceinline__ void near_part(const cx<float>* d, const cx<float>* s
   for (int c = 0; c < NREC / 2; ++c) acc[c] = mk(A[c].x, A[c].y);
 }
 
+// The same sums in complex64 with the accumulator split as acc = P + j Q:
+// x s adds (s.re, s.re) * (x.re, x.im) to P and (s.im, s.im) * (x.re, x.im)
+// to Q, so that every record value enters the packed FMAs as the (re, im)
+// pair it is loaded as, and only the few source factors are duplicated.
+__device__ __forceinline__ void near_pq(const cx<float>* d, const cx<float>* sv, float2* P, float2* Q) {
+  float2 x[NCORR];
+#pragma unroll
+  for (int c = 0; c < NCORR; ++c) x[c] = make_float2(d[c].re, d[c].im);
+  const float2 ar = make_float2(sv[0].re, sv[0].re), ai = make_float2(sv[0].im, sv[0].im);
+  const float2 a2r = make_float2(2.f * sv[0].re, 2.f * sv[0].re), a2i = make_float2(2.f * sv[0].im, 2.f * sv[0].im);
+  float2 br[3], bi[3], nbr[3], nbi[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    br[c] = make_float2(sv[1 + c].re, sv[1 + c].re);
+    bi[c] = make_float2(sv[1 + c].im, sv[1 + c].im);
+    nbr[c] = make_float2(-sv[1 + c].re, -sv[1 + c].re);
+    nbi[c] = make_float2(-sv[1 + c].im, -sv[1 + c].im);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    P[c] = __ffma2_rn(x[1 + c], ar, P[c]);  // A += a dP1 - beta dP0
+    Q[c] = __ffma2_rn(x[1 + c], ai, Q[c]);
+    P[c] = __ffma2_rn(x[0], nbr[c], P[c]);
+    Q[c] = __ffma2_rn(x[0], nbi[c], Q[c]);
+    P[4 + c] = __ffma2_rn(x[4 + c], a2r, P[4 + c]);  // grad phi += 2a dQ
+    Q[4 + c] = __ffma2_rn(x[4 + c], a2i, Q[4 + c]);
+    P[7 + c] = __ffma2_rn(x[7 + c], ar, P[7 + c]);  // curl A += a dC
+    Q[7 + c] = __ffma2_rn(x[7 + c], ai, Q[7 + c]);
+  }
+  P[3] = __ffma2_rn(x[0], a2r, P[3]);  // phi += 2a dP0
+  Q[3] = __ffma2_rn(x[0], a2i, Q[3]);
+  // curl A -= dQ x beta
+  P[7] = __ffma2_rn(x[5], nbr[2], P[7]);
+  Q[7] = __ffma2_rn(x[5], nbi[2], Q[7]);
+  P[7] = __ffma2_rn(x[6], br[1], P[7]);
+  Q[7] = __ffma2_rn(x[6], bi[1], Q[7]);
+  P[8] = __ffma2_rn(x[6], nbr[0], P[8]);
+  Q[8] = __ffma2_rn(x[6], nbi[0], Q[8]);
+  P[8] = __ffma2_rn(x[4], br[2], P[8]);
+  Q[8] = __ffma2_rn(x[4], bi[2], Q[8]);
+  P[9] = __ffma2_rn(x[4], nbr[1], P[9]);
+  Q[9] = __ffma2_rn(x[4], nbi[1], Q[9]);
+  P[9] = __ffma2_rn(x[5], br[0], P[9]);
+  Q[9] = __ffma2_rn(x[5], bi[0], Q[9]);
+}
+
+// Near-field accumulation state of one lane: complex64 keeps acc = P + j Q
+// through the near loop (near_pq); complex128 keeps acc itself (near_part).
+template <typename R>
+struct NearAcc;
+template <>
+struct NearAcc<float> {
+  float2 P[NREC / 2], Q[NREC / 2];
+  __device__ __forceinline__ void begin(const cx<float>* acc) {
+#pragma unroll
+    for (int c = 0; c < NREC / 2; ++c) {
+      P[c] = make_float2(acc[c].re, acc[c].im);
+      Q[c] = make_float2(0.f, 0.f);
+    }
+  }
+  __device__ __forceinline__ void add(const cx<float>* d, const cx<float>* sv) { near_pq(d, sv, P, Q); }
+  __device__ __forceinline__ void end(cx<float>* acc) const {
+#pragma unroll
+    for (int c = 0; c < NREC / 2; ++c) acc[c] = mk(P[c].x - Q[c].y, P[c].y + Q[c].x);
+  }
+};
+
 // One near record (dP0, dP1, dQ, dC) applied to source summary sv (a, beta):
 // A += a dP1 - beta dP0, phi += 2a dP0, grad phi += 2a dQ,
 // curl A += a dC - dQ x beta (the same for F, psi of an M source).
@@ -370,6 +437,20 @@ __device__ __forceinline__ void near_part(const cx<R>* d, const cx<R>* sv, cx<R>
   acc[8] -= d[6] * be[0] - d[4] * be[2];
   acc[9] -= d[4] * be[1] - d[5] * be[0];
 }
+
+template <>
+struct NearAcc<double> {
+  cx<double> a[NREC / 2];
+  __device__ __forceinline__ void begin(const cx<double>* acc) {
+#pragma unroll
+    for (int c = 0; c < NREC / 2; ++c) a[c] = acc[c];
+  }
+  __device__ __forceinline__ void add(const cx<double>* d, const cx<double>* sv) { near_part(d, sv, a); }
+  __device__ __forceinline__ void end(cx<double>* acc) const {
+#pragma unroll
+    for (int c = 0; c < NREC / 2; ++c) acc[c] = a[c];
+  }
+};
 
 template <typename R>
 __device__ __forceinline__ cx<R> dot3(const R* X, const cx<R>* V) {
@@ -580,14 +661,20 @@ __host__ __device__ constexpr size_t pt_smem_bytes(int q, size_t csize) {
 // SENS = true (conductivity sensitivity): instead of testing into y, the
 // kernel writes hs[t q + a] = eta0 sum_kk (lam_row2 d2 + lam_row3 d3), the
 // derivative of lam^T A x with respect to the conductivity [S] at the point.
-template <typename R, int P, bool SENS = false>
+//
+// QT > 0 fixes q at compile time (then every shared-memory offset of a record
+// is an immediate); QT = 0 takes the argument.  Lanes past the 4q of phase 1
+// repeat lane 4q - 4 .. 4q - 1's work without storing it, so that the near
+// loop runs without divergence.
+template <typename R, int P, bool SENS = false, int QT = 0>
 __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 6) : 3) k_points(
     const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
     const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
     const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
-    const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki,
+    const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q_arg, int n0, int n1, int n2, R ke, R ki,
     R ze, R zi, int has_near, const int32_t* __restrict__ valrow, cx<R>* __restrict__ y, int* __restrict__ tmo,
     const cx<R>* __restrict__ lam, cx<R>* __restrict__ hs) {
+  const int q = QT > 0 ? QT : q_arg;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
@@ -600,7 +687,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
   cx<R>* part = recs + 2 * q * NREC;  // [3][q][4]
 
   const bool act = lane < 4 * q;
-  const int a = lane >> 2, med = (lane >> 1) & 1, h = lane & 1;
+  const int a = min(lane >> 2, q - 1), med = (lane >> 1) & 1, h = lane & 1;
   const int j0 = has_near ? noff[t] : 0, j1 = has_near ? noff[t + 1] : 0;
   const int nst = (j1 - j0 + PT_KP - 1) / PT_KP;
   const unsigned pair_bytes = (unsigned)(pairc * sizeof(cx<R>));
@@ -625,7 +712,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
   const int npair = j1 - j0;
   int src_nxt = lane < npair ? nsrc[j0 + lane] : 0, src_cur = 0;
   cx<R> acc[NREC / 2];
-  if (act) interp_group<R, P>(grids, base, L, dL, t * q + a, med, h, n1, n2, acc);
+  interp_group<R, P>(grids, base, L, dL, t * q + a, med, h, n1, n2, acc);
   if (nst > 0) {
     const int set = h ? 2 : med;  // source J of this medium, or M
     // the interior medium sees -M: accumulate -acc + sum, then negate back
@@ -633,6 +720,8 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
     if (neg)
 #pragma unroll
       for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
+    NearAcc<R> na;
+    na.begin(acc);
     int st = 0;
     bool ok = true;
     for (; st < nst; ++st) {
@@ -649,13 +738,11 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
             src_nxt = jj + 32 + lane < npair ? nsrc[j0 + jj + 32 + lane] : 0;
           }
           const int64_t sj = __shfl_sync(0xffffffffu, src_cur, jj & 31);
-          if (act) {
-            cx<R> d[NCORR], sv[4];
-            load_group(summ + (3 * sj + set) * 4, sv);
+          cx<R> d[NCORR], sv[4];
+          load_group(summ + (3 * sj + set) * 4, sv);
 #pragma unroll
-            for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
-            near_part(d, sv, acc);
-          }
+          for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
+          na.add(d, sv);
         }
       }
       __syncwarp();
@@ -666,6 +753,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
       if (lane == 0) atomicOr(tmo, 1);
     }
     __syncwarp();  // every lane is done with the ring before it holds records
+    na.end(acc);
     if (neg)
 #pragma unroll
       for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
@@ -736,14 +824,15 @@ __host__ __device__ constexpr size_t pb_smem_bytes(int q, int kc, size_t csize) 
   return ((size_t)pb_ring_complex(q) + (size_t)kc * pb_warp_complex(q)) * csize + PB_NSTG * sizeof(uint64_t);
 }
 
-template <typename R, int P>
+template <typename R, int P, int QT = 0>
 __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3) : 1) k_points_batch(
     const cx<R>* __restrict__ grids, const int32_t* __restrict__ base, const R* __restrict__ L,
     const R* __restrict__ dL, const cx<R>* __restrict__ corr, const int32_t* __restrict__ noff,
     const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
-    const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q, int n0, int n1, int n2, R ke, R ki,
+    const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q_arg, int n0, int n1, int n2, R ke, R ki,
     R ze, R zi, int has_near, const int32_t* __restrict__ valrow, cx<R>* __restrict__ y, int* __restrict__ tmo,
     int64_t cs_grid, int64_t cs_summ, int64_t ldy) {
+  const int q = QT > 0 ? QT : q_arg;  // as in k_points
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kc = blockDim.x >> 5;
@@ -758,7 +847,7 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + pb_ring_complex(q) + (int64_t)kc * pb_warp_complex(q));
 
   const bool act = lane < 4 * q;
-  const int a = lane >> 2, med = (lane >> 1) & 1, h = lane & 1;
+  const int a = min(lane >> 2, q - 1), med = (lane >> 1) & 1, h = lane & 1;  // lanes past 4q repeat, as in k_points
   const int j0 = has_near ? noff[t] : 0, j1 = has_near ? noff[t + 1] : 0;
   const int nst = (j1 - j0 + PB_KP - 1) / PB_KP;  // the same for every warp of the CTA
   const unsigned pair_bytes = (unsigned)(pairc * sizeof(cx<R>));
@@ -781,13 +870,15 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
   const int npair = j1 - j0;
   int src_nxt = lane < npair ? nsrc[j0 + lane] : 0, src_cur = 0;
   cx<R> acc[NREC / 2];
-  if (act) interp_group<R, P>(grids, base, L, dL, t * q + a, med, h, n1, n2, acc);
+  interp_group<R, P>(grids, base, L, dL, t * q + a, med, h, n1, n2, acc);
   if (nst > 0) {
     const int set = h ? 2 : med;
     const bool neg = h && med;
     if (neg)
 #pragma unroll
       for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
+    NearAcc<R> na;
+    na.begin(acc);
     int st = 0;
     bool ok = true;
     for (; st < nst; ++st) {
@@ -805,13 +896,11 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
               src_nxt = jj + 32 + lane < npair ? nsrc[j0 + jj + 32 + lane] : 0;
             }
             const int64_t sj = __shfl_sync(0xffffffffu, src_cur, jj & 31);
-            if (act) {
-              cx<R> d[NCORR], sv[4];
-              load_group(summ + (3 * sj + set) * 4, sv);
+            cx<R> d[NCORR], sv[4];
+            load_group(summ + (3 * sj + set) * 4, sv);
 #pragma unroll
-              for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
-              near_part(d, sv, acc);
-            }
+            for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
+            na.add(d, sv);
           }
         }
       }
@@ -824,6 +913,7 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
         (void)mbar_wait(bars + s2 % PB_NSTG, (s2 / PB_NSTG) & 1);
       atomicOr(tmo, 1);
     }
+    na.end(acc);
     if (neg)
 #pragma unroll
       for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
@@ -1308,7 +1398,9 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
   prof_mark(op, s);
   {
     const size_t sm = pt_smem_bytes(op->q, sizeof(cx<R>));
-    PointsFn<R> fn = op->p == 2 ? k_points<R, 2> : op->p == 3 ? k_points<R, 3> : k_points<R, 4>;
+    PointsFn<R> fn = op->q == 6 ? (op->p == 2 ? k_points<R, 2, false, 6> : op->p == 3 ? k_points<R, 3, false, 6>
+                                                                                   : k_points<R, 4, false, 6>)
+                                : (op->p == 2 ? k_points<R, 2> : op->p == 3 ? k_points<R, 3> : k_points<R, 4>);
     if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)sm)) return rc_;
     fn<<<(int)cdiv(nt, PT_WARPS), PT_WARPS * 32, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
                                                   op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, (R)op->ke, (R)op->ki,
@@ -1352,7 +1444,9 @@ int apply_batch(scabem_op* op, const cx<R>* x, int64_t ldx, cx<R>* y, int64_t ld
   prof_mark(op, s);
   {
     const size_t sm = pb_smem_bytes(op->q, k, sizeof(cx<R>));
-    PointsBatchFn<R> fn = op->p == 2 ? k_points_batch<R, 2> : op->p == 3 ? k_points_batch<R, 3> : k_points_batch<R, 4>;
+    PointsBatchFn<R> fn =
+        op->q == 6 ? (op->p == 2 ? k_points_batch<R, 2, 6> : op->p == 3 ? k_points_batch<R, 3, 6> : k_points_batch<R, 4, 6>)
+                   : (op->p == 2 ? k_points_batch<R, 2> : op->p == 3 ? k_points_batch<R, 3> : k_points_batch<R, 4>);
     if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)pb_smem_bytes(op->q, KBATCH, sizeof(cx<R>))))
       return rc_;
     fn<<<(unsigned)nt, 32 * k, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
