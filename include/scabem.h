@@ -207,9 +207,11 @@ int scabem_apply(scabem_op_t op, const void* x, void* y, int32_t nrhs, int64_t l
  * [x0 + k dx, x0 + (k + 1) dx) along `axis`; the plain-surface edges between
  * lateral (not end-cap) triangles of slices first .. first + count - 1 must
  * be translates of those of slice `first` (SCABEM_E_MESH otherwise).  Its
- * blocks come from the operator's own columns for the unknowns of the middle
- * slice (complex128 operator when built, else complex64), and Strang's
- * circulant keeps the blocks of offsets up to count / 2 and wraps them.  The
+ * blocks come from the operator's own columns (complex128 operator when
+ * built, else complex64): kind 0 takes Strang's circulant (the blocks of
+ * offsets up to count / 2, wrapped; columns of the middle slice), kind 1
+ * T. Chan's optimal circulant (each wrapped diagonal averaged, c_k =
+ * ((R - k) T[k] + k T[k - R]) / R; columns of the first and last slice).  The
  * R = count DFT blocks (m x m, m = unknowns per slice) are inverted on the
  * device by Gauss-Jordan elimination with partial pivoting
  * (SCABEM_E_BREAKDOWN if one is singular).  From then on scabem_solve
@@ -221,6 +223,7 @@ typedef struct {
   int32_t axis;
   double x0, dx;
   int32_t first, count;
+  int32_t kind; /* 0: Strang's circulant; 1: T. Chan's optimal circulant */
 } scabem_circulant;
 int scabem_set_precond_circulant(scabem_op_t op, scabem_mesh_t mesh, const scabem_circulant* c, void* stream);
 
@@ -231,6 +234,22 @@ int scabem_set_precond_circulant(scabem_op_t op, scabem_mesh_t mesh, const scabe
  * own Krylov method.  Stream-ordered. */
 int scabem_precond_apply(scabem_op_t op, const void* v, void* z, int32_t nrhs, int64_t ld, int32_t transpose,
                          void* stream);
+
+/* Autotuner (a convenience, not part of the paper's method): times the
+ * operator's runtime shape choices for an apply of nrhs (1..8) right-hand
+ * sides in precision prec on the device, with CUDA events on `stream` (one
+ * warm-up and five timed applies each, on an internal seeded vector), and
+ * keeps the fastest for the operator's later applies and solves:
+ *   - the (y, z) convolution: direct sums over the active columns or 2-D FFT
+ *     planes, where both fit (the set-up builds both Green tables then);
+ *   - the lines per CTA of the axis-0 transforms: 1, 2, 4, 8 or 16, as far
+ *     as the transform length and shared memory allow.
+ * out (host, 4 doubles): {best ms per apply, ms per apply of the
+ * configuration found on entry, 1 if the direct sums won (0: FFT planes),
+ * axis-0 lines per CTA}.  The results are the same linear operator in every
+ * configuration (up to rounding).  Allocates and frees two vectors;
+ * synchronises `stream`; on an error the operator keeps its configuration. */
+int scabem_autotune(scabem_op_t op, int32_t prec, int32_t nrhs, void* stream, double* out);
 
 /* Self-test of the bounded device waits behind SCABEM_E_TIMEOUT.  One warp
  * waits on an mbarrier that nothing ever completes, through the same wait

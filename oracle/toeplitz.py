@@ -122,6 +122,18 @@ def strang(T, R):
     return c
 
 
+def chan(T, R):
+    """T. Chan's optimal circulant of the block Toeplitz matrix with blocks T[d]: the block
+    circulant nearest in the Frobenius norm, c_0 = T[0] and c_k = ((R - k) T[k] + k T[k - R]) / R
+    for 0 < k < R (every offset -(R-1) .. R-1 must be in T).  Returns c (R, m, m)."""
+    m = T[0].shape[0]
+    c = np.zeros((R, m, m), dtype=np.complex128)
+    c[0] = T[0]
+    for k in range(1, R):
+        c[k] = ((R - k) * T[k] + k * T[k - R]) / R
+    return c
+
+
 def circulant_apply(c, xs):
     """y_i = sum_j c[(i - j) mod R] x_j for slice vectors xs (R, m), by the definition."""
     R = len(c)

@@ -73,7 +73,7 @@ class Poynting(C.Structure):
 
 class Circulant(C.Structure):
     _fields_ = [("axis", C.c_int32), ("x0", C.c_double), ("dx", C.c_double), ("first", C.c_int32),
-                ("count", C.c_int32)]
+                ("count", C.c_int32), ("kind", C.c_int32)]
 
 
 class Probe(C.Structure):
@@ -128,6 +128,7 @@ def lib():
     L.scabem_peak_fma.argtypes = [i32, C.POINTER(C.c_double), vp]
     L.scabem_fields_eh.argtypes = [vp, vp, i32, i64, vp, i32, i32, C.POINTER(Source), vp, vp, vp]
     L.scabem_set_precond_circulant.argtypes = [vp, vp, C.POINTER(Circulant), vp]
+    L.scabem_autotune.argtypes = [vp, i32, i32, vp, vp]
     L.scabem_precond_apply.argtypes = [vp, vp, vp, i32, i64, i32, vp]
     L.scabem_poynting_rate.argtypes = [vp, vp, i32, i64, C.POINTER(Poynting), C.POINTER(Source), vp, vp]
     L.scabem_last_error.argtypes = []
@@ -354,9 +355,18 @@ def scabem_fields(op, x, pts, inc=None, nrhs=1, ld=None, stream=None):
     return E
 
 
-def scabem_set_precond_circulant(op, mesh, axis=0, x0=0.0, dx=1.0, first=1, count=0, stream=None):
-    """Strang circulant preconditioner on regular slices first .. first+count-1 (count = 0 removes it)."""
-    c = Circulant(int(axis), float(x0), float(dx), int(first), int(count))
+def scabem_autotune(op, prec=SCABEM_C64, nrhs=1, stream=None):
+    """Time the operator's runtime shapes and keep the fastest: returns
+    {"ms": best, "ms_initial": ..., "direct": bool, "axis0_lines": int}."""
+    out = np.zeros(4, np.float64)
+    _check(lib().scabem_autotune(op, int(prec), int(nrhs), _stream(stream), _ptr(out)))
+    return {"ms": out[0], "ms_initial": out[1], "direct": bool(out[2]), "axis0_lines": int(out[3])}
+
+
+def scabem_set_precond_circulant(op, mesh, axis=0, x0=0.0, dx=1.0, first=1, count=0, kind="strang", stream=None):
+    """Circulant preconditioner (kind "strang" or "chan") on regular slices first .. first+count-1
+    (count = 0 removes it)."""
+    c = Circulant(int(axis), float(x0), float(dx), int(first), int(count), {"strang": 0, "chan": 1}[kind])
     _check(lib().scabem_set_precond_circulant(op, mesh, C.byref(c), _stream(stream)))
 
 

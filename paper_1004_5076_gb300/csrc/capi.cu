@@ -1069,11 +1069,147 @@ int scabem_fields(scabem_op_t op, const void* x, int32_t nrhs, int64_t ld, const
   return rc;
 }
 
+}  // extern "C"
+
+namespace {
+// Reallocate the axis-0 intermediates of one precision for the current
+// (y, z) mode and batch capacity (zero, as at creation).
+template <typename R>
+int realloc_st(scabem_op* op, PrecData<R>& pd, cudaStream_t s) {
+  if (!pd.built) return SCABEM_OK;
+  cudaFree(pd.stA);
+  cudaFree(pd.stB);
+  pd.stA = pd.stB = nullptr;
+  const int64_t n = col_stride_st(op) * pd.kcap;
+  int rc;
+  if ((rc = dalloc(&pd.stA, n)) || (rc = dalloc(&pd.stB, n))) return rc;
+  CK(cudaMemsetAsync(pd.stA, 0, sizeof(cx<R>) * n, s));
+  CK(cudaMemsetAsync(pd.stB, 0, sizeof(cx<R>) * n, s));
+  return SCABEM_OK;
+}
+
+int set_transverse_mode(scabem_op* op, bool direct, cudaStream_t s) {
+  if (direct == op->tdirect) return SCABEM_OK;
+  CK(cudaStreamSynchronize(s));
+  op->tdirect = direct;
+  op->cst = direct ? op->nac : (int64_t)op->n[1] * op->n[2];
+  int rc = realloc_st(op, op->d, s);
+  if (!rc) rc = realloc_st(op, op->f, s);
+  return rc;
+}
+
+template <typename R>
+__global__ void k_tune_pattern(cx<R>* x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = mk((R)sin(0.37 * (double)(i % 100003)), (R)cos(0.11 * (double)(i % 99991)));
+}
+
+template <typename R>
+int autotune_prec(scabem_op* op, int nrhs, cudaStream_t s, double* out) {
+  PrecData<R>& pd = *reinterpret_cast<PrecData<R>*>(sizeof(R) == 4 ? (void*)&op->f : (void*)&op->d);
+  if (nrhs > 1)
+    if (int rc = ensure_batch<R>(op, nrhs, s)) return rc;
+  const int64_t N = op->N;
+  cx<R>* x = nullptr;
+  cx<R>* y = nullptr;
+  if (int rc = dalloc(&x, N * nrhs)) return rc;
+  if (int rc = dalloc(&y, N * nrhs)) {
+    cudaFree(x);
+    return rc;
+  }
+  k_tune_pattern<R><<<152, 256, 0, s>>>(x, N * nrhs);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = SCABEM_OK;
+  auto timed = [&](float& ms) -> int {
+    auto apply = [&]() { return nrhs == 1 ? apply_one<R>(op, x, y, s) : apply_batch<R>(op, x, N, y, N, nrhs, s); };
+    if (int r = apply()) return r;  // warm
+    CK(cudaEventRecord(e0, s));
+    for (int i = 0; i < 5; ++i)
+      if (int r = apply()) return r;
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= 5;
+    return SCABEM_OK;
+  };
+  float ms0 = 0.f;
+  const bool dir0 = op->tdirect;
+  const int lines0 = op->a0_lines;
+  do {
+    if ((rc = timed(ms0))) break;
+    float best = ms0;
+    bool bdir = dir0;
+    int blines = lines0;
+    const int csz = (int)sizeof(cx<R>);
+    const int totl = sizeof(R) == 4 ? 13 : 12;  // largest transform one CTA holds (log2 elements)
+    int lp = 0;
+    while ((1 << lp) < op->P[0]) ++lp;
+    for (int mode = 0; mode < 2 && !rc; ++mode) {
+      const bool direct = mode == 0;
+      if (direct ? !op->direct_fits : !op->planes_fit) continue;
+      if ((rc = set_transverse_mode(op, direct, s))) break;
+      for (int L = 1; L <= 16 && !rc; L *= 2) {
+        const int cbC = L >= 4 ? L : 4;
+        if ((1 << lp) * L > (1 << totl) || (1 << lp) * cbC > (1 << totl) ||
+            (int64_t)op->P[0] * (L + 1) * csz > 227 * 1024 || (int64_t)op->P[0] * (cbC + 1) * csz > 227 * 1024)
+          continue;
+        op->a0_lines = L;
+        float ms = 0.f;
+        if ((rc = timed(ms))) break;
+        if (ms < best) {
+          best = ms;
+          bdir = direct;
+          blines = L;
+        }
+      }
+    }
+    if (rc) break;
+    if ((rc = set_transverse_mode(op, bdir, s))) break;
+    op->a0_lines = blines;
+    out[0] = best;
+    out[1] = ms0;
+    out[2] = bdir ? 1.0 : 0.0;
+    out[3] = blines > 0 ? blines : 0.0;
+  } while (0);
+  if (rc) {  // leave the operator as it was
+    set_transverse_mode(op, dir0, s);
+    op->a0_lines = lines0;
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  return rc;
+}
+}  // namespace
+
+extern "C" {
+
+int scabem_autotune(scabem_op_t op, int32_t prec, int32_t nrhs, void* stream, double* out) {
+  if (!op || !out || (prec != SCABEM_C64 && prec != SCABEM_C128) || nrhs < 1 || nrhs > KBATCH) {
+    set_error("scabem_autotune: bad argument (prec SCABEM_C64 or SCABEM_C128, 1 <= nrhs <= 8)");
+    return SCABEM_E_ARG;
+  }
+  if ((prec == SCABEM_C64 && !op->f.built) || (prec == SCABEM_C128 && !op->d.built)) {
+    set_error("scabem_autotune: the operator was not built for this precision");
+    return SCABEM_E_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = take_timeout(op)) return rc;
+  const int rc = prec == SCABEM_C64 ? autotune_prec<float>(op, nrhs, s, out) : autotune_prec<double>(op, nrhs, s, out);
+  const int rt = take_timeout(op);
+  return rc ? rc : rt;
+}
+
 int scabem_set_precond_circulant(scabem_op_t op, scabem_mesh_t mesh, const scabem_circulant* c, void* stream) {
   if (!op || !mesh || !c || c->axis < 0 || c->axis > 2 || !(c->dx > 0) || !std::isfinite(c->x0) || c->first < 0 ||
-      c->count < 0 || (c->count > 0 && c->count < 2) || c->count > 4096 || mesh->nt != op->nt || mesh->N != op->N) {
+      c->count < 0 || (c->count > 0 && c->count < 2) || c->count > 4096 || mesh->nt != op->nt || mesh->N != op->N ||
+      c->kind < 0 || c->kind > 1) {
     set_error("scabem_set_precond_circulant: bad argument (axis 0..2, dx > 0, first >= 0, count 0 or 2..4096, "
-              "the operator's mesh)");
+              "kind 0 or 1, the operator's mesh)");
     return SCABEM_E_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;

@@ -194,7 +194,9 @@ struct scabem_op {
   // Green table for |d1| < R1, |d2| < R2 (the active box), or 2-D FFT planes
   // with ghat.  acoord[j] = (i1 - b1) << 16 | (i2 - b2) of active column j.
   int transverse = 0;
-  bool planes_fit = true;  // the (y, z) plane fits the 2-D FFT plane kernels
+  bool planes_fit = true;   // the (y, z) plane fits the 2-D FFT plane kernels
+  bool direct_fits = true;  // the active columns fit one CTA of the direct (y, z) sums
+  int a0_lines = 0;         // lines per CTA of the axis-0 transforms (0: the default rule)
   // columns per (field, k0) of the axis-0 intermediates stA, stB: the nac
   // active columns in order (compact) for the direct (y, z) sums, all n1 n2
   // for the FFT planes

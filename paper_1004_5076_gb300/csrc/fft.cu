@@ -825,7 +825,8 @@ template <typename R>
 static int axis0_inverse(scabem_op* op, PrecData<R>& pd, cudaStream_t s, int ncol) {
   const int n0 = op->n[0], P0 = op->P[0];
   const int C = op->n[1] * op->n[2];
-  const int nc = pruned_lines<R>(P0) >= 4 ? pruned_lines<R>(P0) / 4 : 1;  // P0 <= 1024: 4 lines fit
+  const int lines = op->a0_lines > 0 ? op->a0_lines : pruned_lines<R>(P0);
+  const int nc = lines >= 4 ? lines / 4 : 1;  // P0 <= 1024: 4 lines fit
   const size_t sm = (size_t)P0 * (4 * nc + 1) * sizeof(cx<R>);
   if (int rc_ = set_max_smem(op->device, (const void*)k_axis0_pm<R>, (int)sm)) return rc_;
   k_axis0_pm<R><<<dim3((unsigned)cdiv(op->nac, nc), NFIELD_OUT / 4, ncol), FFT_THREADS, sm, s>>>(
@@ -846,7 +847,7 @@ int fft_conv(scabem_op* op, PrecData<R>& pd, cudaStream_t s, bool adjoint, int n
     set_error("grid: no grid point is covered by a stencil");
     return SCABEM_E_ARG;
   }
-  const int cb = pruned_lines<R>(P0);
+  const int cb = op->a0_lines > 0 ? op->a0_lines : pruned_lines<R>(P0);
   const size_t sm0 = (size_t)P0 * (cb + 1) * sizeof(cx<R>);
   // stage A
   if (int rc_ = set_max_smem(op->device, (const void*)k_axis0<R>, (int)sm0)) return rc_;

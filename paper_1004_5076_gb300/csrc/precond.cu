@@ -6,12 +6,14 @@
 //
 // Set-up: the regular slices' plain-surface edges are put in one local
 // order (translates of the first slice, with the orientation sign of each
-// edge); the operator's own columns for the unknowns of the middle slice
-// give the blocks T[d] = A(slice k0 + d, slice k0) (the grid operator is
-// translation invariant up to the grid, so these stand for every slice);
-// Strang's circulant keeps c_k = T[k] for k <= R/2 and T[k - R] above; its
-// DFT blocks C_f = sum_k c_k exp(-2 pi i f k / R) are inverted one per CTA
-// by Gauss-Jordan elimination with partial pivoting.
+// edge); the operator's own columns give the blocks T[d] = A(slice j + d,
+// slice j) (the grid operator is translation invariant up to the grid).
+// Strang's circulant keeps c_k = T[k] for k <= R/2 and T[k - R] above, from
+// the columns of the middle slice; T. Chan's optimal circulant averages each
+// wrapped diagonal, c_k = ((R - k) T[k] + k T[k - R]) / R, from the columns
+// of the first and the last slice.  The DFT blocks
+// C_f = sum_k c_k exp(-2 pi i f k / R) are inverted one per CTA by
+// Gauss-Jordan elimination with partial pivoting.
 // Apply: v (periodic unknowns, signed) -> DFT over the slices -> C_f^-1 per
 // frequency -> inverse DFT -> z, after the block-diagonal preconditioner has
 // written every unknown.
@@ -35,26 +37,29 @@ __device__ __forceinline__ cd twiddle(const cd* tw, int64_t e, int R) {
   return tw[(int)(((e % R) + R) % R)];  // exp(-2 pi i e / R)
 }
 
-// c[k][i][j] for the batch of columns j0 .. j0 + kb - 1 of the middle slice
-// k0: Y holds A applied to sgn[k0][j] e_idx[k0][j] (column j - j0, leading
-// dimension N); the block of offset d = (k <= R/2 ? k : k - R) is read from
-// the rows of slice k0 + d (zero when that slice does not exist).
+// c[k][i][j] += w_k T[d_k] for the batch of columns j0 .. j0 + kb - 1 of the
+// source slice: Y holds A applied to sgn[src][j] e_idx[src][j] (column
+// j - j0, leading dimension N), and the block of offset d is read from the
+// rows of slice src + d.  mode 0 (Strang, source = the middle slice R/2):
+// d = k for k <= R/2, k - R above, weight 1 (0 when slice src + d does not
+// exist); mode 1 (Chan, source = slice 0): d = k, weight (R - k) / R;
+// mode 2 (Chan, source = slice R - 1): d = k - R, weight k / R.
 template <typename R_>
 __global__ void k_circ_gather(const cx<R_>* __restrict__ Y, int64_t N, int kb, int j0, const int32_t* __restrict__ idx,
-                              const double* __restrict__ sgn, int R, int m, int k0, cd* __restrict__ c) {
+                              const double* __restrict__ sgn, int R, int m, int src, int mode, cd* __restrict__ c) {
   const int64_t tot = (int64_t)R * m * kb;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int jj = (int)(t % kb);
     const int i = (int)((t / kb) % m);
     const int k = (int)(t / ((int64_t)kb * m));
-    const int d = k <= R / 2 ? k : k - R;
-    const int src = k0 + d;
-    cd v = mk(0.0, 0.0);
-    if (src >= 0 && src < R) {
-      const cx<R_> y = Y[(int64_t)jj * N + idx[src * m + i]];
-      v = mk(sgn[src * m + i] * (double)y.re, sgn[src * m + i] * (double)y.im);
+    const int d = mode == 0 ? (k <= R / 2 ? k : k - R) : (mode == 1 ? k : k - R);
+    const double w = mode == 0 ? 1.0 : (mode == 1 ? (double)(R - k) / R : (double)k / R);
+    const int row = src + d;
+    if (row >= 0 && row < R && w != 0.0) {
+      const cx<R_> y = Y[(int64_t)jj * N + idx[row * m + i]];
+      const double sw = w * sgn[row * m + i];
+      c[((int64_t)k * m + i) * m + j0 + jj] += mk(sw * (double)y.re, sw * (double)y.im);
     }
-    c[((int64_t)k * m + i) * m + j0 + jj] = v;
   }
 }
 
@@ -344,9 +349,17 @@ int setup_circulant(scabem_op* op, const scabem_mesh* mesh, const scabem_circula
   CK(cudaMemcpyAsync(C.sgn, sgn.data(), sizeof(double) * R * m, cudaMemcpyHostToDevice, s));
   k_circ_twiddles<<<(int)cdiv(R, 128), 128, 0, s>>>(C.tw, R);
   CK(cudaGetLastError());
-  // ---- blocks from the operator's columns of the middle slice
-  const int k0 = R / 2;
+  // ---- blocks from the operator's columns: the middle slice (Strang) or the
+  // first and the last slice (Chan)
   const int prec = op->d.built ? SCABEM_C128 : SCABEM_C64;
+  struct Pass {
+    int src, mode;
+  };
+  std::vector<Pass> passes;
+  if (P->kind == 1)
+    passes = {{0, 1}, {R - 1, 2}};
+  else
+    passes = {{R / 2, 0}};
   const size_t csz = prec == SCABEM_C128 ? sizeof(cd) : sizeof(cx<float>);
   const int kb = std::min(KBATCH, m);
   if (kb > 1) {
@@ -366,27 +379,33 @@ int setup_circulant(scabem_op* op, const scabem_mesh* mesh, const scabem_circula
       rc = SCABEM_E_NOMEM;
       break;
     }
-    for (int j0 = 0; j0 < m && !rc; j0 += kb) {
-      const int nb = std::min(kb, m - j0);
-      if (cudaMemsetAsync(X, 0, csz * op->N * kb, s) != cudaSuccess) {
-        rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
-        break;
-      }
-      k_unit_columns<<<1, 32, 0, s>>>(X, prec, op->N, nb, C.idx, C.sgn, k0 * m + j0);
-      if (prec == SCABEM_C128) {
-        rc = nb == 1 ? apply_one<double>(op, (const cd*)X, (cd*)Y, s)
-                     : apply_batch<double>(op, (const cd*)X, op->N, (cd*)Y, op->N, nb, s);
-        if (!rc)
-          k_circ_gather<double><<<(int)cdiv((int64_t)R * m * nb, 256), 256, 0, s>>>(
-              (const cd*)Y, op->N, nb, j0, C.idx, C.sgn, R, m, k0, cblk);
-      } else {
-        rc = nb == 1 ? apply_one<float>(op, (const cx<float>*)X, (cx<float>*)Y, s)
-                     : apply_batch<float>(op, (const cx<float>*)X, op->N, (cx<float>*)Y, op->N, nb, s);
-        if (!rc)
-          k_circ_gather<float><<<(int)cdiv((int64_t)R * m * nb, 256), 256, 0, s>>>(
-              (const cx<float>*)Y, op->N, nb, j0, C.idx, C.sgn, R, m, k0, cblk);
-      }
+    if (cudaMemsetAsync(cblk, 0, sizeof(cd) * (size_t)R * m * m, s) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+      break;
     }
+    for (const Pass& ps : passes)
+      for (int j0 = 0; j0 < m && !rc; j0 += kb) {
+        const int nb = std::min(kb, m - j0);
+        if (cudaMemsetAsync(X, 0, csz * op->N * kb, s) != cudaSuccess) {
+          rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+          break;
+        }
+        k_unit_columns<<<1, 32, 0, s>>>(X, prec, op->N, nb, C.idx, C.sgn, ps.src * m + j0);
+        const unsigned gb = (unsigned)cdiv((int64_t)R * m * nb, 256);
+        if (prec == SCABEM_C128) {
+          rc = nb == 1 ? apply_one<double>(op, (const cd*)X, (cd*)Y, s)
+                       : apply_batch<double>(op, (const cd*)X, op->N, (cd*)Y, op->N, nb, s);
+          if (!rc)
+            k_circ_gather<double><<<gb, 256, 0, s>>>((const cd*)Y, op->N, nb, j0, C.idx, C.sgn, R, m, ps.src, ps.mode,
+                                                     cblk);
+        } else {
+          rc = nb == 1 ? apply_one<float>(op, (const cx<float>*)X, (cx<float>*)Y, s)
+                       : apply_batch<float>(op, (const cx<float>*)X, op->N, (cx<float>*)Y, op->N, nb, s);
+          if (!rc)
+            k_circ_gather<float><<<gb, 256, 0, s>>>((const cx<float>*)Y, op->N, nb, j0, C.idx, C.sgn, R, m, ps.src,
+                                                    ps.mode, cblk);
+        }
+      }
     if (rc) break;
     k_circ_dft_blocks<<<R, 256, 0, s>>>(cblk, C.tw, R, m, Cf);
     if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) {

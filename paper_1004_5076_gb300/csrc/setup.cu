@@ -858,15 +858,21 @@ int setup_gather(scabem_op* op, cudaStream_t s) {
     CK(cudaMalloc(&op->acoord, sizeof(int32_t) * op->nac));
     CK(cudaMemcpyAsync(op->acoord, coord.data(), sizeof(int32_t) * op->nac, cudaMemcpyHostToDevice, s));
   }
-  op->tdirect = op->transverse == 2 || !op->planes_fit ||
-                (op->transverse == 0 && op->nac * op->nac <= 16 * (int64_t)op->P[1] * op->P[2]);
-  if (op->tdirect) {
+  {
     // one CTA of the direct (y, z) sums holds the active columns' sources and the table
     const size_t csz = (op->prec_mask & 2) ? sizeof(cx<double>) : sizeof(cx<float>);
     const size_t sm = ((size_t)op->nac * 8 + (size_t)op->R1 * op->R2) * csz + sizeof(int32_t) * op->nac;
-    if (sm > 227 * 1024) {
+    op->direct_fits = sm <= 227 * 1024;
+    const bool want = op->transverse == 2 || !op->planes_fit ||
+                      (op->transverse == 0 && op->nac * op->nac <= 16 * (int64_t)op->P[1] * op->P[2]);
+    op->tdirect = want && (op->direct_fits || !op->planes_fit);
+    if (op->tdirect && !op->direct_fits) {
       set_error("grid: " + std::to_string(op->nac) + " active (y, z) columns are too many for the direct sums (" +
                 std::to_string(sm) + " bytes of shared memory)");
+      return SCABEM_E_ARG;
+    }
+    if (op->transverse == 2 && !op->direct_fits) {
+      set_error("grid: the direct (y, z) sums were asked for, but their columns do not fit in shared memory");
       return SCABEM_E_ARG;
     }
   }
@@ -963,21 +969,21 @@ int setup_green(scabem_op* op, cudaStream_t s) {
                                                      op->n[1], op->n[2], op->h, k);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(F, op->gspatial[med], sizeof(cx<double>) * tot, cudaMemcpyDeviceToDevice, s));
-    if (op->tdirect) {
-      // axis-0 transform only, then the active box of offsets
-      int rc = fft_axis_full<double>(op, F, 0, twd[0], -1, s);
-      if (rc) return rc;
+    // the axis-0 transform serves both (y, z) modes: the direct sums take the
+    // active box of offsets from it; the FFT planes transform on along y and z
+    int rc = fft_axis_full<double>(op, F, 0, twd[0], -1, s);
+    if (rc) return rc;
+    if (op->direct_fits) {
       const int64_t nt_ = (int64_t)(op->P[0] / 2 + 1) * op->R1 * op->R2;
       if (op->prec_mask & 2) CK(cudaMalloc(&op->d.gt[med], sizeof(cx<double>) * nt_));
       if (op->prec_mask & 1) CK(cudaMalloc(&op->f.gt[med], sizeof(cx<float>) * nt_));
       k_transverse<<<(int)cdiv(nt_, 256), 256, 0, s>>>(F, op->P[0], op->P[1], op->P[2], op->R1, op->R2,
                                                        op->d.gt[med], op->f.gt[med]);
       CK(cudaGetLastError());
-      continue;
     }
-    const cx<double>* const tws[3] = {twd[0], twd[1], twd[2]};
-    int rc = fft3d_full<double>(op, F, tws, -1, s);
-    if (rc) return rc;
+    if (!op->planes_fit) continue;
+    for (int a = 1; a < 3; ++a)
+      if ((rc = fft_axis_full<double>(op, F, a, twd[a], -1, s))) return rc;
     if (op->prec_mask & 2) CK(cudaMalloc(&op->d.ghat[med], sizeof(cx<double>) * oct));
     if (op->prec_mask & 1) CK(cudaMalloc(&op->f.ghat[med], sizeof(cx<float>) * oct));
     k_octant<<<(int)cdiv(oct, 256), 256, 0, s>>>(F, op->d.ghat[med], op->f.ghat[med], op->P[0], op->P[1], op->P[2]);

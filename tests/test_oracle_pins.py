@@ -709,6 +709,29 @@ def test_strang_circulant_preconditioner():
     assert np.allclose(full @ x.reshape(-1), v.reshape(-1), rtol=0, atol=1e-12)
     assert np.allclose(toeplitz.circulant_apply(c, x), v, rtol=0, atol=1e-12)
     assert np.allclose(x.reshape(-1), np.linalg.solve(full, v.reshape(-1)), atol=1e-12)
+    assert np.allclose(toeplitz.chan(T, R), base, rtol=0, atol=1e-15)  # Chan: exact on a circulant too
+    # Chan's circulant is the nearest block circulant: its blocks are the averages of the
+    # Toeplitz matrix's blocks along each wrapped diagonal, so it beats Strang's in Frobenius norm
+    T3 = {d: rng.standard_normal((m, m)) for d in range(-(R - 1), R)}
+    toep = np.zeros((R * m, R * m))
+    for i in range(R):
+        for j in range(R):
+            toep[i * m:(i + 1) * m, j * m:(j + 1) * m] = T3[i - j]
+
+    def assembled(cc):
+        out = np.zeros((R * m, R * m), dtype=np.complex128)
+        for i in range(R):
+            for j in range(R):
+                out[i * m:(i + 1) * m, j * m:(j + 1) * m] = cc[(i - j) % R]
+        return out
+
+    ec, es = (np.linalg.norm(assembled(f(T3, R)) - toep) for f in (toeplitz.chan, toeplitz.strang))
+    assert ec < es
+    # the wrapped-diagonal average, entry by entry
+    cc = toeplitz.chan(T3, R)
+    for k in range(R):
+        avg = sum(toep[i * m:(i + 1) * m, ((i - k) % R) * m:(((i - k) % R) + 1) * m] for i in range(R)) / R
+        assert np.allclose(cc[k], avg, atol=1e-14)
     # Strang's choice on a genuinely Toeplitz (non-circulant) matrix: central blocks kept
     T2 = {d: rng.standard_normal((m, m)) for d in range(-(R - 1), R)}
     c2 = toeplitz.strang(T2, R)
