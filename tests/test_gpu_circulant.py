@@ -50,7 +50,10 @@ _cols = {}
 
 
 def _oracle_blocks(case, g, med, sig, lay, slices):
-    """T[d] from the oracle's O2 columns of the given regular slices (signed unit vectors)."""
+    """T[d] from the oracle's O2 columns of the given regular slices (signed unit vectors).  An
+    offset that two slices both give keeps the first slice's block: Chan's c_0 = T[0] is the
+    diagonal block of the first block column (the operator is Toeplitz only up to the absorbers
+    and the grid, so the last slice's diagonal block differs slightly)."""
     T = {}
     for k0 in slices:
         if k0 not in _cols:
@@ -60,7 +63,7 @@ def _oracle_blocks(case, g, med, sig, lay, slices):
             _cols[k0] = oracle_op(case, g, med).apply(E, sig)
         for k in range(lay.count):
             idx, sg = lay.unknowns(g, k)
-            T[k - k0] = sg[:, None] * _cols[k0][idx]
+            T.setdefault(k - k0, sg[:, None] * _cols[k0][idx])
     return T
 
 
