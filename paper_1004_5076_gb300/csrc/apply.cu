@@ -307,49 +307,6 @@ __device__ __forceinline__ void interp_group(const cx<R>* __restrict__ grids, co
   r[9] = gx[1] - gy[0];
 }
 
-// a += x * B in complex64 with the factor B kept as (B, j B): two packed
-// FP32x2 FMAs, (x.re, x.re) * B + (x.im, x.im) * jB.
-struct Fac2 {
-  float2 b, jb;
-};
-__device__ __forceinline__ Fac2 fac2(cx<float> v, float s) {
-  Fac2 f;
-  f.b = make_float2(s * v.re, s * v.im);
-  f.jb = make_float2(-s * v.im, s * v.re);
-  return f;
-}
-__device__ __forceinline__ void cmac2(float2& acc, cx<float> x, const Fac2& f) {
-  acc = __ffma2_rn(make_float2(x.re, x.re), f.b, acc);
-  acc = __ffma2_rn(make_float2(x.im, x.im), f.jb, acc);
-}
-
-// complex64 form of near_part (the same sums, packed FP32x2 arithmetic)
-__device__ __forceinline__ void near_part(const cx<float>* d, const cx<float>* sv, cx<float>* acc) {
-  const Fac2 al = fac2(sv[0], 1.f), al2 = fac2(sv[0], 2.f);
-  const Fac2 be[3] = {fac2(sv[1], 1.f), fac2(sv[2], 1.f), fac2(sv[3], 1.f)};
-  const Fac2 nbe[3] = {fac2(sv[1], -1.f), fac2(sv[2], -1.f), fac2(sv[3], -1.f)};
-  float2 A[NREC / 2];
-#pragma unroll
-  for (int c = 0; c < NREC / 2; ++c) A[c] = make_float2(acc[c].re, acc[c].im);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    cmac2(A[c], d[1 + c], al);     // A += a dP1
-    cmac2(A[c], d[0], nbe[c]);     //    - beta dP0
-    cmac2(A[4 + c], d[4 + c], al2);  // grad phi += 2a dQ
-    cmac2(A[7 + c], d[7 + c], al);   // curl A += a dC
-  }
-  cmac2(A[3], d[0], al2);  // phi += 2a dP0
-  // curl A -= dQ x beta
-  cmac2(A[7], d[5], nbe[2]);
-  cmac2(A[7], d[6], be[1]);
-  cmac2(A[8], d[6], nbe[0]);
-  cmac2(A[8], d[4], be[2]);
-  cmac2(A[9], d[4], nbe[1]);
-  cmac2(A[9], d[5], be[0]);
-#pragma unroll
-  for (int c = 0; c < NREC / 2; ++c) acc[c] = mk(A[c].x, A[c].y);
-}
-
 // The same sums in complex64 with the accumulator split as acc = P + j Q:
 // x s adds (s.re, s.re) * (x.re, x.im) to P and (s.im, s.im) * (x.re, x.im)
 // to Q, so that every record value enters the packed FMAs as the (re, im)
@@ -569,13 +526,17 @@ __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-// one arrival that also expects `bytes` of transaction, then the copy
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
+// The near records are read once per apply: their copies carry an L2
+// evict-first policy, so that the stream of records does not push the
+// apply's reused data (grids, sources, geometry) and the caller's vectors out
+// of L2.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
 }
 // The arrival of one thread that expects `bytes` of copies on `bar`, and one
@@ -584,11 +545,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
+// one arrival that also expects `bytes` of transaction, then the copy
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  mbar_expect_tx(bar, bytes);
+  bulk_copy(dst, src, bytes, bar);
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
@@ -679,7 +639,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * PT_WARPS + warp;
   if (t >= nt) return;  // whole warp; no CTA-wide barrier below
-  const int pairc = NCORR * 2 * q;  // complex per pair: [component][point][medium]
+  const int pairc = NCORR * 2 * q;  // complex per pair: [point][medium][component]
   cx<R>* ring = reinterpret_cast<cx<R>*>(smem_raw) + (int64_t)warp * pt_warp_complex(q);
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<cx<R>*>(smem_raw) + PT_WARPS * pt_warp_complex(q)) +
                    warp * PT_NSTG;
@@ -728,7 +688,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
       if (lane == 0 && st + PT_NSTG - 1 < nst) issue(st + PT_NSTG - 1);  // slot consumed at st - 1
       ok = __all_sync(0xffffffffu, mbar_wait(bars + st % PT_NSTG, (st / PT_NSTG) & 1));
       if (!ok) break;
-      const cx<R>* rs = ring + (st % PT_NSTG) * PT_KP * pairc + a * 2 + med;
+      const cx<R>* rs = ring + (st % PT_NSTG) * PT_KP * pairc + (a * 2 + med) * NCORR;
 #pragma unroll
       for (int k = 0; k < PT_KP; ++k) {
         const int jj = st * PT_KP + k;  // pair within the triangle (warp-uniform)
@@ -741,7 +701,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
           cx<R> d[NCORR], sv[4];
           load_group(summ + (3 * sj + set) * 4, sv);
 #pragma unroll
-          for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
+          for (int c = 0; c < NCORR; c += 2) load_pair_smem(rs + k * pairc + c, d + c);
           na.add(d, sv);
         }
       }
@@ -886,7 +846,7 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
       if (threadIdx.x == 0 && st + PB_NSTG - 1 < nst) issue(st + PB_NSTG - 1);
       const bool here = __all_sync(0xffffffffu, mbar_wait(bars + st % PB_NSTG, (st / PB_NSTG) & 1));
       if (here) {
-        const cx<R>* rs = ring + (st % PB_NSTG) * PB_KP * pairc + a * 2 + med;
+        const cx<R>* rs = ring + (st % PB_NSTG) * PB_KP * pairc + (a * 2 + med) * NCORR;
 #pragma unroll
         for (int k = 0; k < PB_KP; ++k) {
           const int jj = st * PB_KP + k;
@@ -899,7 +859,7 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
             cx<R> d[NCORR], sv[4];
             load_group(summ + (3 * sj + set) * 4, sv);
 #pragma unroll
-            for (int c = 0; c < NCORR; ++c) d[c] = rs[k * pairc + c * 2 * q];
+            for (int c = 0; c < NCORR; c += 2) load_pair_smem(rs + k * pairc + c, d + c);
             na.add(d, sv);
           }
         }
@@ -1136,7 +1096,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, 4)
     ok = __all_sync(0xffffffffu, mbar_wait(bars + st % NA_NSTG, (st / NA_NSTG) & 1));
     if (!ok) break;
     const int j = j0 + st * NA_KP + k;
-    const cx<R>* dp = ring + ((st % NA_NSTG) * NA_KP + k) * slot + m;
+    const cx<R>* dp = ring + ((st % NA_NSTG) * NA_KP + k) * slot + m * NCORR;
     cx<R> al = czero<R>(), be[3] = {czero<R>(), czero<R>(), czero<R>()};
     if (j < j1) {
       for (int a = ah; a < q; a += NA_AH) {
@@ -1144,7 +1104,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, 4)
 #pragma unroll
         for (int c = 0; c < 10; c += 2) load_pair_smem(rl + a * 40 + c, r + c);
 #pragma unroll
-        for (int c = 0; c < NCORR; ++c) d[c] = dp[c * 2 * q + 2 * a];
+        for (int c = 0; c < NCORR; c += 2) load_pair_smem(dp + a * 2 * NCORR + c, d + c);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           cfma(al, r[c], d[1 + c]);

@@ -284,6 +284,11 @@ int setup_gather(scabem_op* op, cudaStream_t s);
 // k right-hand sides: column c of in / out starts at c * cs_in / c * cs_out
 int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed = false,
                   int k = 1, int64_t cs_in = 0, int64_t cs_out = 0);
+// block-diagonal part only, complex64 output (the input of the complex64
+// operator); SCABEM_E_ARG when a circulant block is set for this direction
+int precond_apply_f32(scabem_op* op, const cx<double>* in, cx<float>* out, cudaStream_t s, bool transposed, int k,
+                      int64_t cs_in, int64_t cs_out);
+bool precond_is_block_diagonal(const scabem_op* op, bool transposed);
 // precond.cu
 int setup_circulant(scabem_op* op, const scabem_mesh* mesh, const scabem_circulant* c, cudaStream_t s);
 int circulant_apply(scabem_op* op, const cx<double>* in, cx<double>* out, int k, int64_t cs_in, int64_t cs_out,

@@ -277,7 +277,8 @@ __device__ void static_tri(const double* r, const double* v, const double* nrm, 
 // Near-field precorrection: one thread per (near pair, target point).  For
 // both media, exact potential moments (P0, P1, Q, C) of the source panel at
 // the target point minus the grid's version of the same interaction.
-// corr layout: [pair][NCORR component][target point][medium].
+// corr layout: [pair][target point][medium][NCORR component], so that the ten
+// values one (point, medium) lane of the point kernel reads are contiguous.
 template <typename RG>
 __global__ void k_near_corr(const double* __restrict__ tri, const double* __restrict__ qp, const double* __restrict__ qw,
                             const int32_t* __restrict__ base, const double* __restrict__ Ld,
@@ -418,9 +419,9 @@ __global__ void k_near_corr(const double* __restrict__ tri, const double* __rest
       o[4 + c] = Qe[c] - Qg[c];
       o[7 + c] = Ce[c] - Cg[c];
     }
-    // component-major within a pair: [pair][component][point][medium]
+    // [pair][point][medium][component]
     for (int c = 0; c < NCORR; ++c) {
-      const int64_t dst = ((j * NCORR + c) * q + a) * 2 + med;
+      const int64_t dst = ((j * q + a) * 2 + med) * NCORR + c;
       if (outd) outd[dst] = o[c];
       if (outf) outf[dst] = mk((float)o[c].re, (float)o[c].im);
     }
@@ -773,8 +774,11 @@ __global__ void k_precond(const double* __restrict__ tri, const double* __restri
 // out[unknowns of e] = Binv_e * in[rows of e] (rows and unknowns of an edge
 // share the same index set).
 // transposed = 1 applies (Binv_e)^T, the inverse blocks of A^T.
+// out = P^-1 in per edge block (P^-T when transposed), written in the output
+// precision TO (complex64 when it feeds the complex64 operator directly)
+template <typename TO>
 __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __restrict__ eunk, int64_t ne,
-                                const cd* __restrict__ in, cd* __restrict__ out, int transposed, int64_t cs_in,
+                                const cd* __restrict__ in, cx<TO>* __restrict__ out, int transposed, int64_t cs_in,
                                 int64_t cs_out) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= ne) return;
@@ -786,7 +790,7 @@ __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __re
   for (int i = 0; i < nb; ++i) {
     cd acc = mk(0.0, 0.0);
     for (int j = 0; j < nb; ++j) acc += pinv[9 * e + (transposed ? 3 * j + i : 3 * i + j)] * v[j];
-    out[eunk[3 * e + i]] = acc;
+    out[eunk[3 * e + i]] = cvt<TO>(acc);
   }
 }
 
@@ -908,11 +912,25 @@ int setup_precond(scabem_op* op, cudaStream_t s) {
 
 int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed, int k,
                   int64_t cs_in, int64_t cs_out) {
-  k_precond_apply<<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out,
-                                                                       transposed ? 1 : 0, cs_in, cs_out);
+  k_precond_apply<double><<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out,
+                                                                               transposed ? 1 : 0, cs_in, cs_out);
   CK(cudaGetLastError());
   // the periodic plain-surface unknowns: the circulant preconditioner (forward solves)
   if (op->circ.R > 0 && !transposed) return circulant_apply(op, in, out, k, cs_in, cs_out, s);
+  return SCABEM_OK;
+}
+
+bool precond_is_block_diagonal(const scabem_op* op, bool transposed) { return !(op->circ.R > 0 && !transposed); }
+
+int precond_apply_f32(scabem_op* op, const cx<double>* in, cx<float>* out, cudaStream_t s, bool transposed, int k,
+                      int64_t cs_in, int64_t cs_out) {
+  if (!precond_is_block_diagonal(op, transposed)) {
+    set_error("internal: complex64 preconditioner output with a circulant block");
+    return SCABEM_E_ARG;
+  }
+  k_precond_apply<float><<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out,
+                                                                              transposed ? 1 : 0, cs_in, cs_out);
+  CK(cudaGetLastError());
   return SCABEM_OK;
 }
 

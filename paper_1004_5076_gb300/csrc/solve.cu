@@ -372,9 +372,12 @@ constexpr int FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2;
 
 // part[(c * rb + b) * ldp + col] = sum over row block b of conj(V_c[:, col]) . w_c,
 // col in the tile blockIdx.y; with self_col, column nv is w_c itself (its
-// squared norm); skipped for columns with need[c] == 0
+// squared norm); skipped for columns with need[c] == 0.  w is read in its
+// own precision WT (the complex64 operator's output in the first pass) and
+// every product is formed in FP64 by four FMAs.
+template <typename WT>
 __global__ void __launch_bounds__(BG_THREADS) k_bdots(const cd* __restrict__ V, int64_t csV, int nv,
-                                                      const cd* __restrict__ w, int64_t N, cd* __restrict__ part,
+                                                      const cx<WT>* __restrict__ w, int64_t N, cd* __restrict__ part,
                                                       int ldp, const int* __restrict__ need, int self_col) {
   const int c = blockIdx.z;
   if (need && !need[c]) return;  // the whole block
@@ -387,13 +390,22 @@ __global__ void __launch_bounds__(BG_THREADS) k_bdots(const cd* __restrict__ V, 
 #pragma unroll
   for (int k = 0; k < BG_TC; ++k) ar[k] = ai[k] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const cd b = w[i];
+    const cx<WT> bw = w[i];
+    const double br = (double)bw.re, bi = (double)bw.im;
 #pragma unroll
     for (int k = 0; k < BG_TC; ++k)
       if (k < nc) {
-        const cd a = c0 + k < nv ? V[(int64_t)(c0 + k) * N + i] : b;
-        ar[k] += a.re * b.re + a.im * b.im;
-        ai[k] += a.re * b.im - a.im * b.re;
+        double vr = br, vi = bi;
+        if (c0 + k < nv) {
+          const cd a = V[(int64_t)(c0 + k) * N + i];
+          vr = a.re;
+          vi = a.im;
+        }
+        // conj(a) b = (a.re b.re + a.im b.im) + j (a.re b.im - a.im b.re)
+        ar[k] = fma(vr, br, ar[k]);
+        ar[k] = fma(vi, bi, ar[k]);
+        ai[k] = fma(vr, bi, ai[k]);
+        ai[k] = fma(-vi, br, ai[k]);
       }
   }
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -444,28 +456,39 @@ __global__ void k_breduce(const cd* __restrict__ part, int rb, int ldp, cd* __re
   if (threadIdx.x == 0) h[(int64_t)c * ldh + col] = mk(sre[0], sim[0]);
 }
 
-// w_c -= V_c h_c (nv basis vectors; none for a plain norm), and the squared
-// norm of the new w_c per row block (grid: BG_BLOCKS x K)
+// wout_c = win_c - V_c h_c (nv basis vectors; none for a plain norm), and the
+// squared norm of the new w_c per row block (grid: BG_BLOCKS x K).  win is
+// read in its own precision WT and may be wout itself (in place); every
+// product is formed in FP64 by four FMAs.
+template <typename WT>
 __global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cd* __restrict__ V, int64_t csV, int nv,
-                                                           const cd* __restrict__ h, int ldh, cd* __restrict__ w,
-                                                           int64_t N, double* __restrict__ nparts,
+                                                           const cd* __restrict__ h, int ldh, const cx<WT>* win,
+                                                           cd* wout, int64_t N, double* __restrict__ nparts,
                                                            const int* __restrict__ need) {
   const int c = blockIdx.y;
   if (need && !need[c]) return;
   V += c * csV;
-  w += c * N;
+  win += c * N;
+  wout += c * N;
   h += (int64_t)c * ldh;
+  const bool store = nv > 0 || (const void*)win != (const void*)wout;
   __shared__ double sm[BG_THREADS / 32];
   double nn = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    cd acc = w[i];
+    const cx<WT> x = win[i];
+    double xr = (double)x.re, xi = (double)x.im;
+#pragma unroll 4
     for (int k = 0; k < nv; ++k) {
       const cd a = V[(int64_t)k * N + i], b = h[k];
-      acc.re -= a.re * b.re - a.im * b.im;
-      acc.im -= a.re * b.im + a.im * b.re;
+      // x -= a b: re -= a.re b.re - a.im b.im, im -= a.re b.im + a.im b.re
+      xr = fma(-a.re, b.re, xr);
+      xr = fma(a.im, b.im, xr);
+      xi = fma(-a.re, b.im, xi);
+      xi = fma(-a.im, b.re, xi);
     }
-    if (nv > 0) w[i] = acc;
-    nn += acc.re * acc.re + acc.im * acc.im;
+    if (store) wout[i] = mk(xr, xi);
+    nn = fma(xr, xr, nn);
+    nn = fma(xi, xi, nn);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
@@ -523,54 +546,80 @@ struct BState {
   int* col;     // K the right-hand side (column of r, d, u, t) that slot c works on
 };
 
-// The Givens step of Arnoldi column j for every active column (one thread
-// per right-hand side): Hessenberg column j = h1 + h2 (the second pass when
+// The Givens step of Arnoldi column j for every active column (warp c for
+// right-hand side c): Hessenberg column j = h1 + h2 (the second pass when
 // taken) and |w|, the previous rotations, a new rotation, the rotated
 // right-hand side and the residual estimate; a column stops when the
-// estimate reaches tol or w vanishes.  word[0] = columns still active,
-// word[1] |= flags (host-mapped).
-__global__ void k_givens(BState S, int j, int m, int K, double tol, int* __restrict__ word) {
-  const int c = threadIdx.x;
+// estimate reaches tol or w vanishes.  The previous rotations run in lane 0
+// on chunks of GV_CH entries and rotations that the warp stages in shared
+// memory, so the sequential chain waits on no global load.  word[0] =
+// columns still active, word[1] |= flags (host-mapped).
+constexpr int GV_CH = 32;
+__global__ void __launch_bounds__(KBATCH * 32) k_givens(BState S, int j, int m, int K, double tol,
+                                                        int* __restrict__ word) {
+  __shared__ cd s_e[KBATCH][GV_CH], s_o[KBATCH][GV_CH], s_cs[KBATCH][GV_CH], s_sn[KBATCH][GV_CH];
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   bool on = false;
-  if (c < K && S.act[c]) {
+  if (c < K && S.act[c]) {  // warp-uniform
     const cd* a1 = S.h1 + (int64_t)c * (m + 1);
     const cd* a2 = S.h2 + (int64_t)c * (m + 1);
     const bool two = S.need[c] != 0;
     const double hn = two ? S.nrm[4 * c + 2] : S.nrm[4 * c + 1];
     cd* col = S.H + ((int64_t)c * m + j) * (m + 1);
-    cd* cs = S.cs + (int64_t)c * m;
-    cd* sn = S.sn + (int64_t)c * m;
-    cd* g = S.g + (int64_t)c * (m + 1);
-    for (int i = 0; i <= j; ++i) col[i] = two ? a1[i] + a2[i] : a1[i];
-    for (int i = 0; i < j; ++i) {
-      const cd a = col[i], b = col[i + 1];
-      col[i] = conj(cs[i]) * a + conj(sn[i]) * b;
-      col[i + 1] = -(sn[i] * a) + cs[i] * b;
+    const cd* cs = S.cs + (int64_t)c * m;
+    const cd* sn = S.sn + (int64_t)c * m;
+    // cur: entry i0 of the column after rotations 0 .. i0 - 1 (lane 0)
+    cd cur = two ? a1[0] + a2[0] : a1[0];
+    for (int i0 = 0; i0 < j; i0 += GV_CH) {
+      const int n = min(GV_CH, j - i0);  // rotations i0 .. i0 + n - 1, entries i0 + 1 .. i0 + n
+      if (lane < n) {
+        const int e = i0 + 1 + lane;
+        s_e[c][lane] = two ? a1[e] + a2[e] : a1[e];
+        s_cs[c][lane] = cs[i0 + lane];
+        s_sn[c][lane] = sn[i0 + lane];
+      }
+      __syncwarp();
+      if (lane == 0)
+        for (int l = 0; l < n; ++l) {
+          const cd nx = s_e[c][l], cl = s_cs[c][l], sl = s_sn[c][l];
+          s_o[c][l] = conj(cl) * cur + conj(sl) * nx;
+          cur = cl * nx - sl * cur;
+        }
+      __syncwarp();
+      if (lane < n) col[i0 + lane] = s_o[c][lane];
+      __syncwarp();
     }
-    const cd a = col[j];
-    const double den = sqrt(a.re * a.re + a.im * a.im + hn * hn);
-    on = true;
-    if (!isfinite(hn) || !isfinite(den)) {
-      atomicOr(word + 1, FLAG_NONFINITE);
-      on = false;
-    } else if (den == 0.0) {
-      atomicOr(word + 1, FLAG_BREAKDOWN);
-      on = false;
-    } else {
-      cs[j] = mk(a.re / den, a.im / den);
-      sn[j] = mk(hn / den, 0.0);
-      col[j] = mk(den, 0.0);
-      col[j + 1] = mk(0.0, 0.0);
-      const cd gj = g[j];
-      g[j] = conj(cs[j]) * gj;
-      g[j + 1] = -(sn[j] * gj);
-      const double e = sqrt(g[j + 1].re * g[j + 1].re + g[j + 1].im * g[j + 1].im) / S.rn0[c];
-      S.est[c] = e;
-      S.jc[c] = j + 1;
-      S.iters[c] += 1;
-      if (hn <= 1e-300 || e <= tol) on = false;
+    if (lane == 0) {
+      cd* csw = S.cs + (int64_t)c * m;
+      cd* snw = S.sn + (int64_t)c * m;
+      cd* g = S.g + (int64_t)c * (m + 1);
+      const cd a = cur;
+      const double den = sqrt(a.re * a.re + a.im * a.im + hn * hn);
+      on = true;
+      if (!isfinite(hn) || !isfinite(den)) {
+        atomicOr(word + 1, FLAG_NONFINITE);
+        on = false;
+      } else if (den == 0.0) {
+        atomicOr(word + 1, FLAG_BREAKDOWN);
+        on = false;
+      } else {
+        const cd cj = mk(a.re / den, a.im / den), sj = mk(hn / den, 0.0);
+        csw[j] = cj;
+        snw[j] = sj;
+        col[j] = mk(den, 0.0);
+        col[j + 1] = mk(0.0, 0.0);
+        const cd gj = g[j];
+        g[j] = conj(cj) * gj;
+        const cd g1 = -(sj * gj);
+        g[j + 1] = g1;
+        const double e = sqrt(g1.re * g1.re + g1.im * g1.im) / S.rn0[c];
+        S.est[c] = e;
+        S.jc[c] = j + 1;
+        S.iters[c] += 1;
+        if (hn <= 1e-300 || e <= tol) on = false;
+      }
+      if (!on) S.act[c] = 0;
     }
-    if (!on) S.act[c] = 0;
   }
   const int n = __syncthreads_count(on);
   if (threadIdx.x == 0) word[0] = n;
@@ -605,20 +654,35 @@ __global__ void k_bstart(const cd* __restrict__ t, const int* __restrict__ col, 
   }
 }
 
-// least squares of the cycle: y_c = R^-1 g_c over its jc[c] columns (one thread per column)
-__global__ void k_backsub(BState S, int m, int K) {
-  const int c = threadIdx.x;
-  if (c >= K) return;
+// least squares of the cycle: y_c = R^-1 g_c over its jc[c] columns (warp c
+// for right-hand side c: the lanes split each row's sum over the solved
+// entries, which stay in shared memory)
+__global__ void __launch_bounds__(KBATCH * 32) k_backsub(BState S, int m, int K) {
+  extern __shared__ cd s_y[];  // KBATCH x m
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c >= K) return;  // warp-uniform; no block barrier below
   const int j = S.jc[c];
   const cd* H = S.H + (int64_t)c * m * (m + 1);
   const cd* g = S.g + (int64_t)c * (m + 1);
   cd* y = S.y + (int64_t)c * m;
+  cd* ys = s_y + (int64_t)c * m;
   for (int i = j - 1; i >= 0; --i) {
-    cd acc = g[i];
-    for (int l = i + 1; l < j; ++l) acc -= H[(int64_t)l * (m + 1) + i] * y[l];
-    const cd hd = H[(int64_t)i * (m + 1) + i];
-    const double dd = hd.re * hd.re + hd.im * hd.im;
-    y[i] = mk((acc.re * hd.re + acc.im * hd.im) / dd, (acc.im * hd.re - acc.re * hd.im) / dd);
+    cd acc = mk(0.0, 0.0);
+    for (int l = i + 1 + lane; l < j; l += 32) acc += H[(int64_t)l * (m + 1) + i] * ys[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) {
+      acc = g[i] - acc;
+      const cd hd = H[(int64_t)i * (m + 1) + i];
+      const double dd = hd.re * hd.re + hd.im * hd.im;
+      const cd yi = mk((acc.re * hd.re + acc.im * hd.im) / dd, (acc.im * hd.re - acc.re * hd.im) / dd);
+      ys[i] = yi;
+      y[i] = yi;
+    }
+    __syncwarp();
   }
 }
 
@@ -711,12 +775,25 @@ struct BWork {
 
 // out[c * ostride] = |x_c| for the K columns of x (c * N apart)
 int bnorms(const cd* x, BWork& W, double* out, int ostride, cudaStream_t s) {
-  k_bvsub_norm<<<dim3(BG_BLOCKS, W.K), BG_THREADS, 0, s>>>(nullptr, 0, 0, nullptr, 0, const_cast<cd*>(x), W.N,
-                                                           W.nparts, nullptr);
+  k_bvsub_norm<double><<<dim3(BG_BLOCKS, W.K), BG_THREADS, 0, s>>>(nullptr, 0, 0, nullptr, 0, x, const_cast<cd*>(x),
+                                                                   W.N, W.nparts, nullptr);
   CK(cudaGetLastError());
   k_bnorm_fin<<<W.K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, out, ostride, nullptr, nullptr, nullptr, 0);
   CK(cudaGetLastError());
   return SCABEM_OK;
+}
+
+// wf = A zf for the K columns with the complex64 operator (the transposed
+// operator when solving A^T)
+int bapply_f32(scabem_op* op, BWork& W, cudaStream_t s) {
+  const int64_t N = W.N;
+  const int K = W.K;
+  if (W.tr) {
+    for (int c = 0; c < K; ++c)
+      if (int rc = apply_adjoint_one<float>(op, W.zf + c * N, W.wf + c * N, s)) return rc;
+    return SCABEM_OK;
+  }
+  return K == 1 ? apply_one<float>(op, W.zf, W.wf, s) : apply_batch<float>(op, W.zf, N, W.wf, N, K, s);
 }
 
 // w = A z for the K columns (FP64 storage, operator arithmetic in prec; the
@@ -734,13 +811,7 @@ int bapply(scabem_op* op, const cd* z, cd* w, int prec, BWork& W, cudaStream_t s
   }
   k_to_f<<<EW_BLOCKS, 256, 0, s>>>(z, W.zf, K * N);
   CK(cudaGetLastError());
-  int rc = SCABEM_OK;
-  if (W.tr) {
-    for (int c = 0; c < K && !rc; ++c) rc = apply_adjoint_one<float>(op, W.zf + c * N, W.wf + c * N, s);
-  } else {
-    rc = K == 1 ? apply_one<float>(op, W.zf, W.wf, s) : apply_batch<float>(op, W.zf, N, W.wf, N, K, s);
-  }
-  if (rc) return rc;
+  if (int rc = bapply_f32(op, W, s)) return rc;
   k_from_f<<<EW_BLOCKS, 256, 0, s>>>(W.wf, w, K * N);
   CK(cudaGetLastError());
   return SCABEM_OK;
@@ -807,9 +878,17 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
     k_bstart<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.t, S.col, W.V, csV, S, m, N);
     CK(cudaGetLastError());
     for (int j = 0; j < m && lock < maxit; ++j, ++lock) {
-      // z = P^-1 v_j (right preconditioning), w = A z
-      if (int rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr, Ka, csV, N)) return rc;
-      if (int rc = bapply(op, W.z, W.w, prec, W, s)) return rc;
+      // z = P^-1 v_j (right preconditioning), w = A z.  The complex64 operator
+      // with the block-diagonal preconditioner takes z in complex64 from the
+      // preconditioner, and the first pass reads its complex64 output.
+      const bool f32 = prec == SCABEM_C64 && precond_is_block_diagonal(op, W.tr);
+      if (f32) {
+        if (int rc = precond_apply_f32(op, W.V + (int64_t)j * N, W.zf, s, W.tr, Ka, csV, N)) return rc;
+        if (int rc = bapply_f32(op, W, s)) return rc;
+      } else {
+        if (int rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr, Ka, csV, N)) return rc;
+        if (int rc = bapply(op, W.z, W.w, prec, W, s)) return rc;
+      }
       // first pass h1 = V^H w with |w|^2 in its column j + 1, w -= V h1, |w|; the
       // DGKS test; the second pass only where it asks
       const int tiles = (int)cdiv(j + 2, BG_TC);
@@ -819,18 +898,26 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
         cd* h = pass ? S.h2 : S.h1;
         const int tl = pass ? (int)cdiv(j + 1, BG_TC) : tiles;
         const int rbp = pass ? std::max(8, BG_BLOCKS / tl) : rb;
-        k_bdots<<<dim3(rbp, tl, Ka), BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.w, N, W.part, m + 1, need,
-                                                         pass ? 0 : 1);
-        CK(cudaGetLastError());
-        k_breduce<<<dim3(j + 1 + (pass ? 0 : 1), Ka), BG_THREADS, 0, s>>>(W.part, rbp, m + 1, h, m + 1, need);
-        CK(cudaGetLastError());
-        k_bvsub_norm<<<dim3(BG_BLOCKS, Ka), BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.w, N, W.nparts, need);
+        const dim3 gd(rbp, tl, Ka), gv(BG_BLOCKS, Ka);
+        if (f32 && pass == 0) {
+          k_bdots<float><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.wf, N, W.part, m + 1, need, 1);
+          CK(cudaGetLastError());
+          k_breduce<<<dim3(j + 2, Ka), BG_THREADS, 0, s>>>(W.part, rbp, m + 1, h, m + 1, need);
+          CK(cudaGetLastError());
+          k_bvsub_norm<float><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.wf, W.w, N, W.nparts, need);
+        } else {
+          k_bdots<double><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.w, N, W.part, m + 1, need, pass ? 0 : 1);
+          CK(cudaGetLastError());
+          k_breduce<<<dim3(j + 1 + (pass ? 0 : 1), Ka), BG_THREADS, 0, s>>>(W.part, rbp, m + 1, h, m + 1, need);
+          CK(cudaGetLastError());
+          k_bvsub_norm<double><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.w, W.w, N, W.nparts, need);
+        }
         CK(cudaGetLastError());
         k_bnorm_fin<<<Ka, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 1 + pass, 4, need,
                                               pass ? nullptr : S.need, pass ? nullptr : S.h1 + (j + 1), m + 1);
         CK(cudaGetLastError());
       }
-      k_givens<<<1, 32, 0, s>>>(S, j, m, Ka, tol, W.word_d);
+      k_givens<<<1, KBATCH * 32, 0, s>>>(S, j, m, Ka, tol, W.word_d);
       CK(cudaGetLastError());
       if (j + 1 < m) {
         k_bscale<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.w, W.V, csV, j + 1, S.nrm, S.need, N);
@@ -856,7 +943,7 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
       }
     }
     // least squares of the cycle into u (at each slot's column), then d = P^-1 u for all columns
-    k_backsub<<<1, 32, 0, s>>>(S, m, Ka);
+    k_backsub<<<1, KBATCH * 32, sizeof(cd) * KBATCH * m, s>>>(S, m, Ka);
     CK(cudaGetLastError());
     k_bupdate<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.V, csV, S, m, S.col, W.u, N);
     CK(cudaGetLastError());
