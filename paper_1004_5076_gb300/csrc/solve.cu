@@ -408,20 +408,32 @@ __global__ void __launch_bounds__(BG_THREADS) k_bdots(const cd* __restrict__ V, 
         ai[k] = fma(-vi, br, ai[k]);
       }
   }
+  // warp sums of the 16 values by halving exchanges: at offset o = 16, 8, 4, 2
+  // each lane keeps half of its values, sends the other half to lane ^ o and
+  // adds what it receives, so that 16 FP64 adds (not 5 per value) leave lane
+  // l with the sum over 16 lanes of value 8 b4 + 4 b3 + 2 b2 + b1 (b = bits
+  // of l); one more exchange at offset 1 completes it.
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  static_assert(BG_TC == 8, "the exchange below reduces 2 BG_TC = 16 values");
+  double v[2 * BG_TC];
 #pragma unroll
-  for (int k = 0; k < BG_TC; ++k)
+  for (int k = 0; k < BG_TC; ++k) {
+    v[2 * k] = ar[k];
+    v[2 * k + 1] = ai[k];
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
-      ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], o);
+  for (int half = BG_TC; half >= 1; half >>= 1) {
+    const int o = 2 * half;  // 16, 8, 4, 2
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int t = 0; t < half; ++t) {
+      const double send = upper ? v[t] : v[t + half];
+      const double keep = upper ? v[t + half] : v[t];
+      v[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < BG_TC; ++k) {
-      sm[wp][2 * k] = ar[k];
-      sm[wp][2 * k + 1] = ai[k];
-    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  if ((lane & 1) == 0) sm[wp][((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1)] = v[0];
   __syncthreads();
   if (threadIdx.x < 2 * nc) {
     double v = 0.0;
@@ -546,18 +558,30 @@ struct BState {
   int* col;     // K the right-hand side (column of r, d, u, t) that slot c works on
 };
 
+__device__ __forceinline__ cd shfl_up_cd(cd v, int d) {
+  return mk(__shfl_up_sync(0xffffffffu, v.re, d), __shfl_up_sync(0xffffffffu, v.im, d));
+}
+__device__ __forceinline__ cd shfl_cd(cd v, int src) {
+  return mk(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+
 // The Givens step of Arnoldi column j for every active column (warp c for
 // right-hand side c): Hessenberg column j = h1 + h2 (the second pass when
 // taken) and |w|, the previous rotations, a new rotation, the rotated
 // right-hand side and the residual estimate; a column stops when the
-// estimate reaches tol or w vanishes.  The previous rotations run in lane 0
-// on chunks of GV_CH entries and rotations that the warp stages in shared
-// memory, so the sequential chain waits on no global load.  word[0] =
-// columns still active, word[1] |= flags (host-mapped).
-constexpr int GV_CH = 32;
+// estimate reaches tol or w vanishes.  word[0] = columns still active,
+// word[1] |= flags (host-mapped).
+//
+// Rotation i maps (e_i, e_i+1) to (conj(c_i) e_i + conj(s_i) e_i+1,
+// c_i e_i+1 - s_i e_i), so the entry it carries on obeys the first-order
+// recurrence r_i+1 = a_i r_i + b_i with a_i = -s_i and b_i = c_i e_i+1.  The
+// warp takes 32 rotations at a time and forms the prefix compositions
+// (a, b) o (a', b') = (a a', a b' + b) by a shuffle scan (5 steps), which
+// gives every r_i of the chunk at once: a sequential chain of FP64
+// operations in one lane would pay the full issue cost of an FP64 warp
+// instruction for every step on this GPU's narrow FP64 units.
 __global__ void __launch_bounds__(KBATCH * 32) k_givens(BState S, int j, int m, int K, double tol,
                                                         int* __restrict__ word) {
-  __shared__ cd s_e[KBATCH][GV_CH], s_o[KBATCH][GV_CH], s_cs[KBATCH][GV_CH], s_sn[KBATCH][GV_CH];
   const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   bool on = false;
   if (c < K && S.act[c]) {  // warp-uniform
@@ -566,60 +590,65 @@ __global__ void __launch_bounds__(KBATCH * 32) k_givens(BState S, int j, int m, 
     const bool two = S.need[c] != 0;
     const double hn = two ? S.nrm[4 * c + 2] : S.nrm[4 * c + 1];
     cd* col = S.H + ((int64_t)c * m + j) * (m + 1);
-    const cd* cs = S.cs + (int64_t)c * m;
-    const cd* sn = S.sn + (int64_t)c * m;
-    // cur: entry i0 of the column after rotations 0 .. i0 - 1 (lane 0)
-    cd cur = two ? a1[0] + a2[0] : a1[0];
-    for (int i0 = 0; i0 < j; i0 += GV_CH) {
-      const int n = min(GV_CH, j - i0);  // rotations i0 .. i0 + n - 1, entries i0 + 1 .. i0 + n
-      if (lane < n) {
-        const int e = i0 + 1 + lane;
-        s_e[c][lane] = two ? a1[e] + a2[e] : a1[e];
-        s_cs[c][lane] = cs[i0 + lane];
-        s_sn[c][lane] = sn[i0 + lane];
+    cd* cs = S.cs + (int64_t)c * m;
+    cd* sn = S.sn + (int64_t)c * m;
+    cd* g = S.g + (int64_t)c * (m + 1);
+    cd r = two ? a1[0] + a2[0] : a1[0];  // r_i0: entry i0 after rotations 0 .. i0 - 1
+    for (int i0 = 0; i0 < j; i0 += 32) {
+      const int n = min(32, j - i0);  // rotations i0 .. i0 + n - 1 (lane l: rotation i0 + l)
+      const bool v = lane < n;
+      cd cl = mk(1.0, 0.0), sl = mk(0.0, 0.0), e = mk(0.0, 0.0);
+      if (v) {
+        const int k = i0 + 1 + lane;
+        cl = cs[i0 + lane];
+        sl = sn[i0 + lane];
+        e = two ? a1[k] + a2[k] : a1[k];
       }
-      __syncwarp();
-      if (lane == 0)
-        for (int l = 0; l < n; ++l) {
-          const cd nx = s_e[c][l], cl = s_cs[c][l], sl = s_sn[c][l];
-          s_o[c][l] = conj(cl) * cur + conj(sl) * nx;
-          cur = cl * nx - sl * cur;
+      cd A = v ? -sl : mk(1.0, 0.0), B = v ? cl * e : mk(0.0, 0.0);
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const cd Ap = shfl_up_cd(A, d), Bp = shfl_up_cd(B, d);
+        if (lane >= d) {
+          B = A * Bp + B;
+          A = A * Ap;
         }
-      __syncwarp();
-      if (lane < n) col[i0 + lane] = s_o[c][lane];
-      __syncwarp();
+      }
+      // r_i0+l = (prefix of lanes 0 .. l - 1) applied to r_i0
+      const cd Al = shfl_up_cd(A, 1), Bl = shfl_up_cd(B, 1);
+      const cd ri = lane == 0 ? r : Al * r + Bl;
+      if (v) col[i0 + lane] = conj(cl) * ri + conj(sl) * e;
+      r = shfl_cd(A, n - 1) * r + shfl_cd(B, n - 1);
     }
-    if (lane == 0) {
-      cd* csw = S.cs + (int64_t)c * m;
-      cd* snw = S.sn + (int64_t)c * m;
-      cd* g = S.g + (int64_t)c * (m + 1);
-      const cd a = cur;
-      const double den = sqrt(a.re * a.re + a.im * a.im + hn * hn);
-      on = true;
-      if (!isfinite(hn) || !isfinite(den)) {
-        atomicOr(word + 1, FLAG_NONFINITE);
-        on = false;
-      } else if (den == 0.0) {
-        atomicOr(word + 1, FLAG_BREAKDOWN);
-        on = false;
-      } else {
-        const cd cj = mk(a.re / den, a.im / den), sj = mk(hn / den, 0.0);
-        csw[j] = cj;
-        snw[j] = sj;
+    // the new rotation, computed by every lane alike, written by lane 0
+    const double r2 = r.re * r.re + r.im * r.im + hn * hn;
+    on = true;
+    if (!isfinite(hn) || !isfinite(r2)) {
+      if (lane == 0) atomicOr(word + 1, FLAG_NONFINITE);
+      on = false;
+    } else if (r2 == 0.0) {
+      if (lane == 0) atomicOr(word + 1, FLAG_BREAKDOWN);
+      on = false;
+    } else {
+      const double inv = rsqrt(r2), den = r2 * inv;
+      const cd cj = mk(r.re * inv, r.im * inv), sj = mk(hn * inv, 0.0);
+      const cd gj = g[j];
+      const cd g1 = -(sj * gj);
+      const double e = sqrt(g1.re * g1.re + g1.im * g1.im) / S.rn0[c];
+      if (lane == 0) {
+        cs[j] = cj;
+        sn[j] = sj;
         col[j] = mk(den, 0.0);
         col[j + 1] = mk(0.0, 0.0);
-        const cd gj = g[j];
         g[j] = conj(cj) * gj;
-        const cd g1 = -(sj * gj);
         g[j + 1] = g1;
-        const double e = sqrt(g1.re * g1.re + g1.im * g1.im) / S.rn0[c];
         S.est[c] = e;
         S.jc[c] = j + 1;
         S.iters[c] += 1;
-        if (hn <= 1e-300 || e <= tol) on = false;
       }
-      if (!on) S.act[c] = 0;
+      if (hn <= 1e-300 || e <= tol) on = false;
     }
+    if (!on && lane == 0) S.act[c] = 0;
+    on = on && lane == 0;
   }
   const int n = __syncthreads_count(on);
   if (threadIdx.x == 0) word[0] = n;
