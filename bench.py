@@ -11,7 +11,7 @@ rows including the sigma-weighted absorber rows) on device-resident x.
 After the timed region the same line also carries (unless --no-extras):
 the complex128 matvec rate against the measured FP64 FMA peak, batched
 complex64 calls of 8 and 32 right-hand sides, GMRES solves (complex64
-operator, FP64 Arnoldi and refinement to 1e-8) of one and of eight
+operator, 48-bit Arnoldi and FP64 refinement to 1e-8) of one and of eight
 excitations on the more accurate operator (near radius 3.05 grid steps) with
 the reflection fitted from the solved field, the transposed operator and a
 conductivity gradient, cuFFT on the full transform grid as a comparison, and
@@ -622,8 +622,9 @@ def run_gpu(args):
                  "rhs": "Gaussian beam (waist parameter 0.15 um) in the core at x = 4.3 um, y-polarised",
                  "operator": "near radius 3.05 grid steps", "matvec_per_s_c64": 1e3 / ms_acc,
                  "ms_per_iteration": t_solve * 1e3 / max(sinfo["iters"], 1),
-                 "mode": ("GMRES(100) on the complex64 operator to 1e-4 with FP64 Arnoldi (classical Gram-Schmidt, "
-                          "second pass by the DGKS test, Givens updates on the device), FP64 refinement to 1e-8"),
+                 "mode": ("GMRES(100) on the complex64 operator to 1e-4 with 48-bit Arnoldi (classical Gram-Schmidt "
+                          "on FP32 (hi, lo) pairs, second pass by the DGKS test, Givens updates on the device), "
+                          "FP64 refinement to 1e-8"),
                  "circulant_preconditioner": circ,
                  "nrhs8": {"seconds": t_solve8, "seconds_per_rhs": t_solve8 / 8,
                            "iterations": [i["iters"] for i in info8], "relres_max": max(i["relres"] for i in info8),

@@ -319,9 +319,10 @@ int scabem_rhs_noalloc(scabem_op_t op, const scabem_source* src, int32_t nsrc, v
  * iterative solver).  An outer loop forms the FP64 residual r = b - A x with
  * the complex128 operator and solves A d = r by restarted GMRES, x += d,
  * until |r|/|b| <= refine_tol or max_refine rounds.  prec = precision of the
- * operator inside GMRES: SCABEM_C128, or SCABEM_C64 (complex64 operator with
- * FP64 Krylov vectors, Arnoldi and least squares; needs both precisions
- * built).  GMRES is right-preconditioned by the inverse per-edge diagonal
+ * operator inside GMRES: SCABEM_C128, or SCABEM_C64 (complex64 operator; needs
+ * both precisions built).  The Krylov vectors are held as FP32 (hi, lo)
+ * pairs, about 48 bits, with exact products and compensated sums; the
+ * Hessenberg least squares, the norms and the refinement are FP64.  GMRES is right-preconditioned by the inverse per-edge diagonal
  * blocks of A (the block-diagonal preconditioner of Appendix B), rebuilt on
  * every scabem_set_sigma.  x holds the initial guess on entry; info reports
  * iterations, refinement rounds and the final FP64 relative residual.

@@ -765,24 +765,28 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
 }
 
 
-// K6-8 for a batch of kc right-hand sides: one CTA of kc warps per target
-// triangle t = blockIdx.x, warp w working on right-hand side w exactly as a
-// warp of k_points does on its own.  The near records of t stream once
-// through one ring shared by the kc warps (PB_NSTG stages of PB_KP pairs,
-// filled by thread 0 with bulk copies), so each record leaves HBM once for
-// all kc columns.  After consuming a stage every warp joins a CTA barrier
-// that also combines the bounded waits' results: the slot is then free for
-// the next copy, and all warps leave the stage loop together when a wait
-// expired.  Interpolation, testing and the row sums are per warp (per
-// column); phases 2-3 use a per-warp area beside the ring.
+// K6-8 for a batch of ncol right-hand sides: one CTA per target triangle
+// t = blockIdx.x.  Thread T works on column T / 4q as lane (point, medium,
+// group) T mod 4q of k_points would, so the 4q lanes of each column are
+// packed back to back (8 columns x 24 lanes = 6 full warps for q = 6, where
+// a warp per column would leave 8 lanes of every warp idle).  The near
+// records of t stream once through one ring shared by all threads (PB_NSTG
+// stages of PB_KP pairs, filled by thread 0 with bulk copies), so each record
+// leaves HBM once for all columns.  After consuming a stage every thread
+// joins a CTA barrier that also combines the bounded waits' results: the
+// slot is then free for the next copy, and all threads leave the stage loop
+// together when a wait expired.  Testing (3q tasks per column) and the row
+// sums (12 per column) are packed the same way, on a per-column area beside
+// the ring.
 constexpr int PB_NSTG = 4;
 constexpr int PB_KP = 4;
 
 __host__ __device__ constexpr int pb_ring_complex(int q) { return PB_NSTG * PB_KP * NCORR * 2 * q; }
-__host__ __device__ constexpr int pb_warp_complex(int q) { return 2 * q * NREC + 3 * q * 4; }
+__host__ __device__ constexpr int pb_col_complex(int q) { return 2 * q * NREC + 3 * q * 4; }
 __host__ __device__ constexpr size_t pb_smem_bytes(int q, int kc, size_t csize) {
-  return ((size_t)pb_ring_complex(q) + (size_t)kc * pb_warp_complex(q)) * csize + PB_NSTG * sizeof(uint64_t);
+  return ((size_t)pb_ring_complex(q) + (size_t)kc * pb_col_complex(q)) * csize + PB_NSTG * sizeof(uint64_t);
 }
+__host__ __device__ constexpr int pb_threads(int q, int ncol) { return (4 * q * ncol + 31) / 32 * 32; }
 
 template <typename R, int P, int QT = 0>
 __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3) : 1) k_points_batch(
@@ -791,25 +795,23 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
     const int32_t* __restrict__ nsrc, const cx<R>* __restrict__ summ, const double* __restrict__ tri,
     const R* __restrict__ tp, const R* __restrict__ sig, int64_t nt, int q_arg, int n0, int n1, int n2, R ke, R ki,
     R ze, R zi, int has_near, const int32_t* __restrict__ valrow, cx<R>* __restrict__ y, int* __restrict__ tmo,
-    int64_t cs_grid, int64_t cs_summ, int64_t ldy) {
+    int64_t cs_grid, int64_t cs_summ, int64_t ldy, int ncol) {
   const int q = QT > 0 ? QT : q_arg;  // as in k_points
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kc = blockDim.x >> 5;
+  const int T = threadIdx.x, lane = T & 31;
+  const int nl = 4 * q;                    // phase-1 tasks per column
+  const bool act = T < ncol * nl;          // threads past them repeat a task of the last column, unstored
+  const int col = act ? T / nl : ncol - 1;
+  const int task = act ? T - col * nl : nl - 1;
   const int64_t t = blockIdx.x;
-  grids += warp * cs_grid;  // this warp's right-hand side
-  summ += warp * cs_summ;
-  y += warp * ldy;
   const int pairc = NCORR * 2 * q;
   cx<R>* ring = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* recs = ring + pb_ring_complex(q) + (int64_t)warp * pb_warp_complex(q);  // [q][2][NREC]
-  cx<R>* part = recs + 2 * q * NREC;                                              // [3][q][4]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + pb_ring_complex(q) + (int64_t)kc * pb_warp_complex(q));
+  cx<R>* area = ring + pb_ring_complex(q);  // per column: recs [q][2][NREC], then part [3][q][4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(area + (int64_t)ncol * pb_col_complex(q));
 
-  const bool act = lane < 4 * q;
-  const int a = min(lane >> 2, q - 1), med = (lane >> 1) & 1, h = lane & 1;  // lanes past 4q repeat, as in k_points
+  const int a = task >> 2, med = (task >> 1) & 1, h = task & 1;
   const int j0 = has_near ? noff[t] : 0, j1 = has_near ? noff[t + 1] : 0;
-  const int nst = (j1 - j0 + PB_KP - 1) / PB_KP;  // the same for every warp of the CTA
+  const int nst = (j1 - j0 + PB_KP - 1) / PB_KP;  // the same for every thread of the CTA
   const unsigned pair_bytes = (unsigned)(pairc * sizeof(cx<R>));
   auto issue = [&](int st) {  // thread 0 only
     const int pj = j0 + st * PB_KP;
@@ -819,7 +821,7 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
               bars + st % PB_NSTG);
   };
   if (nst > 0) {
-    if (threadIdx.x == 0) {
+    if (T == 0) {
 #pragma unroll
       for (int i = 0; i < PB_NSTG; ++i) mbar_init(bars + i, 1);
       mbar_init_fence();
@@ -828,9 +830,10 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
     __syncthreads();  // the barriers are initialised before anyone waits on them
   }
   const int npair = j1 - j0;
+  const cx<R>* summ_c = summ + col * cs_summ;
   int src_nxt = lane < npair ? nsrc[j0 + lane] : 0, src_cur = 0;
   cx<R> acc[NREC / 2];
-  interp_group<R, P>(grids, base, L, dL, t * q + a, med, h, n1, n2, acc);
+  interp_group<R, P>(grids + col * cs_grid, base, L, dL, t * q + a, med, h, n1, n2, acc);
   if (nst > 0) {
     const int set = h ? 2 : med;
     const bool neg = h && med;
@@ -842,8 +845,8 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
     int st = 0;
     bool ok = true;
     for (; st < nst; ++st) {
-      // slot (st - 1) % PB_NSTG was released by every warp at the barrier ending stage st - 1
-      if (threadIdx.x == 0 && st + PB_NSTG - 1 < nst) issue(st + PB_NSTG - 1);
+      // slot (st - 1) % PB_NSTG was released by every thread at the barrier ending stage st - 1
+      if (T == 0 && st + PB_NSTG - 1 < nst) issue(st + PB_NSTG - 1);
       const bool here = __all_sync(0xffffffffu, mbar_wait(bars + st % PB_NSTG, (st / PB_NSTG) & 1));
       if (here) {
         const cx<R>* rs = ring + (st % PB_NSTG) * PB_KP * pairc + (a * 2 + med) * NCORR;
@@ -857,7 +860,7 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
             }
             const int64_t sj = __shfl_sync(0xffffffffu, src_cur, jj & 31);
             cx<R> d[NCORR], sv[4];
-            load_group(summ + (3 * sj + set) * 4, sv);
+            load_group(summ_c + (3 * sj + set) * 4, sv);
 #pragma unroll
             for (int c = 0; c < NCORR; c += 2) load_pair_smem(rs + k * pairc + c, d + c);
             na.add(d, sv);
@@ -867,7 +870,7 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
       ok = __syncthreads_and(here) != 0;
       if (!ok) break;
     }
-    if (!ok && threadIdx.x == 0) {
+    if (!ok && T == 0) {
       // stages st .. min(st + PB_NSTG - 1, nst - 1) may still be in flight: let them land
       for (int s2 = st; s2 < nst && s2 < st + PB_NSTG; ++s2)
         (void)mbar_wait(bars + s2 % PB_NSTG, (s2 / PB_NSTG) & 1);
@@ -878,30 +881,35 @@ __global__ void __launch_bounds__(KBATCH * 32, sizeof(R) == 4 ? (P == 4 ? 2 : 3)
 #pragma unroll
       for (int c = 0; c < NREC / 2; ++c) acc[c] = -acc[c];
   }
+  // the ring is dead from here on: every thread passed the last stage's barrier
   if (act) {
-    cx<R>* o = recs + (a * 2 + med) * NREC + 10 * h;
+    cx<R>* o = area + (int64_t)col * pb_col_complex(q) + (a * 2 + med) * NREC + 10 * h;
 #pragma unroll
     for (int c = 0; c < NREC / 2; ++c) o[c] = acc[c];
   }
-  __syncwarp();
-  if (lane < 3 * q) {
-    const int kk = lane / q, pa = lane - kk * q;
+  __syncthreads();
+  if (T < ncol * 3 * q) {
+    const int c2 = T / (3 * q), r = T - c2 * 3 * q;
+    const int kk = r / q, pa = r - kk * q;
+    cx<R>* ar = area + (int64_t)c2 * pb_col_complex(q);
     cx<R> o[4];
-    test_point(recs + pa * 2 * NREC, summ, tri, tp, sig, t, kk, pa, q, ke, ki, ze, zi, o);
-    cx<R>* d = part + (kk * q + pa) * 4;
+    test_point(ar + pa * 2 * NREC, summ + c2 * cs_summ, tri, tp, sig, t, kk, pa, q, ke, ki, ze, zi, o);
+    cx<R>* d = ar + 2 * q * NREC + (kk * q + pa) * 4;
 #pragma unroll
     for (int c = 0; c < 4; ++c) d[c] = o[c];
   }
-  __syncwarp();
-  if (lane < 12) {
-    const int kk = lane >> 2, c = lane & 3;
-    const cx<R>* sp = part + kk * q * 4 + c;
+  __syncthreads();
+  for (int u = T; u < ncol * 12; u += blockDim.x) {  // more tasks than threads when q = 1
+    const int c2 = u / 12, r = u - c2 * 12;
+    const int kk = r >> 2, c = r & 3;
+    const cx<R>* sp = area + (int64_t)c2 * pb_col_complex(q) + 2 * q * NREC + kk * q * 4 + c;
     cx<R> v = czero<R>();
     for (int pa = 0; pa < q; ++pa) v += sp[pa * 4];
     const int row = valrow[(t * 3 + kk) * 4 + c];
     if (row >= 0) {
-      atomicAdd(&y[row].re, v.re);
-      atomicAdd(&y[row].im, v.im);
+      cx<R>* yc = y + c2 * ldy;
+      atomicAdd(&yc[row].re, v.re);
+      atomicAdd(&yc[row].im, v.im);
     }
   }
 }
@@ -1375,7 +1383,7 @@ int apply_one(scabem_op* op, const cx<R>* x, cx<R>* y, cudaStream_t s) {
 template <typename R>
 using PointsBatchFn = void (*)(const cx<R>*, const int32_t*, const R*, const R*, const cx<R>*, const int32_t*,
                                const int32_t*, const cx<R>*, const double*, const R*, const R*, int64_t, int, int, int,
-                               int, R, R, R, R, int, const int32_t*, cx<R>*, int*, int64_t, int64_t, int64_t);
+                               int, R, R, R, R, int, const int32_t*, cx<R>*, int*, int64_t, int64_t, int64_t, int);
 
 template <typename R>
 int apply_batch(scabem_op* op, const cx<R>* x, int64_t ldx, cx<R>* y, int64_t ldy, int k, cudaStream_t s) {
@@ -1409,10 +1417,10 @@ int apply_batch(scabem_op* op, const cx<R>* x, int64_t ldx, cx<R>* y, int64_t ld
                    : (op->p == 2 ? k_points_batch<R, 2> : op->p == 3 ? k_points_batch<R, 3> : k_points_batch<R, 4>);
     if (int rc_ = set_max_smem(op->device, (const void*)fn, (int)pb_smem_bytes(op->q, KBATCH, sizeof(cx<R>))))
       return rc_;
-    fn<<<(unsigned)nt, 32 * k, sm, s>>>(pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ,
-                                       op->tri, pd.tp, pd.sig, nt, op->q, n0, n1, n2, (R)op->ke, (R)op->ki,
-                                       (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, op->valrow, y, op->tmo_d,
-                                       col_stride_grid(op), col_stride_summ(op), ldy);
+    fn<<<(unsigned)nt, pb_threads(op->q, k), sm, s>>>(
+        pd.grid, op->base, pd.L, pd.dL, pd.near, op->noff, op->nsrc, pd.summ, op->tri, pd.tp, pd.sig, nt, op->q, n0,
+        n1, n2, (R)op->ke, (R)op->ki, (R)op->ze, (R)op->zi, op->npairs > 0 ? 1 : 0, op->valrow, y, op->tmo_d,
+        col_stride_grid(op), col_stride_summ(op), ldy, k);
     CK(cudaGetLastError());
   }
   prof_mark(op, s);

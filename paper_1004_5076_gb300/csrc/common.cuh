@@ -70,6 +70,26 @@ __host__ __device__ __forceinline__ void cfma(cx<R>& a, cx<R> b, cx<R> c) {
 template <typename R>
 __host__ __device__ __forceinline__ cx<R> cvt(cx<double> a) { return mk(R(a.re), R(a.im)); }
 
+// A complex value as FP32 (hi, lo) pairs: re = rh + rl, im = ih + il, each
+// lo at most half an ulp of its hi, so about 48 significant bits in the 16
+// bytes of a complex128.  The GMRES basis is held this way: its products
+// and sums then run on the FP32 units (exact products by FMA, compensated
+// sums), which this GPU has some 75 times more of than FP64 units.
+struct __align__(16) cdf {
+  float rh, ih, rl, il;
+};
+__device__ __forceinline__ cx<double> df_join(cdf v) {
+  return mk((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+}
+__device__ __forceinline__ cdf df_split(cx<double> v) {
+  cdf o;
+  o.rh = __double2float_rn(v.re);
+  o.ih = __double2float_rn(v.im);
+  o.rl = __double2float_rn(v.re - (double)o.rh);
+  o.il = __double2float_rn(v.im - (double)o.ih);
+  return o;
+}
+
 // small 3-vectors of complex
 template <typename R>
 struct cv3 {
@@ -284,10 +304,11 @@ int setup_gather(scabem_op* op, cudaStream_t s);
 // k right-hand sides: column c of in / out starts at c * cs_in / c * cs_out
 int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed = false,
                   int k = 1, int64_t cs_in = 0, int64_t cs_out = 0);
-// block-diagonal part only, complex64 output (the input of the complex64
-// operator); SCABEM_E_ARG when a circulant block is set for this direction
-int precond_apply_f32(scabem_op* op, const cx<double>* in, cx<float>* out, cudaStream_t s, bool transposed, int k,
-                      int64_t cs_in, int64_t cs_out);
+// block-diagonal part only, from a basis held as FP32 (hi, lo) pairs, into
+// complex64 (outf, the input of the complex64 operator) or complex128 (outd);
+// SCABEM_E_ARG when a circulant block is set for this direction
+int precond_apply_df(scabem_op* op, const cdf* in, cx<float>* outf, cx<double>* outd, cudaStream_t s,
+                     bool transposed, int k, int64_t cs_in, int64_t cs_out);
 bool precond_is_block_diagonal(const scabem_op* op, bool transposed);
 // precond.cu
 int setup_circulant(scabem_op* op, const scabem_mesh* mesh, const scabem_circulant* c, cudaStream_t s);

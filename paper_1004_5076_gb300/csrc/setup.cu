@@ -774,11 +774,15 @@ __global__ void k_precond(const double* __restrict__ tri, const double* __restri
 // out[unknowns of e] = Binv_e * in[rows of e] (rows and unknowns of an edge
 // share the same index set).
 // transposed = 1 applies (Binv_e)^T, the inverse blocks of A^T.
-// out = P^-1 in per edge block (P^-T when transposed), written in the output
-// precision TO (complex64 when it feeds the complex64 operator directly)
-template <typename TO>
+__device__ __forceinline__ cd ld_cd(const cd* p) { return *p; }
+__device__ __forceinline__ cd ld_cd(const cdf* p) { return df_join(*p); }
+
+// out = P^-1 in per edge block (P^-T when transposed), read from TI
+// (complex128, or FP32 (hi, lo) pairs) and written in the output precision
+// TO (complex64 when it feeds the complex64 operator directly)
+template <typename TI, typename TO>
 __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __restrict__ eunk, int64_t ne,
-                                const cd* __restrict__ in, cx<TO>* __restrict__ out, int transposed, int64_t cs_in,
+                                const TI* __restrict__ in, cx<TO>* __restrict__ out, int transposed, int64_t cs_in,
                                 int64_t cs_out) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= ne) return;
@@ -786,7 +790,7 @@ __global__ void k_precond_apply(const cd* __restrict__ pinv, const int32_t* __re
   out += blockIdx.y * cs_out;
   const int nb = eunk[3 * e + 2] < 0 ? 2 : 3;
   cd v[3];
-  for (int i = 0; i < nb; ++i) v[i] = in[eunk[3 * e + i]];
+  for (int i = 0; i < nb; ++i) v[i] = ld_cd(in + eunk[3 * e + i]);
   for (int i = 0; i < nb; ++i) {
     cd acc = mk(0.0, 0.0);
     for (int j = 0; j < nb; ++j) acc += pinv[9 * e + (transposed ? 3 * j + i : 3 * i + j)] * v[j];
@@ -912,8 +916,8 @@ int setup_precond(scabem_op* op, cudaStream_t s) {
 
 int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStream_t s, bool transposed, int k,
                   int64_t cs_in, int64_t cs_out) {
-  k_precond_apply<double><<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out,
-                                                                               transposed ? 1 : 0, cs_in, cs_out);
+  k_precond_apply<cd, double><<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(
+      op->pinv, op->eunk, op->ne, in, out, transposed ? 1 : 0, cs_in, cs_out);
   CK(cudaGetLastError());
   // the periodic plain-surface unknowns: the circulant preconditioner (forward solves)
   if (op->circ.R > 0 && !transposed) return circulant_apply(op, in, out, k, cs_in, cs_out, s);
@@ -922,14 +926,19 @@ int precond_apply(scabem_op* op, const cx<double>* in, cx<double>* out, cudaStre
 
 bool precond_is_block_diagonal(const scabem_op* op, bool transposed) { return !(op->circ.R > 0 && !transposed); }
 
-int precond_apply_f32(scabem_op* op, const cx<double>* in, cx<float>* out, cudaStream_t s, bool transposed, int k,
-                      int64_t cs_in, int64_t cs_out) {
+int precond_apply_df(scabem_op* op, const cdf* in, cx<float>* outf, cx<double>* outd, cudaStream_t s,
+                     bool transposed, int k, int64_t cs_in, int64_t cs_out) {
   if (!precond_is_block_diagonal(op, transposed)) {
-    set_error("internal: complex64 preconditioner output with a circulant block");
+    set_error("internal: basis preconditioner call with a circulant block");
     return SCABEM_E_ARG;
   }
-  k_precond_apply<float><<<dim3((unsigned)cdiv(op->ne, 256), k), 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, out,
-                                                                              transposed ? 1 : 0, cs_in, cs_out);
+  const dim3 g((unsigned)cdiv(op->ne, 256), k);
+  if (outf)
+    k_precond_apply<cdf, float><<<g, 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, outf, transposed ? 1 : 0, cs_in,
+                                                  cs_out);
+  else
+    k_precond_apply<cdf, double><<<g, 256, 0, s>>>(op->pinv, op->eunk, op->ne, in, outd, transposed ? 1 : 0, cs_in,
+                                                   cs_out);
   CK(cudaGetLastError());
   return SCABEM_OK;
 }

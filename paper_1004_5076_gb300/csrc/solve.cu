@@ -1,4 +1,4 @@
-// Right-hand side, GMRES with FP64 Arnoldi and iterative refinement, fields
+// Right-hand side, GMRES with iterative refinement, fields
 // at interior points and the reflection fit.
 //
 // * rhs: tested incident field b (Appendix A): per row type <X, E_inc>,
@@ -6,12 +6,13 @@
 //   interior source (Eqs. 8-9); the mirrored combination, with
 //   <sigma n x X, E_inc> in Eq. 13, for an exterior source.
 // * solve: restarted GMRES (the paper's iterative solver, Appendix B) with
-//   classical Gram-Schmidt applied twice in FP64 on the device; Hessenberg
-//   least squares by Givens rotations; right-preconditioned by the inverse
-//   per-edge diagonal blocks (the block-diagonal preconditioner of
-//   Appendix B).  In complex64 mode the Krylov vectors stay FP64 and only
-//   the operator runs in complex64.  An outer FP64 residual r = b - A x
-//   drives iterative refinement in both modes.
+//   classical Gram-Schmidt on the device, its second pass where the DGKS
+//   test asks, on Krylov vectors held as FP32 (hi, lo) pairs (about 48
+//   bits, products and sums on the FP32 units); Hessenberg least squares by
+//   Givens rotations in FP64; right-preconditioned by the inverse per-edge
+//   diagonal blocks (the block-diagonal preconditioner of Appendix B).  In
+//   complex64 mode only the operator runs in complex64.  An outer FP64
+//   residual r = b - A x drives iterative refinement in both modes.
 // * fields / reflection: total interior field E_inc + E_i(J_i, M_i) (Eq. 8) at
 //   probe points by the triangle quadrature, and a least-squares split of the
 //   on-axis field into forward and backward waves (Table 1's reflection).
@@ -21,6 +22,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -370,76 +372,131 @@ constexpr int BG_BLOCKS = 4 * 152;  // row blocks per column of the reductions (
 constexpr int BG_TC = 8;        // basis vectors per tile of the dot products
 constexpr int FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2;
 
+// Error-free transformations in round-to-nearest intrinsics, which the
+// compiler neither contracts nor reassociates: Knuth's two-sum (s + e = a + b
+// exactly) and the product's rounding error by FMA (a b = p + e exactly).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+struct dfa {  // h + l
+  float h, l;
+};
+// acc += a b: the product exactly, the sum compensated
+__device__ __forceinline__ void df_mac(dfa& acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  float sh, t;
+  two_sum(acc.h, p, sh, t);
+  acc.h = sh;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(t, e));
+}
+// acc += a b for a term below the precision of acc.h (a cross term with a lo part)
+__device__ __forceinline__ void df_small(dfa& acc, float a, float b) { acc.l = __fmaf_rn(a, b, acc.l); }
+__device__ __forceinline__ dfa df_renorm(dfa a) {
+  dfa r;
+  two_sum(a.h, a.l, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ dfa df_add(dfa a, dfa b) {
+  float sh, e;
+  two_sum(a.h, b.h, sh, e);
+  dfa r;
+  two_sum(sh, __fadd_rn(e, __fadd_rn(a.l, b.l)), r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ dfa df_shfl_xor(dfa a, int o) {
+  dfa r;
+  r.h = __shfl_xor_sync(0xffffffffu, a.h, o);
+  r.l = __shfl_xor_sync(0xffffffffu, a.l, o);
+  return r;
+}
+__device__ __forceinline__ double df_d(dfa a) { return (double)a.h + (double)a.l; }
+// a vector element in its storage precision as (hi, lo) pairs
+__device__ __forceinline__ cdf ld_df(const cx<float>* p) {
+  const cx<float> v = *p;
+  cdf o;
+  o.rh = v.re;
+  o.ih = v.im;
+  o.rl = 0.f;
+  o.il = 0.f;
+  return o;
+}
+__device__ __forceinline__ cdf ld_df(const cx<double>* p) { return df_split(*p); }
+__device__ __forceinline__ cdf ld_df(const cdf* p) { return *p; }
+
 // part[(c * rb + b) * ldp + col] = sum over row block b of conj(V_c[:, col]) . w_c,
 // col in the tile blockIdx.y; with self_col, column nv is w_c itself (its
-// squared norm); skipped for columns with need[c] == 0.  w is read in its
-// own precision WT (the complex64 operator's output in the first pass) and
-// every product is formed in FP64 by four FMAs.
+// squared norm); skipped for columns with need[c] == 0.  The basis is held
+// as FP32 (hi, lo) pairs and w is read in its own precision WT (the
+// complex64 operator's output in the first pass, exact as a hi part); every
+// product is formed on the FP32 units with its rounding error and summed
+// with compensation, so that the sums keep about 48 bits.
 template <typename WT>
-__global__ void __launch_bounds__(BG_THREADS) k_bdots(const cd* __restrict__ V, int64_t csV, int nv,
-                                                      const cx<WT>* __restrict__ w, int64_t N, cd* __restrict__ part,
+__global__ void __launch_bounds__(BG_THREADS) k_bdots(const cdf* __restrict__ V, int64_t csV, int nv,
+                                                      const WT* __restrict__ w, int64_t N, cd* __restrict__ part,
                                                       int ldp, const int* __restrict__ need, int self_col) {
+  constexpr bool WLO = !std::is_same<WT, cx<float>>::value;  // w has lo parts
   const int c = blockIdx.z;
   if (need && !need[c]) return;  // the whole block
   V += c * csV;
   w += c * N;
-  __shared__ double sm[BG_THREADS / 32][2 * BG_TC];
+  __shared__ dfa sm[BG_THREADS / 32][2 * BG_TC];
   const int c0 = blockIdx.y * BG_TC;
   const int nc = min(BG_TC, nv + self_col - c0);
-  double ar[BG_TC], ai[BG_TC];
+  dfa v[2 * BG_TC];  // v[2k]: real part of column c0 + k, v[2k + 1]: imaginary part
 #pragma unroll
-  for (int k = 0; k < BG_TC; ++k) ar[k] = ai[k] = 0.0;
+  for (int k = 0; k < 2 * BG_TC; ++k) v[k] = dfa{0.f, 0.f};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const cx<WT> bw = w[i];
-    const double br = (double)bw.re, bi = (double)bw.im;
+    const cdf b = ld_df(w + i);
 #pragma unroll
     for (int k = 0; k < BG_TC; ++k)
       if (k < nc) {
-        double vr = br, vi = bi;
-        if (c0 + k < nv) {
-          const cd a = V[(int64_t)(c0 + k) * N + i];
-          vr = a.re;
-          vi = a.im;
-        }
+        const cdf a = c0 + k < nv ? V[(int64_t)(c0 + k) * N + i] : b;
         // conj(a) b = (a.re b.re + a.im b.im) + j (a.re b.im - a.im b.re)
-        ar[k] = fma(vr, br, ar[k]);
-        ar[k] = fma(vi, bi, ar[k]);
-        ai[k] = fma(vr, bi, ai[k]);
-        ai[k] = fma(-vi, br, ai[k]);
+        df_mac(v[2 * k], a.rh, b.rh);
+        df_mac(v[2 * k], a.ih, b.ih);
+        df_mac(v[2 * k + 1], a.rh, b.ih);
+        df_mac(v[2 * k + 1], -a.ih, b.rh);
+        df_small(v[2 * k], a.rl, b.rh);
+        df_small(v[2 * k], a.il, b.ih);
+        df_small(v[2 * k + 1], a.rl, b.ih);
+        df_small(v[2 * k + 1], -a.il, b.rh);
+        if (WLO) {
+          df_small(v[2 * k], a.rh, b.rl);
+          df_small(v[2 * k], a.ih, b.il);
+          df_small(v[2 * k + 1], a.rh, b.il);
+          df_small(v[2 * k + 1], -a.ih, b.rl);
+        }
       }
   }
   // warp sums of the 16 values by halving exchanges: at offset o = 16, 8, 4, 2
   // each lane keeps half of its values, sends the other half to lane ^ o and
-  // adds what it receives, so that 16 FP64 adds (not 5 per value) leave lane
+  // adds what it receives, so that 16 additions (not 5 per value) leave lane
   // l with the sum over 16 lanes of value 8 b4 + 4 b3 + 2 b2 + b1 (b = bits
   // of l); one more exchange at offset 1 completes it.
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   static_assert(BG_TC == 8, "the exchange below reduces 2 BG_TC = 16 values");
-  double v[2 * BG_TC];
-#pragma unroll
-  for (int k = 0; k < BG_TC; ++k) {
-    v[2 * k] = ar[k];
-    v[2 * k + 1] = ai[k];
-  }
 #pragma unroll
   for (int half = BG_TC; half >= 1; half >>= 1) {
     const int o = 2 * half;  // 16, 8, 4, 2
     const bool upper = (lane & o) != 0;
 #pragma unroll
     for (int t = 0; t < half; ++t) {
-      const double send = upper ? v[t] : v[t + half];
-      const double keep = upper ? v[t + half] : v[t];
-      v[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      const dfa send = upper ? v[t] : v[t + half];
+      const dfa keep = upper ? v[t + half] : v[t];
+      v[t] = df_add(keep, df_shfl_xor(send, o));
     }
   }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  v[0] = df_add(v[0], df_shfl_xor(v[0], 1));
   if ((lane & 1) == 0) sm[wp][((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1)] = v[0];
   __syncthreads();
   if (threadIdx.x < 2 * nc) {
-    double v = 0.0;
-    for (int k = 0; k < BG_THREADS / 32; ++k) v += sm[k][threadIdx.x];
+    dfa t = sm[0][threadIdx.x];
+    for (int k = 1; k < BG_THREADS / 32; ++k) t = df_add(t, sm[k][threadIdx.x]);
     double* o = reinterpret_cast<double*>(part + ((int64_t)c * gridDim.x + blockIdx.x) * ldp + c0);
-    o[threadIdx.x] = v;
+    o[threadIdx.x] = df_d(t);
   }
 }
 
@@ -468,39 +525,18 @@ __global__ void k_breduce(const cd* __restrict__ part, int rb, int ldp, cd* __re
   if (threadIdx.x == 0) h[(int64_t)c * ldh + col] = mk(sre[0], sim[0]);
 }
 
-// wout_c = win_c - V_c h_c (nv basis vectors; none for a plain norm), and the
-// squared norm of the new w_c per row block (grid: BG_BLOCKS x K).  win is
-// read in its own precision WT and may be wout itself (in place); every
-// product is formed in FP64 by four FMAs.
-template <typename WT>
-__global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cd* __restrict__ V, int64_t csV, int nv,
-                                                           const cd* __restrict__ h, int ldh, const cx<WT>* win,
-                                                           cd* wout, int64_t N, double* __restrict__ nparts,
-                                                           const int* __restrict__ need) {
+// Squared norm of each column of an FP64 vector per row block (grid:
+// BG_BLOCKS x K), for the residual norms at the start and the restarts.
+__global__ void __launch_bounds__(BG_THREADS) k_bnorm_parts(const cd* __restrict__ x, int64_t N,
+                                                            double* __restrict__ nparts) {
   const int c = blockIdx.y;
-  if (need && !need[c]) return;
-  V += c * csV;
-  win += c * N;
-  wout += c * N;
-  h += (int64_t)c * ldh;
-  const bool store = nv > 0 || (const void*)win != (const void*)wout;
+  x += c * N;
   __shared__ double sm[BG_THREADS / 32];
   double nn = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const cx<WT> x = win[i];
-    double xr = (double)x.re, xi = (double)x.im;
-#pragma unroll 4
-    for (int k = 0; k < nv; ++k) {
-      const cd a = V[(int64_t)k * N + i], b = h[k];
-      // x -= a b: re -= a.re b.re - a.im b.im, im -= a.re b.im + a.im b.re
-      xr = fma(-a.re, b.re, xr);
-      xr = fma(a.im, b.im, xr);
-      xi = fma(-a.re, b.im, xi);
-      xi = fma(-a.im, b.re, xi);
-    }
-    if (store) wout[i] = mk(xr, xi);
-    nn = fma(xr, xr, nn);
-    nn = fma(xi, xi, nn);
+    const cd v = x[i];
+    nn = fma(v.re, v.re, nn);
+    nn = fma(v.im, v.im, nn);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
@@ -510,6 +546,77 @@ __global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cd* __restrict_
     double v = 0.0;
     for (int k = 0; k < BG_THREADS / 32; ++k) v += sm[k];
     nparts[(int64_t)c * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// wout_c = win_c - V_c h_c over nv basis vectors, stored as (hi, lo) pairs,
+// and the squared norm of the new w_c per row block (grid: BG_BLOCKS x K).
+// win is read in its own precision WT and may be wout itself (in place).  The
+// coefficients h (FP64) are split into (hi, lo) pairs once per block; every
+// product is formed with its rounding error and summed with compensation.
+constexpr int GM_MAXM = 200;  // largest restart length (checked by the C ABI)
+template <typename WT>
+__global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cdf* __restrict__ V, int64_t csV, int nv,
+                                                           const cd* __restrict__ h, int ldh, const WT* win,
+                                                           cdf* wout, int64_t N, double* __restrict__ nparts,
+                                                           const int* __restrict__ need) {
+  const int c = blockIdx.y;
+  if (need && !need[c]) return;
+  V += c * csV;
+  win += c * N;
+  wout += c * N;
+  h += (int64_t)c * ldh;
+  __shared__ cdf hs[GM_MAXM + 1];
+  __shared__ dfa sm[BG_THREADS / 32];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = df_split(h[k]);
+  __syncthreads();
+  dfa nn = {0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const cdf x0 = ld_df(win + i);
+    dfa xr = {x0.rh, x0.rl}, xi = {x0.ih, x0.il};
+#pragma unroll 4
+    for (int k = 0; k < nv; ++k) {
+      const cdf a = V[(int64_t)k * N + i], b = hs[k];
+      // x -= a b: re += -a.re b.re + a.im b.im, im += -a.re b.im - a.im b.re
+      df_mac(xr, -a.rh, b.rh);
+      df_mac(xr, a.ih, b.ih);
+      df_mac(xi, -a.rh, b.ih);
+      df_mac(xi, -a.ih, b.rh);
+      df_small(xr, -a.rh, b.rl);
+      df_small(xr, -a.rl, b.rh);
+      df_small(xr, a.ih, b.il);
+      df_small(xr, a.il, b.ih);
+      df_small(xi, -a.rh, b.il);
+      df_small(xi, -a.rl, b.ih);
+      df_small(xi, -a.ih, b.rl);
+      df_small(xi, -a.il, b.rh);
+      if ((k & 7) == 7) {
+        xr = df_renorm(xr);
+        xi = df_renorm(xi);
+      }
+    }
+    xr = df_renorm(xr);
+    xi = df_renorm(xi);
+    cdf o;
+    o.rh = xr.h;
+    o.ih = xi.h;
+    o.rl = xr.l;
+    o.il = xi.l;
+    wout[i] = o;
+    // |x|^2 = h^2 + 2 h l + l^2 per part
+    df_mac(nn, xr.h, xr.h);
+    df_small(nn, 2.f * xr.h, xr.l);
+    df_mac(nn, xi.h, xi.h);
+    df_small(nn, 2.f * xi.h, xi.l);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nn = df_add(nn, df_shfl_xor(nn, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dfa v = sm[0];
+    for (int k = 1; k < BG_THREADS / 32; ++k) v = df_add(v, sm[k]);
+    nparts[(int64_t)c * gridDim.x + blockIdx.x] = df_d(v);
   }
 }
 
@@ -654,21 +761,46 @@ __global__ void __launch_bounds__(KBATCH * 32) k_givens(BState S, int j, int m, 
   if (threadIdx.x == 0) word[0] = n;
 }
 
-// v_c,j+1 = w_c / |w_c| (|w| after the last pass; zero when it vanishes)
-__global__ void k_bscale(const cd* __restrict__ w, cd* __restrict__ V, int64_t csV, int j1, const double* __restrict__ nrm,
-                         const int* __restrict__ need, int64_t N) {
+// v_c,j+1 = w_c / |w_c| (|w| after the last pass; zero when it vanishes), in
+// (hi, lo) pairs: 1 / |w| is split once per block and each product is
+// formed with its rounding error
+__global__ void k_bscale(const cdf* __restrict__ w, cdf* __restrict__ V, int64_t csV, int j1,
+                         const double* __restrict__ nrm, const int* __restrict__ need, int64_t N) {
   const int c = blockIdx.y;
-  const double n = need[c] ? nrm[4 * c + 2] : nrm[4 * c + 1];
-  const double s = n > 1e-300 ? 1.0 / n : 0.0;
+  __shared__ float s_s[2];
+  if (threadIdx.x == 0) {
+    const double n = need[c] ? nrm[4 * c + 2] : nrm[4 * c + 1];
+    const double sd = n > 1e-300 ? 1.0 / n : 0.0;
+    s_s[0] = __double2float_rn(sd);
+    s_s[1] = __double2float_rn(sd - (double)s_s[0]);
+  }
+  __syncthreads();
+  const float sh = s_s[0], sl = s_s[1];
   w += c * N;
   V += c * csV + (int64_t)j1 * N;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    V[i] = s * w[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const cdf x = w[i];
+    dfa r = {0.f, 0.f}, m = {0.f, 0.f};
+    df_mac(r, x.rh, sh);
+    df_small(r, x.rh, sl);
+    df_small(r, x.rl, sh);
+    df_mac(m, x.ih, sh);
+    df_small(m, x.ih, sl);
+    df_small(m, x.il, sh);
+    r = df_renorm(r);
+    m = df_renorm(m);
+    cdf o;
+    o.rh = r.h;
+    o.ih = m.h;
+    o.rl = r.l;
+    o.il = m.l;
+    V[i] = o;
+  }
 }
 
 // start of a cycle in slot c (the slot's right-hand side is column col[c]
 // of t): v_c,0 = t / beta_c, g_c = beta_c e_1
-__global__ void k_bstart(const cd* __restrict__ t, const int* __restrict__ col, cd* __restrict__ V, int64_t csV,
+__global__ void k_bstart(const cd* __restrict__ t, const int* __restrict__ col, cdf* __restrict__ V, int64_t csV,
                          BState S, int m, int64_t N) {
   const int c = blockIdx.y;
   const double beta = S.nrm[4 * c + 3];
@@ -676,11 +808,21 @@ __global__ void k_bstart(const cd* __restrict__ t, const int* __restrict__ col, 
   t += col[c] * N;
   V += c * csV;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    V[i] = s * t[i];
+    V[i] = df_split(s * t[i]);
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i <= m; i += blockDim.x) S.g[(int64_t)c * (m + 1) + i] = mk(i == 0 ? beta : 0.0, 0.0);
     if (threadIdx.x == 0) S.jc[c] = 0;
   }
+}
+
+// out (column c, leading dimension N) = v_c,j in FP64, for the preconditioners
+// that take FP64 input (the circulant block)
+__global__ void k_bjoin(const cdf* __restrict__ V, int64_t csV, cd* __restrict__ out, int64_t N) {
+  const int c = blockIdx.y;
+  V += c * csV;
+  out += c * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df_join(V[i]);
 }
 
 // least squares of the cycle: y_c = R^-1 g_c over its jc[c] columns (warp c
@@ -716,7 +858,7 @@ __global__ void __launch_bounds__(KBATCH * 32) k_backsub(BState S, int m, int K)
 }
 
 // u (column col[c]) += V_c y_c over slot c's jc[c] basis vectors
-__global__ void k_bupdate(const cd* __restrict__ V, int64_t csV, BState S, int m, const int* __restrict__ col,
+__global__ void k_bupdate(const cdf* __restrict__ V, int64_t csV, BState S, int m, const int* __restrict__ col,
                           cd* __restrict__ u, int64_t N) {
   const int c = blockIdx.y;
   const int j = S.jc[c];
@@ -726,7 +868,7 @@ __global__ void k_bupdate(const cd* __restrict__ V, int64_t csV, BState S, int m
   const cd* y = S.y + (int64_t)c * m;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     cd acc = u[i];
-    for (int l = 0; l < j; ++l) cfma(acc, V[(int64_t)l * N + i], y[l]);
+    for (int l = 0; l < j; ++l) cfma(acc, df_join(V[(int64_t)l * N + i]), y[l]);
     u[i] = acc;
   }
 }
@@ -754,8 +896,9 @@ struct BWork {
   int K = 0, m = 0;
   int64_t N = 0;
   bool tr = false;
-  cd* V = nullptr;           // K (m + 1) N basis
-  cd* w = nullptr;           // K N
+  cdf* V = nullptr;          // K (m + 1) N basis, (hi, lo) pairs
+  cdf* wdf = nullptr;        // K N vector under orthogonalisation, (hi, lo) pairs
+  cd* w = nullptr;           // K N FP64 operator output
   cd* z = nullptr;           // K N preconditioned basis vector
   cd* u = nullptr;           // K N solution in the preconditioned variables
   cd* t = nullptr;           // K N working residual
@@ -786,7 +929,7 @@ struct BWork {
     m = mm;
     N = n;
     int rc;
-    if ((rc = get(&V, (int64_t)K * (m + 1) * N)) || (rc = get(&w, K * N)) || (rc = get(&z, K * N)) ||
+    if ((rc = get(&V, (int64_t)K * (m + 1) * N)) || (rc = get(&wdf, K * N)) || (rc = get(&w, K * N)) || (rc = get(&z, K * N)) ||
         (rc = get(&u, K * N)) || (rc = get(&t, K * N)) || (rc = get(&part, (int64_t)K * BG_BLOCKS * (m + 1))) ||
         (rc = get(&nparts, (int64_t)K * BG_BLOCKS)) || (rc = get(&S.H, (int64_t)K * m * (m + 1))) ||
         (rc = get(&S.cs, K * m)) || (rc = get(&S.sn, K * m)) || (rc = get(&S.g, K * (m + 1))) ||
@@ -804,8 +947,7 @@ struct BWork {
 
 // out[c * ostride] = |x_c| for the K columns of x (c * N apart)
 int bnorms(const cd* x, BWork& W, double* out, int ostride, cudaStream_t s) {
-  k_bvsub_norm<double><<<dim3(BG_BLOCKS, W.K), BG_THREADS, 0, s>>>(nullptr, 0, 0, nullptr, 0, x, const_cast<cd*>(x),
-                                                                   W.N, W.nparts, nullptr);
+  k_bnorm_parts<<<dim3(BG_BLOCKS, W.K), BG_THREADS, 0, s>>>(x, W.N, W.nparts);
   CK(cudaGetLastError());
   k_bnorm_fin<<<W.K, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, out, ostride, nullptr, nullptr, nullptr, 0);
   CK(cudaGetLastError());
@@ -907,15 +1049,25 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
     k_bstart<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.t, S.col, W.V, csV, S, m, N);
     CK(cudaGetLastError());
     for (int j = 0; j < m && lock < maxit; ++j, ++lock) {
-      // z = P^-1 v_j (right preconditioning), w = A z.  The complex64 operator
-      // with the block-diagonal preconditioner takes z in complex64 from the
-      // preconditioner, and the first pass reads its complex64 output.
-      const bool f32 = prec == SCABEM_C64 && precond_is_block_diagonal(op, W.tr);
+      // z = P^-1 v_j (right preconditioning), w = A z.  The block-diagonal
+      // preconditioner reads v_j as (hi, lo) pairs and, for the complex64
+      // operator, writes its complex64 input directly; the first pass then
+      // reads the complex64 output.  A circulant block takes v_j in FP64
+      // (t is free during a cycle: it is read at the cycle's start only).
+      const cdf* vj = W.V + (int64_t)j * N;
+      const bool bd = precond_is_block_diagonal(op, W.tr);
+      const bool f32 = prec == SCABEM_C64 && bd;
       if (f32) {
-        if (int rc = precond_apply_f32(op, W.V + (int64_t)j * N, W.zf, s, W.tr, Ka, csV, N)) return rc;
+        if (int rc = precond_apply_df(op, vj, W.zf, nullptr, s, W.tr, Ka, csV, N)) return rc;
         if (int rc = bapply_f32(op, W, s)) return rc;
       } else {
-        if (int rc = precond_apply(op, W.V + (int64_t)j * N, W.z, s, W.tr, Ka, csV, N)) return rc;
+        if (bd) {
+          if (int rc = precond_apply_df(op, vj, nullptr, W.z, s, W.tr, Ka, csV, N)) return rc;
+        } else {
+          k_bjoin<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(vj, csV, W.t, N);
+          CK(cudaGetLastError());
+          if (int rc = precond_apply(op, W.t, W.z, s, W.tr, Ka, N, N)) return rc;
+        }
         if (int rc = bapply(op, W.z, W.w, prec, W, s)) return rc;
       }
       // first pass h1 = V^H w with |w|^2 in its column j + 1, w -= V h1, |w|; the
@@ -928,19 +1080,23 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
         const int tl = pass ? (int)cdiv(j + 1, BG_TC) : tiles;
         const int rbp = pass ? std::max(8, BG_BLOCKS / tl) : rb;
         const dim3 gd(rbp, tl, Ka), gv(BG_BLOCKS, Ka);
-        if (f32 && pass == 0) {
-          k_bdots<float><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.wf, N, W.part, m + 1, need, 1);
-          CK(cudaGetLastError());
-          k_breduce<<<dim3(j + 2, Ka), BG_THREADS, 0, s>>>(W.part, rbp, m + 1, h, m + 1, need);
-          CK(cudaGetLastError());
-          k_bvsub_norm<float><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.wf, W.w, N, W.nparts, need);
-        } else {
-          k_bdots<double><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.w, N, W.part, m + 1, need, pass ? 0 : 1);
-          CK(cudaGetLastError());
-          k_breduce<<<dim3(j + 1 + (pass ? 0 : 1), Ka), BG_THREADS, 0, s>>>(W.part, rbp, m + 1, h, m + 1, need);
-          CK(cudaGetLastError());
-          k_bvsub_norm<double><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.w, W.w, N, W.nparts, need);
-        }
+        if (pass == 0 && f32)
+          k_bdots<cx<float>><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.wf, N, W.part, m + 1, need, 1);
+        else if (pass == 0)
+          k_bdots<cx<double>><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.w, N, W.part, m + 1, need, 1);
+        else
+          k_bdots<cdf><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.wdf, N, W.part, m + 1, need, 0);
+        CK(cudaGetLastError());
+        k_breduce<<<dim3(j + 1 + (pass ? 0 : 1), Ka), BG_THREADS, 0, s>>>(W.part, rbp, m + 1, h, m + 1, need);
+        CK(cudaGetLastError());
+        if (pass == 0 && f32)
+          k_bvsub_norm<cx<float>><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.wf, W.wdf, N, W.nparts,
+                                                            need);
+        else if (pass == 0)
+          k_bvsub_norm<cx<double>><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.w, W.wdf, N, W.nparts,
+                                                             need);
+        else
+          k_bvsub_norm<cdf><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.wdf, W.wdf, N, W.nparts, need);
         CK(cudaGetLastError());
         k_bnorm_fin<<<Ka, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 1 + pass, 4, need,
                                               pass ? nullptr : S.need, pass ? nullptr : S.h1 + (j + 1), m + 1);
@@ -949,7 +1105,7 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
       k_givens<<<1, KBATCH * 32, 0, s>>>(S, j, m, Ka, tol, W.word_d);
       CK(cudaGetLastError());
       if (j + 1 < m) {
-        k_bscale<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.w, W.V, csV, j + 1, S.nrm, S.need, N);
+        k_bscale<<<dim3(EW_BLOCKS / 4, Ka), 256, 0, s>>>(W.wdf, W.V, csV, j + 1, S.nrm, S.need, N);
         CK(cudaGetLastError());
       }
       // the host stays one step ahead: wait for the previous step, read its word

@@ -181,7 +181,7 @@ def test_rhs_matches_oracle(mk, src, side):
 
 @pytest.mark.parametrize("prec", [sc.SCABEM_C128, sc.SCABEM_C64], ids=["c128", "c64_refined"])
 def test_solve_reaches_oracle_residual(prec):
-    """GMRES (FP64 Arnoldi; complex64 inner operator with FP64 refinement) solves the oracle's system."""
+    """GMRES (complex64 or complex128 inner operator, FP64 refinement) solves the oracle's system."""
     case = cases.sphere_mixed()
     mh, op, g, med, sig = build(case)
     s = sc.make_source("planewave", "e", dir=(0, 0, 1), pol=(1, 0, 0))

@@ -3,7 +3,7 @@
 The oracle assembles its grid operator O2 (the plain definition of the
 precorrected-FFT product) column by column and solves it by LU; the CUDA
 path solves the same system with GMRES (complex128 operator, and complex64
-operator with FP64 Arnoldi and FP64 iterative refinement).  The solutions
+operator with FP64 iterative refinement).  The solutions
 and the reflection fitted from them (Sec. I, Table 1: two-wave fit of the
 axis field) must agree to 1e-8 relative; the solves are run to a relative
 residual of 1e-12 so that the conditioning of the system does not eat the
