@@ -560,7 +560,7 @@ def run_gpu(args):
         bvec = torch.empty(N, dtype=torch.complex128, device="cuda")
         sc.scabem_rhs(op2, src, bvec, prec=sc.SCABEM_C128, stream=stream)
         xs = torch.zeros_like(bvec)
-        sopt = dict(tol=1e-4, restart=100, maxit=20000, refine_tol=1e-8, max_refine=10, prec=sc.SCABEM_C64)
+        sopt = dict(tol=1e-4, restart=200, maxit=20000, refine_tol=1e-8, max_refine=10, prec=sc.SCABEM_C64)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sinfo = sc.scabem_solve(op2, bvec, xs, stream=stream, **sopt)[0]
@@ -622,7 +622,7 @@ def run_gpu(args):
                  "rhs": "Gaussian beam (waist parameter 0.15 um) in the core at x = 4.3 um, y-polarised",
                  "operator": "near radius 3.05 grid steps", "matvec_per_s_c64": 1e3 / ms_acc,
                  "ms_per_iteration": t_solve * 1e3 / max(sinfo["iters"], 1),
-                 "mode": ("GMRES(100) on the complex64 operator to 1e-4 with 48-bit Arnoldi (classical Gram-Schmidt "
+                 "mode": ("GMRES(200) on the complex64 operator to 1e-4 with 48-bit Arnoldi (classical Gram-Schmidt "
                           "on FP32 (hi, lo) pairs, second pass by the DGKS test, Givens updates on the device), "
                           "FP64 refinement to 1e-8"),
                  "circulant_preconditioner": circ,

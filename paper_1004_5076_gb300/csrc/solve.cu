@@ -369,7 +369,8 @@ __global__ void k_band_loss(const cd* __restrict__ summ, const double* __restric
 // m + 1 vectors of N from c * (m + 1) * N.
 constexpr int BG_THREADS = 256;
 constexpr int BG_BLOCKS = 4 * 152;  // row blocks per column of the reductions (four per SM)
-constexpr int BG_TC = 8;        // basis vectors per tile of the dot products
+constexpr int BG_TC = 4;        // basis vectors per tile of the dot products
+constexpr int BG_WAVE = 3 * 152;  // dot-product blocks in one wave (4 resident per SM)
 constexpr int FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2;
 
 // Error-free transformations in round-to-nearest intrinsics, which the
@@ -448,40 +449,61 @@ __global__ void __launch_bounds__(BG_THREADS) k_bdots(const cdf* __restrict__ V,
   dfa v[2 * BG_TC];  // v[2k]: real part of column c0 + k, v[2k + 1]: imaginary part
 #pragma unroll
   for (int k = 0; k < 2 * BG_TC; ++k) v[k] = dfa{0.f, 0.f};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const cdf b = ld_df(w + i);
+  // two rows per step (their loads in flight together)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < N; i0 += 2 * stride) {
+    const int64_t i1 = i0 + stride;
+    const bool two = i1 < N;
+    const cdf b0 = ld_df(w + i0);
+    cdf b1 = b0;
+    if (two) b1 = ld_df(w + i1);
+    cdf a0[BG_TC], a1[BG_TC];
 #pragma unroll
-    for (int k = 0; k < BG_TC; ++k)
-      if (k < nc) {
-        const cdf a = c0 + k < nv ? V[(int64_t)(c0 + k) * N + i] : b;
-        // conj(a) b = (a.re b.re + a.im b.im) + j (a.re b.im - a.im b.re)
-        df_mac(v[2 * k], a.rh, b.rh);
-        df_mac(v[2 * k], a.ih, b.ih);
-        df_mac(v[2 * k + 1], a.rh, b.ih);
-        df_mac(v[2 * k + 1], -a.ih, b.rh);
-        df_small(v[2 * k], a.rl, b.rh);
-        df_small(v[2 * k], a.il, b.ih);
-        df_small(v[2 * k + 1], a.rl, b.ih);
-        df_small(v[2 * k + 1], -a.il, b.rh);
-        if (WLO) {
-          df_small(v[2 * k], a.rh, b.rl);
-          df_small(v[2 * k], a.ih, b.il);
-          df_small(v[2 * k + 1], a.rh, b.il);
-          df_small(v[2 * k + 1], -a.ih, b.rl);
+    for (int k = 0; k < BG_TC; ++k) {
+      const bool basis = c0 + k < nv;
+      a0[k] = basis && k < nc ? V[(int64_t)(c0 + k) * N + i0] : b0;
+      a1[k] = basis && k < nc && two ? V[(int64_t)(c0 + k) * N + i1] : b1;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !two) break;
+      const cdf b = r ? b1 : b0;
+#pragma unroll
+      for (int k = 0; k < BG_TC; ++k)
+        if (k < nc) {
+          const cdf a = r ? a1[k] : a0[k];
+          // conj(a) b = (a.re b.re + a.im b.im) + j (a.re b.im - a.im b.re)
+          df_mac(v[2 * k], a.rh, b.rh);
+          df_mac(v[2 * k], a.ih, b.ih);
+          df_mac(v[2 * k + 1], a.rh, b.ih);
+          df_mac(v[2 * k + 1], -a.ih, b.rh);
+          df_small(v[2 * k], a.rl, b.rh);
+          df_small(v[2 * k], a.il, b.ih);
+          df_small(v[2 * k + 1], a.rl, b.ih);
+          df_small(v[2 * k + 1], -a.il, b.rh);
+          if (WLO) {
+            df_small(v[2 * k], a.rh, b.rl);
+            df_small(v[2 * k], a.ih, b.il);
+            df_small(v[2 * k + 1], a.rh, b.il);
+            df_small(v[2 * k + 1], -a.ih, b.rl);
+          }
         }
-      }
+    }
   }
-  // warp sums of the 16 values by halving exchanges: at offset o = 16, 8, 4, 2
-  // each lane keeps half of its values, sends the other half to lane ^ o and
-  // adds what it receives, so that 16 additions (not 5 per value) leave lane
-  // l with the sum over 16 lanes of value 8 b4 + 4 b3 + 2 b2 + b1 (b = bits
-  // of l); one more exchange at offset 1 completes it.
+  // warp sums of the NV = 2 BG_TC values by halving exchanges: at offset
+  // o = NV, NV / 2, .., 2 each lane keeps half of its values, sends the other
+  // half to lane ^ o and adds what it receives, so that NV additions (not 5
+  // per value) leave lane l with a value whose index is given by those bits
+  // of l; plain exchanges over the remaining lane bits complete the sums.
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  static_assert(BG_TC == 8, "the exchange below reduces 2 BG_TC = 16 values");
+  constexpr int NV = 2 * BG_TC;
+  static_assert(NV >= 2 && NV <= 16 && (NV & (NV - 1)) == 0, "halving exchanges need a power of two");
+  int idx = 0;
 #pragma unroll
-  for (int half = BG_TC; half >= 1; half >>= 1) {
-    const int o = 2 * half;  // 16, 8, 4, 2
+  for (int half = NV / 2; half >= 1; half >>= 1) {
+    const int o = 2 * half;
     const bool upper = (lane & o) != 0;
+    if (upper) idx += half;
 #pragma unroll
     for (int t = 0; t < half; ++t) {
       const dfa send = upper ? v[t] : v[t + half];
@@ -489,8 +511,10 @@ __global__ void __launch_bounds__(BG_THREADS) k_bdots(const cdf* __restrict__ V,
       v[t] = df_add(keep, df_shfl_xor(send, o));
     }
   }
+#pragma unroll
+  for (int o = 2 * NV; o < 32; o <<= 1) v[0] = df_add(v[0], df_shfl_xor(v[0], o));
   v[0] = df_add(v[0], df_shfl_xor(v[0], 1));
-  if ((lane & 1) == 0) sm[wp][((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1)] = v[0];
+  if ((lane & ~(2 * NV - 2)) == 0) sm[wp][idx] = v[0];  // one lane per value index
   __syncthreads();
   if (threadIdx.x < 2 * nc) {
     dfa t = sm[0][threadIdx.x];
@@ -550,11 +574,19 @@ __global__ void __launch_bounds__(BG_THREADS) k_bnorm_parts(const cd* __restrict
 }
 
 // wout_c = win_c - V_c h_c over nv basis vectors, stored as (hi, lo) pairs,
-// and the squared norm of the new w_c per row block (grid: BG_BLOCKS x K).
-// win is read in its own precision WT and may be wout itself (in place).  The
-// coefficients h (FP64) are split into (hi, lo) pairs once per block; every
-// product is formed with its rounding error and summed with compensation.
+// and the squared norm of the new w_c per row block (grid: at most
+// BG_BLOCKS x K; nparts gets gridDim.x values per column).  win is read in
+// its own precision WT and may be wout itself (in place).  BV_KS lanes share
+// a row and take every BV_KS-th basis vector, so that each thread's chain of
+// dependent loads is BV_KS times shorter; their partial sums meet by
+// shuffles.  The coefficients h (FP64) are split into (hi, lo) pairs once
+// per block; every product is formed with its rounding error and summed
+// with compensation.
 constexpr int GM_MAXM = 200;  // largest restart length (checked by the C ABI)
+constexpr int BV_KS = 4;
+inline unsigned bv_blocks(int64_t N) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(BG_BLOCKS, cdiv(N * BV_KS, BG_THREADS)));
+}
 template <typename WT>
 __global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cdf* __restrict__ V, int64_t csV, int nv,
                                                            const cd* __restrict__ h, int ldh, const WT* win,
@@ -570,44 +602,62 @@ __global__ void __launch_bounds__(BG_THREADS) k_bvsub_norm(const cdf* __restrict
   __shared__ dfa sm[BG_THREADS / 32];
   for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = df_split(h[k]);
   __syncthreads();
+  const int sub = threadIdx.x & (BV_KS - 1);
   dfa nn = {0.f, 0.f};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const cdf x0 = ld_df(win + i);
-    dfa xr = {x0.rh, x0.rl}, xi = {x0.ih, x0.il};
+  const int64_t rows_per_pass = (int64_t)gridDim.x * (blockDim.x / BV_KS);
+  for (int64_t i0 = (int64_t)blockIdx.x * (blockDim.x / BV_KS); i0 < N; i0 += rows_per_pass) {
+    const int64_t i = i0 + threadIdx.x / BV_KS;  // uniform trip count: every lane reaches the shuffles
+    const bool row = i < N;
+    dfa xr = {0.f, 0.f}, xi = {0.f, 0.f};
+    if (row && sub == 0) {
+      const cdf x0 = ld_df(win + i);
+      xr = dfa{x0.rh, x0.rl};
+      xi = dfa{x0.ih, x0.il};
+    }
+    if (row) {
+      int n = 0;
 #pragma unroll 4
-    for (int k = 0; k < nv; ++k) {
-      const cdf a = V[(int64_t)k * N + i], b = hs[k];
-      // x -= a b: re += -a.re b.re + a.im b.im, im += -a.re b.im - a.im b.re
-      df_mac(xr, -a.rh, b.rh);
-      df_mac(xr, a.ih, b.ih);
-      df_mac(xi, -a.rh, b.ih);
-      df_mac(xi, -a.ih, b.rh);
-      df_small(xr, -a.rh, b.rl);
-      df_small(xr, -a.rl, b.rh);
-      df_small(xr, a.ih, b.il);
-      df_small(xr, a.il, b.ih);
-      df_small(xi, -a.rh, b.il);
-      df_small(xi, -a.rl, b.ih);
-      df_small(xi, -a.ih, b.rl);
-      df_small(xi, -a.il, b.rh);
-      if ((k & 7) == 7) {
-        xr = df_renorm(xr);
-        xi = df_renorm(xi);
+      for (int k = sub; k < nv; k += BV_KS, ++n) {
+        const cdf a = V[(int64_t)k * N + i], b = hs[k];
+        // x -= a b: re += -a.re b.re + a.im b.im, im += -a.re b.im - a.im b.re
+        df_mac(xr, -a.rh, b.rh);
+        df_mac(xr, a.ih, b.ih);
+        df_mac(xi, -a.rh, b.ih);
+        df_mac(xi, -a.ih, b.rh);
+        df_small(xr, -a.rh, b.rl);
+        df_small(xr, -a.rl, b.rh);
+        df_small(xr, a.ih, b.il);
+        df_small(xr, a.il, b.ih);
+        df_small(xi, -a.rh, b.il);
+        df_small(xi, -a.rl, b.ih);
+        df_small(xi, -a.ih, b.rl);
+        df_small(xi, -a.il, b.rh);
+        if ((n & 7) == 7) {
+          xr = df_renorm(xr);
+          xi = df_renorm(xi);
+        }
       }
     }
-    xr = df_renorm(xr);
-    xi = df_renorm(xi);
-    cdf o;
-    o.rh = xr.h;
-    o.ih = xi.h;
-    o.rl = xr.l;
-    o.il = xi.l;
-    wout[i] = o;
-    // |x|^2 = h^2 + 2 h l + l^2 per part
-    df_mac(nn, xr.h, xr.h);
-    df_small(nn, 2.f * xr.h, xr.l);
-    df_mac(nn, xi.h, xi.h);
-    df_small(nn, 2.f * xi.h, xi.l);
+#pragma unroll
+    for (int o = 1; o < BV_KS; o <<= 1) {
+      xr = df_add(xr, df_shfl_xor(xr, o));
+      xi = df_add(xi, df_shfl_xor(xi, o));
+    }
+    if (row && sub == 0) {
+      xr = df_renorm(xr);
+      xi = df_renorm(xi);
+      cdf o;
+      o.rh = xr.h;
+      o.ih = xi.h;
+      o.rl = xr.l;
+      o.il = xi.l;
+      wout[i] = o;
+      // |x|^2 = h^2 + 2 h l + l^2 per part
+      df_mac(nn, xr.h, xr.h);
+      df_small(nn, 2.f * xr.h, xr.l);
+      df_mac(nn, xi.h, xi.h);
+      df_small(nn, 2.f * xi.h, xi.l);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nn = df_add(nn, df_shfl_xor(nn, o));
@@ -1073,13 +1123,13 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
       // first pass h1 = V^H w with |w|^2 in its column j + 1, w -= V h1, |w|; the
       // DGKS test; the second pass only where it asks
       const int tiles = (int)cdiv(j + 2, BG_TC);
-      const int rb = std::max(8, BG_BLOCKS / tiles);
+      const int rb = std::max(8, BG_WAVE / tiles);
       for (int pass = 0; pass < 2; ++pass) {
         const int* need = pass ? S.need : nullptr;
         cd* h = pass ? S.h2 : S.h1;
         const int tl = pass ? (int)cdiv(j + 1, BG_TC) : tiles;
-        const int rbp = pass ? std::max(8, BG_BLOCKS / tl) : rb;
-        const dim3 gd(rbp, tl, Ka), gv(BG_BLOCKS, Ka);
+        const int rbp = pass ? std::max(8, BG_WAVE / tl) : rb;
+        const dim3 gd(rbp, tl, Ka), gv(bv_blocks(N), Ka);
         if (pass == 0 && f32)
           k_bdots<cx<float>><<<gd, BG_THREADS, 0, s>>>(W.V, csV, j + 1, W.wf, N, W.part, m + 1, need, 1);
         else if (pass == 0)
@@ -1098,7 +1148,7 @@ int gmres_batch(scabem_op* op, const cd* r, cd* d, const std::vector<char>& use,
         else
           k_bvsub_norm<cdf><<<gv, BG_THREADS, 0, s>>>(W.V, csV, j + 1, h, m + 1, W.wdf, W.wdf, N, W.nparts, need);
         CK(cudaGetLastError());
-        k_bnorm_fin<<<Ka, BG_THREADS, 0, s>>>(W.nparts, BG_BLOCKS, S.nrm + 1 + pass, 4, need,
+        k_bnorm_fin<<<Ka, BG_THREADS, 0, s>>>(W.nparts, (int)gv.x, S.nrm + 1 + pass, 4, need,
                                               pass ? nullptr : S.need, pass ? nullptr : S.h1 + (j + 1), m + 1);
         CK(cudaGetLastError());
       }
