@@ -801,6 +801,72 @@ def platform_info():
     return {"machine": platform.machine(), "cpu": model or platform.processor(), "nproc": os.cpu_count()}
 
 
+def run_solve(args):
+    """--mode solve: the GMRES iteration time on the 12 um guide.  The beam
+    right-hand side is solved with the complex64 operator inside GMRES(100)
+    (tol 1e-14, so that no column converges) for --solve-its and for three
+    times as many iterations; the difference over 2 --solve-its iterations
+    is the cost of one iteration without set-up.  The apply alone is timed
+    beside it (200 back-to-back calls); their difference is the GMRES work.
+    Rank 0 only (one GPU)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import cases
+    import torch
+
+    import paper_1004_5076_gb300 as sc
+    from paper_1004_5076_gb300 import build
+
+    build.build()
+    case = cases.guide_full()
+    m = case.mesh
+    mh = sc.scabem_mesh_create(m.V, m.T, m.region)
+    r_near = args.near_radius_h * case.grid.h
+    op = sc.scabem_op_create(mh, case.media, case.grid.n, case.grid.h, case.grid.origin, case.grid.p, case.q, r_near, 3)
+    sc.scabem_set_sigma(op, segments=case.sigma_segments)
+    N = sc.scabem_mesh_info(mh)[2]
+    src = [sc.make_source("beam", "i", pos=(4.3, 0, 0), dir=(1, 0, 0), pol=(0, 1, 0), b=0.15)]
+    b = torch.empty(N, dtype=torch.complex128, device="cuda")
+    sc.scabem_rhs(op, src, b, prec=sc.SCABEM_C128)
+    x = torch.randn(N, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        sc.scabem_apply(op, x, y, prec=sc.SCABEM_C64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(200):
+        sc.scabem_apply(op, x, y, prec=sc.SCABEM_C64)
+    torch.cuda.synchronize()
+    t_apply = (time.perf_counter() - t0) / 200
+
+    def solve(its):
+        xs = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        try:
+            sc.scabem_solve(op, b, xs, tol=1e-14, restart=100, maxit=its, refine_tol=1e-14, max_refine=0,
+                            prec=sc.SCABEM_C64)
+        except sc.ScabemError:
+            pass  # SCABEM_E_NOCONV: the iteration bound was the point
+        torch.cuda.synchronize()
+        return time.perf_counter() - t
+
+    k = args.solve_its
+    t1, t3 = solve(k), solve(3 * k)
+    per_it = (t3 - t1) / (2 * k)
+    line = {"metric": "GMRES iteration time (complex64 operator inside GMRES(100), beam right-hand side)",
+            "value": per_it * 1e3, "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "c64",
+            "data": "synthetic", "apply_ms": t_apply * 1e3, "gmres_work_ms": (per_it - t_apply) * 1e3,
+            "iterations": [k, 3 * k], "seconds": [t1, t3],
+            "config": {"workload": "guide_12um (as the matvec line)", "unknowns": int(N),
+                       "r_near_h": args.near_radius_h, "restart": 100,
+                       "basis_vectors": "0 .. 99 (mean about 50 over a cycle)"}}
+    print(json.dumps(line), flush=True)
+    sc.scabem_op_destroy(op)
+    sc.scabem_mesh_destroy(mh)
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -838,6 +904,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--mode", default="matvec", choices=["matvec", "solve"],
+                    help="matvec: the benchmark line; solve: the GMRES iteration time on the same guide")
+    ap.add_argument("--solve-its", type=int, default=200, help="--mode solve: iterations of the shorter solve")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--near-radius-h", type=float, default=2.05,
                     help="near-field radius in grid steps (2.05: the headline configuration)")
@@ -854,6 +923,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "solve":
+        run_solve(args)
     else:
         run_gpu(args)
 
