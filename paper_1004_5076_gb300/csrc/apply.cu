@@ -604,8 +604,8 @@ __global__ void k_wait_selftest(int* __restrict__ tmo) {
 //    weighted tested values; phase 3: lane (kk, value type) sums them over the
 //    points in point order.
 constexpr int PT_WARPS = 4;
-constexpr int PT_NSTG = 4;
-constexpr int PT_KP = 2;
+constexpr int PT_NSTG = 2;  // 2 stages of 4 pairs: the bytes in flight of 4 stages of 2, with half the
+constexpr int PT_KP = 4;    // stages' waits, fences and copy issues per pair
 
 // complex values of per-warp shared memory: the ring, which the records and
 // point parts of phases 2-3 reuse once the near loop is done
