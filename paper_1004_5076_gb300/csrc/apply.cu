@@ -778,8 +778,8 @@ __global__ void __launch_bounds__(PT_WARPS * 32, sizeof(R) == 4 ? (P == 4 ? 4 : 
 // together when a wait expired.  Testing (3q tasks per column) and the row
 // sums (12 per column) are packed the same way, on a per-column area beside
 // the ring.
-constexpr int PB_NSTG = 4;
-constexpr int PB_KP = 4;
+constexpr int PB_NSTG = 2;  // 2 stages of 8 pairs: half the CTA barriers and waits of 4 stages of 4
+constexpr int PB_KP = 8;
 
 __host__ __device__ constexpr int pb_ring_complex(int q) { return PB_NSTG * PB_KP * NCORR * 2 * q; }
 __host__ __device__ constexpr int pb_col_complex(int q) { return 2 * q * NREC + 3 * q * 4; }
