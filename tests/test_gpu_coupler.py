@@ -1,7 +1,7 @@
 """The directional coupler on the 1024 x 256 x 256 transform grid.
 
 Two 40 um guides 0.2 um apart with absorbers at all four ports: 128,440
-triangles, 385k unknowns, 13 M near pairs (12.7 GB of complex64 records,
+triangles, 424k unknowns, 13 M near pairs (12.7 GB of complex64 records,
 byte offsets beyond 32 bits), (y, z) planes of 256 x 256 that only the direct sums over the active
 columns handle.  Every row of 24 random edges (both triangles of each edge as
 targets) against the oracle's grid operator O2 at those rows, in complex128
